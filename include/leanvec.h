@@ -1,0 +1,241 @@
+/*
+ * leanvec.h -- C ABI of the GB300 (sm_103a) LeanVec search library.
+ *
+ * LeanVec (Tepper et al., "LeanVec: Searching vectors faster by making them
+ * fit", arXiv 2312.16335) approximates the inner product <q, x> by
+ * <A q, quant(B x)> with A, B in R^{d x D}, d < D (Sec. 2, Eq. 1).  A graph is
+ * traversed with the "primary" vectors quant(B x); the best candidates are then
+ * rescored with the full-dimensional "secondary" vectors quant(x) and the top k
+ * returned (Sec. 2, "Search").  quant() is LVQ, a per-vector scalar quantiser
+ * around the dataset mean (cited in Sec. 2).
+ *
+ * Conventions for every function:
+ *   - Returns 0 (LV_OK) or a negative lv_status.  leanvec_last_error() gives a
+ *     message for the calling thread.  No C++ exception crosses this ABI.
+ *   - Pointers named as "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  Work is enqueued asynchronously on the
+ *     given stream (NULL = legacy default stream) unless stated otherwise.
+ *   - Matrices are row-major float32: database X is n x D, queries Q are m x D,
+ *     projections A and B are d x D (so the paper's X, a D x n column stack, is
+ *     the transpose of the X here).
+ *   - Ids are int32; n < 2^31.  Inner product is the similarity (higher is
+ *     better); ties are broken by the smaller id.
+ *   - Errors found while a kernel runs (a clamped capacity, an out-of-range id
+ *     in a user graph) are recorded in a per-index device status word and are
+ *     returned by leanvec_sync_status().
+ */
+#ifndef LEANVEC_H
+#define LEANVEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lv_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    LV_OK = 0,
+    LV_ERR_ARG = -1,       /* invalid argument; nothing was launched */
+    LV_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    LV_ERR_OOM = -3,       /* device allocation failed */
+    LV_ERR_CAPACITY = -4,  /* a per-query size exceeded a compiled/allocated capacity */
+    LV_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    LV_ERR_CANCELLED = -6,
+    LV_ERR_CORRUPT = -7,   /* malformed input data (e.g. a graph id out of range) */
+    LV_ERR_STATE = -8      /* the index lacks what the call needs (no graph, no store) */
+} lv_status;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *leanvec_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Record layout                                                            */
+/* ------------------------------------------------------------------------ */
+/*
+ * An LVQ record of a dim-dimensional vector v (already minus the dataset mean
+ * mu) with b in {4, 8} bits:
+ *   bytes [0, cb)            codes, cb = dim (b = 8) or ceil(dim / 2) (b = 4);
+ *                            for b = 4 code 2j is the low and 2j+1 the high nibble
+ *                            of byte j; the code area is zero-padded to a multiple
+ *                            of 16 bytes (padding codes decode to l and are never
+ *                            multiplied by a non-zero query entry)
+ *   bytes [co, co + 16)      float32 {delta, lower, G, H}, co = code area size
+ *   stride                   co + 16 rounded up to 32 bytes
+ * decode: x_j = mu_j + lower + delta * code_j.  With l = min v, u = max v:
+ *   delta = (u - l) / (2^b - 1)   (IEEE float32 division, round to nearest)
+ *   code  = floor((v_j - l) / delta + 0.5), clamped to [0, 2^b - 1]; 0 if delta = 0
+ * G and H serve the graph build's exact pair score (leanvec_build_graph):
+ *   mui_j = round(mu_j * 2^20) (int32),  M = sum_j mui_j code_j (int64),
+ *   G = lower * float(sum_j mui_j) * 2^-20 + delta * float(M) * 2^-20,
+ *   H = delta * float(sum_j code_j)        (float32, no fused multiply-add)
+ * and are NaN when some |mu_j| >= 8.
+ * A float32 record (bits = 32, the full-dimensional baseline) is the dim floats
+ * zero-padded to a multiple of 32 bytes.
+ * Returns the stride in bytes, or a negative lv_status for unsupported bits.
+ */
+int64_t leanvec_record_stride(int dim, int bits);
+
+/* ------------------------------------------------------------------------ */
+/* Stand-alone kernels on caller-owned device buffers                        */
+/* ------------------------------------------------------------------------ */
+
+/* Column mean of X (n x dim, device) accumulated in FP64 in a fixed order and
+ * rounded to float32 into mean (dim, device).  The dataset mean around which
+ * LVQ quantises (Sec. 2 cites LVQ for quant()). */
+int leanvec_column_mean(const float *X, int64_t n, int dim, float *mean, lv_stream_t stream);
+
+/* LVQ-encode the n rows of V (n x dim, device) around mean (dim, device) into
+ * records (n x leanvec_record_stride(dim, bits) bytes, device), bits in {4, 8}.
+ * Layout and arithmetic as documented above; the codes are bit-identical to an
+ * IEEE float32 evaluation of the stated formula. */
+int leanvec_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int bits,
+                       uint8_t *records, lv_stream_t stream);
+
+/* Precision of a projection GEMM. */
+typedef enum {
+    LV_PREC_FP32 = 0,  /* float32 CUDA-core GEMM, float32 accumulate */
+    LV_PREC_BF16 = 1,  /* bf16 operands on the tcgen05 tensor cores, float32 accumulate */
+    LV_PREC_FP8 = 2    /* e4m3 operands with per-row scales, float32 accumulate */
+} lv_precision;
+
+/* Y = X P^T: X is n x D, P is d x D, Y is n x ldy with ldy >= d (device); the
+ * columns d..ldy-1 of Y are written with zeros.  This is the projection
+ * x -> B x (encode) and q -> A q (search) of Eq. 1. */
+int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
+                    int precision, lv_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Index                                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct lv_index lv_index;
+
+/* Create an empty index bound to CUDA device `device` (the library allocates its
+ * stores there).  Free with leanvec_index_free. */
+int leanvec_index_create(lv_index **out, int device);
+int leanvec_index_free(lv_index *idx);
+
+typedef struct {
+    int64_t n;              /* database size */
+    int32_t D;              /* original dimensionality */
+    int32_t d;              /* primary dimensionality (D for the float32 baseline) */
+    int32_t primary_bits;   /* 4, 8, or 32 (float32 records) */
+    int32_t secondary_bits; /* 8, or 0 when there is no secondary store */
+    int64_t primary_stride;
+    int64_t secondary_stride;
+    int32_t R;              /* graph max out-degree, 0 when no graph */
+    int32_t entry;          /* search entry point, -1 when no graph */
+    float mu2;              /* build-score constant sum_j (mui_j 2^-20)^2 */
+    int32_t reserved;
+} lv_index_info;
+
+int leanvec_index_info(const lv_index *idx, lv_index_info *out);
+
+/* Device pointers to the index's stores (read-only views, owned by the index;
+ * valid until the index is freed or re-encoded). Any output may be NULL. */
+int leanvec_index_buffers(const lv_index *idx, const uint8_t **primary, const float **primary_mean,
+                          const uint8_t **secondary, const float **secondary_mean,
+                          const int32_t **graph);
+
+/* Encode the database (Sec. 2 "primary vectors" and "secondary vectors"):
+ *   primary   = LVQ_{primary_bits}(B x - mu_B), mu_B = mean of B x over the database
+ *   secondary = LVQ_{secondary_bits}(x - mu),  mu = mean of x
+ * X: n x D (device), B: d x D (device).  primary_bits in {4, 8};
+ * secondary_bits in {8, 0} (0: no secondary store, search cannot rerank).
+ * projection_precision: lv_precision of the B x GEMM.  Replaces any previous
+ * store and graph of the index. Synchronises `stream` before returning. */
+int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float *B, int d,
+                   int primary_bits, int secondary_bits, int projection_precision,
+                   lv_stream_t stream);
+
+/* Install the primary store from already reduced vectors: Y is n x d (device, e.g.
+ * B x computed by the caller), mean (d, device) the vector to quantise around, or
+ * NULL for the column mean of Y; bits in {4, 8}; D is the dimensionality of the
+ * original vectors (the row length of the queries given to leanvec_search).  Drops
+ * the graph, and the secondary store when n changes. Synchronises `stream`. */
+int leanvec_set_primary(lv_index *idx, const float *Y, int64_t n, int d, const float *mean, int bits, int D,
+                        lv_stream_t stream);
+
+/* Install the LVQ-8 secondary store from the original vectors X (n x D, device)
+ * around mean (D, device) or, when NULL, the column mean of X.  n and D must match
+ * the primary store. Synchronises `stream`. */
+int leanvec_set_secondary(lv_index *idx, const float *X, int64_t n, int D, const float *mean,
+                          lv_stream_t stream);
+
+/* Full-dimensional float32 baseline: the primary store holds x itself (D floats),
+ * no projection, no secondary. Synchronises `stream` before returning. */
+int leanvec_encode_fp32(lv_index *idx, const float *X, int64_t n, int D, lv_stream_t stream);
+
+/* Install a graph: adj is n x R int32 (device), -1 marks an empty slot.  Repeated
+ * ids within a row are removed (first kept).  entry < 0 selects the default entry
+ * argmax_i <mu, decoded primary_i> (ties -> smaller id).  R <= 128. */
+int leanvec_set_graph(lv_index *idx, const int32_t *adj, int R, int32_t entry, lv_stream_t stream);
+
+/* Copy the graph (n x R int32) into adj (device) and the entry into *entry (host). */
+int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stream_t stream);
+
+/* Build the graph on the primaries (App. A: search + prune for every node; App. D:
+ * Vamana with R, L, alpha).  Batch-synchronous Vamana:
+ *   - initial graph: node v takes the first min(R, n-1) ids splitmix64(seed, v, j)
+ *     mod n (j = 0, 1, ..) that are neither v nor repeated;
+ *   - order: Fisher-Yates permutation with draws splitmix64(seed + 1, i, 0) mod (i+1);
+ *   - pass t uses alpha_t = 1 for t < passes - 1 and alpha in the last pass;
+ *   - each batch of `batch` nodes searches the graph as it was at the batch start
+ *     (query = the node's primary, beam L_build, from the entry), prunes
+ *     pool = beam u old out-list (minus itself) with RobustPrune
+ *     (drop p' when alpha * s(p*, p') >= s(p, p')), then adds the reverse edges by
+ *     (target, source) ascending, pruning targets that exceed R;
+ *   - pair scores are the exact build score described with the record layout,
+ *     so the adjacency is reproducible bit for bit.
+ * splitmix64(s, a, b) is the SplitMix64 finaliser applied to
+ * s + 0x9E3779B97F4A7C15 * (1 + a * 2^32 + b).  R <= 128, L_build <= 512. */
+int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int passes, int batch,
+                        uint64_t seed, lv_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Search (Sec. 2 "Search"; App. D "greedy traversal with backtracking")     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t k;         /* results per query (<= ldo) */
+    int32_t L;         /* beam width (search window) */
+    int32_t rerank;    /* candidates rescored with the secondary store; 0 = no rerank */
+    int32_t max_hops;  /* expansion limit, 0 = none */
+} lv_query_desc;
+
+typedef struct {
+    lv_query_desc uniform;   /* used for every query when desc == NULL */
+    int32_t projection;      /* lv_precision of the q -> A q GEMM */
+    int32_t hash_slots;      /* visited-cache slots per query (power of two, 0 = default 2048) */
+    int32_t warps_per_block; /* 0 = default */
+    int32_t reserved;
+} lv_search_params;
+
+/* Per-query counters (device, m entries) when stats != NULL. */
+typedef struct {
+    int32_t hops;    /* beam expansions */
+    int32_t scored;  /* primary records scored (re-scores of evicted visited ids included) */
+} lv_search_stats;
+
+/* Search m queries Q (m x D, device).  A (d x D, device) projects the queries
+ * (ignored for a float32 baseline index).  desc (device, m entries) gives per-query
+ * {k, L, rerank, max_hops}; NULL uses params->uniform.  For each query the best
+ * unexpanded beam member is expanded until none is left (or max_hops); the top
+ * min(rerank, |beam|) members are rescored with the secondary store against the
+ * unreduced query and the best k written, sorted by score (ties -> smaller id), to
+ * ids/scores (m x ldo, device); the rest of each row (fewer than k reachable
+ * candidates, or k < ldo) is filled with -1 / -inf.  Reported scores are the
+ * decoded inner products (secondary after rerank, primary otherwise). */
+int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
+                   const lv_search_params *params, const lv_query_desc *desc,
+                   int32_t *ids, float *scores, int ldo, lv_search_stats *stats,
+                   lv_stream_t stream);
+
+/* Synchronise `stream` and return (and clear) the index's device status word. */
+int leanvec_sync_status(lv_index *idx, lv_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEANVEC_H */

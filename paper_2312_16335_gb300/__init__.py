@@ -1,0 +1,203 @@
+"""LeanVec search on GB300: Python binding of the C ABI in include/leanvec.h.
+
+Every function here only marshals arguments (torch CUDA tensors -> device
+pointers, the current CUDA stream) and calls the same-named C entry point; all
+arithmetic runs in the library's CUDA kernels.  The functions mirror the paper's
+pipeline (LeanVec, arXiv 2312.16335, Sec. 2): learn A, B; encode primary
+(LVQ(B x)) and secondary (LVQ(x)) vectors; build a graph on the primaries; search
+with A q and rerank with the secondaries.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._native import (LVIndexInfo, LVQueryDesc, LVSearchParams, LeanVecError, check, lib)
+
+__all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
+           "leanvec_project", "PREC_FP32", "PREC_BF16", "PREC_FP8"]
+
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _f32(t: torch.Tensor) -> torch.Tensor:
+    if t.dtype != torch.float32:
+        raise TypeError("expected float32")
+    return t.contiguous()
+
+
+def leanvec_record_stride(dim: int, bits: int) -> int:
+    return check(lib().leanvec_record_stride(dim, bits))
+
+
+def leanvec_column_mean(X: torch.Tensor) -> torch.Tensor:
+    X = _f32(X)
+    out = torch.empty(X.shape[1], dtype=torch.float32, device=X.device)
+    check(lib().leanvec_column_mean(_ptr(X), X.shape[0], X.shape[1], _ptr(out), _stream(X.device)))
+    return out
+
+
+def leanvec_lvq_encode(V: torch.Tensor, mean: torch.Tensor, bits: int) -> torch.Tensor:
+    V = _f32(V)
+    mean = _f32(mean)
+    n, dim = V.shape
+    rec = torch.empty((n, leanvec_record_stride(dim, bits)), dtype=torch.uint8, device=V.device)
+    check(lib().leanvec_lvq_encode(_ptr(V), n, dim, _ptr(mean), bits, _ptr(rec), _stream(V.device)))
+    return rec
+
+
+def leanvec_project(X: torch.Tensor, P: torch.Tensor, ldy: int | None = None, precision: int = PREC_FP32) -> torch.Tensor:
+    X = _f32(X)
+    P = _f32(P)
+    n, D = X.shape
+    d = P.shape[0]
+    ldy = d if ldy is None else ldy
+    Y = torch.empty((n, ldy), dtype=torch.float32, device=X.device)
+    check(lib().leanvec_project(_ptr(X), n, D, _ptr(P), d, _ptr(Y), ldy, precision, _stream(X.device)))
+    return Y
+
+
+class Index:
+    """Owns an ``lv_index*`` (stores + graph on one CUDA device)."""
+
+    def __init__(self, device: int | torch.device | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device if isinstance(device, int) else device.index or 0)
+        h = ctypes.c_void_p()
+        check(lib().leanvec_index_create(ctypes.byref(h), self.device.index))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().leanvec_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = LVIndexInfo()
+        check(lib().leanvec_index_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in LVIndexInfo._fields_ if f != "reserved"}
+
+    def buffers(self) -> dict:
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        check(lib().leanvec_index_buffers(self._h, *[ctypes.byref(p) for p in ptrs]))
+        return dict(zip(["primary", "primary_mean", "secondary", "secondary_mean", "graph"], [p.value for p in ptrs]))
+
+    def _view(self, ptr: int, shape, dtype) -> torch.Tensor:
+        """Copy a device buffer owned by the index into a new tensor (inspection, tests)."""
+        typestr = {torch.uint8: "|u1", torch.float32: "<f4", torch.int32: "<i4"}[dtype]
+
+        class _Buf:
+            __cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                        "data": (int(ptr), True), "version": 2, "strides": None}
+
+        torch.cuda.current_stream(self.device).synchronize()
+        return torch.as_tensor(_Buf(), device=self.device).clone()
+
+    def primary_records(self) -> torch.Tensor:
+        inf = self.info()
+        return self._view(self.buffers()["primary"], (inf["n"], inf["primary_stride"]), torch.uint8)
+
+    def secondary_records(self) -> torch.Tensor:
+        inf = self.info()
+        return self._view(self.buffers()["secondary"], (inf["n"], inf["secondary_stride"]), torch.uint8)
+
+    def primary_mean(self) -> torch.Tensor:
+        return self._view(self.buffers()["primary_mean"], (self.info()["d"],), torch.float32)
+
+    # -- encoding ------------------------------------------------------------
+    def encode(self, X: torch.Tensor, B: torch.Tensor, primary_bits: int = 8, secondary_bits: int = 8,
+               precision: int = PREC_FP32) -> "Index":
+        X, B = _f32(X), _f32(B)
+        check(lib().leanvec_encode(self._h, _ptr(X), X.shape[0], X.shape[1], _ptr(B), B.shape[0], primary_bits,
+                                   secondary_bits, precision, _stream(self.device)))
+        return self
+
+    def set_primary(self, Y: torch.Tensor, mean: torch.Tensor | None, bits: int, D: int) -> "Index":
+        Y = _f32(Y)
+        m = _f32(mean) if mean is not None else None
+        check(lib().leanvec_set_primary(self._h, _ptr(Y), Y.shape[0], Y.shape[1], _ptr(m), bits, D,
+                                        _stream(self.device)))
+        return self
+
+    def set_secondary(self, X: torch.Tensor, mean: torch.Tensor | None = None) -> "Index":
+        X = _f32(X)
+        m = _f32(mean) if mean is not None else None
+        check(lib().leanvec_set_secondary(self._h, _ptr(X), X.shape[0], X.shape[1], _ptr(m), _stream(self.device)))
+        return self
+
+    def encode_fp32(self, X: torch.Tensor) -> "Index":
+        X = _f32(X)
+        check(lib().leanvec_encode_fp32(self._h, _ptr(X), X.shape[0], X.shape[1], _stream(self.device)))
+        return self
+
+    # -- graph ----------------------------------------------------------------
+    def set_graph(self, adj: torch.Tensor, entry: int = -1) -> "Index":
+        adj = adj.to(device=self.device, dtype=torch.int32).contiguous()
+        check(lib().leanvec_set_graph(self._h, _ptr(adj), adj.shape[1], entry, _stream(self.device)))
+        return self
+
+    def get_graph(self) -> tuple[torch.Tensor, int]:
+        inf = self.info()
+        adj = torch.empty((inf["n"], inf["R"]), dtype=torch.int32, device=self.device)
+        e = ctypes.c_int32()
+        check(lib().leanvec_get_graph(self._h, _ptr(adj), ctypes.byref(e), _stream(self.device)))
+        torch.cuda.current_stream(self.device).synchronize()
+        return adj, int(e.value)
+
+    def build_graph(self, R: int, L_build: int, alpha: float, passes: int = 2, batch: int = 4096,
+                    seed: int = 5000) -> "Index":
+        check(lib().leanvec_build_graph(self._h, R, L_build, float(alpha), passes, batch, seed, _stream(self.device)))
+        return self
+
+    # -- search ----------------------------------------------------------------
+    def search(self, Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0, max_hops: int = 0,
+               desc: torch.Tensor | None = None, ldo: int | None = None, stats: bool = False,
+               projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0,
+               out: tuple[torch.Tensor, torch.Tensor] | None = None):
+        """Search m queries. desc: optional (m, 4) int32 CUDA tensor of per-query
+        (k, L, rerank, max_hops); then k/L are the upper bounds used for capacity."""
+        Q = _f32(Q)
+        m = Q.shape[0]
+        ldo = k if ldo is None else ldo
+        if out is None:
+            ids = torch.empty((m, ldo), dtype=torch.int32, device=self.device)
+            sc = torch.empty((m, ldo), dtype=torch.float32, device=self.device)
+        else:
+            ids, sc = out
+        st = torch.empty((m, 2), dtype=torch.int32, device=self.device) if stats else None
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, 0)
+        if desc is not None:
+            desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
+        Ac = _f32(A) if A is not None else None
+        check(lib().leanvec_search(self._h, _ptr(Q), m, _ptr(Ac), ctypes.byref(prm), _ptr(desc), _ptr(ids), _ptr(sc),
+                                   ldo, _ptr(st), _stream(self.device)))
+        return (ids, sc, st) if stats else (ids, sc)
+
+    def sync_status(self) -> int:
+        return check(lib().leanvec_sync_status(self._h, _stream(self.device)))

@@ -1,0 +1,82 @@
+"""ctypes loader for ``_build/libleanvec.so`` (the C ABI of include/leanvec.h).
+
+There is no fallback: if the library is missing or cannot be loaded, every call
+raises.  Build it with ``__graft_entry__.build()`` or ``python -m
+paper_2312_16335_gb300.build_lib``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build_lib
+
+_lib = None
+
+c_i32, c_i64, c_u64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
+
+
+class LVQueryDesc(ctypes.Structure):
+    _fields_ = [("k", c_i32), ("L", c_i32), ("rerank", c_i32), ("max_hops", c_i32)]
+
+
+class LVSearchParams(ctypes.Structure):
+    _fields_ = [("uniform", LVQueryDesc), ("projection", c_i32), ("hash_slots", c_i32),
+                ("warps_per_block", c_i32), ("reserved", c_i32)]
+
+
+class LVIndexInfo(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("D", c_i32), ("d", c_i32), ("primary_bits", c_i32),
+                ("secondary_bits", c_i32), ("primary_stride", c_i64), ("secondary_stride", c_i64),
+                ("R", c_i32), ("entry", c_i32), ("mu2", c_f32), ("reserved", c_i32)]
+
+
+# (name, restype, argtypes) for every symbol of include/leanvec.h
+SIGNATURES = {
+    "leanvec_last_error": (ctypes.c_char_p, []),
+    "leanvec_record_stride": (c_i64, [c_i32, c_i32]),
+    "leanvec_column_mean": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp]),
+    "leanvec_lvq_encode": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp, c_vp]),
+    "leanvec_project": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp, c_i32, c_i32, c_vp]),
+    "leanvec_index_create": (c_i32, [ctypes.POINTER(c_vp), c_i32]),
+    "leanvec_index_free": (c_i32, [c_vp]),
+    "leanvec_index_info": (c_i32, [c_vp, ctypes.POINTER(LVIndexInfo)]),
+    "leanvec_index_buffers": (c_i32, [c_vp] + [ctypes.POINTER(c_vp)] * 5),
+    "leanvec_encode": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_i32, c_i32, c_i32, c_i32, c_vp]),
+    "leanvec_set_primary": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_i32, c_i32, c_vp]),
+    "leanvec_set_secondary": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp]),
+    "leanvec_encode_fp32": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp]),
+    "leanvec_set_graph": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp]),
+    "leanvec_get_graph": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32), c_vp]),
+    "leanvec_build_graph": (c_i32, [c_vp, c_i32, c_i32, c_f32, c_i32, c_i32, c_u64, c_vp]),
+    "leanvec_search": (c_i32, [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(LVSearchParams), c_vp, c_vp, c_vp,
+                               c_i32, c_vp, c_vp]),
+    "leanvec_sync_status": (c_i32, [c_vp, c_vp]),
+}
+
+
+class LeanVecError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"leanvec error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_lib.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first (__graft_entry__.build())")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        raise LeanVecError(rc, lib().leanvec_last_error().decode())
+    return rc

@@ -1,0 +1,516 @@
+// Host side of the C ABI declared in include/leanvec.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "beam.cuh"
+#include "common.cuh"
+#include "index.cuh"
+
+namespace lv {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LV_ERR_OOM : LV_ERR_CUDA;
+}
+
+// kernels of other translation units
+int launch_column_mean(const float *X, int64_t n, int dim, float *mean, cudaStream_t st);
+int launch_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int bits, uint8_t *rec,
+                      cudaStream_t st);
+int launch_fp32_records(const float *X, int64_t n, int dim, uint8_t *rec, int64_t stride, cudaStream_t st);
+int launch_mu2(const float *mean, int dim, float *out, cudaStream_t st);
+int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
+                        cudaStream_t st);
+int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStream_t st);
+int launch_query_consts(const float *Qp, int ldq, int d, const float *mu_p, const float *Q, int D,
+                        const float *mu_s, int64_t m, float4 *out, cudaStream_t st);
+int launch_graph_sanitize(int32_t *graph, int64_t n, int R, int *status, cudaStream_t st);
+int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int32_t *out,
+                        cudaStream_t st);
+int build_graph_impl(lv_index *idx, int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
+                     cudaStream_t st);
+
+// Makes the index's device current for the scope of an API call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess)) ok = true;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace lv
+
+using namespace lv;
+
+
+namespace lv {
+void index_free_stores(lv_index *idx) {
+    cudaFree(idx->prim);
+    cudaFree(idx->pmean);
+    cudaFree(idx->sec);
+    cudaFree(idx->smean);
+    cudaFree(idx->graph);
+    idx->prim = nullptr;
+    idx->pmean = nullptr;
+    idx->sec = nullptr;
+    idx->smean = nullptr;
+    idx->graph = nullptr;
+    idx->n = 0;
+    idx->R = 0;
+    idx->entry = -1;
+    idx->pbits = idx->sbits = 0;
+}
+
+int ensure_ws(void **p, size_t *have, size_t want) {
+    if (*have >= want) return LV_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    if (cudaMalloc(p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LV_ERR_OOM, "workspace allocation failed");
+    }
+    *have = want;
+    return LV_OK;
+}
+
+int *index_status(lv_index *idx) { return idx->status; }
+int index_num_sms(lv_index *idx) { return idx->num_sms; }
+}  // namespace lv
+
+extern "C" {
+
+const char *leanvec_last_error(void) { return g_last_error.c_str(); }
+
+int64_t leanvec_record_stride(int dim, int bits) {
+    RecGeom g;
+    if (!rec_geom(dim, bits, g)) return fail(LV_ERR_ARG, "record_stride: dim must be > 0 and bits in {4, 8, 32}");
+    return g.stride;
+}
+
+int leanvec_column_mean(const float *X, int64_t n, int dim, float *mean, lv_stream_t stream) {
+    if (!X || !mean || n <= 0 || dim <= 0) return fail(LV_ERR_ARG, "column_mean: empty input or null pointer");
+    return launch_column_mean(X, n, dim, mean, (cudaStream_t)stream);
+}
+
+int leanvec_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int bits, uint8_t *records,
+                       lv_stream_t stream) {
+    if (n < 0 || dim <= 0 || (n > 0 && (!V || !mean || !records)))
+        return fail(LV_ERR_ARG, "lvq_encode: invalid sizes or null pointer");
+    if (bits != 4 && bits != 8) return fail(LV_ERR_ARG, "lvq_encode: bits must be 4 or 8");
+    return launch_lvq_encode(V, n, dim, mean, bits, records, (cudaStream_t)stream);
+}
+
+int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, int precision,
+                    lv_stream_t stream) {
+    if (n < 0 || D <= 0 || d <= 0 || ldy < d || (n > 0 && (!X || !P || !Y)))
+        return fail(LV_ERR_ARG, "project: invalid sizes or null pointer");
+    if (precision != LV_PREC_FP32) return fail(LV_ERR_ARG, "project: only LV_PREC_FP32 is available in this build");
+    return launch_project_fp32(X, n, D, P, d, Y, ldy, (cudaStream_t)stream);
+}
+
+int leanvec_index_create(lv_index **out, int device) {
+    if (!out) return fail(LV_ERR_ARG, "index_create: null output");
+    *out = nullptr;
+    int ndev = 0;
+    LV_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(LV_ERR_ARG, "index_create: no such CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "index_create: cannot select device");
+    lv_index *idx = new lv_index();
+    idx->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete idx;
+        return fail(LV_ERR_CUDA, "index_create: cudaGetDeviceProperties failed");
+    }
+    idx->num_sms = prop.multiProcessorCount;
+    if (cudaMalloc(&idx->status, 4 * sizeof(int)) != cudaSuccess || cudaMemset(idx->status, 0, 4 * sizeof(int)) != cudaSuccess) {
+        cudaFree(idx->status);
+        delete idx;
+        return fail(LV_ERR_OOM, "index_create: status allocation failed");
+    }
+    *out = idx;
+    return LV_OK;
+}
+
+int leanvec_index_free(lv_index *idx) {
+    if (!idx) return LV_OK;
+    DeviceGuard g(idx->device);
+    index_free_stores(idx);
+    cudaFree(idx->status);
+    cudaFree(idx->ws_q);
+    cudaFree(idx->ws_c);
+    cudaFree(idx->bws);
+    delete idx;
+    return LV_OK;
+}
+
+int leanvec_index_info(const lv_index *idx, lv_index_info *out) {
+    if (!idx || !out) return fail(LV_ERR_ARG, "index_info: null pointer");
+    memset(out, 0, sizeof(*out));
+    out->n = idx->n;
+    out->D = idx->D;
+    out->d = idx->d;
+    out->primary_bits = idx->pbits;
+    out->secondary_bits = idx->sbits;
+    out->primary_stride = idx->pg.stride;
+    out->secondary_stride = idx->sbits ? idx->sg.stride : 0;
+    out->R = idx->R;
+    out->entry = idx->entry;
+    out->mu2 = idx->mu2;
+    return LV_OK;
+}
+
+int leanvec_index_buffers(const lv_index *idx, const uint8_t **primary, const float **primary_mean,
+                          const uint8_t **secondary, const float **secondary_mean, const int32_t **graph) {
+    if (!idx) return fail(LV_ERR_ARG, "index_buffers: null index");
+    if (primary) *primary = idx->prim;
+    if (primary_mean) *primary_mean = idx->pmean;
+    if (secondary) *secondary = idx->sec;
+    if (secondary_mean) *secondary_mean = idx->smean;
+    if (graph) *graph = idx->graph;
+    return LV_OK;
+}
+
+#define LV_TRY(x)                      \
+    do {                               \
+        rc = (x);                      \
+        if (rc != LV_OK) goto cleanup; \
+    } while (0)
+#define LV_TRYC(x)                      \
+    do {                                \
+        cudaError_t _e = (x);           \
+        if (_e != cudaSuccess) {        \
+            rc = cuda_fail(_e, #x);     \
+            goto cleanup;               \
+        }                               \
+    } while (0)
+
+static void drop_primary(lv_index *idx) {
+    cudaFree(idx->prim);
+    cudaFree(idx->pmean);
+    cudaFree(idx->graph);
+    idx->prim = nullptr;
+    idx->pmean = nullptr;
+    idx->graph = nullptr;
+    idx->R = 0;
+    idx->entry = -1;
+    idx->pbits = 0;
+}
+
+static void drop_secondary(lv_index *idx) {
+    cudaFree(idx->sec);
+    cudaFree(idx->smean);
+    idx->sec = nullptr;
+    idx->smean = nullptr;
+    idx->sbits = 0;
+}
+
+static int set_primary_impl(lv_index *idx, const float *Y, int64_t n, int d, const float *mean, int bits, int D,
+                            cudaStream_t st) {
+    RecGeom pg;
+    rec_geom(d, bits, pg);
+    float *mu2d = nullptr;
+    int rc = LV_OK;
+    drop_primary(idx);
+    if (idx->n != n) drop_secondary(idx);
+    LV_TRYC(cudaMalloc(&mu2d, sizeof(float)));
+    LV_TRYC(cudaMalloc(&idx->prim, (size_t)n * pg.stride));
+    LV_TRYC(cudaMalloc(&idx->pmean, sizeof(float) * d));
+    if (mean)
+        LV_TRYC(cudaMemcpyAsync(idx->pmean, mean, sizeof(float) * d, cudaMemcpyDeviceToDevice, st));
+    else
+        LV_TRY(launch_column_mean(Y, n, d, idx->pmean, st));
+    LV_TRY(launch_lvq_encode(Y, n, d, idx->pmean, bits, idx->prim, st));
+    LV_TRY(launch_mu2(idx->pmean, d, mu2d, st));
+    LV_TRYC(cudaMemcpyAsync(&idx->mu2, mu2d, sizeof(float), cudaMemcpyDeviceToHost, st));
+    LV_TRYC(cudaStreamSynchronize(st));
+    idx->n = n;
+    idx->d = d;
+    idx->D = D;
+    idx->pbits = bits;
+    idx->pg = pg;
+cleanup:
+    cudaFree(mu2d);
+    if (rc != LV_OK) {
+        drop_primary(idx);
+        drop_secondary(idx);
+        idx->n = 0;
+    }
+    return rc;
+}
+
+static int set_secondary_impl(lv_index *idx, const float *X, int64_t n, int D, const float *mean, cudaStream_t st) {
+    RecGeom sg;
+    rec_geom(D, 8, sg);
+    int rc = LV_OK;
+    drop_secondary(idx);
+    LV_TRYC(cudaMalloc(&idx->sec, (size_t)n * sg.stride));
+    LV_TRYC(cudaMalloc(&idx->smean, sizeof(float) * D));
+    if (mean)
+        LV_TRYC(cudaMemcpyAsync(idx->smean, mean, sizeof(float) * D, cudaMemcpyDeviceToDevice, st));
+    else
+        LV_TRY(launch_column_mean(X, n, D, idx->smean, st));
+    LV_TRY(launch_lvq_encode(X, n, D, idx->smean, 8, idx->sec, st));
+    LV_TRYC(cudaStreamSynchronize(st));
+    idx->sbits = 8;
+    idx->sg = sg;
+cleanup:
+    if (rc != LV_OK) drop_secondary(idx);
+    return rc;
+}
+
+int leanvec_set_primary(lv_index *idx, const float *Y, int64_t n, int d, const float *mean, int bits, int D,
+                        lv_stream_t stream) {
+    if (!idx || !Y) return fail(LV_ERR_ARG, "set_primary: null pointer");
+    if (n <= 0 || n >= (int64_t)0x7fffffff) return fail(LV_ERR_ARG, "set_primary: n must be in [1, 2^31 - 1)");
+    if (d <= 0 || D < d) return fail(LV_ERR_ARG, "set_primary: need 0 < d <= D");
+    if (bits != 4 && bits != 8) return fail(LV_ERR_ARG, "set_primary: bits must be 4 or 8");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "set_primary: cannot select device");
+    return set_primary_impl(idx, Y, n, d, mean, bits, D, (cudaStream_t)stream);
+}
+
+int leanvec_set_secondary(lv_index *idx, const float *X, int64_t n, int D, const float *mean, lv_stream_t stream) {
+    if (!idx || !X) return fail(LV_ERR_ARG, "set_secondary: null pointer");
+    if (idx->n == 0 || idx->pbits == 32) return fail(LV_ERR_STATE, "set_secondary: set an LVQ primary store first");
+    if (n != idx->n || D != idx->D) return fail(LV_ERR_ARG, "set_secondary: n and D must match the primary store");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "set_secondary: cannot select device");
+    return set_secondary_impl(idx, X, n, D, mean, (cudaStream_t)stream);
+}
+
+int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float *B, int d, int primary_bits,
+                   int secondary_bits, int projection_precision, lv_stream_t stream) {
+    if (!idx || !X || !B) return fail(LV_ERR_ARG, "encode: null pointer");
+    if (n <= 0 || n >= (int64_t)0x7fffffff) return fail(LV_ERR_ARG, "encode: n must be in [1, 2^31 - 1)");
+    if (D <= 0 || d <= 0 || d > D) return fail(LV_ERR_ARG, "encode: need 0 < d <= D");
+    if (primary_bits != 4 && primary_bits != 8) return fail(LV_ERR_ARG, "encode: primary_bits must be 4 or 8");
+    if (secondary_bits != 0 && secondary_bits != 8) return fail(LV_ERR_ARG, "encode: secondary_bits must be 0 or 8");
+    if (projection_precision != LV_PREC_FP32)
+        return fail(LV_ERR_ARG, "encode: only LV_PREC_FP32 projection is available in this build");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "encode: cannot select device");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *Y = nullptr;
+    int rc = LV_OK;
+    index_free_stores(idx);
+    LV_TRYC(cudaMalloc(&Y, sizeof(float) * (size_t)n * d));
+    LV_TRY(launch_project_fp32(X, n, D, B, d, Y, d, st));
+    LV_TRY(set_primary_impl(idx, Y, n, d, nullptr, primary_bits, D, st));
+    if (secondary_bits) LV_TRY(set_secondary_impl(idx, X, n, D, nullptr, st));
+cleanup:
+    cudaFree(Y);
+    if (rc != LV_OK) index_free_stores(idx);
+    return rc;
+}
+
+int leanvec_encode_fp32(lv_index *idx, const float *X, int64_t n, int D, lv_stream_t stream) {
+    if (!idx || !X) return fail(LV_ERR_ARG, "encode_fp32: null pointer");
+    if (n <= 0 || n >= (int64_t)0x7fffffff || D <= 0) return fail(LV_ERR_ARG, "encode_fp32: invalid sizes");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "encode_fp32: cannot select device");
+    cudaStream_t st = (cudaStream_t)stream;
+    index_free_stores(idx);
+    RecGeom pg;
+    rec_geom(D, 32, pg);
+    int rc = LV_OK;
+    LV_TRYC(cudaMalloc(&idx->prim, (size_t)n * pg.stride));
+    LV_TRY(launch_fp32_records(X, n, D, idx->prim, pg.stride, st));
+    LV_TRYC(cudaStreamSynchronize(st));
+    idx->n = n;
+    idx->D = D;
+    idx->d = D;
+    idx->pbits = 32;
+    idx->sbits = 0;
+    idx->pg = pg;
+    idx->mu2 = 0.f;
+cleanup:
+    if (rc != LV_OK) index_free_stores(idx);
+    return rc;
+}
+
+int leanvec_set_graph(lv_index *idx, const int32_t *adj, int R, int32_t entry, lv_stream_t stream) {
+    if (!idx || !adj) return fail(LV_ERR_ARG, "set_graph: null pointer");
+    if (idx->n == 0) return fail(LV_ERR_STATE, "set_graph: the index has no store");
+    if (R < 1 || R > RMAX) return fail(LV_ERR_ARG, "set_graph: R must be in [1, 128]");
+    if (entry >= idx->n) return fail(LV_ERR_ARG, "set_graph: entry out of range");
+    if (entry < 0 && idx->pbits == 32)
+        return fail(LV_ERR_ARG, "set_graph: a float32 index needs an explicit entry point");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "set_graph: cannot select device");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaFree(idx->graph);
+    idx->graph = nullptr;
+    idx->R = 0;
+    idx->entry = -1;
+    LV_CUDA(cudaMalloc(&idx->graph, sizeof(int32_t) * (size_t)idx->n * R));
+    LV_CUDA(cudaMemcpyAsync(idx->graph, adj, sizeof(int32_t) * (size_t)idx->n * R, cudaMemcpyDeviceToDevice, st));
+    int rc = launch_graph_sanitize(idx->graph, idx->n, R, idx->status, st);
+    if (rc != LV_OK) return rc;
+    if (entry < 0) {
+        int32_t *e = nullptr;
+        LV_CUDA(cudaMalloc(&e, sizeof(int32_t)));
+        rc = launch_entry_argmax(idx->prim, idx->n, idx->pg.stride, idx->pg.code_bytes, e, st);
+        if (rc == LV_OK && cudaMemcpyAsync(&entry, e, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = fail(LV_ERR_CUDA, "set_graph: entry copy failed");
+        if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "set_graph: sync failed");
+        cudaFree(e);
+        if (rc != LV_OK) return rc;
+    }
+    idx->R = R;
+    idx->entry = entry;
+    return LV_OK;
+}
+
+int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stream_t stream) {
+    if (!idx || !adj) return fail(LV_ERR_ARG, "get_graph: null pointer");
+    if (!idx->graph) return fail(LV_ERR_STATE, "get_graph: the index has no graph");
+    DeviceGuard g(idx->device);
+    LV_CUDA(cudaMemcpyAsync(adj, idx->graph, sizeof(int32_t) * (size_t)idx->n * idx->R, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    if (entry) *entry = idx->entry;
+    return LV_OK;
+}
+
+int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
+                        lv_stream_t stream) {
+    if (!idx) return fail(LV_ERR_ARG, "build_graph: null index");
+    if (idx->n == 0 || (idx->pbits != 8 && idx->pbits != 4))
+        return fail(LV_ERR_STATE, "build_graph: the index has no LVQ primary store");
+    if (R < 1 || R > RMAX || L_build < 1 || L_build > LCAP_MAX || passes < 1 || batch < 1 || !(alpha > 0.f))
+        return fail(LV_ERR_ARG, "build_graph: need 1 <= R <= 128, 1 <= L_build <= 512, passes >= 1, batch >= 1, alpha > 0");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "build_graph: cannot select device");
+    return build_graph_impl(idx, R, L_build, alpha, passes, batch, seed, (cudaStream_t)stream);
+}
+
+static int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, const lv_search_params *params,
+                   const lv_query_desc *desc, int32_t *ids, float *scores, int ldo, lv_search_stats *stats,
+                   lv_stream_t stream) {
+    if (!idx || !params) return fail(LV_ERR_ARG, "search: null index or params");
+    if (m < 0 || m >= (int64_t)0x7fffffff) return fail(LV_ERR_ARG, "search: invalid m");
+    if (m == 0) return LV_OK;
+    if (!Q || !ids || !scores) return fail(LV_ERR_ARG, "search: null query or output pointer");
+    if (idx->n == 0) return fail(LV_ERR_STATE, "search: the index has no store");
+    if (!idx->graph) return fail(LV_ERR_STATE, "search: the index has no graph");
+    if (idx->pbits != 32 && !A) return fail(LV_ERR_ARG, "search: an LVQ index needs the projection A");
+    const lv_query_desc &u = params->uniform;
+    if (u.L < 1 || u.L > LCAP_MAX) return fail(LV_ERR_ARG, "search: L must be in [1, 512]");
+    if (!desc && (u.k < 1 || u.k > u.L || u.k > ldo || u.rerank < 0 || u.rerank > u.L || u.max_hops < 0))
+        return fail(LV_ERR_ARG, "search: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
+    if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search: rerank needs a secondary store");
+    if (params->projection != LV_PREC_FP32)
+        return fail(LV_ERR_ARG, "search: only LV_PREC_FP32 projection is available in this build");
+    DeviceGuard g(idx->device);
+    if (!g.ok) return fail(LV_ERR_CUDA, "search: cannot select device");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // padded queries in the primary space + per-query constants
+    int cpc = idx->pbits == 8 ? 16 : idx->pbits == 4 ? 32 : 4;
+    int ldq = idx->pg.code_chunks * cpc;
+    int rc = ensure_ws((void **)&idx->ws_q, &idx->ws_q_bytes, sizeof(float) * (size_t)m * ldq);
+    if (rc) return rc;
+    rc = ensure_ws((void **)&idx->ws_c, &idx->ws_c_bytes, sizeof(float4) * (size_t)m);
+    if (rc) return rc;
+    if (idx->pbits == 32) {
+        rc = launch_pad_rows(Q, m, idx->D, idx->ws_q, ldq, st);
+    } else {
+        rc = launch_project_fp32(Q, m, idx->D, A, idx->d, idx->ws_q, ldq, st);
+    }
+    if (rc) return rc;
+    rc = launch_query_consts(idx->ws_q, ldq, idx->d, idx->pbits == 32 ? nullptr : idx->pmean, Q, idx->D, idx->smean,
+                             m, idx->ws_c, st);
+    if (rc) return rc;
+
+    BeamParams p;
+    memset(&p, 0, sizeof(p));
+    p.prim = idx->prim;
+    p.prim_stride = idx->pg.stride;
+    p.prim_chunks = idx->pg.code_chunks;
+    p.prim_dim = idx->d;
+    p.graph = idx->graph;
+    p.R = idx->R;
+    p.n = idx->n;
+    p.entry = idx->entry;
+    p.qp = idx->ws_q;
+    p.ldq = ldq;
+    p.qconst = idx->ws_c;
+    p.desc = reinterpret_cast<const int4 *>(desc);
+    p.uni = make_int4(u.k, u.L, idx->sec ? u.rerank : 0, u.max_hops);
+    p.m = m;
+    p.sec = idx->sec;
+    p.sec_stride = idx->sbits ? idx->sg.stride : 0;
+    p.sec_chunks = idx->sbits ? idx->sg.code_chunks : 0;
+    p.Q = Q;
+    p.D = idx->D;
+    p.ids = ids;
+    p.scores = scores;
+    p.ldo = ldo;
+    p.stats = reinterpret_cast<int2 *>(stats);
+    p.status = idx->status;
+    p.work = idx->status + 1;
+    p.Lcap = (int)round_up(u.L, 32);
+    int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(8 * u.L)));
+    if (hs & (hs - 1)) return fail(LV_ERR_ARG, "search: hash_slots must be a power of two");
+    hs = std::max(hs, next_pow2(2 * p.Lcap));
+    p.Hcap = hs;
+    p.hbits = 0;
+    while ((1 << p.hbits) < hs) p.hbits++;
+    p.Rcap = (int)round_up(idx->R, 32);
+    p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap);
+    int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
+    while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;
+    if ((size_t)warps * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
+    if (idx->sbits && idx->sg.code_chunks + 1 > 64) return fail(LV_ERR_ARG, "search: D > 1008 is not supported by the rerank");
+    LV_CUDA(cudaMemsetAsync(p.work, 0, sizeof(int), st));
+    const size_t smem = (size_t)warps * p.warp_smem;
+    const int block = warps * 32;
+    if (idx->pbits == 32) {
+        int ncw = (idx->pg.code_chunks + 31) / 32;
+        return launch_search_fp32(p, ncw, block, smem, idx->num_sms, st);
+    }
+    int nc = (idx->pg.code_chunks + 1 + 3) / 4;
+    if (idx->pbits == 8) return launch_search_lvq8(p, nc, block, smem, idx->num_sms, st);
+    return launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
+}
+
+int leanvec_sync_status(lv_index *idx, lv_stream_t stream) {
+    if (!idx) return fail(LV_ERR_ARG, "sync_status: null index");
+    DeviceGuard g(idx->device);
+    int s = 0;
+    LV_CUDA(cudaMemcpyAsync(&s, idx->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    LV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    LV_CUDA(cudaMemsetAsync(idx->status, 0, sizeof(int), (cudaStream_t)stream));
+    LV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (s & ST_CORRUPT) return fail(LV_ERR_CORRUPT, "a graph id was out of range");
+    if (s & ST_CAPACITY) return fail(LV_ERR_CAPACITY, "a per-query size exceeded the launch capacity and was clamped");
+    if (s & ST_TIMEOUT) return fail(LV_ERR_TIMEOUT, "a bounded device wait gave up");
+    return LV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,656 @@
+// Persistent best-first beam search over the primary vectors with a rerank over the
+// secondary vectors (Sec. 2 "Search"; App. D: greedy traversal with backtracking,
+// Vamana graph).  One warp serves one query at a time; warps pull queries from a
+// global counter until the batch is exhausted.
+//
+// Per warp, shared memory holds a double-buffered beam (scores + ids, the top bit of
+// an id marks "expanded"), a visited cache, and the candidate buffers of one
+// expansion.  The visited cache is an open-addressing table that may forget ids
+// (overwrite when a probe run is full) but never reports an unvisited id as visited;
+// a forgotten id that is met again is rescored and then rejected by the merge,
+// because it is either still in the beam (exact key match) or worse than the beam's
+// last member (the last member only improves).  The beam is therefore identical to
+// the one of an exact visited set.
+#pragma once
+
+#include "common.cuh"
+
+namespace lv {
+
+struct BeamParams {
+    // primary store + graph
+    const uint8_t *prim;
+    int64_t prim_stride;
+    int prim_chunks;  // 16-byte code chunks of a primary record
+    int prim_dim;     // codes per record (build score)
+    const int32_t *graph;
+    int R;
+    int64_t n;
+    int32_t entry;
+    // queries
+    const float *qp;  // padded queries in the primary space (search mode)
+    int ldq;
+    const float4 *qconst;  // (cq, sq, cQ, sQ)
+    const int4 *desc;      // per query (k, L, r, max_hops) or NULL
+    int4 uni;
+    int64_t m;
+    // secondary store (rerank)
+    const uint8_t *sec;
+    int64_t sec_stride;
+    int sec_chunks;
+    const float *Q;  // unreduced queries m x D
+    int D;
+    // build mode
+    const int32_t *qnodes;
+    float mu2;
+    // outputs
+    int32_t *ids;
+    float *scores;
+    int ldo;
+    int2 *stats;
+    // scheduling / capacities
+    int *work;
+    int *status;
+    int Lcap;   // beam capacity (multiple of 32)
+    int Hcap;   // visited cache slots (power of two, >= 2 * Lcap)
+    int hbits;  // log2(Hcap)
+    int Rcap;   // candidate buffer capacity (multiple of 32, >= R)
+    int warp_smem;
+};
+
+inline int beam_warp_smem(int Lcap, int Hcap, int Rcap) { return 16 * Lcap + 4 * Hcap + 20 * Rcap; }
+
+// --------------------------------------------------------------------------------
+// Primary scorer: LVQ records, 4 lanes per record, 8 records per warp pass.
+// score = cq + lower * sq + delta * <q', codes>    (decoded inner product, Eq. 1)
+// --------------------------------------------------------------------------------
+template <int NC, int BITS>
+struct LvqGroupScorer {
+    static constexpr int CPC = BITS == 8 ? 16 : 32;  // codes per 16-byte chunk
+    float q[NC][CPC];
+    float cq, sq;
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+        CH = p.prim_chunks;
+        base = p.prim;
+        stride = p.prim_stride;
+        const int g = lane & 3;
+        const float *row = p.qp + qi * p.ldq;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const int c = g + 4 * t;
+#pragma unroll
+            for (int e = 0; e < CPC; e += 4) {
+                float4 v = c < CH ? *reinterpret_cast<const float4 *>(row + c * CPC + e) : make_float4(0, 0, 0, 0);
+                q[t][e] = v.x;
+                q[t][e + 1] = v.y;
+                q[t][e + 2] = v.z;
+                q[t][e + 3] = v.w;
+            }
+        }
+        float4 k = p.qconst[qi];
+        cq = k.x;
+        sq = k.y;
+    }
+
+    __device__ __forceinline__ float dot(const uint4 (&v)[NC]) const {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const uint32_t w[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (BITS == 8) {
+                    a0 = fmaf(q[t][4 * i + 0], byte_to_float<0>(w[i]), a0);
+                    a1 = fmaf(q[t][4 * i + 1], byte_to_float<1>(w[i]), a1);
+                    a2 = fmaf(q[t][4 * i + 2], byte_to_float<2>(w[i]), a2);
+                    a3 = fmaf(q[t][4 * i + 3], byte_to_float<3>(w[i]), a3);
+                } else {
+                    const uint32_t lo = w[i] & 0x0F0F0F0Fu, hi = (w[i] >> 4) & 0x0F0F0F0Fu;
+                    a0 = fmaf(q[t][8 * i + 0], byte_to_float<0>(lo), a0);
+                    a1 = fmaf(q[t][8 * i + 1], byte_to_float<0>(hi), a1);
+                    a2 = fmaf(q[t][8 * i + 2], byte_to_float<1>(lo), a2);
+                    a3 = fmaf(q[t][8 * i + 3], byte_to_float<1>(hi), a3);
+                    a0 = fmaf(q[t][8 * i + 4], byte_to_float<2>(lo), a0);
+                    a1 = fmaf(q[t][8 * i + 5], byte_to_float<2>(hi), a1);
+                    a2 = fmaf(q[t][8 * i + 6], byte_to_float<3>(lo), a2);
+                    a3 = fmaf(q[t][8 * i + 7], byte_to_float<3>(hi), a3);
+                }
+            }
+        }
+        return (a0 + a1) + (a2 + a3);
+    }
+
+    // scores of ids[0..cnt) into out[0..cnt) (shared memory); warp-collective
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        const int g = lane & 3, grp = lane >> 2;
+        const int holder = (lane & ~3) | (CH & 3);
+        for (int b = 0; b < cnt; b += 16) {
+            const int j0 = b + grp, j1 = b + 8 + grp;
+            const int id0 = j0 < cnt ? ids[j0] : -1;
+            const int id1 = j1 < cnt ? ids[j1] : -1;
+            const uint8_t *r0 = base + (int64_t)(id0 < 0 ? 0 : id0) * stride;
+            const uint8_t *r1 = base + (int64_t)(id1 < 0 ? 0 : id1) * stride;
+            uint4 v0[NC], v1[NC];
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+                const int c = g + 4 * t;
+                v0[t] = (c <= CH && id0 >= 0) ? ldg_stream(r0 + 16 * c) : make_uint4(0, 0, 0, 0);
+                v1[t] = (c <= CH && id1 >= 0) ? ldg_stream(r1 + 16 * c) : make_uint4(0, 0, 0, 0);
+            }
+            float s0 = dot(v0), s1 = dot(v1);
+            float d0 = 0.f, l0 = 0.f, d1 = 0.f, l1 = 0.f;
+#pragma unroll
+            for (int t = 0; t < NC; ++t)
+                if (g + 4 * t == CH) {
+                    d0 = __uint_as_float(v0[t].x);
+                    l0 = __uint_as_float(v0[t].y);
+                    d1 = __uint_as_float(v1[t].x);
+                    l1 = __uint_as_float(v1[t].y);
+                }
+            s0 += __shfl_xor_sync(FULL, s0, 1);
+            s1 += __shfl_xor_sync(FULL, s1, 1);
+            s0 += __shfl_xor_sync(FULL, s0, 2);
+            s1 += __shfl_xor_sync(FULL, s1, 2);
+            d0 = __shfl_sync(FULL, d0, holder);
+            l0 = __shfl_sync(FULL, l0, holder);
+            d1 = __shfl_sync(FULL, d1, holder);
+            l1 = __shfl_sync(FULL, l1, holder);
+            if (g == 0) {
+                if (j0 < cnt) out[j0] = fmaf(d0, s0, fmaf(l0, sq, cq));
+                if (j1 < cnt) out[j1] = fmaf(d1, s1, fmaf(l1, sq, cq));
+            }
+        }
+    }
+};
+
+// --------------------------------------------------------------------------------
+// Build scorer: the query is a database node's own primary record; the pair score is
+// the exact build score (integer sums + a fixed float32 expression, see leanvec.h).
+// --------------------------------------------------------------------------------
+__device__ __forceinline__ float build_pair_score(float mu2, float fdim, float da, float la, float Ga, float Ha,
+                                                  float db, float lb, float Gb, float Hb, int P) {
+    float t1 = __fadd_rn(Ga, Gb);
+    float t2 = __fmul_rn(fdim, __fmul_rn(la, lb));
+    float t3 = __fadd_rn(__fmul_rn(lb, Ha), __fmul_rn(la, Hb));
+    float t4 = __fmul_rn(__fmul_rn(da, db), __int2float_rn(P));
+    float s = __fadd_rn(mu2, t1);
+    s = __fadd_rn(s, t2);
+    s = __fadd_rn(s, t3);
+    return __fadd_rn(s, t4);
+}
+
+// sum of products of the unsigned codes held in two 16-byte chunks (exact)
+template <int BITS>
+__device__ __forceinline__ int code_dot(const uint4 &a, const uint4 &b) {
+    unsigned s = 0u;
+    if (BITS == 8) {
+        s = __dp4a(a.x, b.x, s);
+        s = __dp4a(a.y, b.y, s);
+        s = __dp4a(a.z, b.z, s);
+        s = __dp4a(a.w, b.w, s);
+    } else {
+        const uint32_t m = 0x0F0F0F0Fu;
+        s = __dp4a(a.x & m, b.x & m, s);
+        s = __dp4a((a.x >> 4) & m, (b.x >> 4) & m, s);
+        s = __dp4a(a.y & m, b.y & m, s);
+        s = __dp4a((a.y >> 4) & m, (b.y >> 4) & m, s);
+        s = __dp4a(a.z & m, b.z & m, s);
+        s = __dp4a((a.z >> 4) & m, (b.z >> 4) & m, s);
+        s = __dp4a(a.w & m, b.w & m, s);
+        s = __dp4a((a.w >> 4) & m, (b.w >> 4) & m, s);
+    }
+    return (int)s;
+}
+
+template <int NC, int BITS>
+struct BuildScorer {
+    uint4 qc[NC];
+    float qd, ql, qG, qH, mu2, fdim;
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+        CH = p.prim_chunks;
+        base = p.prim;
+        stride = p.prim_stride;
+        mu2 = p.mu2;
+        fdim = (float)p.prim_dim;
+        const int g = lane & 3;
+        const uint8_t *r = base + (int64_t)p.qnodes[qi] * stride;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const int c = g + 4 * t;
+            qc[t] = c < CH ? *reinterpret_cast<const uint4 *>(r + 16 * c) : make_uint4(0, 0, 0, 0);
+        }
+        float4 k = *reinterpret_cast<const float4 *>(r + 16 * CH);
+        qd = k.x;
+        ql = k.y;
+        qG = k.z;
+        qH = k.w;
+    }
+
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        const int g = lane & 3, grp = lane >> 2;
+        const int holder = (lane & ~3) | (CH & 3);
+        for (int b = 0; b < cnt; b += 16) {
+            const int j0 = b + grp, j1 = b + 8 + grp;
+            const int id0 = j0 < cnt ? ids[j0] : -1;
+            const int id1 = j1 < cnt ? ids[j1] : -1;
+            const uint8_t *r0 = base + (int64_t)(id0 < 0 ? 0 : id0) * stride;
+            const uint8_t *r1 = base + (int64_t)(id1 < 0 ? 0 : id1) * stride;
+            uint4 v0[NC], v1[NC];
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+                const int c = g + 4 * t;
+                v0[t] = (c <= CH && id0 >= 0) ? ldg_stream(r0 + 16 * c) : make_uint4(0, 0, 0, 0);
+                v1[t] = (c <= CH && id1 >= 0) ? ldg_stream(r1 + 16 * c) : make_uint4(0, 0, 0, 0);
+            }
+            int P0 = 0, P1 = 0;
+            float4 k0 = make_float4(0, 0, 0, 0), k1 = make_float4(0, 0, 0, 0);
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+                P0 += code_dot<BITS>(v0[t], qc[t]);
+                P1 += code_dot<BITS>(v1[t], qc[t]);
+                if (g + 4 * t == CH) {
+                    k0 = make_float4(__uint_as_float(v0[t].x), __uint_as_float(v0[t].y), __uint_as_float(v0[t].z),
+                                     __uint_as_float(v0[t].w));
+                    k1 = make_float4(__uint_as_float(v1[t].x), __uint_as_float(v1[t].y), __uint_as_float(v1[t].z),
+                                     __uint_as_float(v1[t].w));
+                }
+            }
+            P0 += __shfl_xor_sync(FULL, P0, 1);
+            P1 += __shfl_xor_sync(FULL, P1, 1);
+            P0 += __shfl_xor_sync(FULL, P0, 2);
+            P1 += __shfl_xor_sync(FULL, P1, 2);
+            k0.x = __shfl_sync(FULL, k0.x, holder);
+            k0.y = __shfl_sync(FULL, k0.y, holder);
+            k0.z = __shfl_sync(FULL, k0.z, holder);
+            k0.w = __shfl_sync(FULL, k0.w, holder);
+            k1.x = __shfl_sync(FULL, k1.x, holder);
+            k1.y = __shfl_sync(FULL, k1.y, holder);
+            k1.z = __shfl_sync(FULL, k1.z, holder);
+            k1.w = __shfl_sync(FULL, k1.w, holder);
+            if (g == 0) {
+                if (j0 < cnt) out[j0] = build_pair_score(mu2, fdim, qd, ql, qG, qH, k0.x, k0.y, k0.z, k0.w, P0);
+                if (j1 < cnt) out[j1] = build_pair_score(mu2, fdim, qd, ql, qG, qH, k1.x, k1.y, k1.z, k1.w, P1);
+            }
+        }
+    }
+};
+
+// --------------------------------------------------------------------------------
+// Whole-warp scorer for long records: float32 vectors (KIND 0, the full-dimensional
+// baseline) or LVQ-8 secondary records (KIND 1, the rerank).  U records per pass.
+// --------------------------------------------------------------------------------
+template <int NCW, int KIND>
+struct WarpScorer {
+    static constexpr int CPC = KIND == 0 ? 4 : 16;
+    static constexpr int U = KIND == 0 ? (NCW > 4 ? 2 : 4) : 4;
+    float q[NCW][CPC];
+    float c0, s0;
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    // qrow: qlen valid floats (the rest read as 0)
+    __device__ __forceinline__ void setup_row(const float *qrow, int qlen, int chunks, const uint8_t *b,
+                                              int64_t st, float cc, float ss, int lane) {
+        CH = chunks;
+        base = b;
+        stride = st;
+        c0 = cc;
+        s0 = ss;
+#pragma unroll
+        for (int t = 0; t < NCW; ++t) {
+            const int c = lane + 32 * t;
+#pragma unroll
+            for (int e = 0; e < CPC; ++e) {
+                const int j = c * CPC + e;
+                q[t][e] = (c < CH && j < qlen) ? qrow[j] : 0.0f;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+        // full-dimensional float32 search: padded queries, no constants
+        setup_row(p.qp + qi * p.ldq, p.ldq, p.prim_chunks, p.prim, p.prim_stride, 0.f, 0.f, lane);
+    }
+
+    __device__ __forceinline__ float dot1(const uint4 (&v)[NCW]) const {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int t = 0; t < NCW; ++t) {
+            if (KIND == 0) {
+                a0 = fmaf(q[t][0], __uint_as_float(v[t].x), a0);
+                a1 = fmaf(q[t][1], __uint_as_float(v[t].y), a1);
+                a2 = fmaf(q[t][2], __uint_as_float(v[t].z), a2);
+                a3 = fmaf(q[t][3], __uint_as_float(v[t].w), a3);
+            } else {
+                const uint32_t w[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    a0 = fmaf(q[t][4 * i + 0], byte_to_float<0>(w[i]), a0);
+                    a1 = fmaf(q[t][4 * i + 1], byte_to_float<1>(w[i]), a1);
+                    a2 = fmaf(q[t][4 * i + 2], byte_to_float<2>(w[i]), a2);
+                    a3 = fmaf(q[t][4 * i + 3], byte_to_float<3>(w[i]), a3);
+                }
+            }
+        }
+        return (a0 + a1) + (a2 + a3);
+    }
+
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        const int tot = CH + (KIND == 1 ? 1 : 0);
+        const int holder = CH & 31, tslot = CH >> 5;
+        for (int b = 0; b < cnt; b += U) {
+            uint4 v[U][NCW];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int id = b + u < cnt ? ids[b + u] : -1;
+                const uint8_t *r = base + (int64_t)(id < 0 ? 0 : id) * stride;
+#pragma unroll
+                for (int t = 0; t < NCW; ++t) {
+                    const int c = lane + 32 * t;
+                    v[u][t] = (c < tot && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float s = dot1(v[u]);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+                float dl = 0.f, lo = 0.f;
+                if (KIND == 1) {
+#pragma unroll
+                    for (int t = 0; t < NCW; ++t)
+                        if (t == tslot) {
+                            dl = __uint_as_float(v[u][t].x);
+                            lo = __uint_as_float(v[u][t].y);
+                        }
+                    dl = __shfl_sync(FULL, dl, holder);
+                    lo = __shfl_sync(FULL, lo, holder);
+                    s = fmaf(dl, s, fmaf(lo, s0, c0));
+                }
+                if (lane == 0 && b + u < cnt) out[b + u] = s;
+            }
+        }
+    }
+};
+
+// --------------------------------------------------------------------------------
+// The beam kernel.  BUILD: queries are nodes (p.qnodes), output = the final beam.
+// RERANK: rescore the top-r of the beam with the secondary store.
+// --------------------------------------------------------------------------------
+template <class PS, bool BUILD, bool RERANK>
+__global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned char *my = smem_raw + (size_t)(threadIdx.x >> 5) * p.warp_smem;
+    float *const bS0 = reinterpret_cast<float *>(my);
+    int *const bI0 = reinterpret_cast<int *>(bS0 + p.Lcap);
+    float *const bS1 = reinterpret_cast<float *>(bI0 + p.Lcap);
+    int *const bI1 = reinterpret_cast<int *>(bS1 + p.Lcap);
+    int *hash = reinterpret_cast<int *>(bI1 + p.Lcap);
+    int *cI = hash + p.Hcap;
+    float *cS = reinterpret_cast<float *>(cI + p.Rcap);
+    int *vI = reinterpret_cast<int *>(cS + p.Rcap);
+    float *vS = reinterpret_cast<float *>(vI + p.Rcap);
+    int *vPB = reinterpret_cast<int *>(vS + p.Rcap);
+    int *sPB = cI;  // reuses the raw candidate ids once they are compacted
+    const int hmask = p.Hcap - 1;
+    const int hshift = 32 - p.hbits;
+    PS ps;
+
+    for (;;) {
+        int qi32 = 0;
+        if (lane == 0) qi32 = atomicAdd(p.work, 1);
+        qi32 = __shfl_sync(FULL, qi32, 0);
+        const int64_t qi = qi32;
+        if (qi >= p.m) break;
+        int4 dq = p.desc ? p.desc[qi] : p.uni;
+        int k = dq.x, L = dq.y, r = dq.z;
+        const int mh = dq.w;
+        if (L > p.Lcap || L < 1 || k > p.ldo || k < 0) {
+            if (lane == 0) atomicOr(p.status, ST_CAPACITY);
+            L = min(max(L, 1), p.Lcap);
+            k = min(max(k, 0), p.ldo);
+        }
+        r = min(max(r, 0), L);
+        ps.setup(p, qi, lane);
+
+        for (int t = lane * 4; t < p.Hcap; t += 128)
+            *reinterpret_cast<int4 *>(hash + t) = make_int4(-1, -1, -1, -1);
+        __syncwarp();
+        const int entry = p.entry;
+        if (lane == 0) {
+            cI[0] = entry;
+            hash[((unsigned)entry * 0x9E3779B1u) >> hshift] = entry;
+        }
+        __syncwarp();
+        ps.score(cI, cS, 1, lane);
+        __syncwarp();
+        if (lane == 0) {
+            bS0[0] = cS[0];
+            bI0[0] = entry;
+        }
+        __syncwarp();
+        // current and spare beam buffers (swapped after every merge)
+        float *curS = bS0, *nxtS = bS1;
+        int *curI = bI0, *nxtI = bI1;
+        int size = 1, hops = 0, scored = 1;
+        const int maxh = mh > 0 ? mh : (int)(p.n < 0x7fffffff ? p.n : 0x7fffffff);
+
+        while (hops < maxh) {
+            // best unexpanded member of the beam
+            int pos = -1;
+            for (int base = 0; base < size; base += 32) {
+                const int i = base + lane;
+                const bool un = i < size && !(curI[i] & (int)EXPANDED);
+                const unsigned bal = __ballot_sync(FULL, un);
+                if (bal) {
+                    pos = base + __ffs(bal) - 1;
+                    break;
+                }
+            }
+            if (pos < 0) break;
+            const int pnode = curI[pos];
+            __syncwarp();
+            if (lane == 0) curI[pos] = pnode | (int)EXPANDED;
+            ++hops;
+
+            // neighbour ids: load all first, then test the visited cache
+            const int32_t *row = p.graph + (int64_t)pnode * p.R;
+            int nb[RMAX / 32];
+#pragma unroll
+            for (int t = 0; t < RMAX / 32; ++t) {
+                const int j = lane + 32 * t;
+                nb[t] = (32 * t < p.R && j < p.R) ? __ldg(row + j) : -1;
+            }
+            int cnt = 0;
+#pragma unroll
+            for (int t = 0; t < RMAX / 32; ++t) {
+                if (32 * t >= p.R) break;
+                int u = nb[t];
+                bool isnew = false;
+                if (u >= 0) {
+                    if (u >= p.n) {
+                        atomicOr(p.status, ST_CORRUPT);
+                    } else {
+                        const unsigned h = ((unsigned)u * 0x9E3779B1u) >> hshift;
+                        int slot = -1;
+                        bool found = false;
+#pragma unroll
+                        for (int pr = 0; pr < 4; ++pr) {
+                            const int s = (int)((h + pr) & hmask);
+                            const int v = hash[s];
+                            if (v == u) {
+                                found = true;
+                                break;
+                            }
+                            if (v < 0) {
+                                slot = s;
+                                break;
+                            }
+                        }
+                        if (!found) {
+                            isnew = true;
+                            hash[slot >= 0 ? slot : (int)h] = u;
+                        }
+                    }
+                }
+                const unsigned bal = __ballot_sync(FULL, isnew);
+                if (isnew) cI[cnt + __popc(bal & lt)] = u;
+                cnt += __popc(bal);
+            }
+            __syncwarp();
+            if (cnt == 0) continue;
+            ps.score(cI, cS, cnt, lane);
+            scored += cnt;
+            __syncwarp();
+
+            // keep candidates that can enter the beam and are not already in it
+            const bool full = size >= L;
+            float wS = 0.f;
+            int wI = 0;
+            if (full) {
+                wS = curS[L - 1];
+                wI = curI[L - 1] & ~(int)EXPANDED;
+            }
+            int cv = 0;
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int j = j0 + lane;
+                bool valid = false;
+                float s = 0.f;
+                int id = 0, pb = 0;
+                if (j < cnt) {
+                    s = cS[j];
+                    id = cI[j];
+                    valid = !full || key_better(s, id, wS, wI);
+                    if (valid) {
+                        int lo = 0, hi = size;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (key_better(curS[mid], curI[mid] & ~(int)EXPANDED, s, id))
+                                lo = mid + 1;
+                            else
+                                hi = mid;
+                        }
+                        pb = lo;
+                        if (pb < size && (curI[pb] & ~(int)EXPANDED) == id) valid = false;
+                    }
+                }
+                const unsigned bal = __ballot_sync(FULL, valid);
+                if (valid) {
+                    const int o = cv + __popc(bal & lt);
+                    vI[o] = id;
+                    vS[o] = s;
+                    vPB[o] = pb;
+                }
+                cv += __popc(bal);
+            }
+            __syncwarp();
+            if (cv == 0) continue;
+            // candidates: position = rank among candidates + beam members ahead of it
+            for (int j = lane; j < cv; j += 32) {
+                const float s = vS[j];
+                const int id = vI[j];
+                int rank = 0;
+                for (int t = 0; t < cv; ++t) rank += key_better(vS[t], vI[t], s, id) ? 1 : 0;
+                const int np = rank + vPB[j];
+                sPB[rank] = vPB[j];
+                if (np < L) {
+                    nxtS[np] = s;
+                    nxtI[np] = id;
+                }
+            }
+            __syncwarp();
+            // beam members: position = own index + candidates ahead of it
+            for (int i = lane; i < size; i += 32) {
+                int lo = 0, hi = cv;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sPB[mid] <= i)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                const int np = i + lo;
+                if (np < L) {
+                    nxtS[np] = curS[i];
+                    nxtI[np] = curI[i];
+                }
+            }
+            size = min(L, size + cv);
+            {
+                float *ts = curS;
+                curS = nxtS;
+                nxtS = ts;
+                int *ti = curI;
+                curI = nxtI;
+                nxtI = ti;
+            }
+            __syncwarp();
+        }
+
+        if (p.stats && lane == 0) p.stats[qi] = make_int2(hops, scored);
+        int32_t *oid = p.ids + qi * p.ldo;
+        float *osc = p.scores + qi * p.ldo;
+        if (BUILD) {
+            for (int t = lane; t < L; t += 32) {
+                oid[t] = t < size ? (curI[t] & ~(int)EXPANDED) : -1;
+                osc[t] = t < size ? curS[t] : -INFINITY;
+            }
+        } else {
+            int nres;
+            if (RERANK && r > 0) {
+                const int nr = min(r, size);
+                float *rS = reinterpret_cast<float *>(hash);
+                int *rI = hash + p.Lcap;
+                for (int t = lane; t < nr; t += 32) rI[t] = curI[t] & ~(int)EXPANDED;
+                __syncwarp();
+                WarpScorer<2, 1> sc;
+                const float4 kq = p.qconst[qi];
+                sc.setup_row(p.Q + qi * p.D, p.D, p.sec_chunks, p.sec, p.sec_stride, kq.z, kq.w, lane);
+                sc.score(rI, rS, nr, lane);
+                __syncwarp();
+                for (int t = lane; t < nr; t += 32) {
+                    const float s = rS[t];
+                    const int id = rI[t];
+                    int rank = 0;
+                    for (int u = 0; u < nr; ++u) rank += key_better(rS[u], rI[u], s, id) ? 1 : 0;
+                    if (rank < k) {
+                        oid[rank] = id;
+                        osc[rank] = s;
+                    }
+                }
+                nres = min(k, nr);
+            } else {
+                nres = min(k, size);
+                for (int t = lane; t < nres; t += 32) {
+                    oid[t] = curI[t] & ~(int)EXPANDED;
+                    osc[t] = curS[t];
+                }
+            }
+            for (int t = nres + lane; t < p.ldo; t += 32) {
+                oid[t] = -1;
+                osc[t] = -INFINITY;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// launchers (one per translation unit); grid = persistent (SMs x resident blocks)
+int launch_search_lvq8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
+int launch_search_lvq4(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
+int launch_search_fp32(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st);
+int launch_build_search(const BeamParams &p, int bits, int nc, int block, size_t smem, int num_sms,
+                        cudaStream_t st);
+
+}  // namespace lv

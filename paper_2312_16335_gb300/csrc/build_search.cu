@@ -1,0 +1,40 @@
+// Beam search in build mode: the queries are database nodes and the scores are the
+// exact build score, so that graph construction is reproducible bit for bit.
+#include "beam.cuh"
+
+namespace lv {
+
+template <int NC, int BITS>
+static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
+    auto k = beam_kernel<BuildScorer<NC, BITS>, true, false>;
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
+    if (per_sm < 1) return fail(LV_ERR_CAPACITY, "build: beam/visited capacity does not fit in shared memory");
+    int64_t want = (p.m + block / 32 - 1) / (block / 32);
+    int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
+    k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);
+    LV_CHECK_LAUNCH("beam_kernel<build>");
+    return LV_OK;
+}
+
+int launch_build_search(const BeamParams &p, int bits, int nc, int block, size_t smem, int num_sms,
+                        cudaStream_t st) {
+    if (bits == 8) {
+        switch (nc) {
+            case 1: return go<1, 8>(p, block, smem, num_sms, st);
+            case 2: return go<2, 8>(p, block, smem, num_sms, st);
+            case 3: return go<3, 8>(p, block, smem, num_sms, st);
+            case 4: return go<4, 8>(p, block, smem, num_sms, st);
+        }
+    } else if (bits == 4) {
+        switch (nc) {
+            case 1: return go<1, 4>(p, block, smem, num_sms, st);
+            case 2: return go<2, 4>(p, block, smem, num_sms, st);
+            case 3: return go<3, 4>(p, block, smem, num_sms, st);
+        }
+    }
+    return fail(LV_ERR_ARG, "build: unsupported primary record size");
+}
+
+}  // namespace lv

@@ -1,0 +1,35 @@
+// Internal definition of the opaque lv_index (shared by the host-side sources).
+#pragma once
+
+#include "common.cuh"
+
+struct lv_index {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0;
+    int D = 0, d = 0;
+    int pbits = 0, sbits = 0;
+    lv::RecGeom pg, sg;
+    uint8_t *prim = nullptr;
+    float *pmean = nullptr;
+    uint8_t *sec = nullptr;
+    float *smean = nullptr;
+    float mu2 = 0.f;
+    int R = 0;
+    int32_t *graph = nullptr;
+    int32_t entry = -1;
+    int *status = nullptr;  // device: [0] status bits, [1] work counter
+    // search workspace
+    float *ws_q = nullptr;
+    size_t ws_q_bytes = 0;
+    float4 *ws_c = nullptr;
+    size_t ws_c_bytes = 0;
+    // build workspace
+    void *bws = nullptr;
+    size_t bws_bytes = 0;
+};
+
+namespace lv {
+void index_free_stores(lv_index *idx);
+int ensure_ws(void **p, size_t *have, size_t want);
+}  // namespace lv

@@ -1,0 +1,30 @@
+// Full-dimensional float32 graph search (the baseline the paper compares against):
+// the same beam kernel with whole-warp float32 record scoring and no rerank.
+#include "beam.cuh"
+
+namespace lv {
+
+template <int NCW>
+static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
+    auto k = beam_kernel<WarpScorer<NCW, 0>, false, false>;
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
+    if (per_sm < 1) return fail(LV_ERR_CAPACITY, "search: beam/visited capacity does not fit in shared memory");
+    int64_t want = (p.m + block / 32 - 1) / (block / 32);
+    int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
+    k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);
+    LV_CHECK_LAUNCH("beam_kernel<fp32>");
+    return LV_OK;
+}
+
+int launch_search_fp32(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st) {
+    if (ncw <= 1) return go<1>(p, block, smem, num_sms, st);
+    if (ncw <= 2) return go<2>(p, block, smem, num_sms, st);
+    if (ncw <= 4) return go<4>(p, block, smem, num_sms, st);
+    if (ncw <= 6) return go<6>(p, block, smem, num_sms, st);
+    if (ncw <= 8) return go<8>(p, block, smem, num_sms, st);
+    return fail(LV_ERR_ARG, "search: float32 records longer than 1024 floats are not supported");
+}
+
+}  // namespace lv

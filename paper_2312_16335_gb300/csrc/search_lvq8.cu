@@ -1,0 +1,30 @@
+// Search + rerank instantiations for LVQ-8 primaries (chunks per lane 1..4).
+#include "beam.cuh"
+
+namespace lv {
+
+template <int NC>
+static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
+    auto k = beam_kernel<LvqGroupScorer<NC, 8>, false, true>;
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
+    if (per_sm < 1) return fail(LV_ERR_CAPACITY, "search: beam/visited capacity does not fit in shared memory");
+    int64_t want = (p.m + block / 32 - 1) / (block / 32);
+    int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
+    k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);
+    LV_CHECK_LAUNCH("beam_kernel<lvq8>");
+    return LV_OK;
+}
+
+int launch_search_lvq8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st) {
+    switch (nc) {
+        case 1: return go<1>(p, block, smem, num_sms, st);
+        case 2: return go<2>(p, block, smem, num_sms, st);
+        case 3: return go<3>(p, block, smem, num_sms, st);
+        case 4: return go<4>(p, block, smem, num_sms, st);
+        default: return fail(LV_ERR_ARG, "search: primary dimension too large for LVQ-8 (d <= 240)");
+    }
+}
+
+}  // namespace lv

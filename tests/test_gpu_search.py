@@ -1,0 +1,173 @@
+"""GPU beam search + rerank against the oracle on the same seeded inputs and graph.
+
+Tolerances: scores within 1e-4 * ||q'|| * ||x_hat|| (FP32 path); ids >= 99 %
+identical position by position; recall@10 against brute force within 0.002."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import gpu_index, small_problem, t
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lv():
+    import paper_2312_16335_gb300 as lv
+    return lv
+
+
+@pytest.fixture(scope="module")
+def pb():
+    return small_problem(oracle, n=3000, D=64, d=16, m=300)
+
+
+def _qp(pb, Q=None):
+    Q = pb["Q"] if Q is None else Q
+    return Q.astype(np.float64) @ pb["P"].T.astype(np.float64)
+
+
+def _check_scores(ids, scores, ref_dec, qv, tol=1e-4):
+    """scores of returned ids agree with the FP64 decoded inner products."""
+    for j in range(ids.shape[0]):
+        sel = ids[j] >= 0
+        u = ids[j][sel]
+        exact = ref_dec[u] @ qv[j]
+        bound = tol * np.linalg.norm(qv[j]) * np.linalg.norm(ref_dec[u], axis=1)
+        assert np.all(np.abs(scores[j][sel] - exact) <= bound), (j, np.abs(scores[j][sel] - exact).max())
+
+
+def test_primary_scores_full_window(lv, pb):
+    """L >= n: the beam holds every reachable node; the GPU primary scores of the
+    returned ids match FP64 decode-then-dot."""
+    n = 400
+    sub = small_problem(oracle, n=n, D=48, d=12, m=20, seed=3)
+    idx = gpu_index(lv, sub)
+    qp = _qp(sub)
+    ids, sc = idx.search(t(sub["Q"]), t(sub["P"]), k=n, L=n, rerank=0)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    _check_scores(ids, sc, sub["prim"].decode(), qp)
+    ref = oracle.search(sub["graph"], sub["entry"], qp, k=n, L=n, prim=sub["prim"])
+    for j in range(20):
+        assert set(ids[j][ids[j] >= 0].tolist()) == set(ref["ids"][j][ref["ids"][j] >= 0].tolist())
+
+
+def test_rerank_scores_full_window(lv):
+    n = 300
+    sub = small_problem(oracle, n=n, D=200, d=24, m=16, seed=4)  # D = 200: ragged secondary chunk
+    idx = gpu_index(lv, sub)
+    ids, sc = idx.search(t(sub["Q"]), t(sub["P"]), k=50, L=n, rerank=n)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    _check_scores(ids, sc, sub["sec"].decode(), sub["Q"].astype(np.float64))
+    ref = oracle.search(sub["graph"], sub["entry"], _qp(sub), k=50, L=n, rerank=n, prim=sub["prim"], sec=sub["sec"],
+                        qs=sub["Q"].astype(np.float64))
+    assert (ids == ref["ids"]).mean() >= 0.99
+
+
+@pytest.mark.parametrize("L,r", [(16, 16), (40, 40), (100, 60)])
+def test_ids_match_oracle(lv, pb, L, r):
+    idx = gpu_index(lv, pb)
+    ids, sc, st = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=L, rerank=r, stats=True)
+    idx.sync_status()
+    ids = ids.cpu().numpy()
+    ref = oracle.search(pb["graph"], pb["entry"], _qp(pb), k=10, L=L, rerank=r, prim=pb["prim"], sec=pb["sec"],
+                        qs=pb["Q"].astype(np.float64))
+    same = (ids == ref["ids"]).mean()
+    assert same >= 0.99, same
+    truth, _ = oracle.bruteforce(pb["X"], pb["Q"], 10)
+    assert abs(oracle.recall(ids, truth, 10) - oracle.recall(ref["ids"], truth, 10)) <= 0.002
+    _check_scores(ids, sc.cpu().numpy(), pb["sec"].decode(), pb["Q"].astype(np.float64))
+    st = st.cpu().numpy()
+    # expansions equal the oracle's (exact beam), scored counts are >= (forgotten ids are rescored)
+    assert np.abs(st[:, 0] - ref["hops"]).mean() <= 0.5
+    assert np.all(st[:, 1] >= 1)
+
+
+def test_small_hash_still_exact(lv, pb):
+    """A tiny visited cache forgets often; the beam (hence the result) is unchanged."""
+    idx = gpu_index(lv, pb)
+    a, _ = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=64, rerank=32, hash_slots=128)
+    b, _ = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=64, rerank=32, hash_slots=8192)
+    assert torch.equal(a, b)
+
+
+def test_uneven_batch_descriptors(lv, pb):
+    idx = gpu_index(lv, pb)
+    m = pb["Q"].shape[0]
+    rng = np.random.default_rng(5)
+    k = rng.choice([1, 5, 10], m)
+    L = np.maximum(rng.integers(10, 80, m), k)
+    r = np.minimum(L, rng.integers(0, 60, m))
+    desc = np.stack([k, L, r, np.zeros(m, int)], 1).astype(np.int32)
+    ids, sc = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=80, rerank=80, desc=t(desc), ldo=10)
+    idx.sync_status()
+    ref = oracle.search(pb["graph"], pb["entry"], _qp(pb), k=10, L=80, rerank=80, prim=pb["prim"], sec=pb["sec"],
+                        qs=pb["Q"].astype(np.float64), desc=desc)
+    ids = ids.cpu().numpy()
+    valid = np.arange(10)[None, :] < k[:, None]
+    assert (ids[valid] == ref["ids"][valid]).mean() >= 0.99
+    assert np.all(ids[~valid] == -1)
+
+
+def test_unreachable_padding_and_max_hops(lv):
+    sub = small_problem(oracle, n=200, D=32, d=8, m=8, seed=6)
+    g = np.full_like(sub["graph"], -1)
+    g[0, :2] = [1, 2]
+    sub2 = dict(sub, graph=g, entry=0)
+    idx = gpu_index(lv, sub2)
+    ids, sc = idx.search(t(sub["Q"]), t(sub["P"]), k=5, L=10, rerank=10)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    assert (ids[:, 3:] == -1).all() and np.isinf(sc[:, 3:]).all() and (sc[:, 3:] < 0).all()
+    assert set(ids[0, :3].tolist()) == {0, 1, 2}
+    idx2 = gpu_index(lv, sub)
+    _, _, st = idx2.search(t(sub["Q"]), t(sub["P"]), k=5, L=30, rerank=0, max_hops=3, stats=True)
+    assert (st[:, 0].cpu().numpy() <= 3).all()
+
+
+def test_repeated_and_out_of_range_ids_in_user_graph(lv):
+    sub = small_problem(oracle, n=300, D=32, d=8, m=10, seed=7)
+    g = sub["graph"].copy()
+    g[:, -1] = g[:, 0]  # repeated id in every row
+    idx = gpu_index(lv, dict(sub, graph=g))
+    ids, _ = idx.search(t(sub["Q"]), t(sub["P"]), k=5, L=20, rerank=20)
+    ref = oracle.search(g, sub["entry"], _qp(sub), k=5, L=20, rerank=20, prim=sub["prim"], sec=sub["sec"],
+                        qs=sub["Q"].astype(np.float64))
+    assert (ids.cpu().numpy() == ref["ids"]).mean() >= 0.99
+    g2 = sub["graph"].copy()
+    g2[3, 0] = 10 ** 6
+    with pytest.raises(lv.LeanVecError):
+        gpu_index(lv, dict(sub, graph=g2)).sync_status()
+
+
+def test_float32_baseline_matches_oracle(lv, pb):
+    idx = lv.Index(0)
+    idx.encode_fp32(t(pb["X"])).set_graph(t(pb["graph"]), pb["entry"])
+    ids, sc = idx.search(t(pb["Q"]), None, k=10, L=40)
+    ids = ids.cpu().numpy()
+    ref = oracle.search(pb["graph"], pb["entry"], pb["Q"].astype(np.float64), k=10, L=40, prim_vecs=pb["X"])
+    assert (ids == ref["ids"]).mean() >= 0.99
+    Xd = pb["X"].astype(np.float64)
+    _check_scores(ids, sc.cpu().numpy(), Xd, pb["Q"].astype(np.float64))
+
+
+def test_lvq4_primary(lv):
+    sub = small_problem(oracle, n=2000, D=64, d=32, m=100, seed=8, bits=4)
+    idx = gpu_index(lv, sub)
+    ids, sc = idx.search(t(sub["Q"]), t(sub["P"]), k=10, L=40, rerank=40)
+    ref = oracle.search(sub["graph"], sub["entry"], _qp(sub), k=10, L=40, rerank=40, prim=sub["prim"], sec=sub["sec"],
+                        qs=sub["Q"].astype(np.float64))
+    assert (ids.cpu().numpy() == ref["ids"]).mean() >= 0.99
+
+
+def test_argument_errors(lv, pb):
+    idx = gpu_index(lv, pb)
+    with pytest.raises(lv.LeanVecError):
+        idx.search(t(pb["Q"]), t(pb["P"]), k=20, L=10)  # k > L
+    with pytest.raises(lv.LeanVecError):
+        idx.search(t(pb["Q"]), t(pb["P"]), k=5, L=1000)  # L > 512
+    empty = lv.Index(0)
+    with pytest.raises(lv.LeanVecError):
+        empty.search(t(pb["Q"]), t(pb["P"]), k=5, L=10)
+    ids, sc = idx.search(t(pb["Q"][:0]), t(pb["P"]), k=5, L=10)
+    assert ids.shape == (0, 5)
