@@ -1,0 +1,407 @@
+"""Benchmark: LeanVec search QPS at 10-recall@10 = 0.90 on one GB300 (per rank).
+
+Workload (default): 1M x 768 anisotropic Gaussian mixture (1000 components, i^-1
+spectrum, unit-normalised, inner product), 10k in-distribution queries; LeanVec-ID
+d = 160 (second moments + FP64 eigh on a 100k subsample), LVQ-8 primary + LVQ-8
+secondary, GPU-built graph R = 64, L_build = 128.  A step is one pass of the
+search path (projection A q -> beam search over primaries -> rerank with
+secondaries -> top-10) over the 10k queries, inputs resident in HBM; the beam width
+L (rerank = L) is the smallest of a sweep whose recall@10 reaches 0.90.
+
+Reported next to it: the same metric end to end through the C ABI with host
+buffers (e2e), the plain full-dimensional float32 graph search on the same graph
+(baseline_fp32, its own L for 0.90), the beam kernel's HBM roofline fraction, and
+the CPU oracle timed on a bounded query sample on this host (cpu_baseline).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+N > 1 runs N independent replicas (one per GPU, weak scaling, no collective on the
+data path; a barrier and a max-reduction of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+L_GRID = [10, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 200, 256]
+TARGET = 0.90
+
+
+def log(*a):
+    if int(os.environ.get("RANK", "0")) == 0:
+        print("[bench]", *a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def ground_truth(X: torch.Tensor, Q: torch.Tensor, k: int = 10, chunk: int = 131072) -> torch.Tensor:
+    """Exact top-k inner products (float32 on the GPU, TF32 off; ties -> smaller id)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    best_s = torch.full((Q.shape[0], k), -float("inf"), device=Q.device)
+    best_i = torch.full((Q.shape[0], k), -1, dtype=torch.int64, device=Q.device)
+    for s in range(0, X.shape[0], chunk):
+        S = Q @ X[s:s + chunk].T
+        v, i = torch.topk(S, k, dim=1)
+        cs = torch.cat([best_s, v], 1)
+        ci = torch.cat([best_i, i + s], 1)
+        o = torch.topk(cs, k, dim=1)
+        best_s, best_i = o.values, torch.gather(ci, 1, o.indices)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return best_i
+
+
+def recall_at(ids: torch.Tensor, truth: torch.Tensor, k: int = 10) -> float:
+    a = ids[:, :k].long()
+    hit = (a.unsqueeze(2) == truth[:, :k].unsqueeze(1)).any(dim=2) & (a >= 0)
+    return float(hit.float().sum().item()) / (k * ids.shape[0])
+
+
+def calibrate(search_fn, truth, k):
+    """Smallest L of the grid with recall@k >= 0.90; the (L, recall) trace."""
+    trace = []
+    chosen = None
+    for L in L_GRID:
+        ids = search_fn(L)
+        r = recall_at(ids, truth, k)
+        trace.append((L, r))
+        if r >= TARGET:
+            chosen = L
+            break
+    return chosen, trace
+
+
+def time_steps(fn, steps, warmup, events=None):
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn(None)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kern = []
+    e0.record(st)
+    for _ in range(steps):
+        if events is not None:
+            pair = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            pair[0].record(st)
+            pair[1].record(st)  # materialise the handles before the library records them
+            kern.append(pair)
+            fn(pair)
+        else:
+            fn(None)
+    e1.record(st)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    kern_ms = [a.elapsed_time(b) for a, b in kern]
+    return total_ms, kern_ms
+
+
+def setup(args, dev):
+    import paper_2312_16335_gb300 as lv
+    t0 = time.time()
+    torch.manual_seed(0)
+    X, Q, _ = workloads.make_workload_torch("anisotropic", args.n, args.m, args.D, args.components, cfg=2, device=dev)
+    torch.cuda.synchronize()
+    log(f"data {tuple(X.shape)} queries {tuple(Q.shape)} in {time.time() - t0:.1f}s")
+    t0 = time.time()
+    sub = torch.from_numpy(workloads.subsample_rows(args.n, min(args.n, 100_000), cfg=2)).to(dev)
+    A = lv.leanvec_fit_id(X.index_select(0, sub).contiguous(), args.d)
+    torch.cuda.synchronize()
+    t_fit = time.time() - t0
+    t0 = time.time()
+    idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8)
+    torch.cuda.synchronize()
+    t_enc = time.time() - t0
+    t0 = time.time()
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+                    seed=workloads.SEED_GRAPH + 2)
+    idx.sync_status()
+    t_build = time.time() - t0
+    log(f"fit {t_fit:.2f}s encode {t_enc:.2f}s build {t_build:.2f}s")
+    graph, entry = idx.get_graph()
+    base = lv.Index(dev.index).encode_fp32(X).set_graph(graph, entry)
+    t0 = time.time()
+    truth = ground_truth(X, Q, 10)
+    log(f"ground truth {time.time() - t0:.1f}s")
+    return dict(lv=lv, X=X, Q=Q, A=A, idx=idx, base=base, graph=graph, entry=entry, truth=truth,
+                t_fit=t_fit, t_enc=t_enc, t_build=t_build)
+
+
+def oracle_prepare(S):
+    """Host copies and the oracle's own LVQ stores of the same vectors and projection."""
+    import oracle
+    X = S["X"].cpu().numpy()
+    A = S["A"].cpu().numpy().astype(np.float64)
+    Y = (X.astype(np.float64) @ A.T).astype(np.float32)
+    prim = oracle.lvq_encode(Y, oracle.mean_fp32(Y), 8)
+    sec = oracle.lvq_encode(X, oracle.mean_fp32(X), 8)
+    Qh = S["Q"].cpu().numpy().astype(np.float64)
+    return dict(prim=prim, sec=sec, g=S["graph"].cpu().numpy(), entry=S["entry"], Qh=Qh, qp=Qh @ A.T,
+                truth=S["truth"].cpu().numpy())
+
+
+def cpu_oracle_sample(O, L, budget_s, nthreads=0):
+    """Time the CPU oracle (C, OpenMP over queries) on a bounded query sample."""
+    import oracle
+    cores = nthreads or os.cpu_count()
+    Qh = O["Qh"]
+    m = 64
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.search(O["g"], O["entry"], O["qp"][:m], k=10, L=L, rerank=L, prim=O["prim"], sec=O["sec"],
+                          qs=Qh[:m], nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or m >= Qh.shape[0]:
+            break
+        m = min(Qh.shape[0], int(m * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    rec = oracle.recall(r["ids"], O["truth"][:m], 10)
+    return {"value": m / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {m} of {Qh.shape[0]} queries, same graph/projection, L = rerank = {L}, k = 10",
+            "recall_at_10": rec, "seconds": dt, "scored_per_query": float(r["scored"].mean()),
+            "hops_per_query": float(r["hops"].mean())}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--m", type=int, default=10_000)
+    ap.add_argument("--D", type=int, default=768)
+    ap.add_argument("--d", type=int, default=160)
+    ap.add_argument("--components", type=int, default=1000)
+    ap.add_argument("--R", type=int, default=64)
+    ap.add_argument("--L_build", type=int, default=128)
+    ap.add_argument("--alpha", type=float, default=1.0)
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
+                f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
+                f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "
+                f"alpha={args.alpha}; k=10, rerank=L")
+    metric = "QPS at 10-recall@10=0.90, LeanVec vs full-D FP32 graph search; HBM GB/s"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        S = setup(args, dev)
+        L = args.L
+        if not L:
+            L, _ = calibrate(lambda L: S["idx"].search(S["Q"], S["A"], k=10, L=L, rerank=L)[0], S["truth"], 10)
+            L = L or L_GRID[-1]
+        vals = []
+        cb = None
+        O = oracle_prepare(S)
+        for i in range(args.warmup + args.steps):
+            r = cpu_oracle_sample(O, L, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
+            if i >= args.warmup:
+                vals.append(r["value"])
+                cb = r
+        v = statistics.median(vals)
+        cb["value"] = v
+        out = {"impl": "reference", "metric": metric, "value": v, "unit": "queries/s", "n_gpus": 1,
+               "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": workload, "L": L, "impl_note": "CPU oracle on the host cores"},
+               "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                                             "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
+
+    S = setup(args, dev)
+    lv, idx, base, Q, A, truth = S["lv"], S["idx"], S["base"], S["Q"], S["A"], S["truth"]
+    m = Q.shape[0]
+    k = 10
+    ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
+    sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
+
+    # -- choose L for recall 0.90 (untimed)
+    if args.L:
+        L, trace = args.L, []
+        rec = recall_at(idx.search(Q, A, k=k, L=L, rerank=L)[0], truth, k)
+        trace = [(L, rec)]
+    else:
+        L, trace = calibrate(lambda L: idx.search(Q, A, k=k, L=L, rerank=L)[0], truth, k)
+        if L is None:
+            L = L_GRID[-1]
+    rec = dict(trace)[L]
+    Lb, trace_b = calibrate(lambda L: base.search(Q, None, k=k, L=L)[0], truth, k)
+    if Lb is None:
+        Lb = L_GRID[-1]
+    rec_b = dict(trace_b)[Lb]
+    log(f"LeanVec L={L} recall={rec:.4f}  trace={trace}")
+    log(f"FP32   L={Lb} recall={rec_b:.4f}  trace={trace_b}")
+
+    # -- per-query work (untimed run with counters)
+    _, _, st = idx.search(Q, A, k=k, L=L, rerank=L, stats=True)
+    hops = float(st[:, 0].double().mean())
+    scored = float(st[:, 1].double().mean())
+    inf = idx.info()
+    bytes_q = (inf["d"] + 4) * 4 + hops * inf["R"] * 4 + scored * inf["primary_stride"] + \
+        L * inf["secondary_stride"] + args.D * 4 + k * 8
+
+    def step(ev):
+        idx.search(Q, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), events=ev)
+
+    if world > 1:
+        torch.distributed.barrier()
+    with Clocks(local) as clk:
+        total_ms, kern_ms = time_steps(step, args.steps, args.warmup, events=True)
+    ck = clk.summary()
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    qps = m * args.steps * world / (total_ms / 1e3)
+    kern_avg = statistics.mean(kern_ms)
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_q * m / (kern_avg / 1e3) / 1e9
+
+    # -- end to end through the C ABI with host buffers
+    Qh = Q.cpu().pin_memory()
+    ids_h = torch.empty((m, k), dtype=torch.int32).pin_memory()
+    sc_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    Qd = torch.empty_like(Q)
+
+    def step_e2e(ev):
+        Qd.copy_(Qh, non_blocking=True)
+        idx.search(Qd, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf))
+        ids_h.copy_(ids_buf, non_blocking=True)
+        sc_h.copy_(sc_buf, non_blocking=True)
+
+    e2e_ms, _ = time_steps(step_e2e, max(5, args.steps // 2), 2)
+    e2e_qps = m * max(5, args.steps // 2) / (e2e_ms / 1e3)
+
+    # -- full-dimensional float32 baseline on the same graph
+    ids_b = torch.empty((m, k), dtype=torch.int32, device=dev)
+    sc_b = torch.empty((m, k), dtype=torch.float32, device=dev)
+    base_ms, _ = time_steps(lambda ev: base.search(Q, None, k=k, L=Lb, out=(ids_b, sc_b)),
+                            max(5, args.steps // 2), 2)
+    qps_b = m * max(5, args.steps // 2) / (base_ms / 1e3)
+    _, _, stb = base.search(Q, None, k=k, L=Lb, stats=True)
+    bytes_b = args.D * 4 + float(stb[:, 0].double().mean()) * inf["R"] * 4 + \
+        float(stb[:, 1].double().mean()) * lv.leanvec_record_stride(args.D, 32) + k * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample(oracle_prepare(S), L, args.cpu_budget)
+        except Exception as e:  # the GPU result stands without the CPU leg
+            cpu = {"error": repr(e)}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": metric, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u8 LVQ codes decoded to f32)",
+        "data": "synthetic",
+        "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
+                   "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
+                   "L_build": args.L_build, "alpha": args.alpha, "projection": "fp32",
+                   "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
+                         ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
+                   "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
+        "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
+                "d2h_bytes_per_step": m * k * 8},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "beam_kernel<LvqGroupScorer<3,8>,search,rerank>",
+                     "kernel_ms": kern_avg, "bytes_per_query": bytes_q, "hops_per_query": hops,
+                     "scored_per_query": scored, "peak_kind": peak_kind},
+        "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "recall_at_10": rec_b,
+                          "recall_trace": trace_b, "bytes_per_query": bytes_b,
+                          "speedup_leanvec": qps / world / qps_b},
+        "cpu_baseline": cpu,
+        "clocks": ck,
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -108,6 +108,30 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
                     int precision, lv_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Learning the projections (Sec. 2.1 - 2.4)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Second moment K = sum_i x_i x_i^T (D x D float32, device) of the n rows of X
+ * (n x D, device): the uncentred K_X = X X^T / K_Q = Q Q^T of Sec. 2.2 "Efficiency"
+ * (the caller passes a uniform subsample when n is large).  precision:
+ * LV_PREC_FP32 (CUDA cores) or LV_PREC_BF16 (bf16 operands, tcgen05 tensor cores,
+ * float32 accumulation). */
+int leanvec_second_moment(const float *X, int64_t n, int D, float *K, int precision, lv_stream_t stream);
+
+/* Eigen-decomposition of a symmetric D x D FP64 matrix K (device) by cyclic
+ * Jacobi rotations in FP64: evals (D, device, may be NULL) in descending order,
+ * evecs (D x D, device) with row r the eigenvector of evals[r], its
+ * largest-magnitude entry positive (first index on ties).  Synchronises `stream`. */
+int leanvec_eigh(const double *K, int D, double *evals, double *evecs, lv_stream_t stream);
+
+/* LeanVec-ID (Sec. 2.1, problem "pca"): A = B = M, the d leading eigenvectors of
+ * K_X = sum x x^T over the n rows of X (the left singular vectors of the paper's
+ * X), computed as second moment (`precision`) + FP64 eigh.  A_out, B_out: d x D
+ * float32 (device; B_out may be NULL or equal A_out).  Synchronises `stream`. */
+int leanvec_fit_id(const float *X, int64_t n, int D, int d, float *A_out, float *B_out, int precision,
+                   lv_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Index                                                                     */
 /* ------------------------------------------------------------------------ */
 typedef struct lv_index lv_index;
@@ -210,6 +234,8 @@ typedef struct {
     int32_t hash_slots;      /* visited-cache slots per query (power of two, 0 = default 2048) */
     int32_t warps_per_block; /* 0 = default */
     int32_t reserved;
+    void *event_begin;       /* optional cudaEvent_t recorded on `stream` right before the */
+    void *event_end;         /* beam-search kernel and right after it (profiling); may be NULL */
 } lv_search_params;
 
 /* Per-query counters (device, m entries) when stats != NULL. */

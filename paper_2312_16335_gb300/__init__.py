@@ -16,7 +16,8 @@ import torch
 from ._native import (LVIndexInfo, LVQueryDesc, LVSearchParams, LeanVecError, check, lib)
 
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
-           "leanvec_project", "PREC_FP32", "PREC_BF16", "PREC_FP8"]
+           "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "PREC_FP32", "PREC_BF16",
+           "PREC_FP8"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 
@@ -70,6 +71,32 @@ def leanvec_project(X: torch.Tensor, P: torch.Tensor, ldy: int | None = None, pr
     Y = torch.empty((n, ldy), dtype=torch.float32, device=X.device)
     check(lib().leanvec_project(_ptr(X), n, D, _ptr(P), d, _ptr(Y), ldy, precision, _stream(X.device)))
     return Y
+
+
+def leanvec_second_moment(X: torch.Tensor, precision: int = PREC_FP32) -> torch.Tensor:
+    X = _f32(X)
+    K = torch.empty((X.shape[1], X.shape[1]), dtype=torch.float32, device=X.device)
+    check(lib().leanvec_second_moment(_ptr(X), X.shape[0], X.shape[1], _ptr(K), precision, _stream(X.device)))
+    return K
+
+
+def leanvec_eigh(K: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    if K.dtype != torch.float64:
+        raise TypeError("expected float64")
+    K = K.contiguous()
+    D = K.shape[0]
+    w = torch.empty(D, dtype=torch.float64, device=K.device)
+    V = torch.empty((D, D), dtype=torch.float64, device=K.device)
+    check(lib().leanvec_eigh(_ptr(K), D, _ptr(w), _ptr(V), _stream(K.device)))
+    return w, V
+
+
+def leanvec_fit_id(X: torch.Tensor, d: int, precision: int = PREC_FP32) -> torch.Tensor:
+    """A = B (d x D) for LeanVec-ID."""
+    X = _f32(X)
+    A = torch.empty((d, X.shape[1]), dtype=torch.float32, device=X.device)
+    check(lib().leanvec_fit_id(_ptr(X), X.shape[0], X.shape[1], d, _ptr(A), None, precision, _stream(X.device)))
+    return A
 
 
 class Index:
@@ -179,9 +206,10 @@ class Index:
     def search(self, Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0, max_hops: int = 0,
                desc: torch.Tensor | None = None, ldo: int | None = None, stats: bool = False,
                projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0,
-               out: tuple[torch.Tensor, torch.Tensor] | None = None):
+               out: tuple[torch.Tensor, torch.Tensor] | None = None, events=None):
         """Search m queries. desc: optional (m, 4) int32 CUDA tensor of per-query
-        (k, L, rerank, max_hops); then k/L are the upper bounds used for capacity."""
+        (k, L, rerank, max_hops); then k/L are the upper bounds used for capacity.
+        events: optional pair of torch.cuda.Event recorded around the beam kernel."""
         Q = _f32(Q)
         m = Q.shape[0]
         ldo = k if ldo is None else ldo
@@ -191,7 +219,8 @@ class Index:
         else:
             ids, sc = out
         st = torch.empty((m, 2), dtype=torch.int32, device=self.device) if stats else None
-        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, 0)
+        ev0, ev1 = (None, None) if events is None else (events[0].cuda_event, events[1].cuda_event)
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, 0, ev0, ev1)
         if desc is not None:
             desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None

@@ -22,7 +22,7 @@ class LVQueryDesc(ctypes.Structure):
 
 class LVSearchParams(ctypes.Structure):
     _fields_ = [("uniform", LVQueryDesc), ("projection", c_i32), ("hash_slots", c_i32),
-                ("warps_per_block", c_i32), ("reserved", c_i32)]
+                ("warps_per_block", c_i32), ("reserved", c_i32), ("event_begin", c_vp), ("event_end", c_vp)]
 
 
 class LVIndexInfo(ctypes.Structure):
@@ -52,6 +52,9 @@ SIGNATURES = {
     "leanvec_search": (c_i32, [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(LVSearchParams), c_vp, c_vp, c_vp,
                                c_i32, c_vp, c_vp]),
     "leanvec_sync_status": (c_i32, [c_vp, c_vp]),
+    "leanvec_second_moment": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp]),
+    "leanvec_eigh": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "leanvec_fit_id": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp]),
 }
 
 

@@ -490,13 +490,18 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     LV_CUDA(cudaMemsetAsync(p.work, 0, sizeof(int), st));
     const size_t smem = (size_t)warps * p.warp_smem;
     const int block = warps * 32;
+    if (params->event_begin) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_begin, st));
     if (idx->pbits == 32) {
         int ncw = (idx->pg.code_chunks + 31) / 32;
-        return launch_search_fp32(p, ncw, block, smem, idx->num_sms, st);
+        rc = launch_search_fp32(p, ncw, block, smem, idx->num_sms, st);
+    } else {
+        int nc = (idx->pg.code_chunks + 1 + 3) / 4;
+        rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
+                             : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
     }
-    int nc = (idx->pg.code_chunks + 1 + 3) / 4;
-    if (idx->pbits == 8) return launch_search_lvq8(p, nc, block, smem, idx->num_sms, st);
-    return launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
+    if (rc) return rc;
+    if (params->event_end) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_end, st));
+    return LV_OK;
 }
 
 int leanvec_sync_status(lv_index *idx, lv_stream_t stream) {

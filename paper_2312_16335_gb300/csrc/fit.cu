@@ -1,0 +1,352 @@
+// Learning the projections: second moments K = sum x x^T (Sec. 2.2 "Efficiency"),
+// an FP64 symmetric eigensolver (cyclic Jacobi rotations, round-robin pair order so
+// that the D/2 rotations of a round are independent), and LeanVec-ID (Sec. 2.1:
+// A = B = the d leading eigenvectors of K_X).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lv {
+
+// ------------------------------------------------------------ Gram matrix (FP32)
+constexpr int GT = 64, GK = 32;
+
+// K[a][b] = sum_i X[i][a] X[i][b]; 256 threads, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) gram_fp32_kernel(const float *__restrict__ X, int64_t n, int D,
+                                                        float *__restrict__ K) {
+    __shared__ float As[GK][GT + 4];
+    __shared__ float Bs[GK][GT + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int a0 = blockIdx.y * GT, b0 = blockIdx.x * GT;
+    float acc[4][4] = {};
+    for (int64_t i0 = 0; i0 < n; i0 += GK) {
+        for (int t = threadIdx.x; t < GK * GT; t += 256) {
+            const int r = t / GT, c = t % GT;
+            const int64_t gi = i0 + r;
+            As[r][c] = (gi < n && a0 + c < D) ? X[gi * D + a0 + c] : 0.0f;
+            Bs[r][c] = (gi < n && b0 + c < D) ? X[gi * D + b0 + c] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = a0 + ty * 4 + u;
+        if (r >= D) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int c = b0 + tx * 4 + v;
+            if (c < D) K[(int64_t)r * D + c] = acc[u][v];
+        }
+    }
+}
+
+int launch_gram_fp32(const float *X, int64_t n, int D, float *K, cudaStream_t st) {
+    dim3 grd((D + GT - 1) / GT, (D + GT - 1) / GT);
+    gram_fp32_kernel<<<grd, 256, 0, st>>>(X, n, D, K);
+    LV_CHECK_LAUNCH("gram_fp32_kernel");
+    return LV_OK;
+}
+
+// ---------------------------------------------------------- FP64 Jacobi eigh
+// Round r of the round-robin schedule on Dp (even) indices pairs slot i:
+//   i = 0: (r, Dp - 1);  i > 0: ((r + i) mod (Dp - 1), (r - i) mod (Dp - 1)).
+__device__ __forceinline__ void rr_pair(int r, int i, int Dp, int &p, int &q) {
+    const int m = Dp - 1;
+    if (i == 0) {
+        p = r % m;
+        q = m;
+    } else {
+        p = (r + i) % m;
+        q = ((r - i) % m + m) % m;
+    }
+    if (p > q) {
+        int t = p;
+        p = q;
+        q = t;
+    }
+}
+
+// Rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) that zeroes A'_pq of J^T A J.
+__global__ void jacobi_rot_kernel(const double *__restrict__ A, int Dp, int r, double2 *__restrict__ cs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Dp / 2) return;
+    int p, q;
+    rr_pair(r, i, Dp, p, q);
+    const double apq = A[(int64_t)p * Dp + q];
+    double c = 1.0, s = 0.0;
+    const double app = A[(int64_t)p * Dp + p], aqq = A[(int64_t)q * Dp + q];
+    if (apq != 0.0 && fabs(apq) > 1e-300) {
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        c = 1.0 / sqrt(t * t + 1.0);
+        s = t * c;
+    }
+    cs[i] = make_double2(c, s);
+}
+
+// rows p, q of A  <-  (c A_p - s A_q, s A_p + c A_q)   for every pair of the round
+__global__ void jacobi_rows_kernel(double *__restrict__ A, int Dp, int r, const double2 *__restrict__ cs) {
+    const int i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Dp) return;
+    int p, q;
+    rr_pair(r, i, Dp, p, q);
+    const double2 k = cs[i];
+    const double a = A[(int64_t)p * Dp + j], b = A[(int64_t)q * Dp + j];
+    A[(int64_t)p * Dp + j] = k.x * a - k.y * b;
+    A[(int64_t)q * Dp + j] = k.y * a + k.x * b;
+}
+
+// columns p, q of A and V  <-  (c X_p - s X_q, s X_p + c X_q)
+__global__ void jacobi_cols_kernel(double *__restrict__ A, double *__restrict__ V, int Dp, int r,
+                                   const double2 *__restrict__ cs) {
+    const int i = blockIdx.y;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= Dp) return;
+    int p, q;
+    rr_pair(r, i, Dp, p, q);
+    const double2 k = cs[i];
+    double *ar = A + (int64_t)row * Dp;
+    double a = ar[p], b = ar[q];
+    ar[p] = k.x * a - k.y * b;
+    ar[q] = k.y * a + k.x * b;
+    double *vr = V + (int64_t)row * Dp;
+    a = vr[p];
+    b = vr[q];
+    vr[p] = k.x * a - k.y * b;
+    vr[q] = k.y * a + k.x * b;
+}
+
+// out[0] = sum of squared off-diagonal entries, out[1] = sum of squared diagonal entries
+__global__ void jacobi_offnorm_kernel(const double *__restrict__ A, int Dp, double *__restrict__ out) {
+    __shared__ double so[256], sd[256];
+    double o = 0.0, d = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)Dp * Dp;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = A[t];
+        if (t / Dp == t % Dp)
+            d += v * v;
+        else
+            o += v * v;
+    }
+    so[threadIdx.x] = o;
+    sd[threadIdx.x] = d;
+    __syncthreads();
+    for (int s = 128; s; s >>= 1) {
+        if (threadIdx.x < s) {
+            so[threadIdx.x] += so[threadIdx.x + s];
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(out, so[0]);
+        atomicAdd(out + 1, sd[0]);
+    }
+}
+
+__global__ void pad_copy_kernel(const double *__restrict__ K, int D, double *__restrict__ A, double *__restrict__ V,
+                                int Dp) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Dp * Dp) return;
+    const int i = (int)(t / Dp), j = (int)(t % Dp);
+    A[t] = (i < D && j < D) ? K[(int64_t)i * D + j] : 0.0;
+    V[t] = i == j ? 1.0 : 0.0;
+}
+
+// evecs[r] = column idx[r] of V (first D entries), sign: largest-|.| entry positive
+// (first index on ties); evals[r] = A[idx[r]][idx[r]].
+__global__ void gather_eig_kernel(const double *__restrict__ A, const double *__restrict__ V, int Dp, int D,
+                                  const int *__restrict__ idx, int nout, double *__restrict__ evals,
+                                  double *__restrict__ evecs) {
+    const int r = blockIdx.x;
+    if (r >= nout) return;
+    const int c = idx[r];
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        const double v = fabs(V[(int64_t)i * Dp + c]);
+        if (v > best || (v == best && i < bi)) {
+            best = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double v = sv[threadIdx.x + s];
+            const int j = si[threadIdx.x + s];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && j < si[threadIdx.x])) {
+                sv[threadIdx.x] = v;
+                si[threadIdx.x] = j;
+            }
+        }
+        __syncthreads();
+    }
+    const double sign = V[(int64_t)si[0] * Dp + c] < 0.0 ? -1.0 : 1.0;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) evecs[(int64_t)r * D + i] = sign * V[(int64_t)i * Dp + c];
+    if (threadIdx.x == 0 && evals) evals[r] = A[(int64_t)c * Dp + c];
+}
+
+__global__ void diag_kernel(const double *__restrict__ A, int Dp, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < Dp) out[i] = A[(int64_t)i * Dp + i];
+}
+
+__global__ void f32_to_f64_kernel(const float *__restrict__ a, int64_t n, double *__restrict__ b) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (double)a[t];
+}
+
+__global__ void f64_to_f32_kernel(const double *__restrict__ a, int64_t n, float *__restrict__ b) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (float)a[t];
+}
+
+// Eigen-decomposition of symmetric K (D x D FP64, device).  Writes the nout leading
+// eigenpairs (descending eigenvalue) to evals (nullable) / evecs (nout x D).
+int eigh_impl(const double *K, int D, int nout, double *evals, double *evecs, cudaStream_t st, int *sweeps_out) {
+    const int Dp = D + (D & 1);
+    double *A = nullptr, *V = nullptr, *acc = nullptr, *dg = nullptr;
+    double2 *cs = nullptr;
+    int *idx_d = nullptr;
+    int rc = LV_OK;
+    std::vector<double> diag(Dp);
+    std::vector<int> order(Dp);
+    double host_acc[2];
+    int sweep = 0;
+    if (cudaMalloc(&A, sizeof(double) * Dp * Dp) != cudaSuccess || cudaMalloc(&V, sizeof(double) * Dp * Dp) != cudaSuccess ||
+        cudaMalloc(&acc, 2 * sizeof(double)) != cudaSuccess || cudaMalloc(&cs, sizeof(double2) * Dp / 2) != cudaSuccess ||
+        cudaMalloc(&idx_d, sizeof(int) * Dp) != cudaSuccess || cudaMalloc(&dg, sizeof(double) * Dp) != cudaSuccess) {
+        rc = fail(LV_ERR_OOM, "eigh: allocation failed");
+        goto done;
+    }
+    pad_copy_kernel<<<(unsigned)(((int64_t)Dp * Dp + 255) / 256), 256, 0, st>>>(K, D, A, V, Dp);
+    for (sweep = 0; sweep < 40; ++sweep) {
+        cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
+        jacobi_offnorm_kernel<<<128, 256, 0, st>>>(A, Dp, acc);
+        cudaMemcpyAsync(host_acc, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = fail(LV_ERR_CUDA, "eigh: kernel failure");
+            goto done;
+        }
+        const double tot = host_acc[0] + host_acc[1];
+        if (!(host_acc[0] > 1e-28 * tot) || tot == 0.0) break;
+        for (int r = 0; r < Dp - 1; ++r) {
+            jacobi_rot_kernel<<<(Dp / 2 + 127) / 128, 128, 0, st>>>(A, Dp, r, cs);
+            jacobi_rows_kernel<<<dim3((Dp + 127) / 128, Dp / 2), 128, 0, st>>>(A, Dp, r, cs);
+            jacobi_cols_kernel<<<dim3((Dp + 127) / 128, Dp / 2), 128, 0, st>>>(A, V, Dp, r, cs);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "jacobi kernels");
+            goto done;
+        }
+    }
+    // sort eigenvalues descending (stable by index); the padding index (D) is dropped
+    {
+        diag_kernel<<<(Dp + 255) / 256, 256, 0, st>>>(A, Dp, dg);
+        cudaMemcpyAsync(diag.data(), dg, sizeof(double) * Dp, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = fail(LV_ERR_CUDA, "eigh: diagonal copy failed");
+            goto done;
+        }
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.begin() + D, [&](int a, int b) { return diag[a] > diag[b]; });
+        cudaMemcpyAsync(idx_d, order.data(), sizeof(int) * D, cudaMemcpyHostToDevice, st);
+        gather_eig_kernel<<<nout, 256, 0, st>>>(A, V, Dp, D, idx_d, nout, evals, evecs);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = fail(LV_ERR_CUDA, "eigh: gather failed");
+            goto done;
+        }
+    }
+done:
+    if (sweeps_out) *sweeps_out = sweep;
+    cudaFree(A);
+    cudaFree(V);
+    cudaFree(acc);
+    cudaFree(cs);
+    cudaFree(idx_d);
+    cudaFree(dg);
+    return rc;
+}
+
+int launch_f32_to_f64(const float *a, int64_t n, double *b, cudaStream_t st) {
+    f32_to_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, b);
+    LV_CHECK_LAUNCH("f32_to_f64_kernel");
+    return LV_OK;
+}
+
+int launch_f64_to_f32(const double *a, int64_t n, float *b, cudaStream_t st) {
+    f64_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, b);
+    LV_CHECK_LAUNCH("f64_to_f32_kernel");
+    return LV_OK;
+}
+
+}  // namespace lv
+
+using namespace lv;
+
+extern "C" {
+
+int leanvec_second_moment(const float *X, int64_t n, int D, float *K, int precision, lv_stream_t stream) {
+    if (!X || !K || n <= 0 || D <= 0) return fail(LV_ERR_ARG, "second_moment: invalid sizes or null pointer");
+    if (precision != LV_PREC_FP32) return fail(LV_ERR_ARG, "second_moment: only LV_PREC_FP32 is available in this build");
+    return launch_gram_fp32(X, n, D, K, (cudaStream_t)stream);
+}
+
+int leanvec_eigh(const double *K, int D, double *evals, double *evecs, lv_stream_t stream) {
+    if (!K || !evecs || D <= 1) return fail(LV_ERR_ARG, "eigh: invalid sizes or null pointer");
+    return eigh_impl(K, D, D, evals, evecs, (cudaStream_t)stream, nullptr);
+}
+
+int leanvec_fit_id(const float *X, int64_t n, int D, int d, float *A_out, float *B_out, int precision,
+                   lv_stream_t stream) {
+    if (!X || !A_out || n <= 0 || D <= 1 || d <= 0 || d > D)
+        return fail(LV_ERR_ARG, "fit_id: invalid sizes or null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *K = nullptr;
+    double *K64 = nullptr, *P = nullptr;
+    int rc = LV_OK;
+    if (cudaMalloc(&K, sizeof(float) * D * D) != cudaSuccess || cudaMalloc(&K64, sizeof(double) * D * D) != cudaSuccess ||
+        cudaMalloc(&P, sizeof(double) * (size_t)d * D) != cudaSuccess) {
+        rc = fail(LV_ERR_OOM, "fit_id: allocation failed");
+    }
+    if (rc == LV_OK) rc = leanvec_second_moment(X, n, D, K, precision, stream);
+    if (rc == LV_OK) rc = launch_f32_to_f64(K, (int64_t)D * D, K64, st);
+    if (rc == LV_OK) rc = eigh_impl(K64, D, d, nullptr, P, st, nullptr);
+    if (rc == LV_OK) rc = launch_f64_to_f32(P, (int64_t)d * D, A_out, st);
+    if (rc == LV_OK && B_out && B_out != A_out)
+        if (cudaMemcpyAsync(B_out, A_out, sizeof(float) * (size_t)d * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = fail(LV_ERR_CUDA, "fit_id: copy failed");
+    if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "fit_id: sync failed");
+    cudaFree(K);
+    cudaFree(K64);
+    cudaFree(P);
+    return rc;
+}
+
+}  // extern "C"

@@ -83,6 +83,28 @@ class Mixture:
         return out
 
 
+    def sample_torch(self, n: int, seed: int, device, chunk: int = 131072):
+        """Same recipe drawn with torch's generator on `device` (for the million-scale
+        workloads; deterministic for a given device type and torch version)."""
+        import torch
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed))
+        C, D = self.means.shape
+        means = torch.as_tensor(self.means, dtype=torch.float32, device=device)
+        basis = torch.as_tensor(self.basis.T, dtype=torch.float32, device=device) if self.basis is not None else None
+        sq = torch.as_tensor(self.sqrt_spec, dtype=torch.float32, device=device) if self.sqrt_spec is not None else None
+        out = torch.empty((n, D), dtype=torch.float32, device=device)
+        for s in range(0, n, chunk):
+            e = min(n, s + chunk)
+            comp = torch.randint(0, C, (e - s,), generator=g, device=device)
+            z = torch.randn((e - s, D), generator=g, device=device)
+            if basis is not None:
+                z = (z * sq) @ basis
+            x = means[comp] + self.sigma * z
+            out[s:e] = x / x.norm(dim=1, keepdim=True).clamp_min(1e-30)
+        return out
+
+
 def isotropic_mixture(D: int, components: int, sigma: float, seed: int) -> Mixture:
     rng = _rng(seed)
     return Mixture(rng.standard_normal((components, D)), None, None, sigma)
@@ -155,6 +177,25 @@ def workload_ood(n: int = 1_000_000, m: int = 10_000, D: int = 512, components: 
     """Shifted-query mixture (database n x D, OOD test + learning queries)."""
     return make_workload("anisotropic", n, m, D, components, cfg=cfg, sigma=0.3, ood=True,
                          m_learn=m, name=f"ood-{n//1000}k-{D}")
+
+
+def make_workload_torch(kind: str, n: int, m: int, D: int, components: int, cfg: int, device,
+                        sigma: float = 0.3, ood: bool = False, m_learn: int | None = None):
+    """make_workload drawn on a CUDA device (float32 tensors X, Q, Q_learn)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        mix = (isotropic_mixture(D, components, sigma, SEED_DATABASE + cfg) if kind == "isotropic"
+               else anisotropic_mixture(D, components, sigma, SEED_DATABASE + cfg))
+        X = mix.sample_torch(n, SEED_DATABASE + cfg + 1, device)
+        qmix = ood_query_mixture(mix, SEED_TEST_QUERIES + cfg + 7) if ood else mix
+        Q = qmix.sample_torch(m, SEED_TEST_QUERIES + cfg, device)
+        ml = m if m_learn is None else m_learn
+        Ql = qmix.sample_torch(ml, SEED_LEARN_QUERIES + cfg, device)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return X, Q, Ql
 
 
 def subsample_rows(n: int, n_s: int, cfg: int) -> np.ndarray:
