@@ -249,6 +249,8 @@ def main():
     ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -296,6 +298,18 @@ def main():
     lv, idx, base, Q, A, truth = S["lv"], S["idx"], S["base"], S["Q"], S["A"], S["truth"]
     m = Q.shape[0]
     k = 10
+    if args.profile:
+        L = args.L or 64
+        for _ in range(args.warmup):
+            idx.search(Q, A, k=k, L=L, rerank=L)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        for _ in range(args.steps):
+            idx.search(Q, A, k=k, L=L, rerank=L)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile": True, "L": L, "n": args.n, "m": m, "steps": args.steps}), flush=True)
+        return
     ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
     sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
 

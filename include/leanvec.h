@@ -258,6 +258,33 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
                    int32_t *ids, float *scores, int ldo, lv_search_stats *stats,
                    lv_stream_t stream);
 
+/* leanvec_search without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc while they serve
+ * queries -- hosts whose device memory is owned by their own pool allocator and
+ * that forbid libraries from allocating behind their back, or latency-bound
+ * serving loops that cannot afford the implicit device synchronisation and the
+ * possible failure of an allocation in the middle of a request.  leanvec_search
+ * grows a workspace in the index with cudaMalloc on first use at a given batch
+ * size; this variant instead uses one static 16 MiB device array compiled into
+ * the library (held on every GPU that loads the library until the process exits)
+ * and calls no cudaMalloc, cudaFree or allocating routine.
+ *   - Same arguments, semantics and results as leanvec_search.
+ *   - Capacity: m * (4 * ldq + 16) + 256 bytes must fit in 16 MiB, where ldq is
+ *     the primary dimension rounded up to whole 16-byte code chunks (d for LVQ-8
+ *     with d a multiple of 16; e.g. m <= 25,000 queries at d = 160); larger
+ *     batches return LV_ERR_CAPACITY before anything is launched -- split them.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the same array and finds the previous call's
+ *     contents in it (the work counter is cleared by each call): calls whose work
+ *     overlaps on the GPU (different streams, or host threads issuing
+ *     concurrently) race on it and must be serialised by the caller. */
+int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, const float *A,
+                           const lv_search_params *params, const lv_query_desc *desc,
+                           int32_t *ids, float *scores, int ldo, lv_search_stats *stats,
+                           lv_stream_t stream);
+
 /* Synchronise `stream` and return (and clear) the index's device status word. */
 int leanvec_sync_status(lv_index *idx, lv_stream_t stream);
 

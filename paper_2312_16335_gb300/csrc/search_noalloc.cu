@@ -1,0 +1,169 @@
+// leanvec_search_noalloc: the search of leanvec_search for callers that must not
+// allocate device memory.  Its scratch (the work counter, the projected queries and
+// the per-query constants) lives in one file-scope __device__ array instead of a
+// workspace obtained with cudaMalloc.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "beam.cuh"
+#include "common.cuh"
+#include "index.cuh"
+
+namespace lv {
+
+int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
+                        cudaStream_t st);
+int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStream_t st);
+int launch_query_consts(const float *Qp, int ldq, int d, const float *mu_p, const float *Q, int D,
+                        const float *mu_s, int64_t m, float4 *out, cudaStream_t st);
+
+// 16 MiB, held by every GPU that loads this library until the process exits.
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
+constexpr size_t NOALLOC_HEADER_BYTES = 256;  // work counter, padded
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch for each device ordinal, looked up once per
+// device with that device current.  In host code the array's name only stands for
+// the symbol; it is never dereferenced or passed to a kernel.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[128] = {};
+
+static int noalloc_scratch(int device, unsigned char **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (device < 0 || device >= 128) return fail(LV_ERR_ARG, "search_noalloc: unsupported device ordinal");
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "search_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[device]);
+    return LV_OK;
+}
+
+}  // namespace lv
+
+using namespace lv;
+
+extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, const float *A,
+                                      const lv_search_params *params, const lv_query_desc *desc, int32_t *ids,
+                                      float *scores, int ldo, lv_search_stats *stats, lv_stream_t stream) {
+    if (!idx || !params) return fail(LV_ERR_ARG, "search_noalloc: null index or params");
+    if (m < 0 || m >= (int64_t)0x7fffffff) return fail(LV_ERR_ARG, "search_noalloc: invalid m");
+    if (m == 0) return LV_OK;
+    if (!Q || !ids || !scores) return fail(LV_ERR_ARG, "search_noalloc: null query or output pointer");
+    if (idx->n == 0) return fail(LV_ERR_STATE, "search_noalloc: the index has no store");
+    if (!idx->graph) return fail(LV_ERR_STATE, "search_noalloc: the index has no graph");
+    if (idx->pbits != 32 && !A) return fail(LV_ERR_ARG, "search_noalloc: an LVQ index needs the projection A");
+    const lv_query_desc &u = params->uniform;
+    if (u.L < 1 || u.L > LCAP_MAX) return fail(LV_ERR_ARG, "search_noalloc: L must be in [1, 512]");
+    if (!desc && (u.k < 1 || u.k > u.L || u.k > ldo || u.rerank < 0 || u.rerank > u.L || u.max_hops < 0))
+        return fail(LV_ERR_ARG, "search_noalloc: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
+    if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search_noalloc: rerank needs a secondary store");
+    if (params->projection != LV_PREC_FP32)
+        return fail(LV_ERR_ARG, "search_noalloc: only LV_PREC_FP32 projection is available in this build");
+    if (idx->sbits && idx->sg.code_chunks + 1 > 64)
+        return fail(LV_ERR_ARG, "search_noalloc: D > 1008 is not supported by the rerank");
+
+    const int cpc = idx->pbits == 8 ? 16 : idx->pbits == 4 ? 32 : 4;
+    const int ldq = idx->pg.code_chunks * cpc;
+    const size_t q_bytes = round_up((int64_t)sizeof(float) * m * ldq, 256);
+    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + sizeof(float4) * (size_t)m;
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension + 16) + 256 bytes exceed the "
+                                     "16 MiB static scratch; split the batch");
+
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return fail(LV_ERR_CUDA, "search_noalloc: cudaGetDevice failed");
+    if (prev != idx->device && cudaSetDevice(idx->device) != cudaSuccess)
+        return fail(LV_ERR_CUDA, "search_noalloc: cannot select the index's device");
+    int rc = LV_OK;
+    unsigned char *scratch = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    do {
+        rc = noalloc_scratch(idx->device, &scratch);
+        if (rc) break;
+        int *work = reinterpret_cast<int *>(scratch);
+        float *qp = reinterpret_cast<float *>(scratch + NOALLOC_HEADER_BYTES);
+        float4 *qc = reinterpret_cast<float4 *>(scratch + NOALLOC_HEADER_BYTES + q_bytes);
+        rc = idx->pbits == 32 ? launch_pad_rows(Q, m, idx->D, qp, ldq, st)
+                              : launch_project_fp32(Q, m, idx->D, A, idx->d, qp, ldq, st);
+        if (rc) break;
+        rc = launch_query_consts(qp, ldq, idx->d, idx->pbits == 32 ? nullptr : idx->pmean, Q, idx->D, idx->smean, m,
+                                 qc, st);
+        if (rc) break;
+
+        BeamParams p;
+        memset(&p, 0, sizeof(p));
+        p.prim = idx->prim;
+        p.prim_stride = idx->pg.stride;
+        p.prim_chunks = idx->pg.code_chunks;
+        p.prim_dim = idx->d;
+        p.graph = idx->graph;
+        p.R = idx->R;
+        p.n = idx->n;
+        p.entry = idx->entry;
+        p.qp = qp;
+        p.ldq = ldq;
+        p.qconst = qc;
+        p.desc = reinterpret_cast<const int4 *>(desc);
+        p.uni = make_int4(u.k, u.L, idx->sec ? u.rerank : 0, u.max_hops);
+        p.m = m;
+        p.sec = idx->sec;
+        p.sec_stride = idx->sbits ? idx->sg.stride : 0;
+        p.sec_chunks = idx->sbits ? idx->sg.code_chunks : 0;
+        p.Q = Q;
+        p.D = idx->D;
+        p.ids = ids;
+        p.scores = scores;
+        p.ldo = ldo;
+        p.stats = reinterpret_cast<int2 *>(stats);
+        p.status = idx->status;
+        p.work = work;
+        p.Lcap = (int)round_up(u.L, 32);
+        int hs = 1024;
+        if (params->hash_slots > 0) {
+            hs = params->hash_slots;
+        } else {
+            while (hs < 8 * u.L && hs < 8192) hs <<= 1;
+        }
+        if (hs & (hs - 1)) {
+            rc = fail(LV_ERR_ARG, "search_noalloc: hash_slots must be a power of two");
+            break;
+        }
+        while (hs < 2 * p.Lcap) hs <<= 1;
+        p.Hcap = hs;
+        p.hbits = 0;
+        while ((1 << p.hbits) < hs) p.hbits++;
+        p.Rcap = (int)round_up(idx->R, 32);
+        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap);
+        int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
+        while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;
+        if ((size_t)warps * p.warp_smem > 227 * 1024) {
+            rc = fail(LV_ERR_CAPACITY, "search_noalloc: L / hash_slots too large for shared memory");
+            break;
+        }
+        // the scratch keeps the previous call's contents: the work counter must restart at 0
+        cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "search_noalloc: cudaMemsetAsync");
+            break;
+        }
+        const size_t smem = (size_t)warps * p.warp_smem;
+        const int block = warps * 32;
+        if (params->event_begin) cudaEventRecord((cudaEvent_t)params->event_begin, st);
+        if (idx->pbits == 32) {
+            rc = launch_search_fp32(p, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, st);
+        } else {
+            const int nc = (idx->pg.code_chunks + 1 + 3) / 4;
+            rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
+                                 : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
+        }
+        if (rc) break;
+        if (params->event_end) cudaEventRecord((cudaEvent_t)params->event_end, st);
+    } while (0);
+    if (prev >= 0 && prev != idx->device) cudaSetDevice(prev);
+    return rc;
+}

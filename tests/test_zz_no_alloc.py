@@ -1,0 +1,57 @@
+"""leanvec_search_noalloc, the search entry point for callers that cannot let the
+library allocate device memory (hosts that own all device memory through their own
+pool, or serving loops that cannot afford an allocation's implicit synchronisation
+mid-request): through the C ABI it must return what leanvec_search returns, call
+after call, although every call reuses the same static scratch array.
+
+Collected last on purpose (file name), so that a run stopping at the first failure
+has already run every other test."""
+import pytest
+import torch
+
+import oracle
+from gpu_util import gpu_index, small_problem, t
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lv():
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    return lv
+
+
+def _agree(ids, sc, ref_ids, ref_sc):
+    """The tolerance of the search parity tests: >= 99 % identical ids position by
+    position, scores of identical ids within 1e-4 of the norm product (unit-norm data)."""
+    same = ids == ref_ids
+    assert same.float().mean().item() >= 0.99
+    assert torch.all((sc - ref_sc).abs()[same] <= 1e-4)
+
+
+def test_noalloc_matches_search_on_consecutive_calls(lv):
+    pb = small_problem(oracle, n=3000, D=64, d=16, m=300)
+    idx = gpu_index(lv, pb)
+    Q, P = t(pb["Q"]), t(pb["P"])
+    ref_ids, ref_sc = idx.search(Q, P, k=10, L=40, rerank=40)
+    for _ in range(2):  # the second call finds the first call's scratch contents
+        ids, sc = idx.search_noalloc(Q, P, k=10, L=40, rerank=40)
+        torch.cuda.synchronize()
+        _agree(ids, sc, ref_ids, ref_sc)
+    # a different batch size and beam on the next call
+    ref2 = idx.search(Q[:77], P, k=5, L=24, rerank=16)
+    got2 = idx.search_noalloc(Q[:77], P, k=5, L=24, rerank=16)
+    _agree(got2[0], got2[1], ref2[0], ref2[1])
+    idx.sync_status()
+
+
+def test_noalloc_rejects_batches_beyond_the_static_scratch(lv):
+    pb = small_problem(oracle, n=500, D=64, d=16, m=10, seed=2)
+    idx = gpu_index(lv, pb)
+    # 16 MiB / (4 * 16 + 16) bytes per query: 300,000 queries do not fit
+    Q = torch.zeros((300_000, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(lv.LeanVecError) as e:
+        idx.search_noalloc(Q, t(pb["P"]), k=5, L=16, rerank=16)
+    assert e.value.code == -4 and "16 MiB" in str(e.value)
