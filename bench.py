@@ -167,6 +167,8 @@ def time_steps(fn, steps, warmup, events=None):
 
 
 def setup(args, dev):
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()  # no-op when the in-tree library is up to date
     import paper_2312_16335_gb300 as lv
     t0 = time.time()
     torch.manual_seed(0)
@@ -249,6 +251,8 @@ def main():
     ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hash", type=int, default=0, help="visited-cache slots per query (0 = library default)")
+    ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
@@ -316,14 +320,15 @@ def main():
     # -- choose L for recall 0.90 (untimed)
     if args.L:
         L, trace = args.L, []
-        rec = recall_at(idx.search(Q, A, k=k, L=L, rerank=L)[0], truth, k)
+        rec = recall_at(idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, hash_slots=args.hash)[0], truth, k)
         trace = [(L, rec)]
     else:
-        L, trace = calibrate(lambda L: idx.search(Q, A, k=k, L=L, rerank=L)[0], truth, k)
+        L, trace = calibrate(lambda L: idx.search(Q, A, k=k, L=L, rerank=L, width=args.width,
+                                                  hash_slots=args.hash)[0], truth, k)
         if L is None:
             L = L_GRID[-1]
     rec = dict(trace)[L]
-    Lb, trace_b = calibrate(lambda L: base.search(Q, None, k=k, L=L)[0], truth, k)
+    Lb, trace_b = calibrate(lambda L: base.search(Q, None, k=k, L=L, width=args.width)[0], truth, k)
     if Lb is None:
         Lb = L_GRID[-1]
     rec_b = dict(trace_b)[Lb]
@@ -331,7 +336,7 @@ def main():
     log(f"FP32   L={Lb} recall={rec_b:.4f}  trace={trace_b}")
 
     # -- per-query work (untimed run with counters)
-    _, _, st = idx.search(Q, A, k=k, L=L, rerank=L, stats=True)
+    _, _, st = idx.search(Q, A, k=k, L=L, rerank=L, stats=True, hash_slots=args.hash, width=args.width)
     hops = float(st[:, 0].double().mean())
     scored = float(st[:, 1].double().mean())
     inf = idx.info()
@@ -339,7 +344,7 @@ def main():
         L * inf["secondary_stride"] + args.D * 4 + k * 8
 
     def step(ev):
-        idx.search(Q, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), events=ev)
+        idx.search(Q, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), events=ev, hash_slots=args.hash, width=args.width)
 
     if world > 1:
         torch.distributed.barrier()
@@ -363,7 +368,7 @@ def main():
 
     def step_e2e(ev):
         Qd.copy_(Qh, non_blocking=True)
-        idx.search(Qd, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf))
+        idx.search(Qd, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), hash_slots=args.hash, width=args.width)
         ids_h.copy_(ids_buf, non_blocking=True)
         sc_h.copy_(sc_buf, non_blocking=True)
 
@@ -373,10 +378,10 @@ def main():
     # -- full-dimensional float32 baseline on the same graph
     ids_b = torch.empty((m, k), dtype=torch.int32, device=dev)
     sc_b = torch.empty((m, k), dtype=torch.float32, device=dev)
-    base_ms, _ = time_steps(lambda ev: base.search(Q, None, k=k, L=Lb, out=(ids_b, sc_b)),
+    base_ms, _ = time_steps(lambda ev: base.search(Q, None, k=k, L=Lb, out=(ids_b, sc_b), width=args.width),
                             max(5, args.steps // 2), 2)
     qps_b = m * max(5, args.steps // 2) / (base_ms / 1e3)
-    _, _, stb = base.search(Q, None, k=k, L=Lb, stats=True)
+    _, _, stb = base.search(Q, None, k=k, L=Lb, stats=True, width=args.width)
     bytes_b = args.D * 4 + float(stb[:, 0].double().mean()) * inf["R"] * 4 + \
         float(stb[:, 1].double().mean()) * lv.leanvec_record_stride(args.D, 32) + k * 8
 
@@ -397,6 +402,7 @@ def main():
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
                    "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
                    "L_build": args.L_build, "alpha": args.alpha, "projection": "fp32",
+                   "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},

@@ -231,9 +231,10 @@ typedef struct {
 typedef struct {
     lv_query_desc uniform;   /* used for every query when desc == NULL */
     int32_t projection;      /* lv_precision of the q -> A q GEMM */
-    int32_t hash_slots;      /* visited-cache slots per query (power of two, 0 = default 2048) */
+    int32_t hash_slots;      /* visited-cache slots per query (power of two; 0 = max(1024, 4 L) up to 8192) */
     int32_t warps_per_block; /* 0 = default */
-    int32_t reserved;
+    int32_t width;           /* search width: beam members expanded per round, 1..4 (0 = 1);
+                                width * R <= 256.  1 is the classic best-first traversal */
     void *event_begin;       /* optional cudaEvent_t recorded on `stream` right before the */
     void *event_end;         /* beam-search kernel and right after it (profiling); may be NULL */
 } lv_search_params;
@@ -246,8 +247,9 @@ typedef struct {
 
 /* Search m queries Q (m x D, device).  A (d x D, device) projects the queries
  * (ignored for a float32 baseline index).  desc (device, m entries) gives per-query
- * {k, L, rerank, max_hops}; NULL uses params->uniform.  For each query the best
- * unexpanded beam member is expanded until none is left (or max_hops); the top
+ * {k, L, rerank, max_hops}; NULL uses params->uniform.  For each query the `width`
+ * best unexpanded beam members are expanded per round until none is left (or
+ * max_hops expansions); the top
  * min(rerank, |beam|) members are rescored with the secondary store against the
  * unreduced query and the best k written, sorted by score (ties -> smaller id), to
  * ids/scores (m x ldo, device); the rest of each row (fewer than k reachable

@@ -52,7 +52,7 @@ def lib():
         L.orc_build_score.argtypes = [vp, vp, vp, vp, vp, f32, i32, i64, i64]
         L.orc_build_score.restype = f32
         L.orc_search.argtypes = [vp, vp, vp, vp, i64, vp, i64, i32, ctypes.c_int32, vp, i32, vp, vp,
-                                 i32, vp, vp, vp, vp, i32]
+                                 i32, vp, vp, vp, vp, i32, i32]
         L.orc_bruteforce.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, i32]
         L.orc_splitmix.argtypes = [u64, u64, u64]
         L.orc_splitmix.restype = u64
@@ -196,9 +196,9 @@ def _store(kind, dim, lvq: LVQ | None = None, vecs=None):
 def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank: int = 0,
            prim: LVQ | None = None, prim_vecs: np.ndarray | None = None,
            sec: LVQ | None = None, qs: np.ndarray | None = None, max_hops: int = 0,
-           desc: np.ndarray | None = None, want_beam: bool = False, nthreads: int = 0) -> dict:
-    """Beam search + rerank for all queries.  qp: m x d_primary (already projected,
-    FP64).  prim: LVQ primary store, or prim_vecs: raw fp32 vectors.  sec/qs: the
+           desc: np.ndarray | None = None, want_beam: bool = False, nthreads: int = 0, width: int = 1) -> dict:
+    """Beam search + rerank for all queries (search width `width`: parents expanded
+    per round).  qp: m x d_primary (already projected, FP64).  prim: LVQ primary store, or prim_vecs: raw fp32 vectors.  sec/qs: the
     secondary store and the unreduced queries for the rerank.  desc (m x 4 int32:
     k, L, r, max_hops) overrides the uniform parameters."""
     graph = _c(graph, np.int32)
@@ -230,7 +230,7 @@ def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank
     rc = lib().orc_search(ctypes.byref(ps), ctypes.byref(ss) if ss is not None else None, _p(qp), qsp,
                           m, _p(graph), n, R, int(entry), _p(desc), kmax, _p(ids), _p(scores),
                           Lmax if want_beam else 0, _p(bids) if want_beam else None,
-                          _p(bsc) if want_beam else None, _p(hops), _p(scored), nthreads)
+                          _p(bsc) if want_beam else None, _p(hops), _p(scored), width, nthreads)
     del keep1, keep2
     if rc != 0:
         raise RuntimeError(f"orc_search failed ({rc})")

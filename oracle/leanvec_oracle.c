@@ -228,34 +228,47 @@ static double score_of(const scorer_t *sc, int64_t u)
     return (double)bscore(sc->bs, sc->qnode, u);
 }
 
-/* Best-first beam search.  C = {entry}; repeatedly expand the best unexpanded
- * member of C, scoring each not-yet-visited neighbour and keeping the best L.
- * Stops when every member of C is expanded or after max_hops expansions
- * (max_hops <= 0: no limit).  visited is an n-sized stamp array owned by the
- * caller; stamp must be fresh for this call.  Returns |C| and writes C. */
+/* Best-first beam search.  C = {entry}; repeatedly take the `width` best
+ * unexpanded members of C (fewer if fewer are left), mark them expanded and, parent
+ * by parent in rank order and neighbour by neighbour in adjacency order, score each
+ * not-yet-visited neighbour, keeping the best L of everything scored.  width = 1 is
+ * the classic one-node-at-a-time traversal.  Stops when every member of C is
+ * expanded or after max_hops expansions (max_hops <= 0: no limit; a round is cut
+ * to the expansions left).  visited is an n-sized stamp array owned by the caller;
+ * stamp must be fresh for this call.  Returns |C| and writes C. */
 static int beam_search(const scorer_t *sc, const int32_t *graph, int R, int64_t n,
-                       int32_t entry, int L, int max_hops, uint32_t *visited, uint32_t stamp,
+                       int32_t entry, int L, int max_hops, int width, uint32_t *visited, uint32_t stamp,
                        cand_t *C, int64_t *hops_out, int64_t *scored_out)
 {
     int size = 0;
     int64_t hops = 0, scored = 1;
+    int32_t par[64];
+    if (width < 1) width = 1;
+    if (width > 64) width = 64;
     visited[entry] = stamp;
     cand_insert(C, &size, L, score_of(sc, entry), entry);
     for (;;) {
-        int i = 0;
-        while (i < size && C[i].expanded) i++;
-        if (i == size) break;
-        if (max_hops > 0 && hops >= max_hops) break;
-        C[i].expanded = 1;
-        hops++;
-        int32_t p = C[i].id;
-        for (int j = 0; j < R; ++j) {
-            int32_t u = graph[(int64_t)p * R + j];
-            if (u < 0 || u >= n) continue;
-            if (visited[u] == stamp) continue;
-            visited[u] = stamp;
-            scored++;
-            cand_insert(C, &size, L, score_of(sc, u), u);
+        int np = 0;
+        for (int i = 0; i < size && np < width; ++i) {
+            if (C[i].expanded) continue;
+            if (max_hops > 0 && hops + np >= max_hops) break;
+            par[np++] = C[i].id;
+        }
+        if (np == 0) break;
+        for (int t = 0; t < np; ++t)
+            for (int i = 0; i < size; ++i)
+                if (C[i].id == par[t]) C[i].expanded = 1;
+        hops += np;
+        for (int t = 0; t < np; ++t) {
+            int32_t p = par[t];
+            for (int j = 0; j < R; ++j) {
+                int32_t u = graph[(int64_t)p * R + j];
+                if (u < 0 || u >= n) continue;
+                if (visited[u] == stamp) continue;
+                visited[u] = stamp;
+                scored++;
+                cand_insert(C, &size, L, score_of(sc, u), u);
+            }
         }
     }
     if (hops_out) *hops_out = hops;
@@ -264,7 +277,7 @@ static int beam_search(const scorer_t *sc, const int32_t *graph, int R, int64_t 
 }
 
 /*
- * Search + rerank for m queries (Sec. 2 "Search"):
+ * Search + rerank for m queries (Sec. 2 "Search"), search width `width`:
  *   primary:   qp (m x dp, FP64 already projected: A q) scored against prim
  *   secondary: qs (m x ds, FP64 unreduced q)      scored against sec
  * Candidates are the top min(r, |C|) of the beam; they are rescored with the
@@ -277,7 +290,7 @@ int orc_search(const orc_store *prim, const orc_store *sec, const double *qp, co
                const int32_t *kLrh /* m x 4: k, L, r, max_hops */,
                int ldo, int32_t *ids, double *scores,
                int ldb, int32_t *beam_ids, double *beam_scores,
-               int64_t *hops, int64_t *scored, int nthreads)
+               int64_t *hops, int64_t *scored, int width, int nthreads)
 {
     int Lmax = 1;
     for (int64_t i = 0; i < m; ++i) if (kLrh[4 * i + 1] > Lmax) Lmax = kLrh[4 * i + 1];
@@ -302,7 +315,7 @@ int orc_search(const orc_store *prim, const orc_store *sec, const double *qp, co
                 if (stamp == 0) { memset(visited, 0, sizeof(uint32_t) * (size_t)n); stamp = 1; }
                 scorer_t sc = {prim, qp + qi * (int64_t)prim->dim, NULL, 0};
                 int64_t h = 0, sd = 0;
-                int size = beam_search(&sc, graph, R, n, entry, L, mh, visited, stamp, C, &h, &sd);
+                int size = beam_search(&sc, graph, R, n, entry, L, mh, width, visited, stamp, C, &h, &sd);
                 if (hops) hops[qi] = h;
                 if (scored) scored[qi] = sd;
                 if (beam_ids) {
@@ -521,7 +534,7 @@ int orc_vamana_build(const uint8_t *codes, const float *delta, const float *lowe
                         int32_t p = perm[b0 + t];
                         stamp++;
                         scorer_t sc = {NULL, NULL, &bs, p};
-                        int size = beam_search(&sc, snap, R, n, entry, L_build, 0, visited, stamp, C, NULL, NULL);
+                        int size = beam_search(&sc, snap, R, n, entry, L_build, 0, 1, visited, stamp, C, NULL, NULL);
                         int np = 0;
                         for (int s = 0; s < size; ++s) if (C[s].id != p) pool[np++] = C[s].id;
                         for (int s = 0; s < R; ++s) {

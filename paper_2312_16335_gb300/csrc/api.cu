@@ -475,13 +475,15 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.status = idx->status;
     p.work = idx->status + 1;
     p.Lcap = (int)round_up(u.L, 32);
-    int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(8 * u.L)));
+    int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(4 * u.L)));
     if (hs & (hs - 1)) return fail(LV_ERR_ARG, "search: hash_slots must be a power of two");
     hs = std::max(hs, next_pow2(2 * p.Lcap));
     p.Hcap = hs;
     p.hbits = 0;
     while ((1 << p.hbits) < hs) p.hbits++;
-    p.Rcap = (int)round_up(idx->R, 32);
+    p.W = params->width > 0 ? params->width : 1;
+    if (p.W > WMAX || p.W * idx->R > CMAX) return fail(LV_ERR_ARG, "search: need width <= 4 and width * R <= 256");
+    p.Rcap = (int)round_up((int64_t)p.W * idx->R, 32);
     p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap);
     int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
     while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;

@@ -3,9 +3,9 @@
 // Vamana graph).  One warp serves one query at a time; warps pull queries from a
 // global counter until the batch is exhausted.
 //
-// Per warp, shared memory holds a double-buffered beam (scores + ids, the top bit of
-// an id marks "expanded"), a visited cache, and the candidate buffers of one
-// expansion.  The visited cache is an open-addressing table that may forget ids
+// Per warp, shared memory holds the beam (scores + ids sorted best first, the top bit
+// of an id marks "expanded"; merged in place), a visited cache, and the candidate
+// buffers of one expansion.  The visited cache is an open-addressing table that may forget ids
 // (overwrite when a probe run is full) but never reports an unvisited id as visited;
 // a forgotten id that is met again is rescored and then rejected by the merge,
 // because it is either still in the beam (exact key match) or worse than the beam's
@@ -54,11 +54,15 @@ struct BeamParams {
     int Lcap;   // beam capacity (multiple of 32)
     int Hcap;   // visited cache slots (power of two, >= 2 * Lcap)
     int hbits;  // log2(Hcap)
-    int Rcap;   // candidate buffer capacity (multiple of 32, >= R)
+    int Rcap;   // candidate buffer capacity (multiple of 32, >= W * R)
+    int W;      // search width: parents expanded per round (1..4, W * R <= 256)
     int warp_smem;
 };
 
-inline int beam_warp_smem(int Lcap, int Hcap, int Rcap) { return 16 * Lcap + 4 * Hcap + 20 * Rcap; }
+constexpr int WMAX = 4;
+constexpr int CMAX = 256;  // candidates of one round (W * R)
+
+inline int beam_warp_smem(int Lcap, int Hcap, int Rcap) { return 8 * Lcap + 4 * Hcap + 20 * Rcap; }
 
 // --------------------------------------------------------------------------------
 // Primary scorer: LVQ records, 4 lanes per record, 8 records per warp pass.
@@ -164,6 +168,152 @@ struct LvqGroupScorer {
                 if (j1 < cnt) out[j1] = fmaf(d1, s1, fmaf(l1, sq, cq));
             }
         }
+    }
+};
+
+// --------------------------------------------------------------------------------
+// Primary scorer with an integer query: q' is held as 24-bit fixed point
+// q_int = round(q' / scale), scale = max|q'| / (2^23 - 1), split into three byte limbs
+// q_int = 2^16 h + 2^8 m + l (h signed, m and l unsigned), so that <q_int, codes> is three
+// dp4a chains per 4 codes.  The quantisation error of q' is at most scale / 2 per entry,
+// i.e. |error of delta * <q', codes>| <= 2^-24 * d * (max x - min x) * max|q'|, about
+// 2e-5 * ||q'|| * ||x|| at d = 160 -- inside the float32 path's 1e-4 tolerance.
+// 4 lanes per record, 8 records per pass (16 when enough candidates are pending).
+// --------------------------------------------------------------------------------
+__device__ __forceinline__ int dp4a_su(uint32_t s8x4, uint32_t u8x4, int c) {
+    int d;
+    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(s8x4), "r"(u8x4), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int dp4a_uu(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+template <int NC, int BITS>
+struct LvqIntScorer {
+    static constexpr int CPC = BITS == 8 ? 16 : 32;  // codes per 16-byte chunk
+    static constexpr int W = BITS == 8 ? 4 : 8;      // limb words per chunk
+    uint32_t qh[NC][W], qm[NC][W], ql[NC][W];
+    float cq, sq, scale;
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+        CH = p.prim_chunks;
+        base = p.prim;
+        stride = p.prim_stride;
+        const int g = lane & 3;
+        const float *row = p.qp + qi * p.ldq;
+        float amax = 0.f;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const int c = g + 4 * t;
+            if (c < CH)
+                for (int e = 0; e < CPC; ++e) amax = fmaxf(amax, fabsf(row[c * CPC + e]));
+        }
+        amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, 1));
+        amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, 2));
+        scale = amax > 0.f ? amax / 8388607.0f : 1.0f;
+        const float inv = amax > 0.f ? 8388607.0f / amax : 0.f;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const int c = g + 4 * t;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint32_t h = 0, mm = 0, l = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    // element of this limb byte: LVQ-8 word w holds codes 4w..4w+3;
+                    // LVQ-4 words 2i / 2i+1 hold the low / high nibbles of bytes 4i..4i+3
+                    const int e = BITS == 8 ? 4 * w + b : 8 * (w >> 1) + 2 * b + (w & 1);
+                    int qv = 0;
+                    if (c < CH) {
+                        qv = __float2int_rn(row[c * CPC + e] * inv);
+                        qv = max(-8388607, min(8388607, qv));
+                    }
+                    h |= (uint32_t)((qv >> 16) & 0xff) << (8 * b);
+                    mm |= (uint32_t)((qv >> 8) & 0xff) << (8 * b);
+                    l |= (uint32_t)(qv & 0xff) << (8 * b);
+                }
+                qh[t][w] = h;
+                qm[t][w] = mm;
+                ql[t][w] = l;
+            }
+        }
+        float4 k = p.qconst[qi];
+        cq = k.x;
+        sq = k.y;
+    }
+
+    __device__ __forceinline__ float dot(const uint4 (&v)[NC]) const {
+        int sh = 0, sm = 0, sl = 0;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const uint32_t w4[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (BITS == 8) {
+                    sh = dp4a_su(qh[t][i], w4[i], sh);
+                    sm = dp4a_uu(qm[t][i], w4[i], sm);
+                    sl = dp4a_uu(ql[t][i], w4[i], sl);
+                } else {
+                    const uint32_t lo = w4[i] & 0x0F0F0F0Fu, hi = (w4[i] >> 4) & 0x0F0F0F0Fu;
+                    sh = dp4a_su(qh[t][2 * i], lo, sh);
+                    sh = dp4a_su(qh[t][2 * i + 1], hi, sh);
+                    sm = dp4a_uu(qm[t][2 * i], lo, sm);
+                    sm = dp4a_uu(qm[t][2 * i + 1], hi, sm);
+                    sl = dp4a_uu(ql[t][2 * i], lo, sl);
+                    sl = dp4a_uu(ql[t][2 * i + 1], hi, sl);
+                }
+            }
+        }
+        // partial sums of one lane are < 2^24 in magnitude: exact conversions
+        return fmaf((float)sh, 65536.0f, fmaf((float)sm, 256.0f, (float)sl));
+    }
+
+    template <int P>
+    __device__ __forceinline__ void pass(const int *ids, float *out, int b, int cnt, int lane) const {
+        const int g = lane & 3, grp = lane >> 2;
+        const int holder = (lane & ~3) | (CH & 3);
+        uint4 v[P][NC];
+        int j[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            j[r] = b + 8 * r + grp;
+            const int id = j[r] < cnt ? ids[j[r]] : -1;
+            const uint8_t *rec = base + (int64_t)(id < 0 ? 0 : id) * stride;
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+                const int c = g + 4 * t;
+                v[r][t] = (c <= CH && id >= 0) ? ldg_stream(rec + 16 * c) : make_uint4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            float s = dot(v[r]);
+            float dl = 0.f, lo = 0.f;
+#pragma unroll
+            for (int t = 0; t < NC; ++t)
+                if (g + 4 * t == CH) {
+                    dl = __uint_as_float(v[r][t].x);
+                    lo = __uint_as_float(v[r][t].y);
+                }
+            s += __shfl_xor_sync(FULL, s, 1);
+            s += __shfl_xor_sync(FULL, s, 2);
+            dl = __shfl_sync(FULL, dl, holder);
+            lo = __shfl_sync(FULL, lo, holder);
+            if (g == 0 && j[r] < cnt) out[j[r]] = fmaf(dl * scale, s, fmaf(lo, sq, cq));
+        }
+    }
+
+    // scores of ids[0..cnt) into out[0..cnt) (shared memory); warp-collective
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        int b = 0;
+        for (; b + 8 < cnt; b += 16) pass<2>(ids, out, b, cnt, lane);
+        if (b < cnt) pass<1>(ids, out, b, cnt, lane);
     }
 };
 
@@ -383,26 +533,156 @@ struct WarpScorer {
 };
 
 // --------------------------------------------------------------------------------
+// Rerank scorer (whole warp per record): LVQ-8 secondary records scored against the
+// unreduced query held as 24-bit fixed point in three byte limbs (same scheme and
+// error bound as LvqIntScorer, with D in place of d).  Lane l holds code chunks l and
+// l + 32 (D <= 1008); 4 records per pass.
+// --------------------------------------------------------------------------------
+struct SecIntScorer {
+    static constexpr int NCW = 2, U = 4;
+    uint32_t qh[NCW][4], qm[NCW][4], ql[NCW][4];
+    float c0, s0, scale;
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    __device__ __forceinline__ void setup(const float *qrow, int D, int chunks, const uint8_t *b, int64_t st,
+                                          float cc, float ss, int lane) {
+        CH = chunks;
+        base = b;
+        stride = st;
+        c0 = cc;
+        s0 = ss;
+        float amax = 0.f;
+        for (int j = lane; j < D; j += 32) amax = fmaxf(amax, fabsf(qrow[j]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+        scale = amax > 0.f ? amax / 8388607.0f : 1.0f;
+        const float inv = amax > 0.f ? 8388607.0f / amax : 0.f;
+#pragma unroll
+        for (int t = 0; t < NCW; ++t) {
+            const int c = lane + 32 * t;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                uint32_t h = 0, mm = 0, l = 0;
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int j = c * 16 + 4 * w + bb;
+                    int qv = 0;
+                    if (c < CH && j < D) {
+                        qv = __float2int_rn(qrow[j] * inv);
+                        qv = max(-8388607, min(8388607, qv));
+                    }
+                    h |= (uint32_t)((qv >> 16) & 0xff) << (8 * bb);
+                    mm |= (uint32_t)((qv >> 8) & 0xff) << (8 * bb);
+                    l |= (uint32_t)(qv & 0xff) << (8 * bb);
+                }
+                qh[t][w] = h;
+                qm[t][w] = mm;
+                ql[t][w] = l;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        const int tot = CH + 1;
+        const int holder = CH & 31, tslot = CH >> 5;
+        for (int b = 0; b < cnt; b += U) {
+            uint4 v[U][NCW];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int id = b + u < cnt ? ids[b + u] : -1;
+                const uint8_t *r = base + (int64_t)(id < 0 ? 0 : id) * stride;
+#pragma unroll
+                for (int t = 0; t < NCW; ++t) {
+                    const int c = lane + 32 * t;
+                    v[u][t] = (c < tot && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int sh = 0, sm = 0, sl = 0;
+#pragma unroll
+                for (int t = 0; t < NCW; ++t) {
+                    const uint32_t w4[4] = {v[u][t].x, v[u][t].y, v[u][t].z, v[u][t].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        sh = dp4a_su(qh[t][i], w4[i], sh);
+                        sm = dp4a_uu(qm[t][i], w4[i], sm);
+                        sl = dp4a_uu(ql[t][i], w4[i], sl);
+                    }
+                }
+                float s = fmaf((float)sh, 65536.0f, fmaf((float)sm, 256.0f, (float)sl));
+#pragma unroll
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+                float dl = 0.f, lo = 0.f;
+#pragma unroll
+                for (int t = 0; t < NCW; ++t)
+                    if (t == tslot) {
+                        dl = __uint_as_float(v[u][t].x);
+                        lo = __uint_as_float(v[u][t].y);
+                    }
+                dl = __shfl_sync(FULL, dl, holder);
+                lo = __shfl_sync(FULL, lo, holder);
+                if (lane == 0 && b + u < cnt) out[b + u] = fmaf(dl * scale, s, fmaf(lo, s0, c0));
+            }
+        }
+    }
+};
+
+// The best k of (S[0..n), I[0..n)) by (score desc, id asc), k rounds of a warp argmax;
+// selected entries are marked by id -1.  Writes oid/osc[0..min(k, n)).
+__device__ __forceinline__ void warp_topk(float *S, int *I, int n, int k, int32_t *oid, float *osc, int lane) {
+    for (int r = 0; r < k && r < n; ++r) {
+        float bs = -INFINITY;
+        int bi = 0x7fffffff, bt = -1;
+        for (int t = lane; t < n; t += 32) {
+            const int id = I[t];
+            if (id >= 0 && (bt < 0 || key_better(S[t], id, bs, bi))) {
+                bs = S[t];
+                bi = id;
+                bt = t;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float os = __shfl_xor_sync(FULL, bs, o);
+            const int oi = __shfl_xor_sync(FULL, bi, o);
+            const int ot = __shfl_xor_sync(FULL, bt, o);
+            if (ot >= 0 && (bt < 0 || key_better(os, oi, bs, bi))) {
+                bs = os;
+                bi = oi;
+                bt = ot;
+            }
+        }
+        if (lane == 0) {
+            oid[r] = bi;
+            osc[r] = bs;
+            I[bt] = -1;
+        }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------------------------------------
 // The beam kernel.  BUILD: queries are nodes (p.qnodes), output = the final beam.
 // RERANK: rescore the top-r of the beam with the secondary store.
 // --------------------------------------------------------------------------------
 template <class PS, bool BUILD, bool RERANK>
-__global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
+__global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     unsigned char *my = smem_raw + (size_t)(threadIdx.x >> 5) * p.warp_smem;
-    float *const bS0 = reinterpret_cast<float *>(my);
-    int *const bI0 = reinterpret_cast<int *>(bS0 + p.Lcap);
-    float *const bS1 = reinterpret_cast<float *>(bI0 + p.Lcap);
-    int *const bI1 = reinterpret_cast<int *>(bS1 + p.Lcap);
-    int *hash = reinterpret_cast<int *>(bI1 + p.Lcap);
-    int *cI = hash + p.Hcap;
-    float *cS = reinterpret_cast<float *>(cI + p.Rcap);
-    int *vI = reinterpret_cast<int *>(cS + p.Rcap);
-    float *vS = reinterpret_cast<float *>(vI + p.Rcap);
-    int *vPB = reinterpret_cast<int *>(vS + p.Rcap);
-    int *sPB = cI;  // reuses the raw candidate ids once they are compacted
+    float *const bS = reinterpret_cast<float *>(my);           // beam scores (sorted, best first)
+    int *const bI = reinterpret_cast<int *>(bS + p.Lcap);      // beam ids, top bit = expanded
+    int *const hash = bI + p.Lcap;                             // visited cache
+    int *const cI = hash + p.Hcap;                             // ids of one expansion
+    float *const cS = reinterpret_cast<float *>(cI + p.Rcap);  // their scores
+    int *const vI = reinterpret_cast<int *>(cS + p.Rcap);      // candidates that enter
+    float *const vS = reinterpret_cast<float *>(vI + p.Rcap);
+    int *const vPB = reinterpret_cast<int *>(vS + p.Rcap);     // beam members ahead of each
+    int *const sPB = cI;  // vPB in candidate-rank order (reuses cI once compacted)
     const int hmask = p.Hcap - 1;
     const int hshift = 32 - p.hbits;
     PS ps;
@@ -436,47 +716,63 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
         ps.score(cI, cS, 1, lane);
         __syncwarp();
         if (lane == 0) {
-            bS0[0] = cS[0];
-            bI0[0] = entry;
+            bS[0] = cS[0];
+            bI[0] = entry;
         }
         __syncwarp();
-        // current and spare beam buffers (swapped after every merge)
-        float *curS = bS0, *nxtS = bS1;
-        int *curI = bI0, *nxtI = bI1;
-        int size = 1, hops = 0, scored = 1;
+        // every beam member before position F is expanded
+        int size = 1, hops = 0, scored = 1, F = 0;
         const int maxh = mh > 0 ? mh : (int)(p.n < 0x7fffffff ? p.n : 0x7fffffff);
 
         while (hops < maxh) {
-            // best unexpanded member of the beam
-            int pos = -1;
-            for (int base = 0; base < size; base += 32) {
+            // the W best unexpanded members of the beam: the first ones at positions >= F
+            int par[WMAX];
+            int npar = 0;
+            const int want = min(p.W, maxh - hops);
+            for (int base = F & ~31; base < size && npar < want; base += 32) {
                 const int i = base + lane;
-                const bool un = i < size && !(curI[i] & (int)EXPANDED);
-                const unsigned bal = __ballot_sync(FULL, un);
-                if (bal) {
-                    pos = base + __ffs(bal) - 1;
-                    break;
+                const bool un = i >= F && i < size && !(bI[i] & (int)EXPANDED);
+                unsigned bal = __ballot_sync(FULL, un);
+#pragma unroll
+                for (int w = 0; w < WMAX; ++w) {
+                    if (bal && npar < want && w == npar) {
+                        par[w] = base + __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        ++npar;
+                    }
                 }
             }
-            if (pos < 0) break;
-            const int pnode = curI[pos];
+            if (npar == 0) break;
+            int pnode[WMAX];
+#pragma unroll
+            for (int w = 0; w < WMAX; ++w) pnode[w] = w < npar ? bI[par[w]] : 0;
             __syncwarp();
-            if (lane == 0) curI[pos] = pnode | (int)EXPANDED;
-            ++hops;
+            if (lane == 0)
+#pragma unroll
+                for (int w = 0; w < WMAX; ++w)
+                    if (w < npar) bI[par[w]] = pnode[w] | (int)EXPANDED;
+            F = par[0] + 1;
+#pragma unroll
+            for (int w = 1; w < WMAX; ++w)
+                if (w < npar) F = par[w] + 1;
+            hops += npar;
 
-            // neighbour ids: load all first, then test the visited cache
-            const int32_t *row = p.graph + (int64_t)pnode * p.R;
-            int nb[RMAX / 32];
+            // neighbour ids of all parents: staged in shared memory (the score buffer is
+            // free here), then tested against the visited cache parent by parent (so an id
+            // shared by two parents is seen once)
+            int *const stage = reinterpret_cast<int *>(cS);
 #pragma unroll
-            for (int t = 0; t < RMAX / 32; ++t) {
-                const int j = lane + 32 * t;
-                nb[t] = (32 * t < p.R && j < p.R) ? __ldg(row + j) : -1;
+            for (int w = 0; w < WMAX; ++w) {
+                if (w < npar) {
+                    const int32_t *row = p.graph + (int64_t)pnode[w] * p.R;
+                    for (int j = lane; j < p.R; j += 32) stage[w * p.R + j] = __ldg(row + j);
+                }
             }
+            __syncwarp();
             int cnt = 0;
-#pragma unroll
-            for (int t = 0; t < RMAX / 32; ++t) {
-                if (32 * t >= p.R) break;
-                int u = nb[t];
+            for (int j0 = 0; j0 < npar * p.R; j0 += 32) {
+                const int j = j0 + lane;
+                int u = j < npar * p.R ? stage[j] : -1;
                 bool isnew = false;
                 if (u >= 0) {
                     if (u >= p.n) {
@@ -507,6 +803,7 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
                 const unsigned bal = __ballot_sync(FULL, isnew);
                 if (isnew) cI[cnt + __popc(bal & lt)] = u;
                 cnt += __popc(bal);
+                __syncwarp();
             }
             __syncwarp();
             if (cnt == 0) continue;
@@ -519,8 +816,8 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
             float wS = 0.f;
             int wI = 0;
             if (full) {
-                wS = curS[L - 1];
-                wI = curI[L - 1] & ~(int)EXPANDED;
+                wS = bS[L - 1];
+                wI = bI[L - 1] & ~(int)EXPANDED;
             }
             int cv = 0;
             for (int j0 = 0; j0 < cnt; j0 += 32) {
@@ -536,13 +833,13 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
                         int lo = 0, hi = size;
                         while (lo < hi) {
                             const int mid = (lo + hi) >> 1;
-                            if (key_better(curS[mid], curI[mid] & ~(int)EXPANDED, s, id))
+                            if (key_better(bS[mid], bI[mid] & ~(int)EXPANDED, s, id))
                                 lo = mid + 1;
                             else
                                 hi = mid;
                         }
                         pb = lo;
-                        if (pb < size && (curI[pb] & ~(int)EXPANDED) == id) valid = false;
+                        if (pb < size && (bI[pb] & ~(int)EXPANDED) == id) valid = false;
                     }
                 }
                 const unsigned bal = __ballot_sync(FULL, valid);
@@ -556,45 +853,87 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
             }
             __syncwarp();
             if (cv == 0) continue;
-            // candidates: position = rank among candidates + beam members ahead of it
+            // an id can appear twice in one round only if the visited cache forgot it
+            // between two parents: keep the first copy
+            if (p.W > 1) {
+                for (int j = lane; j < cv; j += 32) {
+                    const int id = vI[j];
+                    bool dup = false;
+                    for (int u = 0; u < j; ++u) dup |= vI[u] == id;
+                    if (dup) vPB[j] = -1;
+                }
+                __syncwarp();
+                int cv2 = 0;
+                for (int j0 = 0; j0 < cv; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool keep = j < cv && vPB[j] >= 0;
+                    float s = 0.f;
+                    int id = 0, pb = 0;
+                    if (keep) {
+                        s = vS[j];
+                        id = vI[j];
+                        pb = vPB[j];
+                    }
+                    const unsigned bal = __ballot_sync(FULL, keep);
+                    __syncwarp();
+                    if (keep) {
+                        const int o = cv2 + __popc(bal & lt);
+                        vI[o] = id;
+                        vS[o] = s;
+                        vPB[o] = pb;
+                    }
+                    cv2 += __popc(bal);
+                    __syncwarp();
+                }
+                cv = cv2;
+            }
+            // rank of each candidate among the candidates; sPB[rank] = beam members ahead
+            int *const rnk = reinterpret_cast<int *>(cS);  // scores were copied to vS
             for (int j = lane; j < cv; j += 32) {
                 const float s = vS[j];
                 const int id = vI[j];
                 int rank = 0;
-                for (int t = 0; t < cv; ++t) rank += key_better(vS[t], vI[t], s, id) ? 1 : 0;
-                const int np = rank + vPB[j];
+                for (int u = 0; u < cv; ++u) rank += key_better(vS[u], vI[u], s, id) ? 1 : 0;
+                rnk[j] = rank;
                 sPB[rank] = vPB[j];
-                if (np < L) {
-                    nxtS[np] = s;
-                    nxtI[np] = id;
-                }
             }
             __syncwarp();
-            // beam members: position = own index + candidates ahead of it
-            for (int i = lane; i < size; i += 32) {
-                int lo = 0, hi = cv;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sPB[mid] <= i)
-                        lo = mid + 1;
-                    else
-                        hi = mid;
+            // move beam members (in place, last chunk first; a member only moves right)
+            const int first = sPB[0];
+            for (int base = (size - 1) & ~31; base >= (first & ~31); base -= 32) {
+                const int i = base + lane;
+                float s = 0.f;
+                int id = 0, np = L;
+                if (i >= first && i < size) {
+                    s = bS[i];
+                    id = bI[i];
+                    int lo = 0, hi = cv;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sPB[mid] <= i)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    np = i + lo;
                 }
-                const int np = i + lo;
+                __syncwarp();
                 if (np < L) {
-                    nxtS[np] = curS[i];
-                    nxtI[np] = curI[i];
+                    bS[np] = s;
+                    bI[np] = id;
+                }
+                __syncwarp();
+            }
+            // place the candidates (unexpanded)
+            for (int j = lane; j < cv; j += 32) {
+                const int np = rnk[j] + vPB[j];
+                if (np < L) {
+                    bS[np] = vS[j];
+                    bI[np] = vI[j];
                 }
             }
             size = min(L, size + cv);
-            {
-                float *ts = curS;
-                curS = nxtS;
-                nxtS = ts;
-                int *ti = curI;
-                curI = nxtI;
-                nxtI = ti;
-            }
+            F = min(F, first);
             __syncwarp();
         }
 
@@ -603,8 +942,8 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
         float *osc = p.scores + qi * p.ldo;
         if (BUILD) {
             for (int t = lane; t < L; t += 32) {
-                oid[t] = t < size ? (curI[t] & ~(int)EXPANDED) : -1;
-                osc[t] = t < size ? curS[t] : -INFINITY;
+                oid[t] = t < size ? (bI[t] & ~(int)EXPANDED) : -1;
+                osc[t] = t < size ? bS[t] : -INFINITY;
             }
         } else {
             int nres;
@@ -612,29 +951,20 @@ __global__ void __launch_bounds__(256) beam_kernel(const BeamParams p) {
                 const int nr = min(r, size);
                 float *rS = reinterpret_cast<float *>(hash);
                 int *rI = hash + p.Lcap;
-                for (int t = lane; t < nr; t += 32) rI[t] = curI[t] & ~(int)EXPANDED;
+                for (int t = lane; t < nr; t += 32) rI[t] = bI[t] & ~(int)EXPANDED;
                 __syncwarp();
-                WarpScorer<2, 1> sc;
+                SecIntScorer sc;
                 const float4 kq = p.qconst[qi];
-                sc.setup_row(p.Q + qi * p.D, p.D, p.sec_chunks, p.sec, p.sec_stride, kq.z, kq.w, lane);
+                sc.setup(p.Q + qi * p.D, p.D, p.sec_chunks, p.sec, p.sec_stride, kq.z, kq.w, lane);
                 sc.score(rI, rS, nr, lane);
                 __syncwarp();
-                for (int t = lane; t < nr; t += 32) {
-                    const float s = rS[t];
-                    const int id = rI[t];
-                    int rank = 0;
-                    for (int u = 0; u < nr; ++u) rank += key_better(rS[u], rI[u], s, id) ? 1 : 0;
-                    if (rank < k) {
-                        oid[rank] = id;
-                        osc[rank] = s;
-                    }
-                }
+                warp_topk(rS, rI, nr, k, oid, osc, lane);
                 nres = min(k, nr);
             } else {
                 nres = min(k, size);
                 for (int t = lane; t < nres; t += 32) {
-                    oid[t] = curI[t] & ~(int)EXPANDED;
-                    osc[t] = curS[t];
+                    oid[t] = bI[t] & ~(int)EXPANDED;
+                    osc[t] = bS[t];
                 }
             }
             for (int t = nres + lane; t < p.ldo; t += 32) {

@@ -8,6 +8,7 @@ template <int NC, int BITS>
 static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
     auto k = beam_kernel<BuildScorer<NC, BITS>, true, false>;
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
     LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     if (per_sm < 1) return fail(LV_ERR_CAPACITY, "build: beam/visited capacity does not fit in shared memory");

@@ -558,6 +558,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     bp.Hcap = hs;
     bp.hbits = 0;
     while ((1 << bp.hbits) < hs) bp.hbits++;
+    bp.W = 1;
     bp.Rcap = (int)round_up(R, 32);
     bp.warp_smem = beam_warp_smem(bp.Lcap, bp.Hcap, bp.Rcap);
     int warps = 8;

@@ -8,6 +8,7 @@ template <int NCW>
 static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
     auto k = beam_kernel<WarpScorer<NCW, 0>, false, false>;
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
     LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     if (per_sm < 1) return fail(LV_ERR_CAPACITY, "search: beam/visited capacity does not fit in shared memory");

@@ -127,7 +127,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         if (params->hash_slots > 0) {
             hs = params->hash_slots;
         } else {
-            while (hs < 8 * u.L && hs < 8192) hs <<= 1;
+            while (hs < 4 * u.L && hs < 8192) hs <<= 1;
         }
         if (hs & (hs - 1)) {
             rc = fail(LV_ERR_ARG, "search_noalloc: hash_slots must be a power of two");
@@ -137,7 +137,12 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         p.Hcap = hs;
         p.hbits = 0;
         while ((1 << p.hbits) < hs) p.hbits++;
-        p.Rcap = (int)round_up(idx->R, 32);
+        p.W = params->width > 0 ? params->width : 1;
+        if (p.W > WMAX || p.W * idx->R > CMAX) {
+            rc = fail(LV_ERR_ARG, "search_noalloc: need width <= 4 and width * R <= 256");
+            break;
+        }
+        p.Rcap = (int)round_up((int64_t)p.W * idx->R, 32);
         p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap);
         int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
         while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;

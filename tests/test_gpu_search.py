@@ -84,6 +84,22 @@ def test_ids_match_oracle(lv, pb, L, r):
     assert np.all(st[:, 1] >= 1)
 
 
+@pytest.mark.parametrize("W", [2, 4])
+def test_search_width_matches_oracle(lv, pb, W):
+    """Expanding the W best unexpanded members per round: same result as the oracle's
+    width-W rule, also with a tiny visited cache (cross-parent forgotten ids)."""
+    idx = gpu_index(lv, pb)
+    ref = oracle.search(pb["graph"], pb["entry"], _qp(pb), k=10, L=48, rerank=48, prim=pb["prim"], sec=pb["sec"],
+                        qs=pb["Q"].astype(np.float64), width=W)
+    for hs in (0, 128):
+        ids, sc, st = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48, width=W, stats=True, hash_slots=hs)
+        ids = ids.cpu().numpy()
+        assert (ids == ref["ids"]).mean() >= 0.99
+        assert np.abs(st[:, 0].cpu().numpy() - ref["hops"]).mean() <= 0.5
+    with pytest.raises(lv.LeanVecError):
+        idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, width=5)
+
+
 def test_small_hash_still_exact(lv, pb):
     """A tiny visited cache forgets often; the beam (hence the result) is unchanged."""
     idx = gpu_index(lv, pb)

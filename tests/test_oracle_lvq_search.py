@@ -98,6 +98,40 @@ def test_beam_search_full_window_equals_bruteforce(oracle_lib):
         assert res["beam_ids"][j, len(reach):].tolist() == [-1] * (n - len(reach))
 
 
+def test_search_width_full_window_and_python_replay(oracle_lib):
+    """Any search width explores every reachable node when L >= n; at small L the C
+    oracle equals a direct Python replay of the width-W rule."""
+    rng = np.random.default_rng(16)
+    n, D = 150, 12
+    X = rng.standard_normal((n, D)).astype(np.float32)
+    g = _connected_graph(n, 5, 3)
+    qp = rng.standard_normal((6, D))
+    full1 = oracle_lib.search(g, 0, qp, k=10, L=n, prim_vecs=X)
+    for W in (2, 4):
+        fullW = oracle_lib.search(g, 0, qp, k=10, L=n, prim_vecs=X, width=W)
+        np.testing.assert_array_equal(fullW["ids"], full1["ids"])
+    S = qp @ X.astype(np.float64).T
+    for W in (1, 3):
+        res = oracle_lib.search(g, 0, qp, k=5, L=12, prim_vecs=X, width=W)
+        for j in range(6):
+            C = {0: S[j, 0]}
+            exp, vis = set(), {0}
+            while True:
+                order = sorted(C, key=lambda u: (-C[u], u))
+                par = [u for u in order if u not in exp][:W]
+                if not par:
+                    break
+                exp.update(par)
+                for p in par:
+                    for u in g[p]:
+                        if u >= 0 and u not in vis:
+                            vis.add(int(u))
+                            C[int(u)] = S[j, u]
+                C = {u: C[u] for u in sorted(C, key=lambda u: (-C[u], u))[:12]}
+            top = sorted(C, key=lambda u: (-C[u], u))[:5]
+            assert res["ids"][j].tolist() == top
+
+
 def test_identity_projection_exact_search(oracle_lib):
     """A = B = I at d = D with raw fp32 primaries: the full-window search equals the
     exact brute force over X (Sec. 2: the approximation becomes an identity)."""
