@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hash", type=int, default=0, help="visited-cache slots per query (0 = library default)")
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
+    ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
+                    help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
@@ -300,16 +302,17 @@ def main():
 
     S = setup(args, dev)
     lv, idx, base, Q, A, truth = S["lv"], S["idx"], S["base"], S["Q"], S["A"], S["truth"]
+    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
     m = Q.shape[0]
     k = 10
     if args.profile:
         L = args.L or 64
         for _ in range(args.warmup):
-            idx.search(Q, A, k=k, L=L, rerank=L)
+            idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, hash_slots=args.hash, projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
-            idx.search(Q, A, k=k, L=L, rerank=L)
+            idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, hash_slots=args.hash, projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile": True, "L": L, "n": args.n, "m": m, "steps": args.steps}), flush=True)
@@ -324,7 +327,7 @@ def main():
         trace = [(L, rec)]
     else:
         L, trace = calibrate(lambda L: idx.search(Q, A, k=k, L=L, rerank=L, width=args.width,
-                                                  hash_slots=args.hash)[0], truth, k)
+                                                  hash_slots=args.hash, projection=proj)[0], truth, k)
         if L is None:
             L = L_GRID[-1]
     rec = dict(trace)[L]
@@ -336,7 +339,7 @@ def main():
     log(f"FP32   L={Lb} recall={rec_b:.4f}  trace={trace_b}")
 
     # -- per-query work (untimed run with counters)
-    _, _, st = idx.search(Q, A, k=k, L=L, rerank=L, stats=True, hash_slots=args.hash, width=args.width)
+    _, _, st = idx.search(Q, A, k=k, L=L, rerank=L, stats=True, hash_slots=args.hash, width=args.width, projection=proj)
     hops = float(st[:, 0].double().mean())
     scored = float(st[:, 1].double().mean())
     inf = idx.info()
@@ -344,7 +347,7 @@ def main():
         L * inf["secondary_stride"] + args.D * 4 + k * 8
 
     def step(ev):
-        idx.search(Q, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), events=ev, hash_slots=args.hash, width=args.width)
+        idx.search(Q, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), events=ev, hash_slots=args.hash, width=args.width, projection=proj)
 
     if world > 1:
         torch.distributed.barrier()
@@ -368,7 +371,7 @@ def main():
 
     def step_e2e(ev):
         Qd.copy_(Qh, non_blocking=True)
-        idx.search(Qd, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), hash_slots=args.hash, width=args.width)
+        idx.search(Qd, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), hash_slots=args.hash, width=args.width, projection=proj)
         ids_h.copy_(ids_buf, non_blocking=True)
         sc_h.copy_(sc_buf, non_blocking=True)
 
@@ -401,14 +404,14 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
                    "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
-                   "L_build": args.L_build, "alpha": args.alpha, "projection": "fp32",
+                   "L_build": args.L_build, "alpha": args.alpha, "projection": args.projection,
                    "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
                 "d2h_bytes_per_step": m * k * 8},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (5 if args.projection == "bf16" else 3) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "kernel": "beam_kernel<LvqGroupScorer<3,8>,search,rerank>",

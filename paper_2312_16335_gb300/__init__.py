@@ -141,7 +141,7 @@ class Index:
 
         class _Buf:
             __cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
-                                        "data": (int(ptr), True), "version": 2, "strides": None}
+                                        "data": (int(ptr), False), "version": 2, "strides": None}
 
         torch.cuda.current_stream(self.device).synchronize()
         return torch.as_tensor(_Buf(), device=self.device).clone()

@@ -41,6 +41,8 @@ int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_
                         cudaStream_t st);
 int build_graph_impl(lv_index *idx, int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
                      cudaStream_t st);
+int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                 size_t *ws_bytes, int *status, cudaStream_t st);
 
 // Makes the index's device current for the scope of an API call.
 struct DeviceGuard {
@@ -122,8 +124,26 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
                     lv_stream_t stream) {
     if (n < 0 || D <= 0 || d <= 0 || ldy < d || (n > 0 && (!X || !P || !Y)))
         return fail(LV_ERR_ARG, "project: invalid sizes or null pointer");
-    if (precision != LV_PREC_FP32) return fail(LV_ERR_ARG, "project: only LV_PREC_FP32 is available in this build");
-    return launch_project_fp32(X, n, D, P, d, Y, ldy, (cudaStream_t)stream);
+    if (precision == LV_PREC_FP32) return launch_project_fp32(X, n, D, P, d, Y, ldy, (cudaStream_t)stream);
+    if (precision != LV_PREC_BF16) return fail(LV_ERR_ARG, "project: precision must be LV_PREC_FP32 or LV_PREC_BF16");
+    if (n == 0) return LV_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *ws = nullptr;
+    size_t wsb = 0;
+    int *status = nullptr;
+    int h_status = 0;
+    int rc = LV_OK;
+    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return fail(LV_ERR_OOM, "project: allocation failed");
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "project: memset failed");
+    if (rc == LV_OK) rc = project_bf16(X, n, D, P, d, Y, ldy, &ws, &wsb, status, st);
+    if (rc == LV_OK && cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = fail(LV_ERR_CUDA, "project: status copy failed");
+    if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "project: sync failed");
+    if (rc == LV_OK && h_status) rc = fail(LV_ERR_TIMEOUT, "project: a tensor-core pipeline wait timed out");
+    cudaStreamSynchronize(st);
+    cudaFree(ws);
+    cudaFree(status);
+    return rc;
 }
 
 int leanvec_index_create(lv_index **out, int device) {
@@ -305,8 +325,8 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     if (D <= 0 || d <= 0 || d > D) return fail(LV_ERR_ARG, "encode: need 0 < d <= D");
     if (primary_bits != 4 && primary_bits != 8) return fail(LV_ERR_ARG, "encode: primary_bits must be 4 or 8");
     if (secondary_bits != 0 && secondary_bits != 8) return fail(LV_ERR_ARG, "encode: secondary_bits must be 0 or 8");
-    if (projection_precision != LV_PREC_FP32)
-        return fail(LV_ERR_ARG, "encode: only LV_PREC_FP32 projection is available in this build");
+    if (projection_precision != LV_PREC_FP32 && projection_precision != LV_PREC_BF16)
+        return fail(LV_ERR_ARG, "encode: projection precision must be LV_PREC_FP32 or LV_PREC_BF16");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "encode: cannot select device");
     cudaStream_t st = (cudaStream_t)stream;
@@ -314,7 +334,11 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     int rc = LV_OK;
     index_free_stores(idx);
     LV_TRYC(cudaMalloc(&Y, sizeof(float) * (size_t)n * d));
-    LV_TRY(launch_project_fp32(X, n, D, B, d, Y, d, st));
+    if (projection_precision == LV_PREC_BF16) {
+        LV_TRY(project_bf16(X, n, D, B, d, Y, d, &idx->bws, &idx->bws_bytes, idx->status, st));
+    } else {
+        LV_TRY(launch_project_fp32(X, n, D, B, d, Y, d, st));
+    }
     LV_TRY(set_primary_impl(idx, Y, n, d, nullptr, primary_bits, D, st));
     if (secondary_bits) LV_TRY(set_secondary_impl(idx, X, n, D, nullptr, st));
 cleanup:
@@ -424,8 +448,8 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (!desc && (u.k < 1 || u.k > u.L || u.k > ldo || u.rerank < 0 || u.rerank > u.L || u.max_hops < 0))
         return fail(LV_ERR_ARG, "search: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search: rerank needs a secondary store");
-    if (params->projection != LV_PREC_FP32)
-        return fail(LV_ERR_ARG, "search: only LV_PREC_FP32 projection is available in this build");
+    if (params->projection != LV_PREC_FP32 && params->projection != LV_PREC_BF16)
+        return fail(LV_ERR_ARG, "search: projection precision must be LV_PREC_FP32 or LV_PREC_BF16");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "search: cannot select device");
     cudaStream_t st = (cudaStream_t)stream;
@@ -439,6 +463,8 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (rc) return rc;
     if (idx->pbits == 32) {
         rc = launch_pad_rows(Q, m, idx->D, idx->ws_q, ldq, st);
+    } else if (params->projection == LV_PREC_BF16) {
+        rc = project_bf16(Q, m, idx->D, A, idx->d, idx->ws_q, ldq, &idx->bws, &idx->bws_bytes, idx->status, st);
     } else {
         rc = launch_project_fp32(Q, m, idx->D, A, idx->d, idx->ws_q, ldq, st);
     }

@@ -294,6 +294,8 @@ done:
     return rc;
 }
 
+int second_moment_bf16(const float *X, int64_t n, int D, float *K, int *status, cudaStream_t st);
+
 int launch_f32_to_f64(const float *a, int64_t n, double *b, cudaStream_t st) {
     f32_to_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, b);
     LV_CHECK_LAUNCH("f32_to_f64_kernel");
@@ -314,8 +316,19 @@ extern "C" {
 
 int leanvec_second_moment(const float *X, int64_t n, int D, float *K, int precision, lv_stream_t stream) {
     if (!X || !K || n <= 0 || D <= 0) return fail(LV_ERR_ARG, "second_moment: invalid sizes or null pointer");
-    if (precision != LV_PREC_FP32) return fail(LV_ERR_ARG, "second_moment: only LV_PREC_FP32 is available in this build");
-    return launch_gram_fp32(X, n, D, K, (cudaStream_t)stream);
+    if (precision == LV_PREC_FP32) return launch_gram_fp32(X, n, D, K, (cudaStream_t)stream);
+    if (precision != LV_PREC_BF16) return fail(LV_ERR_ARG, "second_moment: precision must be LV_PREC_FP32 or LV_PREC_BF16");
+    cudaStream_t st = (cudaStream_t)stream;
+    int *status = nullptr, h = 0;
+    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return fail(LV_ERR_OOM, "second_moment: allocation failed");
+    int rc = cudaMemsetAsync(status, 0, sizeof(int), st) == cudaSuccess ? LV_OK : fail(LV_ERR_CUDA, "memset failed");
+    if (rc == LV_OK) rc = second_moment_bf16(X, n, D, K, status, st);
+    if (rc == LV_OK && cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = fail(LV_ERR_CUDA, "second_moment: status copy failed");
+    if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "second_moment: sync failed");
+    if (rc == LV_OK && h) rc = fail(LV_ERR_TIMEOUT, "second_moment: a tensor-core pipeline wait timed out");
+    cudaFree(status);
+    return rc;
 }
 
 int leanvec_eigh(const double *K, int D, double *evals, double *evecs, lv_stream_t stream) {

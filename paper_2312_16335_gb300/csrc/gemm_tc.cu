@@ -1,0 +1,381 @@
+// BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
+//   C[M x N] (float32) = A[M x K] * B[N x K]^T,  A and B bf16, K-major (K contiguous).
+// Used for the dense contractions of the path: the query projection q -> A q and the
+// database projection x -> B x (Eq. 1), and the second moments K = sum x x^T
+// (Sec. 2.2 "Efficiency", as Xt * Xt^T with Xt = X^T in bf16).
+//
+// One CTA (4 warps) owns a 128 x BN output tile and a range of K (split-K):
+//   warp 0, one thread : TMA producer, 4-stage ring of (A 128x64, B BNx64) bf16 tiles
+//                        in 128-byte-swizzled shared memory, mbarrier transaction counts;
+//   warp 1, one thread : issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction)
+//                        with the float32 accumulator in tensor memory; tcgen05.commit
+//                        releases each stage and finally signals the epilogue;
+//   all 4 warps        : epilogue, tcgen05.ld of their 32 TMEM lanes, float32 stores.
+// Every mbarrier wait is bounded: on time-out the kernel records LV status TIMEOUT,
+// skips its remaining work, waits (bounded) for its own copies and frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace lv {
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr long long TC_SPIN_LIMIT = 1ll << 22;  // try_wait may suspend: keeps a give-up within seconds
+
+struct TcParams {
+    int M, N, K;
+    int BN;
+    int kb_per_split;
+    float *C;        // direct output (split == 1) ...
+    int ldc;
+    float *partial;  // ... or partial[split][M][N] (split > 1)
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with parity `parity`; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(const void *p) {
+    const uint64_t a = smem_u32(p);
+    uint64_t d = (a >> 4) & 0x3FFFull;
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused with 128B swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // version
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor, kind::f16: D float32, A and B bf16, both K-major, M = 128
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                        const TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int BN = p.BN;
+    const uint32_t a_bytes = TC_BM * TC_BK * 2, b_bytes = (uint32_t)BN * TC_BK * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;  // multiple of 1024 (BN % 16 == 0... and BN*128 % 1024 == 0)
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + TC_STAGES * stage_bytes);
+    uint64_t *empty = full + TC_STAGES;
+    uint64_t *accum = empty + TC_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    const int total_kb = (p.K + TC_BK - 1) / TC_BK;
+    const int kb0 = blockIdx.z * p.kb_per_split;
+    const int nkb = min(kb0 + p.kb_per_split, total_kb) - kb0;
+    uint32_t tcols = 32;
+    while (tcols < (uint32_t)BN) tcols <<= 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (nkb > 0 && warp == 0 && lane == 0) {
+        // producer
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % TC_STAGES;
+            if (kb >= TC_STAGES && !mbar_wait(empty + s, ((kb / TC_STAGES) - 1) & 1)) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            if (*abort_flag) break;
+            uint8_t *sa = base + s * stage_bytes;
+            mbar_expect_tx(full + s, stage_bytes);
+            const int kx = (kb0 + kb) * TC_BK;  // multiple of 64 elements = 128 bytes
+            tma_load_2d(sa, &ta, kx, m0, full + s);
+            tma_load_2d(sa + a_bytes, &tb, kx, n0, full + s);
+        }
+    } else if (nkb > 0 && warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_bf16(TC_BM, BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % TC_STAGES;
+            if (!mbar_wait(full + s, (kb / TC_STAGES) & 1)) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t *sa = base + s * stage_bytes;
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+                const uint64_t ad = sdesc(sa + 32 * k);
+                const uint64_t bd = sdesc(sa + a_bytes + 32 * k);
+                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(empty + s))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(accum))
+                     : "memory");
+    }
+    __syncwarp();
+
+    // epilogue: TMEM lane = output row of the tile, one warp per 32 lanes
+    bool ok = nkb > 0 && mbar_wait(accum, 0) && !*abort_flag;
+    if (nkb > 0 && !ok && threadIdx.x == 0) atomicOr(p.status, ST_TIMEOUT);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+    if (ok) {
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < p.M) {
+                const int col0 = n0 + c0;
+                float *dst = p.partial ? p.partial + ((int64_t)blockIdx.z * p.M + row) * p.N + col0
+                                       : p.C + (int64_t)row * p.ldc + col0;
+                const int ncol = p.partial ? p.N : p.N;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (col0 + j < ncol) dst[j] = __uint_as_float(r[j]);
+            }
+        }
+    } else if (nkb > 0 && warp == 0 && lane == 0) {
+        // drain: wait (bounded) for the copies this CTA may still have in flight
+        for (int s = 0; s < TC_STAGES && s < nkb; ++s) mbar_wait(full + s, 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+// sum of the split-K partials in a fixed order
+__global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, float *__restrict__ C,
+                                     int ldc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M * N) return;
+    const int r = (int)(t / N), c = (int)(t % N);
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * M * N + t];
+    C[(int64_t)r * ldc + c] = s;
+}
+
+// float32 rows (n x D, stride D) -> bf16 rows (n x ldo, zero-padded)
+__global__ void cast_bf16_kernel(const float *__restrict__ X, int64_t n, int D, __nv_bfloat16 *__restrict__ Y, int ldo) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * ldo) return;
+    const int64_t r = t / ldo;
+    const int c = (int)(t % ldo);
+    Y[t] = __float2bfloat16_rn(c < D ? X[r * D + c] : 0.f);
+}
+
+// float32 X (n x D) -> bf16 X^T (D x ldo), ldo >= n, zero-padded; 32 x 32 tiles
+__global__ void cast_transpose_bf16_kernel(const float *__restrict__ X, int64_t n, int D,
+                                           __nv_bfloat16 *__restrict__ Y, int64_t ldo) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i;
+        const int c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < n && c < D) ? X[r * D + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < D && r < ldo) Y[(int64_t)c * ldo + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+    }
+}
+
+// ------------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+// 2-D bf16 tensor map over rows x cols (cols contiguous, row stride ld elements).
+static int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled unavailable");
+    if (((uintptr_t)ptr & 15) || (ld * 2) % 16) return fail(LV_ERR_ARG, "tcgen05 GEMM: operands must be 16-byte aligned");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled failed");
+    return LV_OK;
+}
+
+static size_t tc_smem(int BN) { return (size_t)TC_STAGES * (TC_BM + BN) * TC_BK * 2 + 256 + 1024; }
+
+// C = A B^T with A (M x K, lda), B (N x K, ldb) bf16 device arrays; C float32 (ldc).
+// `work` (nullable) holds split-K partials: splits * M * N floats.
+int gemm_bf16_tc(const __nv_bfloat16 *A, int64_t M, int64_t lda, const __nv_bfloat16 *B, int N, int64_t ldb, int64_t K,
+                 float *C, int ldc, int splits, float *work, int *status, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return fail(LV_ERR_ARG, "tcgen05 GEMM: empty operand");
+    if (M >= (int64_t)1 << 31 || K >= (int64_t)1 << 31) return fail(LV_ERR_ARG, "tcgen05 GEMM: sizes too large");
+    int BN = N <= 256 ? (int)round_up(N, 16) : 256;
+    while ((BN * TC_BK * 2) % 1024) BN += 16;  // keep every stage 1024-byte aligned
+    const int total_kb = (int)((K + TC_BK - 1) / TC_BK);
+    splits = std::max(1, std::min(splits, total_kb));
+    if (splits > 1 && !work) splits = 1;
+    const int kbps = (total_kb + splits - 1) / splits;
+    splits = (total_kb + kbps - 1) / kbps;
+    CUtensorMap ta, tb;
+    int rc = make_map(&ta, A, M, K, lda, TC_BM);
+    if (rc) return rc;
+    rc = make_map(&tb, B, N, K, ldb, BN);
+    if (rc) return rc;
+    TcParams p;
+    p.M = (int)M;
+    p.N = N;
+    p.K = (int)K;
+    p.BN = BN;
+    p.kb_per_split = kbps;
+    p.C = C;
+    p.ldc = ldc;
+    p.partial = splits > 1 ? work : nullptr;
+    p.status = status;
+    const size_t sm = tc_smem(BN);
+    LV_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
+    gemm_bf16_tc_kernel<<<grid, 128, sm, st>>>(ta, tb, p);
+    LV_CHECK_LAUNCH("gemm_bf16_tc_kernel");
+    if (splits > 1) {
+        splitk_reduce_kernel<<<(unsigned)((M * N + 255) / 256), 256, 0, st>>>(work, splits, (int)M, N, C, ldc);
+        LV_CHECK_LAUNCH("splitk_reduce_kernel");
+    }
+    return LV_OK;
+}
+
+int launch_cast_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *Y, int ldo, cudaStream_t st) {
+    const int64_t tot = n * ldo;
+    cast_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, n, D, Y, ldo);
+    LV_CHECK_LAUNCH("cast_bf16_kernel");
+    return LV_OK;
+}
+
+int launch_cast_transpose_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *Y, int64_t ldo, cudaStream_t st) {
+    dim3 grd((unsigned)((ldo + 31) / 32), (unsigned)((D + 31) / 32));
+    cast_transpose_bf16_kernel<<<grd, dim3(32, 8), 0, st>>>(X, n, D, Y, ldo);
+    LV_CHECK_LAUNCH("cast_transpose_bf16_kernel");
+    return LV_OK;
+}
+
+int ensure_ws(void **p, size_t *have, size_t want);
+
+// Y (n x ldy) = X P^T with bf16 operands on the tensor cores; columns d..ldy-1 zeroed.
+// The bf16 copies of X and P live in the caller's workspace (*ws, grown as needed).
+int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                 size_t *ws_bytes, int *status, cudaStream_t st) {
+    const int ldx = (int)round_up(D, 8);
+    const size_t xb = round_up((int64_t)n * ldx * 2, 256), pb = round_up((int64_t)d * ldx * 2, 256);
+    int rc = ensure_ws(ws, ws_bytes, xb + pb);
+    if (rc) return rc;
+    __nv_bfloat16 *Xb = reinterpret_cast<__nv_bfloat16 *>(*ws);
+    __nv_bfloat16 *Pb = reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<uint8_t *>(*ws) + xb);
+    rc = launch_cast_bf16(X, n, D, Xb, ldx, st);
+    if (rc) return rc;
+    rc = launch_cast_bf16(P, d, D, Pb, ldx, st);
+    if (rc) return rc;
+    if (ldy > d) LV_CUDA(cudaMemset2DAsync(Y + d, (size_t)ldy * 4, 0, (size_t)(ldy - d) * 4, (size_t)n, st));
+    return gemm_bf16_tc(Xb, n, ldx, Pb, d, ldx, D, Y, ldy, 1, nullptr, status, st);
+}
+
+// K (D x D) = X^T X over the n rows of X with bf16 operands (X^T staged in bf16).
+int second_moment_bf16(const float *X, int64_t n, int D, float *K, int *status, cudaStream_t st) {
+    const int64_t ldt = round_up(n, 8);
+    const int tiles = (int)(((D + TC_BM - 1) / TC_BM) * ((D + 255) / 256));
+    const int splits = std::max(1, std::min(64, 148 / std::max(1, tiles)));
+    __nv_bfloat16 *Xt = nullptr;
+    float *work = nullptr;
+    int rc = LV_OK;
+    if (cudaMallocAsync((void **)&Xt, (size_t)D * ldt * 2, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&work, sizeof(float) * (size_t)splits * D * D, st) != cudaSuccess)
+        rc = fail(LV_ERR_OOM, "second_moment: allocation failed");
+    if (rc == LV_OK) rc = launch_cast_transpose_bf16(X, n, D, Xt, ldt, st);
+    if (rc == LV_OK) rc = gemm_bf16_tc(Xt, D, ldt, Xt, D, ldt, n, K, D, splits, work, status, st);
+    if (Xt) cudaFreeAsync(Xt, st);
+    if (work) cudaFreeAsync(work, st);
+    return rc;
+}
+
+}  // namespace lv

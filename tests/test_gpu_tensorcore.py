@@ -1,0 +1,82 @@
+"""The BF16 tcgen05 GEMM (projection q -> A q / x -> B x and second moments K = X^T X)
+against FP64 references.
+
+Tolerance: bf16 keeps 8 significant bits, so each operand carries a relative error
+<= 2^-9; a dot product of two rounded vectors is then off by at most about
+2 * 2^-9 * sum|x_i p_i| <= 2^-8 * ||x|| * ||p||.  The tests use 2^-7 * ||x|| * ||p||."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import gpu_index, small_problem, t
+from oracle import fit
+
+pytestmark = pytest.mark.gpu
+TOL = 2.0 ** -7
+
+
+@pytest.fixture(scope="module")
+def lv():
+    import paper_2312_16335_gb300 as lv
+    return lv
+
+
+@pytest.mark.parametrize("n,D,d,ldy", [(300, 128, 32, 32), (1000, 768, 160, 160), (77, 200, 64, 80),
+                                       (5000, 512, 128, 128), (129, 64, 16, 16), (1, 768, 160, 176)])
+def test_projection_bf16(lv, n, D, d, ldy):
+    rng = np.random.default_rng(n + D + d)
+    X = rng.standard_normal((n, D)).astype(np.float32)
+    P = rng.standard_normal((d, D)).astype(np.float32)
+    Y = lv.leanvec_project(t(X), t(P), ldy=ldy, precision=lv.PREC_BF16).cpu().numpy()
+    ref = X.astype(np.float64) @ P.T.astype(np.float64)
+    bound = TOL * np.linalg.norm(X, axis=1)[:, None] * np.linalg.norm(P, axis=1)[None, :]
+    assert np.all(np.abs(Y[:, :d] - ref) <= bound)
+    assert not Y[:, d:].any()
+    # and not merely within tolerance by luck: the error is of the bf16 size, not zero
+    assert np.abs(Y[:, :d] - ref).max() > 0
+
+
+@pytest.mark.parametrize("n,D", [(1000, 64), (20000, 768), (3001, 200)])
+def test_second_moment_bf16(lv, n, D):
+    rng = np.random.default_rng(n * 7 + D)
+    X = rng.standard_normal((n, D)).astype(np.float32)
+    K = lv.leanvec_second_moment(t(X), precision=lv.PREC_BF16).cpu().numpy().astype(np.float64)
+    ref = fit.second_moment(X)
+    norms = np.linalg.norm(X, axis=0)
+    assert np.all(np.abs(K - ref) <= TOL * np.outer(norms, norms))
+    np.testing.assert_allclose(K, K.T, rtol=0, atol=1e-3 * norms.max() ** 2)
+
+
+def test_search_with_bf16_projection(lv):
+    """BF16 query projection: the candidates may differ slightly from the FP64-projected
+    oracle, the rerank restores FP32-accurate final scores; recall stays within 0.01."""
+    pb = small_problem(oracle, n=3000, D=64, d=16, m=300)
+    idx = gpu_index(lv, pb)
+    ids, sc = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48, projection=lv.PREC_BF16)
+    idx.sync_status()
+    ids = ids.cpu().numpy()
+    ref = oracle.search(pb["graph"], pb["entry"], pb["Q"].astype(np.float64) @ pb["P"].T.astype(np.float64),
+                        k=10, L=48, rerank=48, prim=pb["prim"], sec=pb["sec"], qs=pb["Q"].astype(np.float64))
+    truth, _ = oracle.bruteforce(pb["X"], pb["Q"], 10)
+    assert abs(oracle.recall(ids, truth, 10) - oracle.recall(ref["ids"], truth, 10)) <= 0.01
+    assert (ids == ref["ids"]).mean() >= 0.95
+    dec = pb["sec"].decode()
+    for j in range(ids.shape[0]):
+        exact = dec[ids[j]] @ pb["Q"][j].astype(np.float64)
+        assert np.all(np.abs(sc.cpu().numpy()[j] - exact) <= 1e-4 * np.linalg.norm(dec[ids[j]], axis=1))
+
+
+def test_encode_with_bf16_projection(lv):
+    pb = small_problem(oracle, n=2000, D=128, d=32, m=10)
+    idx = lv.Index(0).encode(t(pb["X"]), t(pb["P"]), 8, 8, precision=lv.PREC_BF16)
+    idx.sync_status()
+    rec = idx.primary_records().cpu().numpy()
+    from gpu_util import unpack_records
+    codes, delta, lower, _, _, _, _ = unpack_records(rec, 32, 8)
+    mean = idx.primary_mean().cpu().numpy().astype(np.float64)
+    dec = mean[None, :] + lower[:, None].astype(np.float64) + delta[:, None].astype(np.float64) * codes
+    Y = pb["X"].astype(np.float64) @ pb["P"].T.astype(np.float64)
+    err = np.abs(dec - Y).max(axis=1)
+    bound = delta / 2 + TOL * np.linalg.norm(pb["X"], axis=1) * np.linalg.norm(pb["P"], axis=1).max()
+    assert np.all(err <= bound)
