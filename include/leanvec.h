@@ -131,6 +131,64 @@ int leanvec_eigh(const double *K, int D, double *evals, double *evecs, lv_stream
 int leanvec_fit_id(const float *X, int64_t n, int D, int d, float *A_out, float *B_out, int precision,
                    lv_stream_t stream);
 
+/* LeanVec-OOD optimisers. */
+typedef enum {
+    LV_FIT_FW = 0,    /* Frank-Wolfe BCD from A = B = 0 (Algorithm 1) */
+    LV_FIT_ES = 1,    /* eigenvector search over beta (Algorithm 2), A = B = P */
+    LV_FIT_ES_FW = 2  /* ES, then Frank-Wolfe BCD from A = B = P with the exact line search */
+} lv_fit_method;
+
+typedef struct {
+    int32_t method;       /* lv_fit_method */
+    float alpha;          /* FW step 1 / (t + 1)^alpha, alpha in (0, 1); 0 = 0.5 */
+    float tol;            /* FW stop: |f(t+1) - f(t)| / f(t) <= tol; 0 = 1e-3 */
+    int32_t max_iter;     /* FW iteration limit; 0 = 500 */
+    int32_t line_search;  /* 1 = exact quadratic step (FP64 solve) instead of 1 / (t + 1)^alpha */
+    int32_t precision;    /* second moments: LV_PREC_FP32 or LV_PREC_BF16 */
+    double es_xatol;      /* ES Brent absolute tolerance on beta; 0 = 1e-5 */
+} lv_fit_opts;
+
+typedef struct {
+    int32_t iterations;   /* FW iterations run */
+    int32_t evaluations;  /* ES loss evaluations */
+    double beta;          /* ES: the chosen beta */
+    double loss0;         /* FW: loss at the starting point */
+    double loss;          /* final loss f(A, B) (trace form, unnormalised K_Q, K_X) */
+    double *loss_trace;   /* optional host array: loss after each FW iteration ([0] = start) */
+    int32_t trace_capacity;
+} lv_fit_report;
+
+/* LeanVec-OOD (Sec. 2.2, problems "leanvec_orthonormal" / "leanvec"): learn A, B (d x D
+ * float32, device) minimising f(A, B) = ||Q^T A^T B X - Q^T X||_F^2 through the second
+ * moments K_X (n rows of X) and K_Q (m rows of Q, the caller's learning queries),
+ * relaxed to the spectral-norm ball.  FW: block coordinate Frank-Wolfe, LMO = polar
+ * factor of -grad (Sec. 2.3; FP64 eig of C C^T); ES: Brent over beta in [0, 1] of the
+ * loss at P(beta) = the d leading eigenvectors of (1-beta)/m K_Q + beta/n K_X (Sec. 2.4;
+ * FP64 eig).  At A = B = 0 the A-gradient vanishes; its LMO then returns the LeanVec-ID
+ * solution.  rep (nullable) receives iterations / beta / losses.  Synchronises `stream`. */
+int leanvec_fit_ood(const float *X, int64_t n, const float *Q, int64_t m, int D, int d, const lv_fit_opts *opts,
+                    float *A_out, float *B_out, lv_fit_report *rep, lv_stream_t stream);
+
+/* Differentiation form of the LeanVec-OOD loss over explicit sample pairs (problem
+ * "leanvec_orthonormal" written per pair, Sec. 2.2):
+ *   r_ij = q_j^T x_i - (A q_j)^T (B x_i),  L = sum_ij r_ij^2 / (n m)
+ * over the m rows of Q (m x D) and the n rows of X (n x D), A, B d x D (all float32,
+ * device; d <= 256).  The m x n residuals are recomputed in 64 x 64 tiles, never stored.
+ * fwd writes L to *loss (host, FP64 sum of float32 tile partials; synchronises).
+ * bwd writes scale * dL/dA and scale * dL/dB (d x D, device):
+ *   dL/dA = -2/(nm) sum_ij r_ij (B x_i) q_j^T,  dL/dB = -2/(nm) sum_ij r_ij (A q_j) x_i^T
+ * (equal to Eq. "leanvec_gradients" divided by n m).  Synchronises `stream`. */
+int leanvec_ood_loss_fwd(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n,
+                         int D, int d, double *loss, lv_stream_t stream);
+int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n,
+                         int D, int d, float scale, float *gA, float *gB, lv_stream_t stream);
+
+/* Euclidean projection of A (d x D float32, device, in place) onto the spectral-norm
+ * unit ball C = {A : ||A||_op <= 1} of Eq. "stiefel_convex_hull": singular values above 1
+ * are clipped to 1 (FP64 eig of A A^T).  Keeps a gradient optimiser of the relaxed
+ * problem "leanvec" feasible.  Synchronises `stream`. */
+int leanvec_spectral_clip(float *A, int d, int D, lv_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Index                                                                     */
 /* ------------------------------------------------------------------------ */

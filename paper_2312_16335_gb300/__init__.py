@@ -13,11 +13,12 @@ import ctypes
 
 import torch
 
-from ._native import (LVIndexInfo, LVQueryDesc, LVSearchParams, LeanVecError, check, lib)
+from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearchParams, LeanVecError, check, lib)
 
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
-           "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "PREC_FP32", "PREC_BF16",
-           "PREC_FP8"]
+           "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
+           "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
+           "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 
@@ -97,6 +98,94 @@ def leanvec_fit_id(X: torch.Tensor, d: int, precision: int = PREC_FP32) -> torch
     A = torch.empty((d, X.shape[1]), dtype=torch.float32, device=X.device)
     check(lib().leanvec_fit_id(_ptr(X), X.shape[0], X.shape[1], d, _ptr(A), None, precision, _stream(X.device)))
     return A
+
+
+FIT_FW, FIT_ES, FIT_ES_FW = 0, 1, 2
+
+
+def leanvec_fit_ood(X: torch.Tensor, Q: torch.Tensor, d: int, method: int = FIT_FW, alpha: float = 0.5,
+                    tol: float = 1e-3, max_iter: int = 500, line_search: bool = False, precision: int = PREC_FP32,
+                    es_xatol: float = 1e-5):
+    """LeanVec-OOD: returns (A, B, report) learned from database rows X and learning queries Q."""
+    X, Q = _f32(X), _f32(Q)
+    D = X.shape[1]
+    A = torch.empty((d, D), dtype=torch.float32, device=X.device)
+    B = torch.empty((d, D), dtype=torch.float32, device=X.device)
+    trace = (ctypes.c_double * (max_iter + 2))()
+    rep = LVFitReport(0, 0, 0.0, 0.0, 0.0, trace, max_iter + 2)
+    opts = LVFitOpts(method, alpha, tol, max_iter, int(line_search), precision, es_xatol)
+    check(lib().leanvec_fit_ood(_ptr(X), X.shape[0], _ptr(Q), Q.shape[0], D, d, ctypes.byref(opts), _ptr(A), _ptr(B),
+                                ctypes.byref(rep), _stream(X.device)))
+    out = {"iterations": rep.iterations, "evaluations": rep.evaluations, "beta": rep.beta, "loss0": rep.loss0,
+           "loss": rep.loss, "loss_trace": [trace[i] for i in range(min(rep.iterations + 1, max_iter + 2))]}
+    return A, B, out
+
+
+def leanvec_ood_loss_fwd(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, X: torch.Tensor) -> float:
+    A, B, Q, X = _f32(A), _f32(B), _f32(Q), _f32(X)
+    out = ctypes.c_double()
+    check(lib().leanvec_ood_loss_fwd(_ptr(A), _ptr(B), _ptr(Q), Q.shape[0], _ptr(X), X.shape[0], X.shape[1],
+                                     A.shape[0], ctypes.byref(out), _stream(A.device)))
+    return out.value
+
+
+def leanvec_ood_loss_bwd(A, B, Q, X, scale: float = 1.0):
+    A, B, Q, X = _f32(A), _f32(B), _f32(Q), _f32(X)
+    gA, gB = torch.empty_like(A), torch.empty_like(B)
+    check(lib().leanvec_ood_loss_bwd(_ptr(A), _ptr(B), _ptr(Q), Q.shape[0], _ptr(X), X.shape[0], X.shape[1],
+                                     A.shape[0], float(scale), _ptr(gA), _ptr(gB), _stream(A.device)))
+    return gA, gB
+
+
+def leanvec_spectral_clip(A: torch.Tensor) -> torch.Tensor:
+    """In place: project A onto {||A||_op <= 1}."""
+    if not A.is_contiguous() or A.dtype != torch.float32:
+        raise ValueError("expected a contiguous float32 tensor")
+    check(lib().leanvec_spectral_clip(_ptr(A), A.shape[0], A.shape[1], _stream(A.device)))
+    return A
+
+
+class OODLoss(torch.autograd.Function):
+    """L(A, B) = sum_ij (q_j^T x_i - (A q_j)^T (B x_i))^2 / (n m) over the sample pairs of
+    Q (m x D) and X (n x D), with the hand-written CUDA forward and backward (pair tiles
+    recomputed, never stored).  Gradients flow to A and B only."""
+
+    @staticmethod
+    def forward(ctx, A, B, Q, X):
+        ctx.save_for_backward(A, B, Q, X)
+        return torch.tensor(leanvec_ood_loss_fwd(A.detach(), B.detach(), Q, X), dtype=torch.float32,
+                            device=A.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        A, B, Q, X = ctx.saved_tensors
+        gA, gB = leanvec_ood_loss_bwd(A.detach(), B.detach(), Q, X, float(grad_out))
+        return gA, gB, None, None
+
+
+def fit_ood_gradient(X: torch.Tensor, Q: torch.Tensor, d: int, steps: int = 100, lr: float = 1e-2,
+                     A0: torch.Tensor | None = None, B0: torch.Tensor | None = None, log=None):
+    """A gradient optimiser for LeanVec-OOD beside Frank-Wolfe: Adam on the pair loss
+    (OODLoss, hand-written fwd/bwd) with a projection onto the spectral-norm ball after
+    every step (the relaxed problem "leanvec").  Starts from LeanVec-ID unless A0/B0 given."""
+    if A0 is None:
+        A0 = leanvec_fit_id(X, d)
+    A = torch.nn.Parameter(A0.clone().contiguous())
+    B = torch.nn.Parameter((A0 if B0 is None else B0).clone().contiguous())
+    opt = torch.optim.Adam([A, B], lr=lr)
+    trace = []
+    for _ in range(steps):
+        opt.zero_grad()
+        loss = OODLoss.apply(A, B, Q, X)
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            leanvec_spectral_clip(A.data)
+            leanvec_spectral_clip(B.data)
+        trace.append(float(loss))
+        if log:
+            log(trace[-1])
+    return A.detach(), B.detach(), trace
 
 
 class Index:

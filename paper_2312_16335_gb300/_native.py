@@ -31,6 +31,17 @@ class LVIndexInfo(ctypes.Structure):
                 ("R", c_i32), ("entry", c_i32), ("mu2", c_f32), ("reserved", c_i32)]
 
 
+class LVFitOpts(ctypes.Structure):
+    _fields_ = [("method", c_i32), ("alpha", c_f32), ("tol", c_f32), ("max_iter", c_i32), ("line_search", c_i32),
+                ("precision", c_i32), ("es_xatol", ctypes.c_double)]
+
+
+class LVFitReport(ctypes.Structure):
+    _fields_ = [("iterations", c_i32), ("evaluations", c_i32), ("beta", ctypes.c_double), ("loss0", ctypes.c_double),
+                ("loss", ctypes.c_double), ("loss_trace", ctypes.POINTER(ctypes.c_double)),
+                ("trace_capacity", c_i32)]
+
+
 # (name, restype, argtypes) for every symbol of include/leanvec.h
 SIGNATURES = {
     "leanvec_last_error": (ctypes.c_char_p, []),
@@ -57,6 +68,12 @@ SIGNATURES = {
     "leanvec_second_moment": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp]),
     "leanvec_eigh": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "leanvec_fit_id": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp]),
+    "leanvec_ood_loss_fwd": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_i64, c_i32, c_i32,
+                                     ctypes.POINTER(ctypes.c_double), c_vp]),
+    "leanvec_ood_loss_bwd": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_i64, c_i32, c_i32, c_f32, c_vp, c_vp, c_vp]),
+    "leanvec_spectral_clip": (c_i32, [c_vp, c_i32, c_i32, c_vp]),
+    "leanvec_fit_ood": (c_i32, [c_vp, c_i64, c_vp, c_i64, c_i32, c_i32, ctypes.POINTER(LVFitOpts), c_vp, c_vp,
+                                ctypes.POINTER(LVFitReport), c_vp]),
 }
 
 

@@ -1,0 +1,270 @@
+// Differentiation form of the LeanVec-OOD loss over explicit sample pairs
+// (problem "leanvec_orthonormal" / Eq. "leanvec_loss" written per pair):
+//   r_ij = q_j^T x_i - (A q_j)^T (B x_i),   L = sum_ij r_ij^2 / (n m)
+//   dL/dA = -2/(nm) sum_ij r_ij (B x_i) q_j^T = -2/(nm) (R X')^T Q
+//   dL/dB = -2/(nm) sum_ij r_ij (A q_j) x_i^T = -2/(nm) (R^T Q')^T X
+// with Q' = Q A^T (m x d), X' = X B^T (n x d) and R (m x n) the residual matrix.  R is
+// never stored: 64 x 64 pair tiles are recomputed from Q, X, Q', X' (float32 CUDA-core
+// tiles; the residual is a small difference of two inner products, which bf16 / tf32
+// operands would swamp).  One kernel walks the database tiles for each query tile
+// (loss, U = R X'), another the query tiles for each database tile (V = R^T Q').
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lv {
+
+int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
+                        cudaStream_t st);
+
+constexpr int PT = 64;    // pair tile
+constexpr int PK = 16;    // k step
+constexpr int DMAX = 256; // largest d
+
+// R tile (PT x PT, rows = "row set", cols = "col set") into smem Rs:
+//   Rs[r][c] = <P_r, Q_c> - <P'_r, Q'_c>, P rows of (rows x D), P' rows of (rows x d)
+__device__ __forceinline__ void residual_tile(const float *__restrict__ P, const float *__restrict__ Pp, int64_t r0,
+                                              int64_t nr, const float *__restrict__ Qm, const float *__restrict__ Qp,
+                                              int64_t c0, int64_t nc, int D, int d, float (*As)[PT + 4],
+                                              float (*Bs)[PT + 4], float (*Rs)[PT + 1]) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int pass = 0; pass < 2; ++pass) {
+        const float *Am = pass == 0 ? P : Pp;
+        const float *Bm = pass == 0 ? Qm : Qp;
+        const int K = pass == 0 ? D : d;
+        const float sgn = pass == 0 ? 1.f : -1.f;
+        for (int k0 = 0; k0 < K; k0 += PK) {
+            for (int t = threadIdx.x; t < PK * PT; t += 256) {
+                const int kk = t % PK, i = t / PK;
+                const int64_t ra = r0 + i, cb = c0 + i;
+                const int k = k0 + kk;
+                As[kk][i] = (ra < nr && k < K) ? Am[ra * K + k] : 0.f;
+                Bs[kk][i] = (cb < nc && k < K) ? sgn * Bm[cb * K + k] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < PK; ++kk) {
+                float a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t r = r0 + ty * 4 + u, c = c0 + tx * 4 + v;
+            Rs[ty * 4 + u][tx * 4 + v] = (r < nr && c < nc) ? acc[u][v] : 0.f;
+        }
+    __syncthreads();
+}
+
+// For the row tile of this block (rows of P): loop over all column tiles, accumulate
+//   loss partial (sum r^2, when lossp != NULL) and  Out[rows] += R * Colp  (PT x d).
+__global__ void __launch_bounds__(256) pair_sweep_kernel(const float *__restrict__ P, const float *__restrict__ Pp,
+                                                         int64_t nr, const float *__restrict__ Qm,
+                                                         const float *__restrict__ Qp, int64_t nc, int D, int d,
+                                                         double *__restrict__ lossp, float *__restrict__ Out) {
+    __shared__ float As[PK][PT + 4];
+    __shared__ float Bs[PK][PT + 4];
+    __shared__ float Rs[PT][PT + 1];
+    __shared__ double red[256];
+    const int64_t r0 = (int64_t)blockIdx.x * PT;
+    // Out tile accumulators: thread owns rows (threadIdx.x / 16) * 4 + u, cols (threadIdx.x % 16) + 16 w
+    const int orow = (threadIdx.x >> 4) * 4, ocol = threadIdx.x & 15;
+    float o[4][DMAX / 16];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < DMAX / 16; ++w) o[u][w] = 0.f;
+    double ls = 0.0;
+    for (int64_t c0 = 0; c0 < nc; c0 += PT) {
+        residual_tile(P, Pp, r0, nr, Qm, Qp, c0, nc, D, d, As, Bs, Rs);
+        if (lossp) {
+            for (int t = threadIdx.x; t < PT * PT; t += 256) {
+                const float r = Rs[t / PT][t % PT];
+                ls += (double)r * (double)r;
+            }
+        }
+        if (Out) {
+            // Out[r][c] += sum_k Rs[r][k] * Qp[c0 + k][c]
+            for (int k = 0; k < PT; ++k) {
+                const int64_t ck = c0 + k;
+                if (ck >= nc) break;
+                const float *qrow = Qp + ck * d;
+                float rv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) rv[u] = Rs[orow + u][k];
+#pragma unroll
+                for (int w = 0; w < DMAX / 16; ++w) {
+                    const int c = ocol + 16 * w;
+                    if (c < d) {
+                        const float q = qrow[c];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) o[u][w] = fmaf(rv[u], q, o[u][w]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (Out) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t r = r0 + orow + u;
+            if (r >= nr) continue;
+#pragma unroll
+            for (int w = 0; w < DMAX / 16; ++w) {
+                const int c = ocol + 16 * w;
+                if (c < d) Out[r * d + c] = o[u][w];
+            }
+        }
+    }
+    if (lossp) {
+        red[threadIdx.x] = ls;
+        __syncthreads();
+        for (int s = 128; s; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) lossp[blockIdx.x] = red[0];
+    }
+}
+
+// out (d x D) = scale * M^T Y with M (rows x d), Y (rows x D): column blocks of D, rows looped
+__global__ void __launch_bounds__(256) tgemm_kernel(const float *__restrict__ M, const float *__restrict__ Y, int64_t rows,
+                                                    int d, int D, float scale, float *__restrict__ out) {
+    const int c = blockIdx.x * 64 + (threadIdx.x & 63);
+    const int r0 = (threadIdx.x >> 6);  // 4 row groups of d
+    __shared__ float Ms[32][DMAX];
+    __shared__ float Ys[32][64];
+    float acc[DMAX / 4];
+#pragma unroll
+    for (int i = 0; i < DMAX / 4; ++i) acc[i] = 0.f;
+    for (int64_t k0 = 0; k0 < rows; k0 += 32) {
+        for (int t = threadIdx.x; t < 32 * d; t += 256) {
+            const int kk = t / d, i = t % d;
+            Ms[kk][i] = (k0 + kk < rows) ? M[(k0 + kk) * d + i] : 0.f;
+        }
+        for (int t = threadIdx.x; t < 32 * 64; t += 256) {
+            const int kk = t / 64, j = t % 64;
+            const int cc = blockIdx.x * 64 + j;
+            Ys[kk][j] = (k0 + kk < rows && cc < D) ? Y[(k0 + kk) * D + cc] : 0.f;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < 32; ++kk) {
+            const float y = Ys[kk][threadIdx.x & 63];
+#pragma unroll
+            for (int i = 0; i < DMAX / 4; ++i) {
+                const int row = r0 + 4 * i;
+                if (row < d) acc[i] = fmaf(Ms[kk][row], y, acc[i]);
+            }
+        }
+        __syncthreads();
+    }
+    if (c < D) {
+#pragma unroll
+        for (int i = 0; i < DMAX / 4; ++i) {
+            const int row = r0 + 4 * i;
+            if (row < d) out[(int64_t)row * D + c] = scale * acc[i];
+        }
+    }
+}
+
+struct PairWork {
+    float *Qp = nullptr, *Xp = nullptr, *U = nullptr, *V = nullptr;
+    double *part = nullptr;
+};
+
+static int pair_prepare(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
+                        int d, PairWork &w, bool grads, cudaStream_t st) {
+    if (cudaMalloc(&w.Qp, sizeof(float) * (size_t)m * d) != cudaSuccess ||
+        cudaMalloc(&w.Xp, sizeof(float) * (size_t)n * d) != cudaSuccess ||
+        cudaMalloc(&w.part, sizeof(double) * (size_t)((m + PT - 1) / PT)) != cudaSuccess)
+        return fail(LV_ERR_OOM, "ood_loss: allocation failed");
+    if (grads && (cudaMalloc(&w.U, sizeof(float) * (size_t)m * d) != cudaSuccess ||
+                  cudaMalloc(&w.V, sizeof(float) * (size_t)n * d) != cudaSuccess))
+        return fail(LV_ERR_OOM, "ood_loss: allocation failed");
+    int rc = launch_project_fp32(Q, m, D, A, d, w.Qp, d, st);
+    if (rc) return rc;
+    return launch_project_fp32(X, n, D, B, d, w.Xp, d, st);
+}
+
+static void pair_free(PairWork &w) {
+    cudaFree(w.Qp);
+    cudaFree(w.Xp);
+    cudaFree(w.U);
+    cudaFree(w.V);
+    cudaFree(w.part);
+}
+
+}  // namespace lv
+
+using namespace lv;
+
+extern "C" {
+
+int leanvec_ood_loss_fwd(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
+                         int d, double *loss, lv_stream_t stream) {
+    if (!A || !B || !Q || !X || !loss || m <= 0 || n <= 0 || D <= 0 || d <= 0)
+        return fail(LV_ERR_ARG, "ood_loss_fwd: invalid sizes or null pointer");
+    if (d > DMAX) return fail(LV_ERR_ARG, "ood_loss_fwd: d <= 256 is supported");
+    cudaStream_t st = (cudaStream_t)stream;
+    PairWork w;
+    int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, false, st);
+    const int nb = (int)((m + PT - 1) / PT);
+    std::vector<double> part(nb);
+    if (rc == LV_OK) {
+        pair_sweep_kernel<<<nb, 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d, w.part, nullptr);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "pair_sweep_kernel");
+    }
+    if (rc == LV_OK && (cudaMemcpyAsync(part.data(), w.part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        rc = fail(LV_ERR_CUDA, "ood_loss_fwd: reduction copy failed");
+    if (rc == LV_OK) {
+        double s = 0.0;
+        for (double v : part) s += v;  // fixed order
+        *loss = s / ((double)n * (double)m);
+    }
+    pair_free(w);
+    return rc;
+}
+
+int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
+                         int d, float scale, float *gA, float *gB, lv_stream_t stream) {
+    if (!A || !B || !Q || !X || !gA || !gB || m <= 0 || n <= 0 || D <= 0 || d <= 0)
+        return fail(LV_ERR_ARG, "ood_loss_bwd: invalid sizes or null pointer");
+    if (d > DMAX) return fail(LV_ERR_ARG, "ood_loss_bwd: d <= 256 is supported");
+    cudaStream_t st = (cudaStream_t)stream;
+    PairWork w;
+    int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, true, st);
+    if (rc == LV_OK) {
+        // U = R X' (query tiles), V = R^T Q' (database tiles: rows X, cols Q, residual sign unchanged)
+        pair_sweep_kernel<<<(unsigned)((m + PT - 1) / PT), 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d, nullptr, w.U);
+        pair_sweep_kernel<<<(unsigned)((n + PT - 1) / PT), 256, 0, st>>>(X, w.Xp, n, Q, w.Qp, m, D, d, nullptr, w.V);
+        const float c = (float)(-2.0 * (double)scale / ((double)n * (double)m));
+        tgemm_kernel<<<(D + 63) / 64, 256, 0, st>>>(w.U, Q, m, d, D, c, gA);
+        tgemm_kernel<<<(D + 63) / 64, 256, 0, st>>>(w.V, X, n, d, D, c, gB);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "ood_loss_bwd kernels");
+    }
+    if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "ood_loss_bwd: sync failed");
+    pair_free(w);
+    return rc;
+}
+
+}  // extern "C"
