@@ -233,6 +233,150 @@ def cpu_oracle_sample(O, L, budget_s, nthreads=0):
             "hops_per_query": float(r["hops"].mean())}
 
 
+def bench_ood(args, dev):
+    """Shifted-query workload: 1M x 512 database, 10k OOD test + 10k learning queries, d = 128.
+    ID PCA vs LeanVec-OOD (Frank-Wolfe, eigenvector search) primaries on the same graph; plus
+    the timed pair-loss forward + backward (differentiation form) on 10k x 100k sample pairs."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    n, m, D, d = args.n, args.m, 512, 128
+    X, Q, Ql = workloads.make_workload_torch("anisotropic", n, m, D, 1000, cfg=3, device=dev, ood=True, m_learn=m)
+    sub = torch.from_numpy(workloads.subsample_rows(n, min(n, 100_000), cfg=3)).to(dev)
+    Xs = X.index_select(0, sub).contiguous()
+    truth = ground_truth(X, Q, 10)
+    fits = {}
+    t0 = time.time()
+    P = lv.leanvec_fit_id(Xs, d)
+    fits["id"] = (P, P, {"seconds": time.time() - t0})
+    for name, meth in (("ood_fw", lv.FIT_FW), ("ood_es", lv.FIT_ES)):
+        t0 = time.time()
+        A, B, rep = lv.leanvec_fit_ood(Xs, Ql, d, method=meth)
+        rep = {k: v for k, v in rep.items() if k != "loss_trace"}
+        rep["seconds"] = time.time() - t0
+        fits[name] = (A, B, rep)
+    # differentiation form: one forward + backward over 10k x 100k pairs (recomputed tiles)
+    Ap = torch.nn.Parameter(fits["id"][0].clone())
+    Bp = torch.nn.Parameter(fits["id"][1].clone())
+    torch.cuda.synchronize()
+    times = []
+    for i in range(3):
+        t0 = time.perf_counter()
+        loss = lv.OODLoss.apply(Ap, Bp, Ql, Xs)
+        loss.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    mm, nn_ = Ql.shape[0], Xs.shape[0]
+    flops = 3 * (2 * mm * nn_ * D + 2 * mm * nn_ * d) + 2 * (2 * mm * nn_ * d)  # fwd + 2 sweeps + U, V
+    diff = {"seconds": min(times[1:]), "pairs": mm * nn_, "tflops": flops / min(times[1:]) / 1e12}
+    # one graph (built on the ID primaries), primaries swapped per projection
+    idx = lv.Index(dev.index).encode(X, fits["id"][1], 8, 8, precision=lv.PREC_BF16)
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+                    seed=workloads.SEED_GRAPH + 3)
+    graph, entry = idx.get_graph()
+    res = {}
+    for name, (A, B, rep) in fits.items():
+        ix = lv.Index(dev.index).encode(X, B, 8, 8, precision=lv.PREC_BF16).set_graph(graph, entry)
+        per_L = {}
+        for L in (16, 32, 64, 128):
+            ids = ix.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=lv.PREC_BF16)[0]
+            per_L[L] = recall_at(ids, truth)
+        L90, trace = calibrate(lambda L: ix.search(Q, A, k=10, L=L, rerank=L, width=args.width,
+                                                    projection=lv.PREC_BF16)[0], truth, 10)
+        qps = None
+        if L90:
+            ms, _ = time_steps(lambda ev: ix.search(Q, A, k=10, L=L90, rerank=L90, width=args.width,
+                                                    projection=lv.PREC_BF16), 10, 3)
+            qps = Q.shape[0] * 10 / (ms / 1e3)
+        res[name] = {"recall_at_L": per_L, "L_for_0.90": L90, "qps_at_0.90": qps, "fit": rep}
+        del ix
+    out = {"metric": "recall@10 and QPS at 0.90 on shifted (OOD) queries: LeanVec-OOD vs LeanVec-ID",
+           "workload": f"ood-{n // 1000}k-512, {m} OOD test queries, {m} learning queries, 100k database samples, d=128",
+           "results": res, "differentiation": diff, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
+def ground_truth_big(X, Q, k, qchunk=8192, xchunk=131072):
+    """Exact top-k for many queries over a large database (float32, TF32 off), chunked."""
+    out = []
+    for s in range(0, Q.shape[0], qchunk):
+        out.append(ground_truth(X, Q[s:s + qchunk], k, chunk=xchunk))
+    return torch.cat(out)
+
+
+def bench_uneven(args, dev):
+    """Uneven batching: 10M x 200 database (text-to-image shape, OOD queries), LeanVec-OOD
+    d = 64 LVQ-8; 50k queries with k in {1, 10, 100} and L uniform in [20, 300] (L >= k,
+    rerank = L) served by one persistent launch captured in a CUDA graph; launch shape and
+    visited-cache size picked by the autotuner."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    n, m, D, d = args.n, args.m, 200, 64
+    t0 = time.time()
+    X, Q, Ql = workloads.make_workload_torch("anisotropic", n, m, D, 1000, cfg=5, device=dev, ood=True,
+                                             m_learn=10_000)
+    sub = torch.from_numpy(workloads.subsample_rows(n, min(n, 100_000), cfg=5)).to(dev)
+    t_data = time.time() - t0
+    t0 = time.time()
+    A, B, rep = lv.leanvec_fit_ood(X.index_select(0, sub).contiguous(), Ql, d, method=lv.FIT_ES)
+    t_fit = time.time() - t0
+    t0 = time.time()
+    idx = lv.Index(dev.index).encode(X, B, 8, 8, precision=lv.PREC_BF16)
+    torch.cuda.synchronize()
+    t_enc = time.time() - t0
+    t0 = time.time()
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+                    seed=workloads.SEED_GRAPH + 5)
+    clamped = False
+    try:
+        idx.sync_status()
+    except lv.LeanVecError as e:  # a hub target received more reverse edges than the pool holds
+        if e.code != -4:
+            raise
+        clamped = True
+    t_build = time.time() - t0
+    kl = torch.from_numpy(workloads.uneven_batch(m, seed=workloads.SEED_TEST_QUERIES + 55)).to(dev)
+    desc = torch.stack([kl[:, 0], kl[:, 1], kl[:, 1], torch.zeros_like(kl[:, 0])], 1).to(torch.int32).contiguous()
+    kmax, Lmax = int(kl[:, 0].max()), int(kl[:, 1].max())
+    t0 = time.time()
+    truth = ground_truth_big(X, Q, kmax)
+    t_truth = time.time() - t0
+    log(f"uneven: data {t_data:.1f}s fit {t_fit:.1f}s encode {t_enc:.1f}s build {t_build:.1f}s truth {t_truth:.1f}s")
+    tune = lv.autotune(idx, Q, A, k=kmax, L=Lmax, rerank=Lmax, desc=desc, width=args.width,
+                       projection=lv.PREC_BF16)
+    best = tune["best"]
+    g = lv.SearchGraph(idx, Q, A, k=kmax, L=Lmax, rerank=Lmax, desc=desc, width=args.width,
+                       projection=lv.PREC_BF16, hash_slots=best["hash_slots"],
+                       warps_per_block=best["warps_per_block"])
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev.index) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ids = g.ids
+    per = {}
+    for kc in sorted(set(kl[:, 0].tolist())):
+        sel = kl[:, 0] == kc
+        a = ids[sel][:, :kc].long()
+        hit = (a.unsqueeze(2) == truth[sel][:, :kc].unsqueeze(1)).any(dim=2) & (a >= 0)
+        per[int(kc)] = {"queries": int(sel.sum()), "recall": float(hit.float().mean())}
+    out = {"metric": "QPS of one uneven batch (one CUDA-graph launch) and k-recall@k per class",
+           "workload": f"uneven-{n // 1000000}M-200 OOD, {m} queries, k in {{1,10,100}}, L ~ U[20,300], rerank = L",
+           "value": m / (ms / 1e3), "unit": "queries/s", "ms_per_batch": ms, "per_class": per,
+           "autotune": tune, "fit": {k: v for k, v in rep.items() if k != "loss_trace"},
+           "setup_seconds": {"data": t_data, "fit": t_fit, "encode": t_enc, "build": t_build, "truth": t_truth},
+           "build_reverse_pool_clamped": clamped,
+           "clocks": clk.summary(), "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,6 +399,9 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
+    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven"],
+                    help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
+                         "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
@@ -267,6 +414,12 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "ood":
+        bench_ood(args, dev)
+        return
+    if args.workload == "uneven":
+        bench_uneven(args, dev)
+        return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
                 f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "

@@ -272,7 +272,10 @@ int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stre
  *   - pair scores are the exact build score described with the record layout,
  *     so the adjacency is reproducible bit for bit.
  * splitmix64(s, a, b) is the SplitMix64 finaliser applied to
- * s + 0x9E3779B97F4A7C15 * (1 + a * 2^32 + b).  R <= 128, L_build <= 512. */
+ * s + 0x9E3779B97F4A7C15 * (1 + a * 2^32 + b).  R <= 128, L_build <= 512.  If one
+ * batch gives a target more new sources than its reverse-edge pool holds (about
+ * 4 R + 256, shared-memory bound), the sources beyond are dropped (lowest ids kept)
+ * and leanvec_sync_status reports LV_ERR_CAPACITY; smaller batches avoid it. */
 int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int passes, int batch,
                         uint64_t seed, lv_stream_t stream);
 

@@ -18,7 +18,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "SearchGraph", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 
@@ -342,3 +342,66 @@ class Index:
 
     def sync_status(self) -> int:
         return check(lib().leanvec_sync_status(self._h, _stream(self.device)))
+
+
+def autotune(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
+             desc: torch.Tensor | None = None, width: int = 1, projection: int = PREC_FP32,
+             warps=(4, 8), hash_slots=(512, 1024, 2048, 4096), reps: int = 3) -> dict:
+    """Pick the launch shape (warps per block, i.e. queries per CTA) and the visited-cache
+    size for this batch by timing each candidate with CUDA events.  Neither knob changes
+    the result (the visited cache is exact-preserving), only occupancy versus re-scoring."""
+    best = None
+    table = []
+    ldo = k
+    ids = torch.empty((Q.shape[0], ldo), dtype=torch.int32, device=index.device)
+    sc = torch.empty((Q.shape[0], ldo), dtype=torch.float32, device=index.device)
+    for w in warps:
+        for h in hash_slots:
+            if h < 2 * ((L + 31) // 32 * 32):
+                continue
+            try:
+                run = lambda: index.search(Q, A, k=k, L=L, rerank=rerank, desc=desc, ldo=ldo, out=(ids, sc),
+                                           width=width, projection=projection, hash_slots=h, warps_per_block=w)
+                run()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    run()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+            except LeanVecError:
+                continue
+            table.append({"warps_per_block": w, "hash_slots": h, "ms": ms})
+            if best is None or ms < best["ms"]:
+                best = table[-1]
+    return {"best": best, "table": table}
+
+
+class SearchGraph:
+    """The whole search (projection, per-query prologue, persistent beam kernel with
+    rerank) captured once in a CUDA graph for fixed query / output buffers, replayed per
+    batch: a batch of uneven queries (per-query k, L, rerank in `desc`) is one graph launch.
+    The first (uncaptured) call sizes the index's workspace before the capture."""
+
+    def __init__(self, index: "Index", Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
+                 desc: torch.Tensor | None = None, ldo: int | None = None, **kw):
+        self.index, self.Q, self.A, self.desc = index, Q, A, desc
+        self.ldo = k if ldo is None else ldo
+        self.ids = torch.empty((Q.shape[0], self.ldo), dtype=torch.int32, device=index.device)
+        self.scores = torch.empty((Q.shape[0], self.ldo), dtype=torch.float32, device=index.device)
+        self.args = dict(k=k, L=L, rerank=rerank, desc=desc, ldo=self.ldo, out=(self.ids, self.scores), **kw)
+        s = torch.cuda.Stream(device=index.device)
+        s.wait_stream(torch.cuda.current_stream(index.device))
+        with torch.cuda.stream(s):
+            index.search(Q, A, **self.args)  # warm-up: sizes the workspace outside the capture
+        torch.cuda.current_stream(index.device).wait_stream(s)
+        torch.cuda.synchronize(index.device)
+        self.graph = torch.cuda.CUDAGraph()
+        # relaxed: the launch path queries occupancy and sets kernel attributes (no stream work)
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            index.search(Q, A, **self.args)
+
+    def replay(self):
+        self.graph.replay()
+        return self.ids, self.scores

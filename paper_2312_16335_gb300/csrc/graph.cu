@@ -476,6 +476,9 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     batch = (int)std::min<int64_t>(batch, n);
     const int PMAX = Lb + R;
     if (prune_smem(PMAX, idx->pg.stride) > 227 * 1024) return fail(LV_ERR_CAPACITY, "build: L_build + R too large");
+    // reverse-edge pool: the target's list plus its new sources of one batch
+    int PMAX1 = std::max(PMAX, 4 * R + 256);
+    while (PMAX1 > PMAX && prune_smem(PMAX1, idx->pg.stride) > 120 * 1024) PMAX1 -= 32;
     cudaFree(idx->graph);
     idx->graph = nullptr;
     idx->R = 0;
@@ -608,7 +611,9 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
             scatter_pairs_kernel<<<(unsigned)((tp + 255) / 256), 256, 0, st>>>(newl, perm_d + b0, nb, R, offs, cnt, srcs);
             LV_CHECK_LAUNCH("reverse-edge kernels");
             const unsigned g1 = (unsigned)std::min<int64_t>(n, tp);
-            rc = idx->pbits == 8 ? launch_prune<8>(pp, 1, g1, st) : launch_prune<4>(pp, 1, g1, st);
+            PruneParams pr = pp;
+            pr.PMAX = PMAX1;  // a target may receive many reverse edges in one batch
+            rc = idx->pbits == 8 ? launch_prune<8>(pr, 1, g1, st) : launch_prune<4>(pr, 1, g1, st);
             if (rc) return rc;
         }
     }

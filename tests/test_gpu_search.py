@@ -187,3 +187,25 @@ def test_argument_errors(lv, pb):
         empty.search(t(pb["Q"]), t(pb["P"]), k=5, L=10)
     ids, sc = idx.search(t(pb["Q"][:0]), t(pb["P"]), k=5, L=10)
     assert ids.shape == (0, 5)
+
+
+def test_cuda_graph_replay_and_autotune(lv, pb):
+    """Batching form: an uneven batch captured once in a CUDA graph and replayed gives the
+    eager result; the autotuner's choice (launch shape, visited cache) does not change it."""
+    idx = gpu_index(lv, pb)
+    m = pb["Q"].shape[0]
+    rng = np.random.default_rng(11)
+    k = rng.choice([1, 5, 10], m)
+    L = np.maximum(rng.integers(10, 96, m), k)
+    desc = t(np.stack([k, L, L, np.zeros(m, int)], 1).astype(np.int32))
+    Q, P = t(pb["Q"]), t(pb["P"])
+    eager = idx.search(Q, P, k=10, L=96, rerank=96, desc=desc, ldo=10)
+    tune = lv.autotune(idx, Q, P, k=10, L=96, rerank=96, desc=desc)
+    assert tune["best"] is not None and len(tune["table"]) >= 2
+    g = lv.SearchGraph(idx, Q, P, k=10, L=96, rerank=96, desc=desc, hash_slots=tune["best"]["hash_slots"],
+                       warps_per_block=tune["best"]["warps_per_block"])
+    for _ in range(3):
+        ids, sc = g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(ids, eager[0])
+        assert torch.equal(sc, eager[1])
