@@ -258,6 +258,8 @@ int leanvec_set_graph(lv_index *idx, const int32_t *adj, int R, int32_t entry, l
 /* Copy the graph (n x R int32) into adj (device) and the entry into *entry (host). */
 int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stream_t stream);
 
+typedef enum { LV_PRUNE_SCALED = 0, LV_PRUNE_UNIT_L2 = 1 } lv_prune_rule;
+
 /* Build the graph on the primaries (App. A: search + prune for every node; App. D:
  * Vamana with R, L, alpha).  Batch-synchronous Vamana:
  *   - initial graph: node v takes the first min(R, n-1) ids splitmix64(seed, v, j)
@@ -266,8 +268,11 @@ int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stre
  *   - pass t uses alpha_t = 1 for t < passes - 1 and alpha in the last pass;
  *   - each batch of `batch` nodes searches the graph as it was at the batch start
  *     (query = the node's primary, beam L_build, from the entry), prunes
- *     pool = beam u old out-list (minus itself) with RobustPrune
- *     (drop p' when alpha * s(p*, p') >= s(p, p')), then adds the reverse edges by
+ *     pool = beam u old out-list (minus itself) with RobustPrune -- drop p' when
+ *       LV_PRUNE_SCALED:  alpha * s(p*, p') >= s(p, p')
+ *       LV_PRUNE_UNIT_L2: alpha * s(p*, p') >= s(p, p') + alpha - 1
+ *     (the second is Vamana's L2 rule alpha d(p*,p') <= d(p,p') with d = 2 - 2 s, i.e. for
+ *     unit-norm vectors; the two coincide at alpha = 1) -- then adds the reverse edges by
  *     (target, source) ascending, pruning targets that exceed R;
  *   - pair scores are the exact build score described with the record layout,
  *     so the adjacency is reproducible bit for bit.
@@ -277,7 +282,7 @@ int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stre
  * 4 R + 256, shared-memory bound), the sources beyond are dropped (lowest ids kept)
  * and leanvec_sync_status reports LV_ERR_CAPACITY; smaller batches avoid it. */
 int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int passes, int batch,
-                        uint64_t seed, lv_stream_t stream);
+                        uint64_t seed, int prune_rule, lv_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Search (Sec. 2 "Search"; App. D "greedy traversal with backtracking")     */

@@ -60,10 +60,10 @@ def lib():
         L.orc_random_graph.restype = None
         L.orc_permutation.argtypes = [i64, u64, vp]
         L.orc_permutation.restype = None
-        L.orc_robust_prune.argtypes = [vp, vp, vp, vp, vp, f32, i32, ctypes.c_int32, vp, i32, f32, i32, vp]
+        L.orc_robust_prune.argtypes = [vp, vp, vp, vp, vp, f32, i32, ctypes.c_int32, vp, i32, f32, f32, i32, vp]
         L.orc_entry_point.argtypes = [vp, i64]
         L.orc_entry_point.restype = ctypes.c_int32
-        L.orc_vamana_build.argtypes = [vp, vp, vp, vp, vp, f32, i32, i64, i32, i32, f32, i32, i32, u64,
+        L.orc_vamana_build.argtypes = [vp, vp, vp, vp, vp, f32, i32, i64, i32, i32, f32, i32, i32, u64, i32,
                                        vp, vp, i32]
         _lib = L
     return _lib
@@ -141,20 +141,22 @@ class BuildStore:
     def entry(self) -> int:
         return int(lib().orc_entry_point(_p(self.G), self.G.shape[0]))
 
-    def robust_prune(self, p: int, pool, alpha: float, R: int) -> np.ndarray:
+    def robust_prune(self, p: int, pool, alpha: float, R: int, shift: float = 0.0) -> np.ndarray:
         pool = _c(pool, np.int32)
         out = np.empty(R, np.int32)
-        k = lib().orc_robust_prune(*self._args(), int(p), _p(pool), len(pool), float(alpha), R, _p(out))
+        k = lib().orc_robust_prune(*self._args(), int(p), _p(pool), len(pool), float(alpha), float(shift), R,
+                                   _p(out))
         return out[:k].copy()
 
 
 def vamana_build(lvq: LVQ, R: int, L_build: int, alpha: float, passes: int, batch: int, seed: int,
-                 nthreads: int = 0):
+                 nthreads: int = 0, rule: int = 0):
+    """rule 0: drop p' when alpha s(p*,p') >= s(p,p'); rule 1: when alpha s(p*,p') >= s(p,p') + alpha - 1."""
     bs = BuildStore(lvq)
     n = lvq.codes.shape[0]
     graph = np.empty((n, R), np.int32)
     entry = ctypes.c_int32(0)
-    rc = lib().orc_vamana_build(*bs._args(), n, R, L_build, float(alpha), passes, batch, seed,
+    rc = lib().orc_vamana_build(*bs._args(), n, R, L_build, float(alpha), passes, batch, seed, rule,
                                 _p(graph), ctypes.byref(entry), nthreads)
     if rc != 0:
         raise RuntimeError(f"orc_vamana_build failed ({rc})")

@@ -431,13 +431,16 @@ void orc_permutation(int64_t n, uint64_t seed, int32_t *perm)
 }
 
 /* ------------------------------------------------------------------ */
-/* RobustPrune (App. A "Pruning"; IP form of the DiskANN rule):          */
+/* RobustPrune (App. A "Pruning"; inner-product forms of the DiskANN rule): */
 /* sort the pool by s(p, .) desc (id asc); repeatedly keep the best      */
-/* remaining p* and drop every remaining p' with alpha*s(p*,p') >= s(p,p').*/
+/* remaining p* and drop every remaining p' with                        */
+/*   alpha * s(p*,p') >= s(p,p') + shift                                 */
+/* shift = 0 (alpha scales the similarity) or alpha - 1 (the L2 rule     */
+/* alpha d(p*,p') <= d(p,p') with d = 2 - 2 s, i.e. unit-norm vectors).  */
 /* The pool must exclude p and hold distinct ids.  Returns |N| <= R.     */
 /* ------------------------------------------------------------------ */
 static int robust_prune(const orc_bstore *bs, int32_t p, const int32_t *pool, int np,
-                        float alpha, int R, int32_t *out)
+                        float alpha, float shift, int R, int32_t *out)
 {
     cand_t *V = (cand_t *)malloc(sizeof(cand_t) * (size_t)(np + 1));
     int nv = 0;
@@ -450,7 +453,8 @@ static int robust_prune(const orc_bstore *bs, int32_t p, const int32_t *pool, in
             if (V[j].expanded) continue;
             float sps = bscore(bs, V[i].id, V[j].id);
             float lhs = alpha * sps;
-            if (lhs >= (float)V[j].s) V[j].expanded = 1;
+            float rhs = (float)V[j].s + shift;
+            if (lhs >= rhs) V[j].expanded = 1;
         }
     }
     free(V);
@@ -459,10 +463,10 @@ static int robust_prune(const orc_bstore *bs, int32_t p, const int32_t *pool, in
 
 int orc_robust_prune(const uint8_t *codes, const float *delta, const float *lower,
                      const float *G, const float *H, float mu2, int dim,
-                     int32_t p, const int32_t *pool, int np, float alpha, int R, int32_t *out)
+                     int32_t p, const int32_t *pool, int np, float alpha, float shift, int R, int32_t *out)
 {
     orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, mu2};
-    return robust_prune(&bs, p, pool, np, alpha, R, out);
+    return robust_prune(&bs, p, pool, np, alpha, shift, R, out);
 }
 
 static int cmp_i64(const void *a, const void *b)
@@ -483,7 +487,7 @@ int32_t orc_entry_point(const float *G, int64_t n)
 /*
  * Batch-synchronous Vamana on primary vectors (App. A: search + prune per
  * node; App. D: R, L, alpha).  Pass t uses alpha_t = 1 for t < passes-1 and
- * alpha for the last pass.  Each batch of `batch` nodes (in permutation order)
+ * alpha for the last pass; rule 0 prunes with shift 0, rule 1 with shift alpha_t - 1.  Each batch of `batch` nodes (in permutation order)
  *   1. searches, from the entry, the graph as it was at the start of the batch
  *      (query = the node's own primary, beam L_build, no rerank);
  *   2. prunes pool = beam ∪ old out-neighbours (minus the node) to <= R;
@@ -495,7 +499,7 @@ int32_t orc_entry_point(const float *G, int64_t n)
  */
 int orc_vamana_build(const uint8_t *codes, const float *delta, const float *lower,
                      const float *G, const float *H, float mu2, int dim, int64_t n,
-                     int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
+                     int R, int L_build, float alpha, int passes, int batch, uint64_t seed, int rule,
                      int32_t *graph, int32_t *entry_out, int nthreads)
 {
     orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, mu2};
@@ -515,6 +519,7 @@ int orc_vamana_build(const uint8_t *codes, const float *delta, const float *lowe
 
     for (int pass = 0; pass < passes; ++pass) {
         float a = (pass < passes - 1) ? 1.0f : alpha;
+        float shift = rule ? a - 1.0f : 0.0f;
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
             int nb = (int)((n - b0) < batch ? (n - b0) : batch);
             memcpy(snap, graph, sizeof(int32_t) * (size_t)n * R);
@@ -545,7 +550,7 @@ int orc_vamana_build(const uint8_t *codes, const float *delta, const float *lowe
                             if (!dup) pool[np++] = u;
                         }
                         int32_t *out = newl + (int64_t)t * R;
-                        int no = robust_prune(&bs, p, pool, np, a, R, out);
+                        int no = robust_prune(&bs, p, pool, np, a, shift, R, out);
                         for (int s = no; s < R; ++s) out[s] = -1;
                     }
                 }
@@ -590,7 +595,7 @@ int orc_vamana_build(const uint8_t *codes, const float *delta, const float *lowe
                     if (!dup) lst[nl++] = p;
                 }
                 if (nl > R) {
-                    int no = robust_prune(&bs, u, lst, nl, a, R, pr);
+                    int no = robust_prune(&bs, u, lst, nl, a, shift, R, pr);
                     for (int s = 0; s < R; ++s) graph[(int64_t)u * R + s] = s < no ? pr[s] : -1;
                 } else {
                     for (int s = 0; s < R; ++s) graph[(int64_t)u * R + s] = s < nl ? lst[s] : -1;

@@ -21,6 +21,7 @@ __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mea
            "autotune", "SearchGraph", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
 
 
 def _ptr(t: torch.Tensor | None):
@@ -287,8 +288,11 @@ class Index:
         return adj, int(e.value)
 
     def build_graph(self, R: int, L_build: int, alpha: float, passes: int = 2, batch: int = 4096,
-                    seed: int = 5000) -> "Index":
-        check(lib().leanvec_build_graph(self._h, R, L_build, float(alpha), passes, batch, seed, _stream(self.device)))
+                    seed: int = 5000, rule: int = 0) -> "Index":
+        """rule 0 (PRUNE_SCALED): drop p' when alpha s(p*,p') >= s(p,p'); rule 1 (PRUNE_UNIT_L2):
+        when alpha s(p*,p') >= s(p,p') + alpha - 1."""
+        check(lib().leanvec_build_graph(self._h, R, L_build, float(alpha), passes, batch, seed, rule,
+                                        _stream(self.device)))
         return self
 
     # -- search ----------------------------------------------------------------

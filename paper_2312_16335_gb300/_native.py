@@ -59,7 +59,7 @@ SIGNATURES = {
     "leanvec_encode_fp32": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp]),
     "leanvec_set_graph": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp]),
     "leanvec_get_graph": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32), c_vp]),
-    "leanvec_build_graph": (c_i32, [c_vp, c_i32, c_i32, c_f32, c_i32, c_i32, c_u64, c_vp]),
+    "leanvec_build_graph": (c_i32, [c_vp, c_i32, c_i32, c_f32, c_i32, c_i32, c_u64, c_i32, c_vp]),
     "leanvec_search": (c_i32, [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(LVSearchParams), c_vp, c_vp, c_vp,
                                c_i32, c_vp, c_vp]),
     "leanvec_sync_status": (c_i32, [c_vp, c_vp]),

@@ -40,7 +40,7 @@ int launch_graph_sanitize(int32_t *graph, int64_t n, int R, int *status, cudaStr
 int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int32_t *out,
                         cudaStream_t st);
 int build_graph_impl(lv_index *idx, int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
-                     cudaStream_t st);
+                     int rule, cudaStream_t st);
 int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                  size_t *ws_bytes, int *status, cudaStream_t st);
 
@@ -416,7 +416,7 @@ int leanvec_get_graph(const lv_index *idx, int32_t *adj, int32_t *entry, lv_stre
 }
 
 int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
-                        lv_stream_t stream) {
+                        int prune_rule, lv_stream_t stream) {
     if (!idx) return fail(LV_ERR_ARG, "build_graph: null index");
     if (idx->n == 0 || (idx->pbits != 8 && idx->pbits != 4))
         return fail(LV_ERR_STATE, "build_graph: the index has no LVQ primary store");
@@ -424,7 +424,9 @@ int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int pass
         return fail(LV_ERR_ARG, "build_graph: need 1 <= R <= 128, 1 <= L_build <= 512, passes >= 1, batch >= 1, alpha > 0");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "build_graph: cannot select device");
-    return build_graph_impl(idx, R, L_build, alpha, passes, batch, seed, (cudaStream_t)stream);
+    if (prune_rule != LV_PRUNE_SCALED && prune_rule != LV_PRUNE_UNIT_L2)
+        return fail(LV_ERR_ARG, "build_graph: unknown prune rule");
+    return build_graph_impl(idx, R, L_build, alpha, passes, batch, seed, prune_rule, (cudaStream_t)stream);
 }
 
 static int next_pow2(int x) {

@@ -20,6 +20,7 @@
 namespace lv {
 
 // -------------------------------------------------------------------- helpers
+static inline float host_fsub(float a, float b) { return a - b; }  // IEEE float32 (host SSE/NEON)
 __host__ __device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t a, uint64_t b) {
     uint64_t z = seed + 0x9E3779B97F4A7C15ULL * (1ULL + (a << 32) + b);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -155,7 +156,7 @@ struct PruneParams {
     const uint8_t *prim;
     int64_t stride;  // record stride (multiple of 32)
     int CH, cb, dim;
-    float mu2, alpha;
+    float mu2, alpha, shift;
     int R, PMAX;
     int64_t n;
     int32_t *graph;        // n x R
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(128) prune_kernel(const PruneParams pp) {
                 const int j = ord[q];
                 if (dead[j]) continue;
                 const float s = smem_pair_score<BITS>(ri, recs + (size_t)j * stride, pp.CH, pp.cb, pp.mu2, fdim);
-                if (__fmul_rn(pp.alpha, s) >= psc[j]) dead[j] = 1;
+                if (__fmul_rn(pp.alpha, s) >= __fadd_rn(psc[j], pp.shift)) dead[j] = 1;
             }
         }
         __syncthreads();
@@ -470,7 +471,7 @@ static int launch_prune(const PruneParams &pp, int mode, unsigned grid, cudaStre
     return LV_OK;
 }
 
-int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int batch, uint64_t seed,
+int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int batch, uint64_t seed, int rule,
                      cudaStream_t st) {
     const int64_t n = idx->n;
     batch = (int)std::min<int64_t>(batch, n);
@@ -592,6 +593,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
 
     for (int pass = 0; pass < passes; ++pass) {
         pp.alpha = pass < passes - 1 ? 1.0f : alpha;
+        pp.shift = rule ? host_fsub(pp.alpha, 1.0f) : 0.0f;
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
             const int nb = (int)std::min<int64_t>(batch, n - b0);
             bp.qnodes = perm_d + b0;

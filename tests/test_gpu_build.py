@@ -24,19 +24,21 @@ def _prims(n, d, bits, seed):
     return Y, mu, oracle.lvq_encode(Y, mu, bits)
 
 
-@pytest.mark.parametrize("n,d,bits,R,Lb,alpha,batch", [
-    (600, 16, 8, 8, 16, 0.95, 1),
-    (600, 16, 8, 8, 16, 1.0, 64),
-    (1000, 24, 4, 12, 24, 0.95, 100),
-    (1500, 32, 8, 16, 40, 1.0, 1500),
-    (777, 40, 8, 32, 64, 1.2, 128),   # ragged sizes, R > 32
+@pytest.mark.parametrize("n,d,bits,R,Lb,alpha,batch,rule", [
+    (600, 16, 8, 8, 16, 0.95, 1, 0),
+    (600, 16, 8, 8, 16, 1.0, 64, 0),
+    (1000, 24, 4, 12, 24, 0.95, 100, 0),
+    (1500, 32, 8, 16, 40, 1.0, 1500, 0),
+    (777, 40, 8, 32, 64, 1.2, 128, 0),   # ragged sizes, R > 32
+    (900, 24, 8, 16, 32, 1.2, 64, 1),    # unit-L2 rule
+    (700, 16, 4, 12, 24, 1.3, 50, 1),
 ])
-def test_build_bit_exact(lv, n, d, bits, R, Lb, alpha, batch):
+def test_build_bit_exact(lv, n, d, bits, R, Lb, alpha, batch, rule):
     Y, mu, q = _prims(n, d, bits, seed=n + d)
-    g_ref, e_ref = oracle.vamana_build(q, R=R, L_build=Lb, alpha=alpha, passes=2, batch=batch, seed=42)
+    g_ref, e_ref = oracle.vamana_build(q, R=R, L_build=Lb, alpha=alpha, passes=2, batch=batch, seed=42, rule=rule)
     idx = lv.Index(0)
     idx.set_primary(t(Y), t(mu), bits, d)
-    idx.build_graph(R=R, L_build=Lb, alpha=alpha, passes=2, batch=batch, seed=42)
+    idx.build_graph(R=R, L_build=Lb, alpha=alpha, passes=2, batch=batch, seed=42, rule=rule)
     idx.sync_status()
     g, e = idx.get_graph()
     assert e == e_ref

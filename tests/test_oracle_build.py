@@ -31,6 +31,27 @@ def test_build_score_matches_fp64_decode(oracle_lib):
         assert bs.score(a, b) == bs.score(b, a)  # symmetric bit for bit
 
 
+def test_robust_prune_unit_l2_rule(oracle_lib):
+    """Rule 1 is the L2 rule alpha |p*-p'|^2 <= |p-p'|^2 on unit-norm vectors, written with
+    s = <.,.> (|a-b|^2 = 2 - 2 s): brute-force replay with explicit squared distances."""
+    rng = np.random.default_rng(30)
+    Y = workloads.unit_rows(rng.standard_normal((50, 6)))
+    q = oracle_lib.lvq_encode(Y, np.zeros(6, np.float32), 8)
+    bs = oracle_lib.BuildStore(q)
+    a = 1.3
+    out = bs.robust_prune(0, list(range(1, 50)), a, 10, float(np.float32(a) - np.float32(1.0)))
+    s = lambda i, j: float(bs.score(i, j))
+    order = sorted(range(1, 50), key=lambda u: (-s(0, u), u))
+    kept, alive = [], list(order)
+    while alive and len(kept) < 10:
+        p = alive.pop(0)
+        kept.append(p)
+        # squared distances of (approximately) unit vectors from the same scores
+        alive = [u for u in alive if not (a * (2 - 2 * s(p, u)) <= 2 - 2 * s(0, u) + 1e-6)]
+    # the float32 rule and the distance replay agree away from rounding ties
+    assert len(set(out.tolist()) ^ set(kept)) <= 1
+
+
 def test_robust_prune_invariants(oracle_lib):
     q = _primaries(oracle_lib, n=60)
     bs = oracle_lib.BuildStore(q)
@@ -54,7 +75,7 @@ def test_robust_prune_invariants(oracle_lib):
         assert out.tolist() == kept
 
 
-def _python_sequential_vamana(oracle_lib, q, R, L, alpha, passes, seed):
+def _python_sequential_vamana(oracle_lib, q, R, L, alpha, passes, seed, rule=0):
     """Textbook sequential Vamana (one node at a time), written independently of the
     C batch build: greedy search from the entry, prune, add reverse edges and prune
     any neighbour that overflows."""
@@ -81,29 +102,30 @@ def _python_sequential_vamana(oracle_lib, q, R, L, alpha, passes, seed):
 
     for t in range(passes):
         a = 1.0 if t < passes - 1 else alpha
+        sh = float(np.float32(a) - np.float32(1.0)) if rule else 0.0
         for p in perm:
             p = int(p)
             pool = [u for _, u in search(p) if u != p]
             for u in G[p]:
                 if u != p and u not in pool:
                     pool.append(u)
-            G[p] = bs.robust_prune(p, pool, a, R).tolist()
+            G[p] = bs.robust_prune(p, pool, a, R, sh).tolist()
             for u in G[p]:
                 if p not in G[u] and u != p:
                     G[u].append(p)
                     if len(G[u]) > R:
-                        G[u] = bs.robust_prune(u, G[u], a, R).tolist()
+                        G[u] = bs.robust_prune(u, G[u], a, R, sh).tolist()
     out = np.full((n, R), -1, np.int32)
     for i, row in enumerate(G):
         out[i, :len(row)] = row
     return out, entry
 
 
-@pytest.mark.parametrize("bits", [8, 4])
-def test_batch_one_equals_sequential_vamana(oracle_lib, bits):
+@pytest.mark.parametrize("bits,rule,alpha", [(8, 0, 0.95), (4, 0, 0.95), (8, 1, 1.2)])
+def test_batch_one_equals_sequential_vamana(oracle_lib, bits, rule, alpha):
     q = _primaries(oracle_lib, n=70, d=10, bits=bits, seed=22)
-    g, e = oracle_lib.vamana_build(q, R=6, L_build=12, alpha=0.95, passes=2, batch=1, seed=77)
-    g2, e2 = _python_sequential_vamana(oracle_lib, q, 6, 12, 0.95, 2, 77)
+    g, e = oracle_lib.vamana_build(q, R=6, L_build=12, alpha=alpha, passes=2, batch=1, seed=77, rule=rule)
+    g2, e2 = _python_sequential_vamana(oracle_lib, q, 6, 12, alpha, 2, 77, rule=rule)
     assert e == e2
     np.testing.assert_array_equal(g, g2)
 
