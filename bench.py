@@ -166,7 +166,7 @@ def time_steps(fn, steps, warmup, events=None):
     return total_ms, kern_ms
 
 
-def setup(args, dev):
+def setup(args, dev, with_base=True):
     from paper_2312_16335_gb300 import build_lib
     build_lib.build()  # no-op when the in-tree library is up to date
     import paper_2312_16335_gb300 as lv
@@ -191,7 +191,7 @@ def setup(args, dev):
     t_build = time.time() - t0
     log(f"fit {t_fit:.2f}s encode {t_enc:.2f}s build {t_build:.2f}s")
     graph, entry = idx.get_graph()
-    base = lv.Index(dev.index).encode_fp32(X).set_graph(graph, entry)
+    base = lv.Index(dev.index).encode_fp32(X).set_graph(graph, entry) if with_base else None
     t0 = time.time()
     truth = ground_truth(X, Q, 10)
     log(f"ground truth {time.time() - t0:.1f}s")
@@ -453,7 +453,7 @@ def main():
         print(json.dumps(out), flush=True)
         return
 
-    S = setup(args, dev)
+    S = setup(args, dev, with_base=not args.profile)
     lv, idx, base, Q, A, truth = S["lv"], S["idx"], S["base"], S["Q"], S["A"], S["truth"]
     proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
     m = Q.shape[0]
@@ -567,7 +567,7 @@ def main():
         "gpu_launches": (5 if args.projection == "bf16" else 3) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
-                     "kernel": "beam_kernel<LvqGroupScorer<3,8>,search,rerank>",
+                     "kernel": "beam_kernel<LvqIntScorer<3,8>,search,rerank>",
                      "kernel_ms": kern_avg, "bytes_per_query": bytes_q, "hops_per_query": hops,
                      "scored_per_query": scored, "peak_kind": peak_kind},
         "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "recall_at_10": rec_b,
