@@ -37,6 +37,31 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 L_GRID = [10, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 200, 256]
+
+# DRAM bytes (read + write) of one beam-kernel launch measured with ncu
+# (profiles/beam_kernel_id1m_768.md), valid only for the kernel sources it was taken on.
+TRAFFIC_RECORDS = [
+    {"src_sha1": "2c82c50a1533d3621d249c70e0f4320359f0537c", "n": 1_000_000, "m": 10_000, "L": 160, "width": 2, "hash": 0,
+     "projection": "bf16", "bytes": 4.53e9 + 7.95e6},
+]
+
+
+def beam_src_sha1() -> str:
+    import hashlib
+    root = os.path.join(ROOT, "paper_2312_16335_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in ("beam.cuh", "search_lvq8.cu"):
+        h.update(open(os.path.join(root, f), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic(args, L):
+    sha = beam_src_sha1()
+    for r in TRAFFIC_RECORDS:
+        if (r["src_sha1"] == sha and r["n"] == args.n and r["m"] == args.m and r["L"] == L and
+                r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection):
+            return r["bytes"]
+    return None
 TARGET = 0.90
 
 
@@ -566,7 +591,7 @@ def main():
                 "d2h_bytes_per_step": m * k * 8},
         "gpu_launches": (5 if args.projection == "bf16" else 3) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L),
                      "kernel": "beam_kernel<LvqIntScorer<3,8>,search,rerank>",
                      "kernel_ms": kern_avg, "bytes_per_query": bytes_q, "hops_per_query": hops,
                      "scored_per_query": scored, "peak_kind": peak_kind},
