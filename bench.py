@@ -402,6 +402,77 @@ def bench_uneven(args, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_precision(args, dev):
+    """Precision form at 10M: 10M x 768 (10,000 components), d = 160 LVQ-4 primaries + LVQ-8
+    secondaries, R = 64; second moments in bf16 (tcgen05) with FP64 eig; query and database
+    projection in e4m3 with per-row scales (tcgen05 f8f6f4); 100k queries.  Errors of the
+    reduced-precision steps are stated against FP64 references on samples."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    n, m, D, d = args.n, args.m, 768, 160
+    t0 = time.time()
+    X, Q, _ = workloads.make_workload_torch("anisotropic", n, m, D, 10_000, cfg=4, device=dev, m_learn=0)
+    t_data = time.time() - t0
+    sub = torch.from_numpy(workloads.subsample_rows(n, 100_000, cfg=4)).to(dev)
+    Xs = X.index_select(0, sub).contiguous()
+    # second moments: bf16 tensor cores vs FP64 (NumPy) on the 100k sample
+    K16 = lv.leanvec_second_moment(Xs, precision=lv.PREC_BF16).double().cpu().numpy()
+    Xs64 = Xs.double().cpu().numpy()
+    K64 = Xs64.T @ Xs64
+    nrm = np.linalg.norm(Xs64, axis=0)
+    k_err = float(np.abs(K16 - K64).max() / np.outer(nrm, nrm).max())
+    t0 = time.time()
+    A = lv.leanvec_fit_id(Xs, d, precision=lv.PREC_BF16)
+    t_fit = time.time() - t0
+    A32 = lv.leanvec_fit_id(Xs, d, precision=lv.PREC_FP32)
+    A64 = np.linalg.eigh(K64)[1][:, ::-1][:, :d].T
+    proj = lambda P: P.T @ P
+    sub_err = float(np.linalg.norm(proj(A.double().cpu().numpy()) - proj(A64)) / np.sqrt(d))
+    # projection: e4m3 vs FP64 on 2000 queries, relative to ||q|| ||a||
+    qs = Q[:2000].contiguous()
+    Y8 = lv.leanvec_project(qs, A, precision=lv.PREC_FP8).double().cpu().numpy()
+    Yr = qs.double().cpu().numpy() @ A.double().cpu().numpy().T
+    sc = np.linalg.norm(qs.double().cpu().numpy(), axis=1)[:, None] * np.linalg.norm(A.double().cpu().numpy(), axis=1)[None, :]
+    p_err = {"max": float((np.abs(Y8 - Yr) / sc).max()), "mean": float((np.abs(Y8 - Yr) / sc).mean())}
+    del K16, Xs64, Y8, Yr
+    t0 = time.time()
+    idx = lv.Index(dev.index).encode(X, A, primary_bits=4, secondary_bits=8, precision=lv.PREC_FP8)
+    torch.cuda.synchronize()
+    t_enc = time.time() - t0
+    t0 = time.time()
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+                    seed=workloads.SEED_GRAPH + 4)
+    clamped = False
+    try:
+        idx.sync_status()
+    except lv.LeanVecError as e:
+        if e.code != -4:
+            raise
+        clamped = True
+    t_build = time.time() - t0
+    mt = min(10_000, m)
+    truth = ground_truth_big(X, Q[:mt], 10)
+    res = {}
+    for pname, prec in (("fp8", lv.PREC_FP8), ("fp32", lv.PREC_FP32)):
+        L90, trace = calibrate(lambda L: idx.search(Q[:mt], A, k=10, L=L, rerank=L, width=args.width,
+                                                     projection=prec)[0], truth, 10)
+        L90 = L90 or L_GRID[-1]
+        ms, _ = time_steps(lambda ev: idx.search(Q, A, k=10, L=L90, rerank=L90, width=args.width, projection=prec),
+                           max(3, args.steps // 5), 2)
+        res[pname] = {"L_for_0.90": L90, "recall_trace": trace, "qps": m / (ms / 1e3)}
+    out = {"metric": "QPS at 10-recall@10 = 0.90 with FP8 (e4m3, per-row scaled) query projection; "
+                     "precision errors vs FP64",
+           "workload": f"prec-{n // 1000000}M-768: 10,000-component mixture, {m} queries (recall on {mt}), "
+                       f"d=160 LVQ-4 primary + LVQ-8 secondary, R={args.R}",
+           "results": res,
+           "errors_vs_fp64": {"second_moment_bf16_max_rel": k_err, "fit_id_bf16_projector_dist": sub_err,
+                              "projection_fp8_rel_to_norms": p_err},
+           "setup_seconds": {"data": t_data, "fit": t_fit, "encode_fp8": t_enc, "build": t_build},
+           "build_reverse_pool_clamped": clamped, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,9 +495,10 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
-    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven"],
+    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
-                         "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch")
+                         "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
+                         "precision: 10M x 768 with FP8 projection and LVQ-4 primaries")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
@@ -444,6 +516,9 @@ def main():
         return
     if args.workload == "uneven":
         bench_uneven(args, dev)
+        return
+    if args.workload == "precision":
+        bench_precision(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "

@@ -43,6 +43,14 @@ int build_graph_impl(lv_index *idx, int R, int L_build, float alpha, int passes,
                      int rule, cudaStream_t st);
 int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                  size_t *ws_bytes, int *status, cudaStream_t st);
+int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                size_t *ws_bytes, int *status, cudaStream_t st);
+// tensor-core projection with bf16 or e4m3 (per-row scaled) operands
+static int project_tc(int prec, const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                      size_t *ws_bytes, int *status, cudaStream_t st) {
+    return prec == LV_PREC_FP8 ? project_fp8(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st)
+                               : project_bf16(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st);
+}
 
 // Makes the index's device current for the scope of an API call.
 struct DeviceGuard {
@@ -125,7 +133,8 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
     if (n < 0 || D <= 0 || d <= 0 || ldy < d || (n > 0 && (!X || !P || !Y)))
         return fail(LV_ERR_ARG, "project: invalid sizes or null pointer");
     if (precision == LV_PREC_FP32) return launch_project_fp32(X, n, D, P, d, Y, ldy, (cudaStream_t)stream);
-    if (precision != LV_PREC_BF16) return fail(LV_ERR_ARG, "project: precision must be LV_PREC_FP32 or LV_PREC_BF16");
+    if (precision != LV_PREC_BF16 && precision != LV_PREC_FP8)
+        return fail(LV_ERR_ARG, "project: precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
     if (n == 0) return LV_OK;
     cudaStream_t st = (cudaStream_t)stream;
     void *ws = nullptr;
@@ -135,7 +144,7 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
     int rc = LV_OK;
     if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return fail(LV_ERR_OOM, "project: allocation failed");
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "project: memset failed");
-    if (rc == LV_OK) rc = project_bf16(X, n, D, P, d, Y, ldy, &ws, &wsb, status, st);
+    if (rc == LV_OK) rc = project_tc(precision, X, n, D, P, d, Y, ldy, &ws, &wsb, status, st);
     if (rc == LV_OK && cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = fail(LV_ERR_CUDA, "project: status copy failed");
     if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "project: sync failed");
@@ -325,8 +334,8 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     if (D <= 0 || d <= 0 || d > D) return fail(LV_ERR_ARG, "encode: need 0 < d <= D");
     if (primary_bits != 4 && primary_bits != 8) return fail(LV_ERR_ARG, "encode: primary_bits must be 4 or 8");
     if (secondary_bits != 0 && secondary_bits != 8) return fail(LV_ERR_ARG, "encode: secondary_bits must be 0 or 8");
-    if (projection_precision != LV_PREC_FP32 && projection_precision != LV_PREC_BF16)
-        return fail(LV_ERR_ARG, "encode: projection precision must be LV_PREC_FP32 or LV_PREC_BF16");
+    if (projection_precision < LV_PREC_FP32 || projection_precision > LV_PREC_FP8)
+        return fail(LV_ERR_ARG, "encode: projection precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "encode: cannot select device");
     cudaStream_t st = (cudaStream_t)stream;
@@ -334,8 +343,8 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     int rc = LV_OK;
     index_free_stores(idx);
     LV_TRYC(cudaMalloc(&Y, sizeof(float) * (size_t)n * d));
-    if (projection_precision == LV_PREC_BF16) {
-        LV_TRY(project_bf16(X, n, D, B, d, Y, d, &idx->bws, &idx->bws_bytes, idx->status, st));
+    if (projection_precision != LV_PREC_FP32) {
+        LV_TRY(project_tc(projection_precision, X, n, D, B, d, Y, d, &idx->bws, &idx->bws_bytes, idx->status, st));
     } else {
         LV_TRY(launch_project_fp32(X, n, D, B, d, Y, d, st));
     }
@@ -450,8 +459,8 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (!desc && (u.k < 1 || u.k > u.L || u.k > ldo || u.rerank < 0 || u.rerank > u.L || u.max_hops < 0))
         return fail(LV_ERR_ARG, "search: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search: rerank needs a secondary store");
-    if (params->projection != LV_PREC_FP32 && params->projection != LV_PREC_BF16)
-        return fail(LV_ERR_ARG, "search: projection precision must be LV_PREC_FP32 or LV_PREC_BF16");
+    if (params->projection < LV_PREC_FP32 || params->projection > LV_PREC_FP8)
+        return fail(LV_ERR_ARG, "search: projection precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "search: cannot select device");
     cudaStream_t st = (cudaStream_t)stream;
@@ -465,8 +474,9 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (rc) return rc;
     if (idx->pbits == 32) {
         rc = launch_pad_rows(Q, m, idx->D, idx->ws_q, ldq, st);
-    } else if (params->projection == LV_PREC_BF16) {
-        rc = project_bf16(Q, m, idx->D, A, idx->d, idx->ws_q, ldq, &idx->bws, &idx->bws_bytes, idx->status, st);
+    } else if (params->projection != LV_PREC_FP32) {
+        rc = project_tc(params->projection, Q, m, idx->D, A, idx->d, idx->ws_q, ldq, &idx->bws, &idx->bws_bytes,
+                        idx->status, st);
     } else {
         rc = launch_project_fp32(Q, m, idx->D, A, idx->d, idx->ws_q, ldq, st);
     }

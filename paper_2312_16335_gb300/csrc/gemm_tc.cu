@@ -15,6 +15,7 @@
 // skips its remaining work, waits (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -24,7 +25,7 @@
 
 namespace lv {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_STAGES = 4;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;  // try_wait may suspend: keeps a give-up within seconds
 
 struct TcParams {
@@ -34,6 +35,8 @@ struct TcParams {
     float *C;        // direct output (split == 1) ...
     int ldc;
     float *partial;  // ... or partial[split][M][N] (split > 1)
+    const float *row_scale;  // fp8: C[r][c] *= row_scale[r] * col_scale[c]
+    const float *col_scale;
     int *status;
 };
 
@@ -84,18 +87,24 @@ __device__ __forceinline__ uint64_t sdesc(const void *p) {
     return d;
 }
 
-// instruction descriptor, kind::f16: D float32, A and B bf16, both K-major, M = 128
-__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor, D float32, A and B K-major, M = 128.
+// FP8 = 0: kind::f16 with bf16 operands (format 1); FP8 = 1: kind::f8f6f4 with e4m3 (format 0).
+template <int FP8>
+__host__ __device__ __forceinline__ uint32_t idesc_tc(int M, int N) {
+    const uint32_t fmt = FP8 ? 0u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// FP8 = 0: bf16 operands, 64 elements (128 B) per K block, K = 16 per MMA;
+// FP8 = 1: e4m3 operands, 128 elements (128 B) per K block, K = 32 per MMA.
+template <int FP8>
 __global__ void __launch_bounds__(128, 1)
-    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-                        const TcParams p) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcParams p) {
+    constexpr int KBLK = FP8 ? 128 : 64;  // elements per 128-byte swizzle row
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int BN = p.BN;
-    const uint32_t a_bytes = TC_BM * TC_BK * 2, b_bytes = (uint32_t)BN * TC_BK * 2;
+    const uint32_t a_bytes = TC_BM * 128, b_bytes = (uint32_t)BN * 128;
     const uint32_t stage_bytes = a_bytes + b_bytes;  // multiple of 1024 (BN % 16 == 0... and BN*128 % 1024 == 0)
     uint64_t *full = reinterpret_cast<uint64_t *>(base + TC_STAGES * stage_bytes);
     uint64_t *empty = full + TC_STAGES;
@@ -104,7 +113,7 @@ __global__ void __launch_bounds__(128, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
-    const int total_kb = (p.K + TC_BK - 1) / TC_BK;
+    const int total_kb = (p.K + KBLK - 1) / KBLK;
     const int kb0 = blockIdx.z * p.kb_per_split;
     const int nkb = min(kb0 + p.kb_per_split, total_kb) - kb0;
     uint32_t tcols = 32;
@@ -141,13 +150,13 @@ __global__ void __launch_bounds__(128, 1)
             if (*abort_flag) break;
             uint8_t *sa = base + s * stage_bytes;
             mbar_expect_tx(full + s, stage_bytes);
-            const int kx = (kb0 + kb) * TC_BK;  // multiple of 64 elements = 128 bytes
+            const int kx = (kb0 + kb) * KBLK;  // a multiple of 128 bytes
             tma_load_2d(sa, &ta, kx, m0, full + s);
             tma_load_2d(sa + a_bytes, &tb, kx, n0, full + s);
         }
     } else if (nkb > 0 && warp == 1 && lane == 0) {
         // MMA issuer
-        const uint32_t idesc = idesc_bf16(TC_BM, BN);
+        const uint32_t idesc = idesc_tc<FP8>(TC_BM, BN);
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % TC_STAGES;
             if (!mbar_wait(full + s, (kb / TC_STAGES) & 1)) {
@@ -158,16 +167,24 @@ __global__ void __launch_bounds__(128, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint8_t *sa = base + s * stage_bytes;
 #pragma unroll
-            for (int k = 0; k < TC_BK / 16; ++k) {
+            for (int k = 0; k < 4; ++k) {  // 4 MMAs of 32 bytes of K each per 128-byte row
                 const uint64_t ad = sdesc(sa + 32 * k);
                 const uint64_t bd = sdesc(sa + a_bytes + 32 * k);
                 const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\t"
-                    "setp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+                if (FP8)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                else
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(empty + s))
@@ -198,10 +215,14 @@ __global__ void __launch_bounds__(128, 1)
                 const int col0 = n0 + c0;
                 float *dst = p.partial ? p.partial + ((int64_t)blockIdx.z * p.M + row) * p.N + col0
                                        : p.C + (int64_t)row * p.ldc + col0;
-                const int ncol = p.partial ? p.N : p.N;
+                const float rs = p.row_scale ? p.row_scale[row] : 1.f;
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    if (col0 + j < ncol) dst[j] = __uint_as_float(r[j]);
+                    if (col0 + j < p.N) {
+                        float v = __uint_as_float(r[j]);
+                        if (p.row_scale) v *= rs * p.col_scale[col0 + j];
+                        dst[j] = v;
+                    }
             }
         }
     } else if (nkb > 0 && warp == 0 && lane == 0) {
@@ -232,6 +253,24 @@ __global__ void cast_bf16_kernel(const float *__restrict__ X, int64_t n, int D, 
     const int64_t r = t / ldo;
     const int c = (int)(t % ldo);
     Y[t] = __float2bfloat16_rn(c < D ? X[r * D + c] : 0.f);
+}
+
+// float32 rows -> e4m3 rows (n x ldo bytes, zero-padded) with per-row scale max|row| / 448;
+// one warp per row
+__global__ void cast_e4m3_kernel(const float *__restrict__ X, int64_t n, int D, uint8_t *__restrict__ Y, int ldo,
+                                 float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    const float *x = X + r * D;
+    float amax = 0.f;
+    for (int j = lane; j < D; j += 32) amax = fmaxf(amax, fabsf(x[j]));
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float s = amax > 0.f ? amax / 448.0f : 1.0f;
+    const float inv = 1.0f / s;
+    for (int j = lane; j < ldo; j += 32)
+        Y[r * ldo + j] = j < D ? (uint8_t)__nv_cvt_float_to_fp8(x[j] * inv, __NV_SATFINITE, __NV_E4M3) : (uint8_t)0;
+    if (lane == 0) scale[r] = s;
 }
 
 // float32 X (n x D) -> bf16 X^T (D x ldo), ldo >= n, zero-padded; 32 x 32 tiles
@@ -268,41 +307,47 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D bf16 tensor map over rows x cols (cols contiguous, row stride ld elements).
-static int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// 2-D tensor map over rows x cols (cols contiguous, row stride ld elements) of bf16
+// (esize 2) or 8-bit (esize 1) elements; 128-byte-wide boxes.
+static int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                    int esize) {
     auto fn = encode_fn();
     if (!fn) return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled unavailable");
-    if (((uintptr_t)ptr & 15) || (ld * 2) % 16) return fail(LV_ERR_ARG, "tcgen05 GEMM: operands must be 16-byte aligned");
+    if (((uintptr_t)ptr & 15) || (ld * esize) % 16)
+        return fail(LV_ERR_ARG, "tcgen05 GEMM: operands must be 16-byte aligned");
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+    CUresult r = fn(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                    const_cast<void *>(ptr), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled failed");
     return LV_OK;
 }
 
-static size_t tc_smem(int BN) { return (size_t)TC_STAGES * (TC_BM + BN) * TC_BK * 2 + 256 + 1024; }
+static size_t tc_smem(int BN) { return (size_t)TC_STAGES * (TC_BM + BN) * 128 + 256 + 1024; }
 
-// C = A B^T with A (M x K, lda), B (N x K, ldb) bf16 device arrays; C float32 (ldc).
-// `work` (nullable) holds split-K partials: splits * M * N floats.
-int gemm_bf16_tc(const __nv_bfloat16 *A, int64_t M, int64_t lda, const __nv_bfloat16 *B, int N, int64_t ldb, int64_t K,
-                 float *C, int ldc, int splits, float *work, int *status, cudaStream_t st) {
+// C = A B^T with A (M x K, lda), B (N x K, ldb) device arrays (bf16, or e4m3 when fp8 with
+// per-row scales rs (M) and cs (N)); C float32 (ldc).  `work` (nullable) holds split-K
+// partials: splits * M * N floats.
+static int gemm_tc(int fp8, const void *A, int64_t M, int64_t lda, const void *B, int N, int64_t ldb, int64_t K,
+                   float *C, int ldc, int splits, float *work, const float *rs, const float *cs, int *status,
+                   cudaStream_t st) {
     if (M <= 0 || N <= 0 || K <= 0) return fail(LV_ERR_ARG, "tcgen05 GEMM: empty operand");
     if (M >= (int64_t)1 << 31 || K >= (int64_t)1 << 31) return fail(LV_ERR_ARG, "tcgen05 GEMM: sizes too large");
+    const int esize = fp8 ? 1 : 2, kblk = 128 / esize;
     int BN = N <= 256 ? (int)round_up(N, 16) : 256;
-    while ((BN * TC_BK * 2) % 1024) BN += 16;  // keep every stage 1024-byte aligned
-    const int total_kb = (int)((K + TC_BK - 1) / TC_BK);
+    const int total_kb = (int)((K + kblk - 1) / kblk);
     splits = std::max(1, std::min(splits, total_kb));
     if (splits > 1 && !work) splits = 1;
     const int kbps = (total_kb + splits - 1) / splits;
     splits = (total_kb + kbps - 1) / kbps;
     CUtensorMap ta, tb;
-    int rc = make_map(&ta, A, M, K, lda, TC_BM);
+    int rc = make_map(&ta, A, M, K, lda, TC_BM, esize);
     if (rc) return rc;
-    rc = make_map(&tb, B, N, K, ldb, BN);
+    rc = make_map(&tb, B, N, K, ldb, BN, esize);
     if (rc) return rc;
     TcParams p;
     p.M = (int)M;
@@ -313,17 +358,29 @@ int gemm_bf16_tc(const __nv_bfloat16 *A, int64_t M, int64_t lda, const __nv_bflo
     p.C = C;
     p.ldc = ldc;
     p.partial = splits > 1 ? work : nullptr;
+    p.row_scale = rs;
+    p.col_scale = cs;
     p.status = status;
     const size_t sm = tc_smem(BN);
-    LV_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
-    gemm_bf16_tc_kernel<<<grid, 128, sm, st>>>(ta, tb, p);
-    LV_CHECK_LAUNCH("gemm_bf16_tc_kernel");
+    if (fp8) {
+        LV_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        gemm_tc_kernel<1><<<grid, 128, sm, st>>>(ta, tb, p);
+    } else {
+        LV_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        gemm_tc_kernel<0><<<grid, 128, sm, st>>>(ta, tb, p);
+    }
+    LV_CHECK_LAUNCH("gemm_tc_kernel");
     if (splits > 1) {
         splitk_reduce_kernel<<<(unsigned)((M * N + 255) / 256), 256, 0, st>>>(work, splits, (int)M, N, C, ldc);
         LV_CHECK_LAUNCH("splitk_reduce_kernel");
     }
     return LV_OK;
+}
+
+int gemm_bf16_tc(const __nv_bfloat16 *A, int64_t M, int64_t lda, const __nv_bfloat16 *B, int N, int64_t ldb, int64_t K,
+                 float *C, int ldc, int splits, float *work, int *status, cudaStream_t st) {
+    return gemm_tc(0, A, M, lda, B, N, ldb, K, C, ldc, splits, work, nullptr, nullptr, status, st);
 }
 
 int launch_cast_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *Y, int ldo, cudaStream_t st) {
@@ -358,6 +415,25 @@ int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float 
     if (rc) return rc;
     if (ldy > d) LV_CUDA(cudaMemset2DAsync(Y + d, (size_t)ldy * 4, 0, (size_t)(ldy - d) * 4, (size_t)n, st));
     return gemm_bf16_tc(Xb, n, ldx, Pb, d, ldx, D, Y, ldy, 1, nullptr, status, st);
+}
+
+// Y (n x ldy) = X P^T with e4m3 operands and per-row scales (X rows and P rows), float32
+// accumulation on the tensor cores; columns d..ldy-1 zeroed.
+int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                size_t *ws_bytes, int *status, cudaStream_t st) {
+    const int ldx = (int)round_up(D, 16);
+    const size_t xb = round_up((int64_t)n * ldx, 256), pb = round_up((int64_t)d * ldx, 256);
+    const size_t sxb = round_up(4 * n, 256), spb = round_up(4 * (int64_t)d, 256);
+    int rc = ensure_ws(ws, ws_bytes, xb + pb + sxb + spb);
+    if (rc) return rc;
+    uint8_t *base = reinterpret_cast<uint8_t *>(*ws);
+    uint8_t *X8 = base, *P8 = base + xb;
+    float *sx = reinterpret_cast<float *>(base + xb + pb), *sp = reinterpret_cast<float *>(base + xb + pb + sxb);
+    cast_e4m3_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(X, n, D, X8, ldx, sx);
+    cast_e4m3_kernel<<<(unsigned)((d + 7) / 8), 256, 0, st>>>(P, d, D, P8, ldx, sp);
+    LV_CHECK_LAUNCH("cast_e4m3_kernel");
+    if (ldy > d) LV_CUDA(cudaMemset2DAsync(Y + d, (size_t)ldy * 4, 0, (size_t)(ldy - d) * 4, (size_t)n, st));
+    return gemm_tc(1, X8, n, ldx, P8, d, ldx, D, Y, ldy, 1, nullptr, sx, sp, status, st);
 }
 
 // K (D x D) = X^T X over the n rows of X with bf16 operands (X^T staged in bf16).

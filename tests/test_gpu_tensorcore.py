@@ -80,3 +80,19 @@ def test_encode_with_bf16_projection(lv):
     err = np.abs(dec - Y).max(axis=1)
     bound = delta / 2 + TOL * np.linalg.norm(pb["X"], axis=1) * np.linalg.norm(pb["P"], axis=1).max()
     assert np.all(err <= bound)
+
+
+@pytest.mark.parametrize("n,D,d", [(300, 128, 32), (1000, 768, 160), (77, 200, 64), (4097, 768, 160)])
+def test_projection_fp8_per_row_scaled(lv, n, D, d):
+    """e4m3 operands (3 mantissa bits, per-row scales max|row|/448) on the tcgen05 f8f6f4 path:
+    each operand is off by <= 2^-4 relative, so a dot product by <= 2^-3 ||x|| ||p||; the test
+    uses 2^-3 and checks the typical error is far smaller."""
+    rng = np.random.default_rng(n + 2 * D + d)
+    X = rng.standard_normal((n, D)).astype(np.float32)
+    P = rng.standard_normal((d, D)).astype(np.float32)
+    Y = lv.leanvec_project(t(X), t(P), precision=lv.PREC_FP8).cpu().numpy()
+    ref = X.astype(np.float64) @ P.T.astype(np.float64)
+    scale = np.linalg.norm(X, axis=1)[:, None] * np.linalg.norm(P, axis=1)[None, :]
+    err = np.abs(Y - ref) / scale
+    assert err.max() <= 2.0 ** -3
+    assert err.mean() <= 2e-2
