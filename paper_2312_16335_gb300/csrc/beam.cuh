@@ -683,8 +683,9 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     float *const vS = reinterpret_cast<float *>(vI + p.Rcap);
     int *const vPB = reinterpret_cast<int *>(vS + p.Rcap);     // beam members ahead of each
     int *const sPB = cI;  // vPB in candidate-rank order (reuses cI once compacted)
-    const int hmask = p.Hcap - 1;
-    const int hshift = 32 - p.hbits;
+    // visited cache: Hcap / 4 buckets of 4 ids, one 16-byte load per lookup
+    int4 *const hash4 = reinterpret_cast<int4 *>(hash);
+    const int bshift = 34 - p.hbits;  // 32 - log2(buckets)
     PS ps;
 
     for (;;) {
@@ -710,7 +711,7 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
         const int entry = p.entry;
         if (lane == 0) {
             cI[0] = entry;
-            hash[((unsigned)entry * 0x9E3779B1u) >> hshift] = entry;
+            hash[4 * (int)(((unsigned)entry * 0x9E3779B1u) >> bshift)] = entry;
         }
         __syncwarp();
         ps.score(cI, cS, 1, lane);
@@ -778,25 +779,15 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                     if (u >= p.n) {
                         atomicOr(p.status, ST_CORRUPT);
                     } else {
-                        const unsigned h = ((unsigned)u * 0x9E3779B1u) >> hshift;
-                        int slot = -1;
-                        bool found = false;
-#pragma unroll
-                        for (int pr = 0; pr < 4; ++pr) {
-                            const int s = (int)((h + pr) & hmask);
-                            const int v = hash[s];
-                            if (v == u) {
-                                found = true;
-                                break;
-                            }
-                            if (v < 0) {
-                                slot = s;
-                                break;
-                            }
-                        }
-                        if (!found) {
+                        // a bucket that is full forgets one id (chosen by two more bits of the
+                        // hash): the cache may forget, it never reports an unvisited id
+                        const unsigned hv = (unsigned)u * 0x9E3779B1u;
+                        const int b = (int)(hv >> bshift);
+                        const int4 v = hash4[b];
+                        if (v.x != u && v.y != u && v.z != u && v.w != u) {
                             isnew = true;
-                            hash[slot >= 0 ? slot : (int)h] = u;
+                            const int s = v.x < 0 ? 0 : v.y < 0 ? 1 : v.z < 0 ? 2 : v.w < 0 ? 3 : (int)((hv >> (bshift - 2)) & 3u);
+                            hash[4 * b + s] = u;
                         }
                     }
                 }
@@ -855,14 +846,30 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             if (cv == 0) continue;
             // an id can appear twice in one round only if the visited cache forgot it
             // between two parents: keep the first copy
+            bool anydup = false;
             if (p.W > 1) {
-                for (int j = lane; j < cv; j += 32) {
-                    const int id = vI[j];
-                    bool dup = false;
-                    for (int u = 0; u < j; ++u) dup |= vI[u] == id;
-                    if (dup) vPB[j] = -1;
+                if (cv <= 32) {
+                    // lanes past cv hold distinct negative keys that match nothing
+                    const int id = lane < cv ? vI[lane] : -2 - lane;
+                    const bool dup = (__match_any_sync(FULL, id) & lt) != 0u;
+                    if (dup) vPB[lane] = -1;
+                    anydup = __any_sync(FULL, dup);
+                } else {
+                    bool d = false;
+                    for (int j = lane; j < cv; j += 32) {
+                        const int id = vI[j];
+                        bool dup = false;
+                        for (int u = 0; u < j; ++u) dup |= vI[u] == id;
+                        if (dup) {
+                            vPB[j] = -1;
+                            d = true;
+                        }
+                    }
+                    anydup = __any_sync(FULL, d);
                 }
                 __syncwarp();
+            }
+            if (anydup) {
                 int cv2 = 0;
                 for (int j0 = 0; j0 < cv; j0 += 32) {
                     const int j = j0 + lane;
