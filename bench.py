@@ -664,10 +664,10 @@ def main():
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
                 "d2h_bytes_per_step": m * k * 8},
-        "gpu_launches": (5 if args.projection == "bf16" else 3) * args.steps,
+        "gpu_launches": (6 if args.projection == "bf16" else 4) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L),
-                     "kernel": "beam_kernel<LvqIntScorer<3,8>,search,rerank>",
+                     "kernel": "beam_kernel<LvqIntScorer<3,8>,search> + rerank_kernel",
                      "kernel_ms": kern_avg, "bytes_per_query": bytes_q, "hops_per_query": hops,
                      "scored_per_query": scored, "peak_kind": peak_kind},
         "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "recall_at_10": rec_b,

@@ -302,7 +302,8 @@ typedef struct {
     int32_t width;           /* search width: beam members expanded per round, 1..4 (0 = 1);
                                 width * R <= 256.  1 is the classic best-first traversal */
     void *event_begin;       /* optional cudaEvent_t recorded on `stream` right before the */
-    void *event_end;         /* beam-search kernel and right after it (profiling); may be NULL */
+    void *event_end;         /* beam-search kernel and right after the rerank kernel (or the
+                                beam-search kernel without rerank) (profiling); may be NULL */
 } lv_search_params;
 
 /* Per-query counters (device, m entries) when stats != NULL. */
@@ -337,10 +338,13 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
  * the library (held on every GPU that loads the library until the process exits)
  * and calls no cudaMalloc, cudaFree or allocating routine.
  *   - Same arguments, semantics and results as leanvec_search.
- *   - Capacity: m * (4 * ldq + 16) + 256 bytes must fit in 16 MiB, where ldq is
- *     the primary dimension rounded up to whole 16-byte code chunks (d for LVQ-8
- *     with d a multiple of 16; e.g. m <= 25,000 queries at d = 160); larger
- *     batches return LV_ERR_CAPACITY before anything is launched -- split them.
+ *   - Capacity: 256 + m * 4 * ldq + m * 16 [+ m * 4 * (Lc + 1) when the search
+ *     reranks] bytes, each of the three parts rounded up to 256, must fit in
+ *     16 MiB, where ldq is the primary dimension rounded up to whole 16-byte code
+ *     chunks (d for LVQ-8 with d a multiple of 16) and Lc is params->uniform.L
+ *     rounded up to 32 (e.g. m <= 12,900 queries at d = 160, L = 160 with
+ *     rerank; m <= 25,000 without); larger batches return LV_ERR_CAPACITY before
+ *     anything is launched -- split them.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

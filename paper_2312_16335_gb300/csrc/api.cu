@@ -187,6 +187,7 @@ int leanvec_index_free(lv_index *idx) {
     cudaFree(idx->status);
     cudaFree(idx->ws_q);
     cudaFree(idx->ws_c);
+    cudaFree(idx->ws_cand);
     cudaFree(idx->bws);
     delete idx;
     return LV_OK;
@@ -522,11 +523,20 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.W = params->width > 0 ? params->width : 1;
     if (p.W > WMAX || p.W * idx->R > CMAX) return fail(LV_ERR_ARG, "search: need width <= 4 and width * R <= 256");
     p.Rcap = (int)round_up((int64_t)p.W * idx->R, 32);
-    p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap);
+    const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + 3) / 4;
+    p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
     int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
     while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;
     if ((size_t)warps * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
     if (idx->sbits && idx->sg.code_chunks + 1 > 64) return fail(LV_ERR_ARG, "search: D > 1008 is not supported by the rerank");
+    const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
+    if (rerank) {
+        p.ldc = p.Lcap;  // r <= L <= Lcap
+        rc = ensure_ws((void **)&idx->ws_cand, &idx->ws_cand_bytes, sizeof(int32_t) * (size_t)m * (p.ldc + 1));
+        if (rc) return rc;
+        p.cand = idx->ws_cand;
+        p.cand_n = idx->ws_cand + (size_t)m * p.ldc;
+    }
     LV_CUDA(cudaMemsetAsync(p.work, 0, sizeof(int), st));
     const size_t smem = (size_t)warps * p.warp_smem;
     const int block = warps * 32;
@@ -538,6 +548,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         int nc = (idx->pg.code_chunks + 1 + 3) / 4;
         rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
                              : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
+        if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
     }
     if (rc) return rc;
     if (params->event_end) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_end, st));

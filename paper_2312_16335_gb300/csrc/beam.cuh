@@ -48,6 +48,12 @@ struct BeamParams {
     float *scores;
     int ldo;
     int2 *stats;
+    // rerank hand-off (RERANK): the best min(r, beam size) ids of query i go to
+    // cand[i * ldc ..] and their count to cand_n[i]; cand_n[i] = -1 when r = 0 and the
+    // query's results were written directly
+    int32_t *cand;
+    int *cand_n;
+    int ldc;
     // scheduling / capacities
     int *work;
     int *status;
@@ -62,7 +68,11 @@ struct BeamParams {
 constexpr int WMAX = 4;
 constexpr int CMAX = 256;  // candidates of one round (W * R)
 
-inline int beam_warp_smem(int Lcap, int Hcap, int Rcap) { return 8 * Lcap + 4 * Hcap + 20 * Rcap; }
+// per-warp shared memory: beam (8 Lcap), visited cache (4 Hcap), 4 candidate arrays (16 Rcap), the
+// scorer's query (qbytes, a multiple of 16)
+inline int beam_warp_smem(int Lcap, int Hcap, int Rcap, int qbytes) { return 8 * Lcap + 4 * Hcap + 16 * Rcap + qbytes; }
+// shared bytes of the LVQ scorer's query limbs (nc chunks per lane, see LvqIntScorer)
+inline int lvq_query_bytes(int bits, int nc) { return bits == 32 ? 0 : 4 * nc * 3 * (bits == 8 ? 1 : 2) * 16; }
 
 // --------------------------------------------------------------------------------
 // Primary scorer: LVQ records, 4 lanes per record, 8 records per warp pass.
@@ -194,35 +204,31 @@ __device__ __forceinline__ int dp4a_uu(uint32_t a, uint32_t b, int c) {
 template <int NC, int BITS>
 struct LvqIntScorer {
     static constexpr int CPC = BITS == 8 ? 16 : 32;  // codes per 16-byte chunk
-    static constexpr int W = BITS == 8 ? 4 : 8;      // limb words per chunk
-    uint32_t qh[NC][W], qm[NC][W], ql[NC][W];
+    static constexpr int V4 = BITS == 8 ? 1 : 2;     // 16-byte limb vectors per limb and chunk
+    // The limbs live in the warp's shared memory, chunk c at lq[(3 c + limb) V4 ..], limb 0 = h,
+    // 1 = m, 2 = l, for the 4 NC chunks a group of 4 lanes covers (chunks >= CH are zero).
+    static constexpr int QBYTES = 4 * NC * 3 * V4 * 16;
+    const uint4 *lq;
     float cq, sq, scale;
     int CH;
     const uint8_t *base;
     int64_t stride;
 
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *qsmem) {
         CH = p.prim_chunks;
         base = p.prim;
         stride = p.prim_stride;
-        const int g = lane & 3;
         const float *row = p.qp + qi * p.ldq;
         float amax = 0.f;
+        for (int j = lane; j < CH * CPC; j += 32) amax = fmaxf(amax, fabsf(row[j]));
 #pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            const int c = g + 4 * t;
-            if (c < CH)
-                for (int e = 0; e < CPC; ++e) amax = fmaxf(amax, fabsf(row[c * CPC + e]));
-        }
-        amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, 1));
-        amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, 2));
+        for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
         scale = amax > 0.f ? amax / 8388607.0f : 1.0f;
         const float inv = amax > 0.f ? 8388607.0f / amax : 0.f;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(qsmem);
+        for (int c = lane; c < 4 * NC; c += 32) {
 #pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            const int c = g + 4 * t;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
+            for (int w = 0; w < 4 * V4; ++w) {
                 uint32_t h = 0, mm = 0, l = 0;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
@@ -238,40 +244,16 @@ struct LvqIntScorer {
                     mm |= (uint32_t)((qv >> 8) & 0xff) << (8 * b);
                     l |= (uint32_t)(qv & 0xff) << (8 * b);
                 }
-                qh[t][w] = h;
-                qm[t][w] = mm;
-                ql[t][w] = l;
+                dst[(3 * c + 0) * 4 * V4 + w] = h;
+                dst[(3 * c + 1) * 4 * V4 + w] = mm;
+                dst[(3 * c + 2) * 4 * V4 + w] = l;
             }
         }
+        __syncwarp();
+        lq = reinterpret_cast<const uint4 *>(qsmem);
         float4 k = p.qconst[qi];
         cq = k.x;
         sq = k.y;
-    }
-
-    __device__ __forceinline__ float dot(const uint4 (&v)[NC]) const {
-        int sh = 0, sm = 0, sl = 0;
-#pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            const uint32_t w4[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (BITS == 8) {
-                    sh = dp4a_su(qh[t][i], w4[i], sh);
-                    sm = dp4a_uu(qm[t][i], w4[i], sm);
-                    sl = dp4a_uu(ql[t][i], w4[i], sl);
-                } else {
-                    const uint32_t lo = w4[i] & 0x0F0F0F0Fu, hi = (w4[i] >> 4) & 0x0F0F0F0Fu;
-                    sh = dp4a_su(qh[t][2 * i], lo, sh);
-                    sh = dp4a_su(qh[t][2 * i + 1], hi, sh);
-                    sm = dp4a_uu(qm[t][2 * i], lo, sm);
-                    sm = dp4a_uu(qm[t][2 * i + 1], hi, sm);
-                    sl = dp4a_uu(ql[t][2 * i], lo, sl);
-                    sl = dp4a_uu(ql[t][2 * i + 1], hi, sl);
-                }
-            }
-        }
-        // partial sums of one lane are < 2^24 in magnitude: exact conversions
-        return fmaf((float)sh, 65536.0f, fmaf((float)sm, 256.0f, (float)sl));
     }
 
     template <int P>
@@ -291,9 +273,49 @@ struct LvqIntScorer {
                 v[r][t] = (c <= CH && id >= 0) ? ldg_stream(rec + 16 * c) : make_uint4(0, 0, 0, 0);
             }
         }
+        int sh[P], sm[P], sl[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) sh[r] = sm[r] = sl[r] = 0;
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const uint4 *L4 = lq + (g + 4 * t) * 3 * V4;
+#pragma unroll
+            for (int vv = 0; vv < V4; ++vv) {
+                const uint4 h4 = L4[vv], m4 = L4[V4 + vv], l4 = L4[2 * V4 + vv];
+                const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w};
+                const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+                const uint32_t lw[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int r = 0; r < P; ++r) {
+                    const uint32_t w4[4] = {v[r][t].x, v[r][t].y, v[r][t].z, v[r][t].w};
+                    if (BITS == 8) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            sh[r] = dp4a_su(hw[i], w4[i], sh[r]);
+                            sm[r] = dp4a_uu(mw[i], w4[i], sm[r]);
+                            sl[r] = dp4a_uu(lw[i], w4[i], sl[r]);
+                        }
+                    } else {
+                        // limb words 4 vv .. 4 vv + 3 = low / high nibbles of code words 2 vv, 2 vv + 1
+#pragma unroll
+                        for (int i2 = 0; i2 < 2; ++i2) {
+                            const uint32_t cw = w4[2 * vv + i2];
+                            const uint32_t lo = cw & 0x0F0F0F0Fu, hi = (cw >> 4) & 0x0F0F0F0Fu;
+                            sh[r] = dp4a_su(hw[2 * i2], lo, sh[r]);
+                            sh[r] = dp4a_su(hw[2 * i2 + 1], hi, sh[r]);
+                            sm[r] = dp4a_uu(mw[2 * i2], lo, sm[r]);
+                            sm[r] = dp4a_uu(mw[2 * i2 + 1], hi, sm[r]);
+                            sl[r] = dp4a_uu(lw[2 * i2], lo, sl[r]);
+                            sl[r] = dp4a_uu(lw[2 * i2 + 1], hi, sl[r]);
+                        }
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int r = 0; r < P; ++r) {
-            float s = dot(v[r]);
+            // partial sums of one lane are < 2^24 in magnitude: exact conversions
+            float s = fmaf((float)sh[r], 65536.0f, fmaf((float)sm[r], 256.0f, (float)sl[r]));
             float dl = 0.f, lo = 0.f;
 #pragma unroll
             for (int t = 0; t < NC; ++t)
@@ -364,7 +386,8 @@ struct BuildScorer {
     const uint8_t *base;
     int64_t stride;
 
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+    static constexpr int QBYTES = 0;
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *) {
         CH = p.prim_chunks;
         base = p.prim;
         stride = p.prim_stride;
@@ -466,7 +489,8 @@ struct WarpScorer {
         }
     }
 
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
+    static constexpr int QBYTES = 0;
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *) {
         // full-dimensional float32 search: padded queries, no constants
         setup_row(p.qp + qi * p.ldq, p.ldq, p.prim_chunks, p.prim, p.prim_stride, 0.f, 0.f, lane);
     }
@@ -533,140 +557,8 @@ struct WarpScorer {
 };
 
 // --------------------------------------------------------------------------------
-// Rerank scorer (whole warp per record): LVQ-8 secondary records scored against the
-// unreduced query held as 24-bit fixed point in three byte limbs (same scheme and
-// error bound as LvqIntScorer, with D in place of d).  Lane l holds code chunks l and
-// l + 32 (D <= 1008); 4 records per pass.
-// --------------------------------------------------------------------------------
-struct SecIntScorer {
-    static constexpr int NCW = 2, U = 4;
-    uint32_t qh[NCW][4], qm[NCW][4], ql[NCW][4];
-    float c0, s0, scale;
-    int CH;
-    const uint8_t *base;
-    int64_t stride;
-
-    __device__ __forceinline__ void setup(const float *qrow, int D, int chunks, const uint8_t *b, int64_t st,
-                                          float cc, float ss, int lane) {
-        CH = chunks;
-        base = b;
-        stride = st;
-        c0 = cc;
-        s0 = ss;
-        float amax = 0.f;
-        for (int j = lane; j < D; j += 32) amax = fmaxf(amax, fabsf(qrow[j]));
-#pragma unroll
-        for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
-        scale = amax > 0.f ? amax / 8388607.0f : 1.0f;
-        const float inv = amax > 0.f ? 8388607.0f / amax : 0.f;
-#pragma unroll
-        for (int t = 0; t < NCW; ++t) {
-            const int c = lane + 32 * t;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                uint32_t h = 0, mm = 0, l = 0;
-#pragma unroll
-                for (int bb = 0; bb < 4; ++bb) {
-                    const int j = c * 16 + 4 * w + bb;
-                    int qv = 0;
-                    if (c < CH && j < D) {
-                        qv = __float2int_rn(qrow[j] * inv);
-                        qv = max(-8388607, min(8388607, qv));
-                    }
-                    h |= (uint32_t)((qv >> 16) & 0xff) << (8 * bb);
-                    mm |= (uint32_t)((qv >> 8) & 0xff) << (8 * bb);
-                    l |= (uint32_t)(qv & 0xff) << (8 * bb);
-                }
-                qh[t][w] = h;
-                qm[t][w] = mm;
-                ql[t][w] = l;
-            }
-        }
-    }
-
-    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
-        const int tot = CH + 1;
-        const int holder = CH & 31, tslot = CH >> 5;
-        for (int b = 0; b < cnt; b += U) {
-            uint4 v[U][NCW];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int id = b + u < cnt ? ids[b + u] : -1;
-                const uint8_t *r = base + (int64_t)(id < 0 ? 0 : id) * stride;
-#pragma unroll
-                for (int t = 0; t < NCW; ++t) {
-                    const int c = lane + 32 * t;
-                    v[u][t] = (c < tot && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int sh = 0, sm = 0, sl = 0;
-#pragma unroll
-                for (int t = 0; t < NCW; ++t) {
-                    const uint32_t w4[4] = {v[u][t].x, v[u][t].y, v[u][t].z, v[u][t].w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        sh = dp4a_su(qh[t][i], w4[i], sh);
-                        sm = dp4a_uu(qm[t][i], w4[i], sm);
-                        sl = dp4a_uu(ql[t][i], w4[i], sl);
-                    }
-                }
-                float s = fmaf((float)sh, 65536.0f, fmaf((float)sm, 256.0f, (float)sl));
-#pragma unroll
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-                float dl = 0.f, lo = 0.f;
-#pragma unroll
-                for (int t = 0; t < NCW; ++t)
-                    if (t == tslot) {
-                        dl = __uint_as_float(v[u][t].x);
-                        lo = __uint_as_float(v[u][t].y);
-                    }
-                dl = __shfl_sync(FULL, dl, holder);
-                lo = __shfl_sync(FULL, lo, holder);
-                if (lane == 0 && b + u < cnt) out[b + u] = fmaf(dl * scale, s, fmaf(lo, s0, c0));
-            }
-        }
-    }
-};
-
-// The best k of (S[0..n), I[0..n)) by (score desc, id asc), k rounds of a warp argmax;
-// selected entries are marked by id -1.  Writes oid/osc[0..min(k, n)).
-__device__ __forceinline__ void warp_topk(float *S, int *I, int n, int k, int32_t *oid, float *osc, int lane) {
-    for (int r = 0; r < k && r < n; ++r) {
-        float bs = -INFINITY;
-        int bi = 0x7fffffff, bt = -1;
-        for (int t = lane; t < n; t += 32) {
-            const int id = I[t];
-            if (id >= 0 && (bt < 0 || key_better(S[t], id, bs, bi))) {
-                bs = S[t];
-                bi = id;
-                bt = t;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const float os = __shfl_xor_sync(FULL, bs, o);
-            const int oi = __shfl_xor_sync(FULL, bi, o);
-            const int ot = __shfl_xor_sync(FULL, bt, o);
-            if (ot >= 0 && (bt < 0 || key_better(os, oi, bs, bi))) {
-                bs = os;
-                bi = oi;
-                bt = ot;
-            }
-        }
-        if (lane == 0) {
-            oid[r] = bi;
-            osc[r] = bs;
-            I[bt] = -1;
-        }
-        __syncwarp();
-    }
-}
-
-// --------------------------------------------------------------------------------
 // The beam kernel.  BUILD: queries are nodes (p.qnodes), output = the final beam.
-// RERANK: rescore the top-r of the beam with the secondary store.
+// RERANK: hand the top-r of the beam to the rerank kernel (rerank.cu).
 // --------------------------------------------------------------------------------
 template <class PS, bool BUILD, bool RERANK>
 __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
@@ -677,12 +569,11 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     float *const bS = reinterpret_cast<float *>(my);           // beam scores (sorted, best first)
     int *const bI = reinterpret_cast<int *>(bS + p.Lcap);      // beam ids, top bit = expanded
     int *const hash = bI + p.Lcap;                             // visited cache
-    int *const cI = hash + p.Hcap;                             // ids of one expansion
-    float *const cS = reinterpret_cast<float *>(cI + p.Rcap);  // their scores
-    int *const vI = reinterpret_cast<int *>(cS + p.Rcap);      // candidates that enter
-    float *const vS = reinterpret_cast<float *>(vI + p.Rcap);
-    int *const vPB = reinterpret_cast<int *>(vS + p.Rcap);     // beam members ahead of each
-    int *const sPB = cI;  // vPB in candidate-rank order (reuses cI once compacted)
+    int *const cI = hash + p.Hcap;                             // ids of one expansion, then of
+    float *const cS = reinterpret_cast<float *>(cI + p.Rcap);  // the candidates that enter (in place)
+    int *const vPB = reinterpret_cast<int *>(cS + p.Rcap);     // beam members ahead of each (| rank << 16)
+    int *const sPB = vPB + p.Rcap;                             // the same in candidate-rank order
+    void *const qsm = sPB + p.Rcap;                            // the scorer's query
     // visited cache: Hcap / 4 buckets of 4 ids, one 16-byte load per lookup
     int4 *const hash4 = reinterpret_cast<int4 *>(hash);
     const int bshift = 34 - p.hbits;  // 32 - log2(buckets)
@@ -703,7 +594,7 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             k = min(max(k, 0), p.ldo);
         }
         r = min(max(r, 0), L);
-        ps.setup(p, qi, lane);
+        ps.setup(p, qi, lane, qsm);
 
         for (int t = lane * 4; t < p.Hcap; t += 128)
             *reinterpret_cast<int4 *>(hash + t) = make_int4(-1, -1, -1, -1);
@@ -834,10 +725,11 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                     }
                 }
                 const unsigned bal = __ballot_sync(FULL, valid);
+                __syncwarp();  // the chunk is read before it is compacted in place
                 if (valid) {
                     const int o = cv + __popc(bal & lt);
-                    vI[o] = id;
-                    vS[o] = s;
+                    cI[o] = id;
+                    cS[o] = s;
                     vPB[o] = pb;
                 }
                 cv += __popc(bal);
@@ -850,16 +742,16 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             if (p.W > 1) {
                 if (cv <= 32) {
                     // lanes past cv hold distinct negative keys that match nothing
-                    const int id = lane < cv ? vI[lane] : -2 - lane;
+                    const int id = lane < cv ? cI[lane] : -2 - lane;
                     const bool dup = (__match_any_sync(FULL, id) & lt) != 0u;
                     if (dup) vPB[lane] = -1;
                     anydup = __any_sync(FULL, dup);
                 } else {
                     bool d = false;
                     for (int j = lane; j < cv; j += 32) {
-                        const int id = vI[j];
+                        const int id = cI[j];
                         bool dup = false;
-                        for (int u = 0; u < j; ++u) dup |= vI[u] == id;
+                        for (int u = 0; u < j; ++u) dup |= cI[u] == id;
                         if (dup) {
                             vPB[j] = -1;
                             d = true;
@@ -877,16 +769,16 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                     float s = 0.f;
                     int id = 0, pb = 0;
                     if (keep) {
-                        s = vS[j];
-                        id = vI[j];
+                        s = cS[j];
+                        id = cI[j];
                         pb = vPB[j];
                     }
                     const unsigned bal = __ballot_sync(FULL, keep);
                     __syncwarp();
                     if (keep) {
                         const int o = cv2 + __popc(bal & lt);
-                        vI[o] = id;
-                        vS[o] = s;
+                        cI[o] = id;
+                        cS[o] = s;
                         vPB[o] = pb;
                     }
                     cv2 += __popc(bal);
@@ -895,14 +787,14 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                 cv = cv2;
             }
             // rank of each candidate among the candidates; sPB[rank] = beam members ahead
-            int *const rnk = reinterpret_cast<int *>(cS);  // scores were copied to vS
             for (int j = lane; j < cv; j += 32) {
-                const float s = vS[j];
-                const int id = vI[j];
+                const float s = cS[j];
+                const int id = cI[j];
                 int rank = 0;
-                for (int u = 0; u < cv; ++u) rank += key_better(vS[u], vI[u], s, id) ? 1 : 0;
-                rnk[j] = rank;
-                sPB[rank] = vPB[j];
+                for (int u = 0; u < cv; ++u) rank += key_better(cS[u], cI[u], s, id) ? 1 : 0;
+                const int pb = vPB[j];
+                sPB[rank] = pb;
+                vPB[j] = pb | (rank << 16);
             }
             __syncwarp();
             // move beam members (in place, last chunk first; a member only moves right)
@@ -933,10 +825,11 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             }
             // place the candidates (unexpanded)
             for (int j = lane; j < cv; j += 32) {
-                const int np = rnk[j] + vPB[j];
+                const int x = vPB[j];
+                const int np = (x & 0xffff) + (x >> 16);
                 if (np < L) {
-                    bS[np] = vS[j];
-                    bI[np] = vI[j];
+                    bS[np] = cS[j];
+                    bI[np] = cI[j];
                 }
             }
             size = min(L, size + cv);
@@ -953,26 +846,20 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                 osc[t] = t < size ? bS[t] : -INFINITY;
             }
         } else {
-            int nres;
-            if (RERANK && r > 0) {
+            if (RERANK && r > 0 && p.cand) {
+                // the rerank kernel scores these with the secondary store and writes the results
                 const int nr = min(r, size);
-                float *rS = reinterpret_cast<float *>(hash);
-                int *rI = hash + p.Lcap;
-                for (int t = lane; t < nr; t += 32) rI[t] = bI[t] & ~(int)EXPANDED;
+                int32_t *cd = p.cand + qi * p.ldc;
+                for (int t = lane; t < nr; t += 32) cd[t] = bI[t] & ~(int)EXPANDED;
+                if (lane == 0) p.cand_n[qi] = nr;
                 __syncwarp();
-                SecIntScorer sc;
-                const float4 kq = p.qconst[qi];
-                sc.setup(p.Q + qi * p.D, p.D, p.sec_chunks, p.sec, p.sec_stride, kq.z, kq.w, lane);
-                sc.score(rI, rS, nr, lane);
-                __syncwarp();
-                warp_topk(rS, rI, nr, k, oid, osc, lane);
-                nres = min(k, nr);
-            } else {
-                nres = min(k, size);
-                for (int t = lane; t < nres; t += 32) {
-                    oid[t] = bI[t] & ~(int)EXPANDED;
-                    osc[t] = bS[t];
-                }
+                continue;
+            }
+            if (RERANK && p.cand_n && lane == 0) p.cand_n[qi] = -1;
+            const int nres = min(k, size);
+            for (int t = lane; t < nres; t += 32) {
+                oid[t] = bI[t] & ~(int)EXPANDED;
+                osc[t] = bS[t];
             }
             for (int t = nres + lane; t < p.ldo; t += 32) {
                 oid[t] = -1;
@@ -989,5 +876,7 @@ int launch_search_lvq4(const BeamParams &p, int nc, int block, size_t smem, int 
 int launch_search_fp32(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_build_search(const BeamParams &p, int bits, int nc, int block, size_t smem, int num_sms,
                         cudaStream_t st);
+// scores the candidates the RERANK beam kernel handed over (p.cand, p.cand_n) and writes p.ids / p.scores
+int launch_rerank(const BeamParams &p, int num_sms, cudaStream_t st);
 
 }  // namespace lv

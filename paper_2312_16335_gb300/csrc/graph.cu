@@ -564,7 +564,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     while ((1 << bp.hbits) < hs) bp.hbits++;
     bp.W = 1;
     bp.Rcap = (int)round_up(R, 32);
-    bp.warp_smem = beam_warp_smem(bp.Lcap, bp.Hcap, bp.Rcap);
+    bp.warp_smem = beam_warp_smem(bp.Lcap, bp.Hcap, bp.Rcap, 0);  // the build scorer keeps its query in registers
     int warps = 8;
     while (warps > 1 && (size_t)warps * bp.warp_smem > 227 * 1024) warps >>= 1;
     const size_t bsmem = (size_t)warps * bp.warp_smem;

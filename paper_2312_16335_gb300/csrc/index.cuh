@@ -24,6 +24,8 @@ struct lv_index {
     size_t ws_q_bytes = 0;
     float4 *ws_c = nullptr;
     size_t ws_c_bytes = 0;
+    int32_t *ws_cand = nullptr;  // rerank hand-off: m x Lcap ids + m counts
+    size_t ws_cand_bytes = 0;
     // build workspace
     void *bws = nullptr;
     size_t bws_bytes = 0;

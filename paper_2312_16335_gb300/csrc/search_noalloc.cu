@@ -70,9 +70,15 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     const int cpc = idx->pbits == 8 ? 16 : idx->pbits == 4 ? 32 : 4;
     const int ldq = idx->pg.code_chunks * cpc;
     const size_t q_bytes = round_up((int64_t)sizeof(float) * m * ldq, 256);
-    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + sizeof(float4) * (size_t)m;
+    const size_t c_bytes = round_up((int64_t)sizeof(float4) * m, 256);
+    // rerank hand-off (beam kernel -> rerank kernel): m x Lcap ids + m counts
+    const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
+    const int Lcap = (int)round_up(u.L, 32);
+    const size_t r_bytes = rerank ? (size_t)round_up((int64_t)sizeof(int32_t) * m * (Lcap + 1), 256) : 0;
+    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + c_bytes + r_bytes;
     if (need > NOALLOC_SCRATCH_BYTES)
-        return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension + 16) + 256 bytes exceed the "
+        return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension + 16 [+ 4 * (L rounded up to "
+                                     "32) + 4 with rerank]) + 256 bytes (each part rounded up to 256) exceed the "
                                      "16 MiB static scratch; split the batch");
 
     int prev = -1;
@@ -88,6 +94,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         int *work = reinterpret_cast<int *>(scratch);
         float *qp = reinterpret_cast<float *>(scratch + NOALLOC_HEADER_BYTES);
         float4 *qc = reinterpret_cast<float4 *>(scratch + NOALLOC_HEADER_BYTES + q_bytes);
+        int32_t *cand = reinterpret_cast<int32_t *>(scratch + NOALLOC_HEADER_BYTES + q_bytes + c_bytes);
         rc = idx->pbits == 32 ? launch_pad_rows(Q, m, idx->D, qp, ldq, st)
                               : launch_project_fp32(Q, m, idx->D, A, idx->d, qp, ldq, st);
         if (rc) break;
@@ -143,12 +150,18 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             break;
         }
         p.Rcap = (int)round_up((int64_t)p.W * idx->R, 32);
-        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap);
+        const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + 3) / 4;
+        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
         int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
         while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;
         if ((size_t)warps * p.warp_smem > 227 * 1024) {
             rc = fail(LV_ERR_CAPACITY, "search_noalloc: L / hash_slots too large for shared memory");
             break;
+        }
+        if (rerank) {
+            p.ldc = p.Lcap;
+            p.cand = cand;
+            p.cand_n = cand + (size_t)m * p.ldc;
         }
         // the scratch keeps the previous call's contents: the work counter must restart at 0
         cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), st);
@@ -165,6 +178,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             const int nc = (idx->pg.code_chunks + 1 + 3) / 4;
             rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
                                  : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
+            if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
         }
         if (rc) break;
         if (params->event_end) cudaEventRecord((cudaEvent_t)params->event_end, st);
