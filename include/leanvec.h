@@ -301,6 +301,10 @@ typedef struct {
     int32_t warps_per_block; /* 0 = default */
     int32_t width;           /* search width: beam members expanded per round, 1..4 (0 = 1);
                                 width * R <= 256.  1 is the classic best-first traversal */
+    int32_t warps_per_query; /* warps that serve one query, 1, 2 or 4, dividing width (0 = 1):
+                                each expands width / warps_per_query of a round's parents.
+                                Results do not depend on it; with more warps per query each
+                                query finishes sooner (shorter batch tail) */
     void *event_begin;       /* optional cudaEvent_t recorded on `stream` right before the */
     void *event_end;         /* beam-search kernel and right after the rerank kernel (or the
                                 beam-search kernel without rerank) (profiling); may be NULL */

@@ -299,11 +299,14 @@ class Index:
     def search(self, Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0, max_hops: int = 0,
                desc: torch.Tensor | None = None, ldo: int | None = None, stats: bool = False,
                projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0,
-               out: tuple[torch.Tensor, torch.Tensor] | None = None, events=None, width: int = 1):
+               out: tuple[torch.Tensor, torch.Tensor] | None = None, events=None, width: int = 1,
+               warps_per_query: int = 0):
         """Search m queries. desc: optional (m, 4) int32 CUDA tensor of per-query
         (k, L, rerank, max_hops); then k/L are the upper bounds used for capacity.
-        events: optional pair of torch.cuda.Event recorded around the beam kernel.
-        width: beam members expanded per round (1 = classic best-first)."""
+        events: optional pair of torch.cuda.Event recorded around the search kernels.
+        width: beam members expanded per round (1 = classic best-first).
+        warps_per_query: warps sharing one query (1, 2, 4; divides width; 0 = 1); the
+        results do not depend on it."""
         Q = _f32(Q)
         m = Q.shape[0]
         ldo = k if ldo is None else ldo
@@ -314,8 +317,8 @@ class Index:
             ids, sc = out
         st = torch.empty((m, 2), dtype=torch.int32, device=self.device) if stats else None
         ev0, ev1 = (None, None) if events is None else (events[0].cuda_event, events[1].cuda_event)
-        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width, ev0,
-                             ev1)
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width,
+                             warps_per_query, ev0, ev1)
         if desc is not None:
             desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None
@@ -338,7 +341,7 @@ class Index:
             sc = torch.empty((m, ldo), dtype=torch.float32, device=self.device)
         else:
             ids, sc = out
-        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), PREC_FP32, 0, 0, 1, None, None)
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), PREC_FP32, 0, 0, 1, 0, None, None)
         Ac = _f32(A) if A is not None else None
         check(lib().leanvec_search_noalloc(self._h, _ptr(Q), m, _ptr(Ac), ctypes.byref(prm), None, _ptr(ids),
                                            _ptr(sc), ldo, None, _stream(self.device)))

@@ -522,12 +522,16 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     while ((1 << p.hbits) < hs) p.hbits++;
     p.W = params->width > 0 ? params->width : 1;
     if (p.W > WMAX || p.W * idx->R > CMAX) return fail(LV_ERR_ARG, "search: need width <= 4 and width * R <= 256");
-    p.Rcap = (int)round_up((int64_t)p.W * idx->R, 32);
+    p.T = params->warps_per_query > 0 ? params->warps_per_query : 1;
+    if ((p.T != 1 && p.T != 2 && p.T != 4) || p.W % p.T)
+        return fail(LV_ERR_ARG, "search: warps_per_query must be 1, 2 or 4 and divide width");
+    p.Rcap = beam_rcap(p.W, p.T, idx->R);
     const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + 3) / 4;
     p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
     int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
-    while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;
-    if ((size_t)warps * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
+    if (warps % p.T || warps > 32) return fail(LV_ERR_ARG, "search: warps_per_block must be <= 32 and a multiple of warps_per_query");
+    while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
+    if ((size_t)(warps / p.T) * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
     if (idx->sbits && idx->sg.code_chunks + 1 > 64) return fail(LV_ERR_ARG, "search: D > 1008 is not supported by the rerank");
     const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
     if (rerank) {
@@ -538,7 +542,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         p.cand_n = idx->ws_cand + (size_t)m * p.ldc;
     }
     LV_CUDA(cudaMemsetAsync(p.work, 0, sizeof(int), st));
-    const size_t smem = (size_t)warps * p.warp_smem;
+    const size_t smem = (size_t)(warps / p.T) * p.warp_smem;
     const int block = warps * 32;
     if (params->event_begin) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_begin, st));
     if (idx->pbits == 32) {

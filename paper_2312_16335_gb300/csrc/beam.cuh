@@ -62,124 +62,22 @@ struct BeamParams {
     int hbits;  // log2(Hcap)
     int Rcap;   // candidate buffer capacity (multiple of 32, >= W * R)
     int W;      // search width: parents expanded per round (1..4, W * R <= 256)
-    int warp_smem;
+    int T;      // warps per query (1, 2 or 4; divides W); Rcap = T * (W / T * R rounded up to 32)
+    int warp_smem;  // shared bytes of one query (one team of T warps)
 };
 
 constexpr int WMAX = 4;
 constexpr int CMAX = 256;  // candidates of one round (W * R)
 
-// per-warp shared memory: beam (8 Lcap), visited cache (4 Hcap), 4 candidate arrays (16 Rcap), the
-// scorer's query (qbytes, a multiple of 16)
-inline int beam_warp_smem(int Lcap, int Hcap, int Rcap, int qbytes) { return 8 * Lcap + 4 * Hcap + 16 * Rcap + qbytes; }
+// shared memory of one query: beam (8 Lcap), visited cache (4 Hcap), 4 candidate arrays (16 Rcap),
+// the scorer's query (qbytes, a multiple of 16), control words (64)
+inline int beam_warp_smem(int Lcap, int Hcap, int Rcap, int qbytes) {
+    return 8 * Lcap + 4 * Hcap + 16 * Rcap + qbytes + 64;  // + 16 control words
+}
+// candidate capacity of a team: T slices of W / T parents' neighbours, each rounded up to 32
+inline int beam_rcap(int W, int T, int R) { return T * ((W / T * R + 31) / 32 * 32); }
 // shared bytes of the LVQ scorer's query limbs (nc chunks per lane, see LvqIntScorer)
 inline int lvq_query_bytes(int bits, int nc) { return bits == 32 ? 0 : 4 * nc * 3 * (bits == 8 ? 1 : 2) * 16; }
-
-// --------------------------------------------------------------------------------
-// Primary scorer: LVQ records, 4 lanes per record, 8 records per warp pass.
-// score = cq + lower * sq + delta * <q', codes>    (decoded inner product, Eq. 1)
-// --------------------------------------------------------------------------------
-template <int NC, int BITS>
-struct LvqGroupScorer {
-    static constexpr int CPC = BITS == 8 ? 16 : 32;  // codes per 16-byte chunk
-    float q[NC][CPC];
-    float cq, sq;
-    int CH;
-    const uint8_t *base;
-    int64_t stride;
-
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane) {
-        CH = p.prim_chunks;
-        base = p.prim;
-        stride = p.prim_stride;
-        const int g = lane & 3;
-        const float *row = p.qp + qi * p.ldq;
-#pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            const int c = g + 4 * t;
-#pragma unroll
-            for (int e = 0; e < CPC; e += 4) {
-                float4 v = c < CH ? *reinterpret_cast<const float4 *>(row + c * CPC + e) : make_float4(0, 0, 0, 0);
-                q[t][e] = v.x;
-                q[t][e + 1] = v.y;
-                q[t][e + 2] = v.z;
-                q[t][e + 3] = v.w;
-            }
-        }
-        float4 k = p.qconst[qi];
-        cq = k.x;
-        sq = k.y;
-    }
-
-    __device__ __forceinline__ float dot(const uint4 (&v)[NC]) const {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-        for (int t = 0; t < NC; ++t) {
-            const uint32_t w[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (BITS == 8) {
-                    a0 = fmaf(q[t][4 * i + 0], byte_to_float<0>(w[i]), a0);
-                    a1 = fmaf(q[t][4 * i + 1], byte_to_float<1>(w[i]), a1);
-                    a2 = fmaf(q[t][4 * i + 2], byte_to_float<2>(w[i]), a2);
-                    a3 = fmaf(q[t][4 * i + 3], byte_to_float<3>(w[i]), a3);
-                } else {
-                    const uint32_t lo = w[i] & 0x0F0F0F0Fu, hi = (w[i] >> 4) & 0x0F0F0F0Fu;
-                    a0 = fmaf(q[t][8 * i + 0], byte_to_float<0>(lo), a0);
-                    a1 = fmaf(q[t][8 * i + 1], byte_to_float<0>(hi), a1);
-                    a2 = fmaf(q[t][8 * i + 2], byte_to_float<1>(lo), a2);
-                    a3 = fmaf(q[t][8 * i + 3], byte_to_float<1>(hi), a3);
-                    a0 = fmaf(q[t][8 * i + 4], byte_to_float<2>(lo), a0);
-                    a1 = fmaf(q[t][8 * i + 5], byte_to_float<2>(hi), a1);
-                    a2 = fmaf(q[t][8 * i + 6], byte_to_float<3>(lo), a2);
-                    a3 = fmaf(q[t][8 * i + 7], byte_to_float<3>(hi), a3);
-                }
-            }
-        }
-        return (a0 + a1) + (a2 + a3);
-    }
-
-    // scores of ids[0..cnt) into out[0..cnt) (shared memory); warp-collective
-    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
-        const int g = lane & 3, grp = lane >> 2;
-        const int holder = (lane & ~3) | (CH & 3);
-        for (int b = 0; b < cnt; b += 16) {
-            const int j0 = b + grp, j1 = b + 8 + grp;
-            const int id0 = j0 < cnt ? ids[j0] : -1;
-            const int id1 = j1 < cnt ? ids[j1] : -1;
-            const uint8_t *r0 = base + (int64_t)(id0 < 0 ? 0 : id0) * stride;
-            const uint8_t *r1 = base + (int64_t)(id1 < 0 ? 0 : id1) * stride;
-            uint4 v0[NC], v1[NC];
-#pragma unroll
-            for (int t = 0; t < NC; ++t) {
-                const int c = g + 4 * t;
-                v0[t] = (c <= CH && id0 >= 0) ? ldg_stream(r0 + 16 * c) : make_uint4(0, 0, 0, 0);
-                v1[t] = (c <= CH && id1 >= 0) ? ldg_stream(r1 + 16 * c) : make_uint4(0, 0, 0, 0);
-            }
-            float s0 = dot(v0), s1 = dot(v1);
-            float d0 = 0.f, l0 = 0.f, d1 = 0.f, l1 = 0.f;
-#pragma unroll
-            for (int t = 0; t < NC; ++t)
-                if (g + 4 * t == CH) {
-                    d0 = __uint_as_float(v0[t].x);
-                    l0 = __uint_as_float(v0[t].y);
-                    d1 = __uint_as_float(v1[t].x);
-                    l1 = __uint_as_float(v1[t].y);
-                }
-            s0 += __shfl_xor_sync(FULL, s0, 1);
-            s1 += __shfl_xor_sync(FULL, s1, 1);
-            s0 += __shfl_xor_sync(FULL, s0, 2);
-            s1 += __shfl_xor_sync(FULL, s1, 2);
-            d0 = __shfl_sync(FULL, d0, holder);
-            l0 = __shfl_sync(FULL, l0, holder);
-            d1 = __shfl_sync(FULL, d1, holder);
-            l1 = __shfl_sync(FULL, l1, holder);
-            if (g == 0) {
-                if (j0 < cnt) out[j0] = fmaf(d0, s0, fmaf(l0, sq, cq));
-                if (j1 < cnt) out[j1] = fmaf(d1, s1, fmaf(l1, sq, cq));
-            }
-        }
-    }
-};
 
 // --------------------------------------------------------------------------------
 // Primary scorer with an integer query: q' is held as 24-bit fixed point
@@ -214,7 +112,8 @@ struct LvqIntScorer {
     const uint8_t *base;
     int64_t stride;
 
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *qsmem) {
+    // every warp of the team computes the scale; the writer stores the limbs
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *qsmem, bool writer) {
         CH = p.prim_chunks;
         base = p.prim;
         stride = p.prim_stride;
@@ -226,7 +125,7 @@ struct LvqIntScorer {
         scale = amax > 0.f ? amax / 8388607.0f : 1.0f;
         const float inv = amax > 0.f ? 8388607.0f / amax : 0.f;
         uint32_t *dst = reinterpret_cast<uint32_t *>(qsmem);
-        for (int c = lane; c < 4 * NC; c += 32) {
+        for (int c = lane; writer && c < 4 * NC; c += 32) {
 #pragma unroll
             for (int w = 0; w < 4 * V4; ++w) {
                 uint32_t h = 0, mm = 0, l = 0;
@@ -387,7 +286,7 @@ struct BuildScorer {
     int64_t stride;
 
     static constexpr int QBYTES = 0;
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *) {
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *, bool) {
         CH = p.prim_chunks;
         base = p.prim;
         stride = p.prim_stride;
@@ -490,7 +389,7 @@ struct WarpScorer {
     }
 
     static constexpr int QBYTES = 0;
-    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *) {
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *, bool) {
         // full-dimensional float32 search: padded queries, no constants
         setup_row(p.qp + qi * p.ldq, p.ldq, p.prim_chunks, p.prim, p.prim_stride, 0.f, 0.f, lane);
     }
@@ -556,8 +455,21 @@ struct WarpScorer {
     }
 };
 
+// team barrier: the T warps of one query (named barrier 1 + team; a warp barrier when T = 1)
+__device__ __forceinline__ void team_sync(int T, int team) {
+    if (T == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(32 * T) : "memory");
+}
+
 // --------------------------------------------------------------------------------
-// The beam kernel.  BUILD: queries are nodes (p.qnodes), output = the final beam.
+// The beam kernel.  A team of T = p.T warps serves one query: per round the W best
+// unexpanded beam members are the parents, warp w of the team expands parents
+// w, w + T, ... (stages their adjacency, tests the visited cache, scores the new ids and
+// keeps those that can enter the beam), then warp 0 merges every warp's candidates into
+// the beam.  The rounds are the same for every T, so are the results.
+// BUILD: queries are nodes (p.qnodes), output = the final beam.
 // RERANK: hand the top-r of the beam to the rerank kernel (rerank.cu).
 // --------------------------------------------------------------------------------
 template <class PS, bool BUILD, bool RERANK>
@@ -565,7 +477,8 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned char *my = smem_raw + (size_t)(threadIdx.x >> 5) * p.warp_smem;
+    const int T = p.T, warp = threadIdx.x >> 5, team = warp / T, tw = warp - team * T;
+    unsigned char *my = smem_raw + (size_t)team * p.warp_smem;
     float *const bS = reinterpret_cast<float *>(my);           // beam scores (sorted, best first)
     int *const bI = reinterpret_cast<int *>(bS + p.Lcap);      // beam ids, top bit = expanded
     int *const hash = bI + p.Lcap;                             // visited cache
@@ -574,50 +487,61 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     int *const vPB = reinterpret_cast<int *>(cS + p.Rcap);     // beam members ahead of each (| rank << 16)
     int *const sPB = vPB + p.Rcap;                             // the same in candidate-rank order
     void *const qsm = sPB + p.Rcap;                            // the scorer's query
+    int *const ctl = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(qsm) + PS::QBYTES);
+    // ctl: [0] query, [1] size, [2] F, [4 + w] candidates of warp w, [8 + w] records scored by warp w
+    // this warp's slice of the candidate arrays (Rw entries)
+    const int Rw = p.Rcap / T;
+    int *const wI = cI + tw * Rw;
+    float *const wS = cS + tw * Rw;
+    int *const wPB = vPB + tw * Rw;
     // visited cache: Hcap / 4 buckets of 4 ids, one 16-byte load per lookup
     int4 *const hash4 = reinterpret_cast<int4 *>(hash);
     const int bshift = 34 - p.hbits;  // 32 - log2(buckets)
+    const bool lead = tw == 0;
     PS ps;
 
     for (;;) {
-        int qi32 = 0;
-        if (lane == 0) qi32 = atomicAdd(p.work, 1);
-        qi32 = __shfl_sync(FULL, qi32, 0);
-        const int64_t qi = qi32;
+        if (lead && lane == 0) ctl[0] = atomicAdd(p.work, 1);
+        team_sync(T, team);
+        const int64_t qi = ctl[0];
         if (qi >= p.m) break;
         int4 dq = p.desc ? p.desc[qi] : p.uni;
         int k = dq.x, L = dq.y, r = dq.z;
         const int mh = dq.w;
         if (L > p.Lcap || L < 1 || k > p.ldo || k < 0) {
-            if (lane == 0) atomicOr(p.status, ST_CAPACITY);
+            if (lead && lane == 0) atomicOr(p.status, ST_CAPACITY);
             L = min(max(L, 1), p.Lcap);
             k = min(max(k, 0), p.ldo);
         }
         r = min(max(r, 0), L);
-        ps.setup(p, qi, lane, qsm);
-
-        for (int t = lane * 4; t < p.Hcap; t += 128)
+        ps.setup(p, qi, lane, qsm, lead);
+        for (int t = (tw * 32 + lane) * 4; t < p.Hcap; t += 128 * T)
             *reinterpret_cast<int4 *>(hash + t) = make_int4(-1, -1, -1, -1);
-        __syncwarp();
+        team_sync(T, team);
         const int entry = p.entry;
-        if (lane == 0) {
-            cI[0] = entry;
-            hash[4 * (int)(((unsigned)entry * 0x9E3779B1u) >> bshift)] = entry;
+        if (lead) {
+            if (lane == 0) {
+                cI[0] = entry;
+                hash[4 * (int)(((unsigned)entry * 0x9E3779B1u) >> bshift)] = entry;
+            }
+            __syncwarp();
+            ps.score(cI, cS, 1, lane);
+            __syncwarp();
+            if (lane == 0) {
+                bS[0] = cS[0];
+                bI[0] = entry;
+                ctl[1] = 1;
+                ctl[2] = 0;
+            }
         }
-        __syncwarp();
-        ps.score(cI, cS, 1, lane);
-        __syncwarp();
-        if (lane == 0) {
-            bS[0] = cS[0];
-            bI[0] = entry;
-        }
-        __syncwarp();
+        team_sync(T, team);
         // every beam member before position F is expanded
-        int size = 1, hops = 0, scored = 1, F = 0;
+        int size = 1, hops = 0, scored = lead ? 1 : 0, F = 0;
         const int maxh = mh > 0 ? mh : (int)(p.n < 0x7fffffff ? p.n : 0x7fffffff);
 
         while (hops < maxh) {
             // the W best unexpanded members of the beam: the first ones at positions >= F
+            // (every warp of the team finds the same ones)
             int par[WMAX];
             int npar = 0;
             const int want = min(p.W, maxh - hops);
@@ -635,36 +559,30 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                 }
             }
             if (npar == 0) break;
-            int pnode[WMAX];
-#pragma unroll
-            for (int w = 0; w < WMAX; ++w) pnode[w] = w < npar ? bI[par[w]] : 0;
-            __syncwarp();
-            if (lane == 0)
-#pragma unroll
-                for (int w = 0; w < WMAX; ++w)
-                    if (w < npar) bI[par[w]] = pnode[w] | (int)EXPANDED;
             F = par[0] + 1;
 #pragma unroll
             for (int w = 1; w < WMAX; ++w)
                 if (w < npar) F = par[w] + 1;
             hops += npar;
 
-            // neighbour ids of all parents: staged in shared memory (the score buffer is
-            // free here), then tested against the visited cache parent by parent (so an id
-            // shared by two parents is seen once)
-            int *const stage = reinterpret_cast<int *>(cS);
+            // this warp's parents w = tw, tw + T, ...: neighbour ids staged in shared memory
+            // (the slice's score buffer is free here), then tested against the visited cache
+            // parent by parent (so an id shared by two parents of one warp is seen once)
+            int *const stage = reinterpret_cast<int *>(wS);
+            int nst = 0;
 #pragma unroll
             for (int w = 0; w < WMAX; ++w) {
-                if (w < npar) {
-                    const int32_t *row = p.graph + (int64_t)pnode[w] * p.R;
-                    for (int j = lane; j < p.R; j += 32) stage[w * p.R + j] = __ldg(row + j);
+                if (w < npar && (w & (T - 1)) == tw) {  // T is a power of two
+                    const int32_t *row = p.graph + (int64_t)(bI[par[w]] & ~(int)EXPANDED) * p.R;
+                    for (int j = lane; j < p.R; j += 32) stage[nst + j] = __ldg(row + j);
+                    nst += p.R;
                 }
             }
             __syncwarp();
             int cnt = 0;
-            for (int j0 = 0; j0 < npar * p.R; j0 += 32) {
+            for (int j0 = 0; j0 < nst; j0 += 32) {
                 const int j = j0 + lane;
-                int u = j < npar * p.R ? stage[j] : -1;
+                int u = j < nst ? stage[j] : -1;
                 bool isnew = false;
                 if (u >= 0) {
                     if (u >= p.n) {
@@ -683,160 +601,215 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                     }
                 }
                 const unsigned bal = __ballot_sync(FULL, isnew);
-                if (isnew) cI[cnt + __popc(bal & lt)] = u;
+                if (isnew) wI[cnt + __popc(bal & lt)] = u;
                 cnt += __popc(bal);
                 __syncwarp();
             }
             __syncwarp();
-            if (cnt == 0) continue;
-            ps.score(cI, cS, cnt, lane);
-            scored += cnt;
-            __syncwarp();
-
-            // keep candidates that can enter the beam and are not already in it
-            const bool full = size >= L;
-            float wS = 0.f;
-            int wI = 0;
-            if (full) {
-                wS = bS[L - 1];
-                wI = bI[L - 1] & ~(int)EXPANDED;
-            }
             int cv = 0;
-            for (int j0 = 0; j0 < cnt; j0 += 32) {
-                const int j = j0 + lane;
-                bool valid = false;
-                float s = 0.f;
-                int id = 0, pb = 0;
-                if (j < cnt) {
-                    s = cS[j];
-                    id = cI[j];
-                    valid = !full || key_better(s, id, wS, wI);
-                    if (valid) {
-                        int lo = 0, hi = size;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (key_better(bS[mid], bI[mid] & ~(int)EXPANDED, s, id))
-                                lo = mid + 1;
-                            else
-                                hi = mid;
-                        }
-                        pb = lo;
-                        if (pb < size && (bI[pb] & ~(int)EXPANDED) == id) valid = false;
-                    }
-                }
-                const unsigned bal = __ballot_sync(FULL, valid);
-                __syncwarp();  // the chunk is read before it is compacted in place
-                if (valid) {
-                    const int o = cv + __popc(bal & lt);
-                    cI[o] = id;
-                    cS[o] = s;
-                    vPB[o] = pb;
-                }
-                cv += __popc(bal);
-            }
-            __syncwarp();
-            if (cv == 0) continue;
-            // an id can appear twice in one round only if the visited cache forgot it
-            // between two parents: keep the first copy
-            bool anydup = false;
-            if (p.W > 1) {
-                if (cv <= 32) {
-                    // lanes past cv hold distinct negative keys that match nothing
-                    const int id = lane < cv ? cI[lane] : -2 - lane;
-                    const bool dup = (__match_any_sync(FULL, id) & lt) != 0u;
-                    if (dup) vPB[lane] = -1;
-                    anydup = __any_sync(FULL, dup);
-                } else {
-                    bool d = false;
-                    for (int j = lane; j < cv; j += 32) {
-                        const int id = cI[j];
-                        bool dup = false;
-                        for (int u = 0; u < j; ++u) dup |= cI[u] == id;
-                        if (dup) {
-                            vPB[j] = -1;
-                            d = true;
-                        }
-                    }
-                    anydup = __any_sync(FULL, d);
-                }
+            if (cnt > 0) {
+                ps.score(wI, wS, cnt, lane);
+                scored += cnt;
                 __syncwarp();
-            }
-            if (anydup) {
-                int cv2 = 0;
-                for (int j0 = 0; j0 < cv; j0 += 32) {
+                // keep candidates that can enter the beam and are not already in it (the beam
+                // does not change until the merge)
+                const bool full = size >= L;
+                float tS = 0.f;
+                int tI = 0;
+                if (full) {
+                    tS = bS[L - 1];
+                    tI = bI[L - 1] & ~(int)EXPANDED;
+                }
+                for (int j0 = 0; j0 < cnt; j0 += 32) {
                     const int j = j0 + lane;
-                    const bool keep = j < cv && vPB[j] >= 0;
+                    bool valid = false;
                     float s = 0.f;
                     int id = 0, pb = 0;
-                    if (keep) {
-                        s = cS[j];
-                        id = cI[j];
-                        pb = vPB[j];
+                    if (j < cnt) {
+                        s = wS[j];
+                        id = wI[j];
+                        valid = !full || key_better(s, id, tS, tI);
+                        if (valid) {
+                            int lo = 0, hi = size;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (key_better(bS[mid], bI[mid] & ~(int)EXPANDED, s, id))
+                                    lo = mid + 1;
+                                else
+                                    hi = mid;
+                            }
+                            pb = lo;
+                            if (pb < size && (bI[pb] & ~(int)EXPANDED) == id) valid = false;
+                        }
                     }
-                    const unsigned bal = __ballot_sync(FULL, keep);
-                    __syncwarp();
-                    if (keep) {
-                        const int o = cv2 + __popc(bal & lt);
-                        cI[o] = id;
-                        cS[o] = s;
-                        vPB[o] = pb;
+                    const unsigned bal = __ballot_sync(FULL, valid);
+                    __syncwarp();  // the chunk is read before it is compacted in place
+                    if (valid) {
+                        const int o = cv + __popc(bal & lt);
+                        wI[o] = id;
+                        wS[o] = s;
+                        wPB[o] = pb;
                     }
-                    cv2 += __popc(bal);
-                    __syncwarp();
+                    cv += __popc(bal);
                 }
-                cv = cv2;
             }
-            // rank of each candidate among the candidates; sPB[rank] = beam members ahead
-            for (int j = lane; j < cv; j += 32) {
-                const float s = cS[j];
-                const int id = cI[j];
-                int rank = 0;
-                for (int u = 0; u < cv; ++u) rank += key_better(cS[u], cI[u], s, id) ? 1 : 0;
-                const int pb = vPB[j];
-                sPB[rank] = pb;
-                vPB[j] = pb | (rank << 16);
+            if (T > 1) {
+                if (lane == 0) ctl[4 + tw] = cv;
+                team_sync(T, team);
             }
-            __syncwarp();
-            // move beam members (in place, last chunk first; a member only moves right)
-            const int first = sPB[0];
-            for (int base = (size - 1) & ~31; base >= (first & ~31); base -= 32) {
-                const int i = base + lane;
-                float s = 0.f;
-                int id = 0, np = L;
-                if (i >= first && i < size) {
-                    s = bS[i];
-                    id = bI[i];
-                    int lo = 0, hi = cv;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sPB[mid] <= i)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
+            if (lead) {
+                // the parents are expanded now (the move below carries the flag along)
+                __syncwarp();
+                if (lane == 0)
+#pragma unroll
+                    for (int w = 0; w < WMAX; ++w)
+                        if (w < npar) bI[par[w]] |= (int)EXPANDED;
+                // the other warps' candidates follow warp 0's (in place: a slice only moves left)
+                for (int w = 1; w < T; ++w) {
+                    const int cw = ctl[4 + w];
+                    const int *sI = cI + w * Rw;
+                    const float *sS = cS + w * Rw;
+                    const int *sP = vPB + w * Rw;
+                    for (int j0 = 0; j0 < cw; j0 += 32) {
+                        const int j = j0 + lane;
+                        int id = 0, pb = 0;
+                        float s = 0.f;
+                        if (j < cw) {
+                            id = sI[j];
+                            s = sS[j];
+                            pb = sP[j];
+                        }
+                        __syncwarp();
+                        if (j < cw) {
+                            cI[cv + j] = id;
+                            cS[cv + j] = s;
+                            vPB[cv + j] = pb;
+                        }
+                        __syncwarp();
                     }
-                    np = i + lo;
+                    cv += cw;
                 }
                 __syncwarp();
-                if (np < L) {
-                    bS[np] = s;
-                    bI[np] = id;
+                if (cv > 0) {
+                    // an id can appear twice in one round when two parents share a neighbour
+                    // that the visited cache did not catch (another warp's concurrent test, or a
+                    // forgotten id): keep the first copy
+                    bool anydup = false;
+                    if (p.W > 1) {
+                        if (cv <= 32) {
+                            // lanes past cv hold distinct negative keys that match nothing
+                            const int id = lane < cv ? cI[lane] : -2 - lane;
+                            const bool dup = (__match_any_sync(FULL, id) & lt) != 0u;
+                            if (dup) vPB[lane] = -1;
+                            anydup = __any_sync(FULL, dup);
+                        } else {
+                            bool d = false;
+                            for (int j = lane; j < cv; j += 32) {
+                                const int id = cI[j];
+                                bool dup = false;
+                                for (int u = 0; u < j; ++u) dup |= cI[u] == id;
+                                if (dup) {
+                                    vPB[j] = -1;
+                                    d = true;
+                                }
+                            }
+                            anydup = __any_sync(FULL, d);
+                        }
+                        __syncwarp();
+                    }
+                    if (anydup) {
+                        int cv2 = 0;
+                        for (int j0 = 0; j0 < cv; j0 += 32) {
+                            const int j = j0 + lane;
+                            const bool keep = j < cv && vPB[j] >= 0;
+                            float s = 0.f;
+                            int id = 0, pb = 0;
+                            if (keep) {
+                                s = cS[j];
+                                id = cI[j];
+                                pb = vPB[j];
+                            }
+                            const unsigned bal = __ballot_sync(FULL, keep);
+                            __syncwarp();
+                            if (keep) {
+                                const int o = cv2 + __popc(bal & lt);
+                                cI[o] = id;
+                                cS[o] = s;
+                                vPB[o] = pb;
+                            }
+                            cv2 += __popc(bal);
+                            __syncwarp();
+                        }
+                        cv = cv2;
+                    }
+                    // rank of each candidate among the candidates; sPB[rank] = beam members ahead
+                    for (int j = lane; j < cv; j += 32) {
+                        const float s = cS[j];
+                        const int id = cI[j];
+                        int rank = 0;
+                        for (int u = 0; u < cv; ++u) rank += key_better(cS[u], cI[u], s, id) ? 1 : 0;
+                        const int pb = vPB[j];
+                        sPB[rank] = pb;
+                        vPB[j] = pb | (rank << 16);
+                    }
+                    __syncwarp();
+                    // move beam members (in place, last chunk first; a member only moves right)
+                    const int first = sPB[0];
+                    for (int base = (size - 1) & ~31; base >= (first & ~31); base -= 32) {
+                        const int i = base + lane;
+                        float s = 0.f;
+                        int id = 0, np = L;
+                        if (i >= first && i < size) {
+                            s = bS[i];
+                            id = bI[i];
+                            int lo = 0, hi = cv;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (sPB[mid] <= i)
+                                    lo = mid + 1;
+                                else
+                                    hi = mid;
+                            }
+                            np = i + lo;
+                        }
+                        __syncwarp();
+                        if (np < L) {
+                            bS[np] = s;
+                            bI[np] = id;
+                        }
+                        __syncwarp();
+                    }
+                    // place the candidates (unexpanded)
+                    for (int j = lane; j < cv; j += 32) {
+                        const int x = vPB[j];
+                        const int np = (x & 0xffff) + (x >> 16);
+                        if (np < L) {
+                            bS[np] = cS[j];
+                            bI[np] = cI[j];
+                        }
+                    }
+                    size = min(L, size + cv);
+                    F = min(F, first);
                 }
-                __syncwarp();
-            }
-            // place the candidates (unexpanded)
-            for (int j = lane; j < cv; j += 32) {
-                const int x = vPB[j];
-                const int np = (x & 0xffff) + (x >> 16);
-                if (np < L) {
-                    bS[np] = cS[j];
-                    bI[np] = cI[j];
+                if (T > 1 && lane == 0) {
+                    ctl[1] = size;
+                    ctl[2] = F;
                 }
             }
-            size = min(L, size + cv);
-            F = min(F, first);
-            __syncwarp();
+            team_sync(T, team);
+            if (T > 1) {
+                size = ctl[1];
+                F = ctl[2];
+            }
         }
 
+        if (T > 1) {
+            if (lane == 0) ctl[8 + tw] = scored;
+            team_sync(T, team);
+            if (lead)
+                for (int w = 1; w < T; ++w) scored += ctl[8 + w];
+        }
+        if (!lead) continue;
         if (p.stats && lane == 0) p.stats[qi] = make_int2(hops, scored);
         int32_t *oid = p.ids + qi * p.ldo;
         float *osc = p.scores + qi * p.ldo;

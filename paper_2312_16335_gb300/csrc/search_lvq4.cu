@@ -11,7 +11,8 @@ static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStre
     int per_sm = 0;
     LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     if (per_sm < 1) return fail(LV_ERR_CAPACITY, "search: beam/visited capacity does not fit in shared memory");
-    int64_t want = (p.m + block / 32 - 1) / (block / 32);
+    const int teams = block / 32 / p.T;  // queries served at once by one block
+    int64_t want = (p.m + teams - 1) / teams;
     int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
     k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);
     LV_CHECK_LAUNCH("beam_kernel<lvq4>");

@@ -149,12 +149,21 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             rc = fail(LV_ERR_ARG, "search_noalloc: need width <= 4 and width * R <= 256");
             break;
         }
-        p.Rcap = (int)round_up((int64_t)p.W * idx->R, 32);
+        p.T = params->warps_per_query > 0 ? params->warps_per_query : 1;
+        if ((p.T != 1 && p.T != 2 && p.T != 4) || p.W % p.T) {
+            rc = fail(LV_ERR_ARG, "search_noalloc: warps_per_query must be 1, 2 or 4 and divide width");
+            break;
+        }
+        p.Rcap = beam_rcap(p.W, p.T, idx->R);
         const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + 3) / 4;
         p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
         int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
-        while (warps > 1 && (size_t)warps * p.warp_smem > 227 * 1024) warps >>= 1;
-        if ((size_t)warps * p.warp_smem > 227 * 1024) {
+        if (warps % p.T || warps > 32) {
+            rc = fail(LV_ERR_ARG, "search_noalloc: warps_per_block must be <= 32 and a multiple of warps_per_query");
+            break;
+        }
+        while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
+        if ((size_t)(warps / p.T) * p.warp_smem > 227 * 1024) {
             rc = fail(LV_ERR_CAPACITY, "search_noalloc: L / hash_slots too large for shared memory");
             break;
         }
@@ -169,7 +178,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             rc = cuda_fail(e, "search_noalloc: cudaMemsetAsync");
             break;
         }
-        const size_t smem = (size_t)warps * p.warp_smem;
+        const size_t smem = (size_t)(warps / p.T) * p.warp_smem;
         const int block = warps * 32;
         if (params->event_begin) cudaEventRecord((cudaEvent_t)params->event_begin, st);
         if (idx->pbits == 32) {

@@ -100,6 +100,39 @@ def test_search_width_matches_oracle(lv, pb, W):
         idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, width=5)
 
 
+@pytest.mark.parametrize("W,T", [(2, 2), (4, 2), (4, 4)])
+def test_warps_per_query_same_result(lv, pb, W, T):
+    """A team of T warps per query expands the same parents per round as one warp:
+    identical ids, scores and expansion counts (also with a tiny visited cache, where
+    the warps' concurrent tests let shared neighbours through twice, and with uneven
+    per-query descriptors)."""
+    idx = gpu_index(lv, pb)
+    for hs in (0, 128):
+        a, sa, ta = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48, width=W, stats=True, hash_slots=hs)
+        b, sb, tb = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48, width=W, stats=True, hash_slots=hs,
+                               warps_per_query=T)
+        idx.sync_status()
+        assert torch.equal(a, b) and torch.equal(sa, sb)
+        assert torch.equal(ta[:, 0], tb[:, 0])
+    m = pb["Q"].shape[0]
+    rng = np.random.default_rng(7)
+    k = rng.choice([1, 5, 10], m)
+    L = np.maximum(rng.integers(10, 80, m), k)
+    r = np.minimum(L, rng.integers(0, 60, m))
+    desc = t(np.stack([k, L, r, rng.integers(0, 40, m)], 1).astype(np.int32))
+    a, sa = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=80, rerank=80, desc=desc, width=W)
+    b, sb = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=80, rerank=80, desc=desc, width=W, warps_per_query=T,
+                       warps_per_block=4)
+    assert torch.equal(a, b) and torch.equal(sa, sb)
+
+
+def test_warps_per_query_errors(lv, pb):
+    idx = gpu_index(lv, pb)
+    for W, T, wpb in ((2, 4, 0), (4, 3, 0), (3, 2, 0), (2, 2, 3)):
+        with pytest.raises(lv.LeanVecError):
+            idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, width=W, warps_per_query=T, warps_per_block=wpb)
+
+
 def test_small_hash_still_exact(lv, pb):
     """A tiny visited cache forgets often; the beam (hence the result) is unchanged."""
     idx = gpu_index(lv, pb)
@@ -165,6 +198,9 @@ def test_float32_baseline_matches_oracle(lv, pb):
     assert (ids == ref["ids"]).mean() >= 0.99
     Xd = pb["X"].astype(np.float64)
     _check_scores(ids, sc.cpu().numpy(), Xd, pb["Q"].astype(np.float64))
+    a, sa = idx.search(t(pb["Q"]), None, k=10, L=40, width=2)
+    b, sb = idx.search(t(pb["Q"]), None, k=10, L=40, width=2, warps_per_query=2)
+    assert torch.equal(a, b) and torch.equal(sa, sb)
 
 
 def test_lvq4_primary(lv):
