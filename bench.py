@@ -41,8 +41,9 @@ L_GRID = [10, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 200
 # DRAM bytes (read + write) of one beam-kernel launch measured with ncu
 # (profiles/beam_kernel_id1m_768.md), valid only for the kernel sources it was taken on.
 TRAFFIC_RECORDS = [
-    {"src_sha1": "2c82c50a1533d3621d249c70e0f4320359f0537c", "n": 1_000_000, "m": 10_000, "L": 160, "width": 2, "hash": 0,
-     "projection": "bf16", "bytes": 4.53e9 + 7.95e6},
+    # beam_kernel (3.067 GB read + 10.7 MB written) + rerank_kernel (1.198 GB + 0.15 MB) of one search
+    {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 160, "width": 2, "hash": 0,
+     "projection": "bf16", "bytes": 3066597888 + 10704640 + 1198200320 + 154624},
 ]
 
 
@@ -50,7 +51,7 @@ def beam_src_sha1() -> str:
     import hashlib
     root = os.path.join(ROOT, "paper_2312_16335_gb300", "csrc")
     h = hashlib.sha1()
-    for f in ("beam.cuh", "search_lvq8.cu"):
+    for f in ("beam.cuh", "search_lvq8.cu", "rerank.cu"):
         h.update(open(os.path.join(root, f), "rb").read())
     return h.hexdigest()
 

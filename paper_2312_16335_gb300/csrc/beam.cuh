@@ -580,30 +580,37 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             }
             __syncwarp();
             int cnt = 0;
-            for (int j0 = 0; j0 < nst; j0 += 32) {
-                const int j = j0 + lane;
-                int u = j < nst ? stage[j] : -1;
-                bool isnew = false;
-                if (u >= 0) {
-                    if (u >= p.n) {
-                        atomicOr(p.status, ST_CORRUPT);
-                    } else {
-                        // a bucket that is full forgets one id (chosen by two more bits of the
-                        // hash): the cache may forget, it never reports an unvisited id
-                        const unsigned hv = (unsigned)u * 0x9E3779B1u;
+            for (int j0 = 0; j0 < nst; j0 += 64) {
+                int u[2], slot[2];
+                bool isnew[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + 32 * h + lane;
+                    u[h] = j < nst ? stage[j] : -1;
+                    if (u[h] >= p.n) { atomicOr(p.status, ST_CORRUPT); u[h] = -1; }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    isnew[h] = false;
+                    slot[h] = 0;
+                    if (u[h] >= 0) {
+                        const unsigned hv = (unsigned)u[h] * 0x9E3779B1u;
                         const int b = (int)(hv >> bshift);
                         const int4 v = hash4[b];
-                        if (v.x != u && v.y != u && v.z != u && v.w != u) {
-                            isnew = true;
-                            const int s = v.x < 0 ? 0 : v.y < 0 ? 1 : v.z < 0 ? 2 : v.w < 0 ? 3 : (int)((hv >> (bshift - 2)) & 3u);
-                            hash[4 * b + s] = u;
+                        const int x = u[h];
+                        if (v.x != x && v.y != x && v.z != x && v.w != x) {
+                            isnew[h] = true;
+                            slot[h] = 4 * b + (v.x < 0 ? 0 : v.y < 0 ? 1 : v.z < 0 ? 2 : v.w < 0 ? 3 : (int)((hv >> (bshift - 2)) & 3u));
                         }
                     }
                 }
-                const unsigned bal = __ballot_sync(FULL, isnew);
-                if (isnew) wI[cnt + __popc(bal & lt)] = u;
-                cnt += __popc(bal);
-                __syncwarp();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (isnew[h]) hash[slot[h]] = u[h];
+                    const unsigned bal = __ballot_sync(FULL, isnew[h]);
+                    if (isnew[h]) wI[cnt + __popc(bal & lt)] = u[h];
+                    cnt += __popc(bal);
+                }
             }
             __syncwarp();
             int cv = 0;
