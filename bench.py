@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-L_GRID = [10, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 200, 256]
+L_GRID = [10, 12, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88, 96, 104, 112, 120, 128, 132, 136,
+          140, 144, 148, 152, 156, 160, 176, 200, 256]
 
 # DRAM bytes (read + write) of one beam-kernel launch measured with ncu
 # (profiles/beam_kernel_id1m_768.md), valid only for the kernel sources it was taken on.
@@ -211,7 +212,7 @@ def setup(args, dev, with_base=True):
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     t0 = time.time()
-    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
                     seed=workloads.SEED_GRAPH + 2)
     idx.sync_status()
     t_build = time.time() - t0
@@ -297,7 +298,7 @@ def bench_ood(args, dev):
     diff = {"seconds": min(times[1:]), "pairs": mm * nn_, "tflops": flops / min(times[1:]) / 1e12}
     # one graph (built on the ID primaries), primaries swapped per projection
     idx = lv.Index(dev.index).encode(X, fits["id"][1], 8, 8, precision=lv.PREC_BF16)
-    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
                     seed=workloads.SEED_GRAPH + 3)
     graph, entry = idx.get_graph()
     res = {}
@@ -352,7 +353,7 @@ def bench_uneven(args, dev):
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     t0 = time.time()
-    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
                     seed=workloads.SEED_GRAPH + 5)
     clamped = False
     try:
@@ -442,7 +443,7 @@ def bench_precision(args, dev):
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     t0 = time.time()
-    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch,
+    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
                     seed=workloads.SEED_GRAPH + 4)
     clamped = False
     try:
@@ -487,7 +488,9 @@ def main():
     ap.add_argument("--components", type=int, default=1000)
     ap.add_argument("--R", type=int, default=64)
     ap.add_argument("--L_build", type=int, default=128)
-    ap.add_argument("--alpha", type=float, default=1.0)
+    ap.add_argument("--alpha", type=float, default=1.02)
+    ap.add_argument("--rule", type=int, default=1,
+                    help="RobustPrune rule: 0 alpha-scaled similarity, 1 Vamana's L2 rule on unit-norm vectors")
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -524,7 +527,7 @@ def main():
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
                 f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "
-                f"alpha={args.alpha}; k=10, rerank=L")
+                f"alpha={args.alpha} ({'unit-norm L2' if args.rule else 'alpha-scaled IP'} prune rule); k=10, rerank=L")
     metric = "QPS at 10-recall@10=0.90, LeanVec vs full-D FP32 graph search; HBM GB/s"
 
     if args.impl == "reference":
@@ -658,7 +661,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
                    "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
-                   "L_build": args.L_build, "alpha": args.alpha, "projection": args.projection,
+                   "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "projection": args.projection,
                    "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
