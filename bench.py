@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 L_GRID = [10, 12, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88, 96, 104, 112, 120, 128, 132, 136,
-          140, 144, 148, 152, 156, 160, 176, 200, 256]
+          140, 144, 148, 152, 156, 160, 176, 200, 256, 320, 384, 448, 512]
 
 # DRAM bytes (read + write) of one beam-kernel launch measured with ncu
 # (profiles/beam_kernel_id1m_768.md), valid only for the kernel sources it was taken on.
@@ -481,8 +481,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
-    ap.add_argument("--m", type=int, default=10_000)
+    ap.add_argument("--n", type=int, default=0, help="database size (default: the workload's, 1M or 10M)")
+    ap.add_argument("--m", type=int, default=0, help="queries (default: the workload's, 10k / 50k / 100k)")
     ap.add_argument("--D", type=int, default=768)
     ap.add_argument("--d", type=int, default=160)
     ap.add_argument("--components", type=int, default=1000)
@@ -506,6 +506,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
+    sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
+             "precision": (10_000_000, 100_000)}[args.workload]
+    args.n = args.n or sizes[0]
+    args.m = args.m or sizes[1]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
