@@ -44,7 +44,10 @@ L_GRID = [10, 12, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88
 TRAFFIC_RECORDS = [
     # beam_kernel (3.067 GB read + 10.7 MB written) + rerank_kernel (1.198 GB + 0.15 MB) of one search
     {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 160, "width": 2, "hash": 0,
-     "projection": "bf16", "bytes": 3066597888 + 10704640 + 1198200320 + 154624},
+     "projection": "bf16", "alpha": 1.0, "rule": 0, "bytes": 3066597888 + 10704640 + 1198200320 + 154624},
+    # the default graph (unit-L2 rule, alpha 1.02) at its L for 0.90: beam 3.271 GB + 10.2 MB, rerank 1.107 GB + 0.25 MB
+    {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 148, "width": 2, "hash": 0,
+     "projection": "bf16", "alpha": 1.02, "rule": 1, "bytes": 3271060992 + 10185216 + 1106905856 + 252160},
 ]
 
 
@@ -61,7 +64,8 @@ def recorded_traffic(args, L):
     sha = beam_src_sha1()
     for r in TRAFFIC_RECORDS:
         if (r["src_sha1"] == sha and r["n"] == args.n and r["m"] == args.m and r["L"] == L and
-                r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection):
+                r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection and
+                r.get("alpha") == args.alpha and r.get("rule") == args.rule):
             return r["bytes"]
     return None
 TARGET = 0.90
