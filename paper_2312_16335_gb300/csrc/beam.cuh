@@ -472,8 +472,11 @@ __device__ __forceinline__ void team_sync(int T, int team) {
 // BUILD: queries are nodes (p.qnodes), output = the final beam.
 // RERANK: hand the top-r of the beam to the rerank kernel (rerank.cu).
 // --------------------------------------------------------------------------------
-template <class PS, bool BUILD, bool RERANK>
+// WT: the search width fixed at compile time (1 or 2; 0 = p.W, up to WMAX)
+template <class PS, bool BUILD, bool RERANK, int WT>
 __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
+    constexpr int WC = WT ? WT : WMAX;  // parents per round at most
+    const int Wr = WT ? WT : p.W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -542,15 +545,15 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
         while (hops < maxh) {
             // the W best unexpanded members of the beam: the first ones at positions >= F
             // (every warp of the team finds the same ones)
-            int par[WMAX];
+            int par[WC];
             int npar = 0;
-            const int want = min(p.W, maxh - hops);
+            const int want = min(Wr, maxh - hops);
             for (int base = F & ~31; base < size && npar < want; base += 32) {
                 const int i = base + lane;
                 const bool un = i >= F && i < size && !(bI[i] & (int)EXPANDED);
                 unsigned bal = __ballot_sync(FULL, un);
 #pragma unroll
-                for (int w = 0; w < WMAX; ++w) {
+                for (int w = 0; w < WC; ++w) {
                     if (bal && npar < want && w == npar) {
                         par[w] = base + __ffs(bal) - 1;
                         bal &= bal - 1;
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             if (npar == 0) break;
             F = par[0] + 1;
 #pragma unroll
-            for (int w = 1; w < WMAX; ++w)
+            for (int w = 1; w < WC; ++w)
                 if (w < npar) F = par[w] + 1;
             hops += npar;
 
@@ -571,7 +574,7 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
             int *const stage = reinterpret_cast<int *>(wS);
             int nst = 0;
 #pragma unroll
-            for (int w = 0; w < WMAX; ++w) {
+            for (int w = 0; w < WC; ++w) {
                 if (w < npar && (w & (T - 1)) == tw) {  // T is a power of two
                     const int32_t *row = p.graph + (int64_t)(bI[par[w]] & ~(int)EXPANDED) * p.R;
                     for (int j = lane; j < p.R; j += 32) stage[nst + j] = __ldg(row + j);
@@ -669,7 +672,7 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                 __syncwarp();
                 if (lane == 0)
 #pragma unroll
-                    for (int w = 0; w < WMAX; ++w)
+                    for (int w = 0; w < WC; ++w)
                         if (w < npar) bI[par[w]] |= (int)EXPANDED;
                 // the other warps' candidates follow warp 0's (in place: a slice only moves left)
                 for (int w = 1; w < T; ++w) {
@@ -702,7 +705,7 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                     // that the visited cache did not catch (another warp's concurrent test, or a
                     // forgotten id): keep the first copy
                     bool anydup = false;
-                    if (p.W > 1) {
+                    if (Wr > 1) {
                         if (cv <= 32) {
                             // lanes past cv hold distinct negative keys that match nothing
                             const int id = lane < cv ? cI[lane] : -2 - lane;

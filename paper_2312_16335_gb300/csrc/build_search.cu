@@ -6,7 +6,7 @@ namespace lv {
 
 template <int NC, int BITS>
 static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
-    auto k = beam_kernel<BuildScorer<NC, BITS>, true, false>;
+    auto k = beam_kernel<BuildScorer<NC, BITS>, true, false, 1>;
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
