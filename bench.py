@@ -172,6 +172,19 @@ def calibrate(search_fn, truth, k):
     return chosen, trace
 
 
+def replica_throughput(total_ms, units_per_step, steps, device=None):
+    """Whole-job throughput of N independent replicas (one per rank, no data exchange): every rank
+    timed the same number of steps; the job lasts as long as the slowest rank (max over ranks) and
+    processed N x steps x units.  Returns (units per second, the max time in ms)."""
+    dist = torch.distributed
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total = float(t.item())
+    return units_per_step * steps * world / (total / 1e3), total
+
+
 def time_steps(fn, steps, warmup, events=None):
     st = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -619,11 +632,7 @@ def main():
     with Clocks(local) as clk:
         total_ms, kern_ms = time_steps(step, args.steps, args.warmup, events=True)
     ck = clk.summary()
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    qps = m * args.steps * world / (total_ms / 1e3)
+    qps, total_ms = replica_throughput(total_ms, m, args.steps, dev)
     kern_avg = statistics.mean(kern_ms)
     hbm_peak, peak_kind = peaks()
     achieved = bytes_q * m / (kern_avg / 1e3) / 1e9
