@@ -186,6 +186,8 @@ def replica_throughput(total_ms, units_per_step, steps, device=None):
 
 
 def time_steps(fn, steps, warmup, events=None):
+    """Run `warmup` untimed steps, then time `steps` steps with CUDA events on the current stream.
+    Returns (total milliseconds of all timed steps, per-step kernel milliseconds when `events`)."""
     st = torch.cuda.current_stream()
     for _ in range(warmup):
         fn(None)
@@ -477,9 +479,10 @@ def bench_precision(args, dev):
         L90, trace = calibrate(lambda L: idx.search(Q[:mt], A, k=10, L=L, rerank=L, width=args.width,
                                                      projection=prec)[0], truth, 10)
         L90 = L90 or L_GRID[-1]
+        nst = max(3, args.steps // 5)
         ms, _ = time_steps(lambda ev: idx.search(Q, A, k=10, L=L90, rerank=L90, width=args.width, projection=prec),
-                           max(3, args.steps // 5), 2)
-        res[pname] = {"L_for_0.90": L90, "recall_trace": trace, "qps": m / (ms / 1e3)}
+                           nst, 2)
+        res[pname] = {"L_for_0.90": L90, "recall_trace": trace, "qps": m * nst / (ms / 1e3)}
     out = {"metric": "QPS at 10-recall@10 = 0.90 with FP8 (e4m3, per-row scaled) query projection; "
                      "precision errors vs FP64",
            "workload": f"prec-{n // 1000000}M-768: 10,000-component mixture, {m} queries (recall on {mt}), "
@@ -489,6 +492,44 @@ def bench_precision(args, dev):
                               "projection_fp8_rel_to_norms": p_err},
            "setup_seconds": {"data": t_data, "fit": t_fit, "encode_fp8": t_enc, "build": t_build},
            "build_reverse_pool_clamped": clamped, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
+def bench_dsweep(args, dev):
+    """Target-d selection on the id-1M-768 workload: one graph (built on the d = 160 primaries), then
+    for each primary dimension d the LeanVec-ID projection of that size, its primaries and
+    secondaries, the smallest grid L with recall@10 >= 0.90 (rerank = L) and the QPS there."""
+    S = setup(args, dev, with_base=False)
+    lv, X, Q, truth = S["lv"], S["X"], S["Q"], S["truth"]
+    graph, entry = S["graph"], S["entry"]
+    del S["idx"]
+    sub = torch.from_numpy(workloads.subsample_rows(args.n, min(args.n, 100_000), cfg=2)).to(dev)
+    Xs = X.index_select(0, sub).contiguous()
+    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
+    res = {}
+    for d in (64, 96, 128, 160, 192, 224, 240):
+        A = lv.leanvec_fit_id(Xs, d)
+        idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8).set_graph(graph, entry)
+        L, trace = calibrate(lambda L: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width,
+                                                  projection=proj)[0], truth, 10)
+        r = {"L_for_0.90": L, "recall_trace": trace[-3:]}
+        if L:
+            nst = max(5, args.steps // 5)
+            ms, _ = time_steps(lambda ev: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=proj),
+                               nst, 2)
+            _, _, st = idx.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=proj, stats=True)
+            r.update(qps=args.m * nst / (ms / 1e3), hops=float(st[:, 0].float().mean()),
+                     scored=float(st[:, 1].float().mean()), primary_stride=idx.info()["primary_stride"])
+        res[d] = r
+        log(f"d={d}: {r}")
+        del idx
+        torch.cuda.empty_cache()
+    ok = {d: r for d, r in res.items() if r.get("qps")}
+    best = max(ok, key=lambda d: ok[d]["qps"]) if ok else None
+    out = {"metric": "QPS at 10-recall@10 = 0.90 vs the primary dimension d (one graph, built on d = 160 primaries)",
+           "workload": f"id-{args.n // 1000}k-{args.D}, {args.m} ID queries, LeanVec-ID LVQ-8 primaries of d dims "
+                       f"+ LVQ-8 secondaries, width {args.width}, {args.projection} projection",
+           "results": res, "best_d": best, "data": "synthetic"}
     print(json.dumps(out), flush=True)
 
 
@@ -516,15 +557,16 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
-    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision"],
+    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
-                         "precision: 10M x 768 with FP8 projection and LVQ-4 primaries")
+                         "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
+                         "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
     sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
-             "precision": (10_000_000, 100_000)}[args.workload]
+             "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000)}[args.workload]
     args.n = args.n or sizes[0]
     args.m = args.m or sizes[1]
 
@@ -544,6 +586,9 @@ def main():
         return
     if args.workload == "precision":
         bench_precision(args, dev)
+        return
+    if args.workload == "dsweep":
+        bench_dsweep(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
