@@ -495,6 +495,59 @@ def bench_precision(args, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_buildstudy(args, dev):
+    """Graph construction on primaries vs on (near) full precision: the graph is built once on the
+    d = 160 LVQ-8 primaries and once on LVQ-8 codes of the unreduced D-dimensional vectors (0.4 %
+    quantisation error: the full-precision stand-in), same R, L_build, alpha, passes, batch and
+    seed; then both the LeanVec search and the full-D FP32 search are calibrated for recall 0.90 on
+    each graph."""
+    S = setup(args, dev)
+    lv, X, Q, A, truth = S["lv"], S["X"], S["Q"], S["A"], S["truth"]
+    idx, base = S["idx"], S["base"]
+    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
+    t0 = time.time()
+    full = lv.Index(dev.index).set_primary(X, None, 8, args.D)
+    torch.cuda.synchronize()
+    t_enc_full = time.time() - t0
+    t0 = time.time()
+    full.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
+                     seed=workloads.SEED_GRAPH + 2)
+    clamped = False
+    try:
+        full.sync_status()
+    except lv.LeanVecError as e:  # reverse-edge pool clamp: the build completed, some reverse edges dropped
+        if e.code != -4:
+            raise
+        clamped = True
+    t_build_full = time.time() - t0
+    graphs = {"primary_d%d" % args.d: (S["graph"], S["entry"]), "full_D_lvq8": full.get_graph()}
+    del full
+    res = {}
+    for name, (g, e) in graphs.items():
+        r = {"mean_degree": float((g >= 0).sum(1).float().mean())}
+        for arm, ix, fn in (("leanvec", idx, lambda L: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width,
+                                                                   projection=proj)),
+                            ("fp32", base, lambda L: base.search(Q, None, k=10, L=L, width=args.width))):
+            ix.set_graph(g, e)
+            L, trace = calibrate(lambda L: fn(L)[0], truth, 10)
+            a = {"L_for_0.90": L, "recall_trace": trace[-3:]}
+            if L:
+                nst = max(5, args.steps // 5)
+                ms, _ = time_steps(lambda ev: fn(L), nst, 2)
+                a["qps"] = args.m * nst / (ms / 1e3)
+            r[arm] = a
+        res[name] = r
+        log(f"{name}: {r}")
+    out = {"metric": "graph construction on d = %d primaries vs on full-D LVQ-8 codes: build seconds, and QPS "
+                     "at recall@10 = 0.90 of the LeanVec and full-D FP32 searches on each graph" % args.d,
+           "workload": f"id-{args.n // 1000}k-{args.D}, {args.m} ID queries, R={args.R}, L_build={args.L_build}, "
+                       f"alpha={args.alpha}, prune rule {args.rule}, 2 passes, batch {args.batch}",
+           "build_seconds": {"primary_d%d" % args.d: S["t_build"], "full_D_lvq8": t_build_full},
+           "encode_seconds": {"primary_d%d" % args.d: S["t_enc"] + S["t_fit"], "full_D_lvq8": t_enc_full},
+           "full_D_reverse_pool_clamped": clamped, "results": res, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def bench_dsweep(args, dev):
     """Target-d selection on the id-1M-768 workload: one graph (built on the d = 160 primaries), then
     for each primary dimension d the LeanVec-ID projection of that size, its primaries and
@@ -557,16 +610,18 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
-    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep"],
+    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
                          "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
-                         "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph")
+                         "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph; "
+                         "buildstudy: graph build on primaries vs on full-D LVQ-8 codes")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
     sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
-             "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000)}[args.workload]
+             "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
+             "buildstudy": (1_000_000, 10_000)}[args.workload]
     args.n = args.n or sizes[0]
     args.m = args.m or sizes[1]
 
@@ -589,6 +644,9 @@ def main():
         return
     if args.workload == "dsweep":
         bench_dsweep(args, dev)
+        return
+    if args.workload == "buildstudy":
+        bench_buildstudy(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "

@@ -355,6 +355,69 @@ struct BuildScorer {
     }
 };
 
+// Build scorer for long records (more code chunks than 4 lanes x 4 chunks hold, e.g. LVQ-8 codes of
+// the unreduced vectors): a whole warp per record, lane l holds chunks l and l + 32 of the node's own
+// record (CH + 1 <= 64); the same exact build score as BuildScorer.  4 records per pass.
+template <int BITS>
+struct BuildWarpScorer {
+    static constexpr int QBYTES = 0;
+    static constexpr int U = 4;
+    uint4 qc[2];
+    float qd, ql, qG, qH, mu2, fdim;
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *, bool) {
+        CH = p.prim_chunks;
+        base = p.prim;
+        stride = p.prim_stride;
+        mu2 = p.mu2;
+        fdim = (float)p.prim_dim;
+        const uint8_t *r = base + (int64_t)p.qnodes[qi] * stride;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int c = lane + 32 * t;
+            qc[t] = c < CH ? *reinterpret_cast<const uint4 *>(r + 16 * c) : make_uint4(0, 0, 0, 0);
+        }
+        const float4 k = *reinterpret_cast<const float4 *>(r + 16 * CH);
+        qd = k.x;
+        ql = k.y;
+        qG = k.z;
+        qH = k.w;
+    }
+
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        const int holder = CH & 31, tslot = CH >> 5;
+        for (int b = 0; b < cnt; b += U) {
+            uint4 v[U][2];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int id = b + u < cnt ? ids[b + u] : -1;
+                const uint8_t *r = base + (int64_t)(id < 0 ? 0 : id) * stride;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int c = lane + 32 * t;
+                    v[u][t] = (c <= CH && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                // the query's chunks past CH are zero, so the constants chunk adds nothing
+                int P = code_dot<BITS>(v[u][0], qc[0]) + code_dot<BITS>(v[u][1], qc[1]);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) P += __shfl_xor_sync(FULL, P, o);
+                const uint4 kv = tslot == 0 ? v[u][0] : v[u][1];
+                const float kd = __shfl_sync(FULL, __uint_as_float(kv.x), holder);
+                const float kl = __shfl_sync(FULL, __uint_as_float(kv.y), holder);
+                const float kG = __shfl_sync(FULL, __uint_as_float(kv.z), holder);
+                const float kH = __shfl_sync(FULL, __uint_as_float(kv.w), holder);
+                if (lane == 0 && b + u < cnt) out[b + u] = build_pair_score(mu2, fdim, qd, ql, qG, qH, kd, kl, kG, kH, P);
+            }
+        }
+    }
+};
+
 // --------------------------------------------------------------------------------
 // Whole-warp scorer for long records: float32 vectors (KIND 0, the full-dimensional
 // baseline) or LVQ-8 secondary records (KIND 1, the rerank).  U records per pass.

@@ -20,8 +20,27 @@ static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStre
     return LV_OK;
 }
 
+template <int BITS>
+static int go_warp(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
+    auto k = beam_kernel<BuildWarpScorer<BITS>, true, false, 1>;
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int per_sm = 0;
+    LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
+    if (per_sm < 1) return fail(LV_ERR_CAPACITY, "build: beam/visited capacity does not fit in shared memory");
+    const int teams = block / 32;
+    int64_t want = (p.m + teams - 1) / teams;
+    int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
+    k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);
+    LV_CHECK_LAUNCH("beam_kernel<build, whole warp>");
+    return LV_OK;
+}
+
 int launch_build_search(const BeamParams &p, int bits, int nc, int block, size_t smem, int num_sms,
                         cudaStream_t st) {
+    // records longer than 4 lanes x 4 (LVQ-8) or 3 (LVQ-4) chunks: a whole warp per record
+    if (p.prim_chunks + 1 <= 64 && ((bits == 8 && nc > 4) || (bits == 4 && nc > 3)))
+        return bits == 8 ? go_warp<8>(p, block, smem, num_sms, st) : go_warp<4>(p, block, smem, num_sms, st);
     if (bits == 8) {
         switch (nc) {
             case 1: return go<1, 8>(p, block, smem, num_sms, st);

@@ -479,7 +479,9 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     if (prune_smem(PMAX, idx->pg.stride) > 227 * 1024) return fail(LV_ERR_CAPACITY, "build: L_build + R too large");
     // reverse-edge pool: the target's list plus its new sources of one batch
     int PMAX1 = std::max(PMAX, 4 * R + 256);
-    while (PMAX1 > PMAX && prune_smem(PMAX1, idx->pg.stride) > 120 * 1024) PMAX1 -= 32;
+    // (two prune blocks per SM for short records; long records may take most of an SM's shared memory)
+    const int cap1 = idx->pg.stride > 256 ? 200 * 1024 : 120 * 1024;
+    while (PMAX1 > PMAX && prune_smem(PMAX1, idx->pg.stride) > cap1) PMAX1 -= 32;
     cudaFree(idx->graph);
     idx->graph = nullptr;
     idx->R = 0;

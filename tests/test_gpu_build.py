@@ -32,6 +32,8 @@ def _prims(n, d, bits, seed):
     (777, 40, 8, 32, 64, 1.2, 128, 0),   # ragged sizes, R > 32
     (900, 24, 8, 16, 32, 1.2, 64, 1),    # unit-L2 rule
     (700, 16, 4, 12, 24, 1.3, 50, 1),
+    (500, 256, 8, 16, 32, 1.0, 64, 0),   # long records: a whole warp per record (17 chunks)
+    (400, 400, 4, 12, 24, 1.02, 50, 1),  # long LVQ-4 records (13 chunks)
 ])
 def test_build_bit_exact(lv, n, d, bits, R, Lb, alpha, batch, rule):
     Y, mu, q = _prims(n, d, bits, seed=n + d)
