@@ -48,6 +48,10 @@ TRAFFIC_RECORDS = [
     # the default graph (unit-L2 rule, alpha 1.02) at its L for 0.90: beam 3.271 GB + 10.2 MB, rerank 1.107 GB + 0.25 MB
     {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 148, "width": 2, "hash": 0,
      "projection": "bf16", "alpha": 1.02, "rule": 1, "bytes": 3271060992 + 10185216 + 1106905856 + 252160},
+    # the default: the same rule on a graph built on full-D LVQ-8 codes, L = 120: beam 2.733 GB + 8.8 MB,
+    # rerank 0.893 GB + 0.31 MB
+    {"src_sha1": "4e2ac9ceadbe546c30cb2a438a18dcf7d48e6ac1", "n": 1_000_000, "m": 10_000, "L": 120, "width": 2, "hash": 0, "projection": "bf16",
+     "alpha": 1.02, "rule": 1, "graph": "full", "bytes": 2732890112 + 8800256 + 892947712 + 306944},
 ]
 
 
@@ -65,7 +69,8 @@ def recorded_traffic(args, L):
     for r in TRAFFIC_RECORDS:
         if (r["src_sha1"] == sha and r["n"] == args.n and r["m"] == args.m and r["L"] == L and
                 r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection and
-                r.get("alpha") == args.alpha and r.get("rule") == args.rule):
+                r.get("alpha") == args.alpha and r.get("rule") == args.rule and
+                r.get("graph", "primary") == getattr(args, "graph", "primary")):
             return r["bytes"]
     return None
 TARGET = 0.90
@@ -231,12 +236,22 @@ def setup(args, dev, with_base=True):
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     t0 = time.time()
-    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
-                    seed=workloads.SEED_GRAPH + 2)
-    idx.sync_status()
+    if getattr(args, "graph", "primary") == "full":
+        # the graph both searches share is built on the unreduced vectors (LVQ-8 codes of x, the
+        # full-precision stand-in), as the paper's search comparisons use a full-precision graph
+        gi = lv.Index(dev.index).set_primary(X, None, 8, args.D)
+    else:
+        gi = idx
+    gi.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
+                   seed=workloads.SEED_GRAPH + 2)
+    gi.sync_status()
+    graph, entry = gi.get_graph()
+    if gi is not idx:
+        idx.set_graph(graph, entry)
+        del gi
+    torch.cuda.synchronize()
     t_build = time.time() - t0
-    log(f"fit {t_fit:.2f}s encode {t_enc:.2f}s build {t_build:.2f}s")
-    graph, entry = idx.get_graph()
+    log(f"fit {t_fit:.2f}s encode {t_enc:.2f}s build {t_build:.2f}s ({getattr(args, 'graph', 'primary')} graph)")
     base = lv.Index(dev.index).encode_fp32(X).set_graph(graph, entry) if with_base else None
     t0 = time.time()
     truth = ground_truth(X, Q, 10)
@@ -501,6 +516,7 @@ def bench_buildstudy(args, dev):
     quantisation error: the full-precision stand-in), same R, L_build, alpha, passes, batch and
     seed; then both the LeanVec search and the full-D FP32 search are calibrated for recall 0.90 on
     each graph."""
+    args.graph = "primary"  # setup builds the primary graph; the full-D one is built below
     S = setup(args, dev)
     lv, X, Q, A, truth = S["lv"], S["X"], S["Q"], S["A"], S["truth"]
     idx, base = S["idx"], S["base"]
@@ -549,7 +565,7 @@ def bench_buildstudy(args, dev):
 
 
 def bench_dsweep(args, dev):
-    """Target-d selection on the id-1M-768 workload: one graph (built on the d = 160 primaries), then
+    """Target-d selection on the id-1M-768 workload: one graph (the id workload's, see --graph), then
     for each primary dimension d the LeanVec-ID projection of that size, its primaries and
     secondaries, the smallest grid L with recall@10 >= 0.90 (rerank = L) and the QPS there."""
     S = setup(args, dev, with_base=False)
@@ -579,7 +595,8 @@ def bench_dsweep(args, dev):
         torch.cuda.empty_cache()
     ok = {d: r for d, r in res.items() if r.get("qps")}
     best = max(ok, key=lambda d: ok[d]["qps"]) if ok else None
-    out = {"metric": "QPS at 10-recall@10 = 0.90 vs the primary dimension d (one graph, built on d = 160 primaries)",
+    out = {"metric": "QPS at 10-recall@10 = 0.90 vs the primary dimension d (one graph, built on "
+                     + ("full-D LVQ-8 codes)" if args.graph == "full" else "the d = 160 primaries)"),
            "workload": f"id-{args.n // 1000}k-{args.D}, {args.m} ID queries, LeanVec-ID LVQ-8 primaries of d dims "
                        f"+ LVQ-8 secondaries, width {args.width}, {args.projection} projection",
            "results": res, "best_d": best, "data": "synthetic"}
@@ -600,6 +617,9 @@ def main():
     ap.add_argument("--R", type=int, default=64)
     ap.add_argument("--L_build", type=int, default=128)
     ap.add_argument("--alpha", type=float, default=1.02)
+    ap.add_argument("--graph", default="full", choices=["full", "primary"],
+                    help="id workload: build the shared graph on LVQ-8 codes of the unreduced vectors (full, the "
+                         "paper's setting for its search comparisons) or on the d-dim primaries")
     ap.add_argument("--rule", type=int, default=1,
                     help="RobustPrune rule: 0 alpha-scaled similarity, 1 Vamana's L2 rule on unit-norm vectors")
     ap.add_argument("--batch", type=int, default=65536)
@@ -651,7 +671,8 @@ def main():
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
                 f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "
-                f"alpha={args.alpha} ({'unit-norm L2' if args.rule else 'alpha-scaled IP'} prune rule); k=10, rerank=L")
+                f"alpha={args.alpha} ({'unit-norm L2' if args.rule else 'alpha-scaled IP'} prune rule), built on "
+                f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L")
     metric = "QPS at 10-recall@10=0.90, LeanVec vs full-D FP32 graph search; HBM GB/s"
 
     if args.impl == "reference":
@@ -781,7 +802,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
                    "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
-                   "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "projection": args.projection,
+                   "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "projection": args.projection,
                    "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
