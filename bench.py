@@ -70,7 +70,8 @@ def recorded_traffic(args, L):
         if (r["src_sha1"] == sha and r["n"] == args.n and r["m"] == args.m and r["L"] == L and
                 r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection and
                 r.get("alpha") == args.alpha and r.get("rule") == args.rule and
-                r.get("graph", "primary") == getattr(args, "graph", "primary")):
+                r.get("graph", "primary") == getattr(args, "graph", "primary") and
+                r.get("secondary", "lvq8") == getattr(args, "secondary", "lvq8")):
             return r["bytes"]
     return None
 TARGET = 0.90
@@ -232,7 +233,8 @@ def setup(args, dev, with_base=True):
     torch.cuda.synchronize()
     t_fit = time.time() - t0
     t0 = time.time()
-    idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8)
+    idx = lv.Index(dev.index).encode(X, A, primary_bits=8,
+                                     secondary_bits=16 if getattr(args, "secondary", "lvq8") == "fp16" else 8)
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     t0 = time.time()
@@ -617,6 +619,9 @@ def main():
     ap.add_argument("--R", type=int, default=64)
     ap.add_argument("--L_build", type=int, default=128)
     ap.add_argument("--alpha", type=float, default=1.02)
+    ap.add_argument("--secondary", default="lvq8", choices=["lvq8", "fp16"],
+                    help="id workload: LVQ-8 secondaries (the configured encoding) or FP16 ones (the paper's "
+                         "default in its experiments)")
     ap.add_argument("--graph", default="full", choices=["full", "primary"],
                     help="id workload: build the shared graph on LVQ-8 codes of the unreduced vectors (full, the "
                          "paper's setting for its search comparisons) or on the d-dim primaries")
@@ -673,6 +678,8 @@ def main():
                 f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "
                 f"alpha={args.alpha} ({'unit-norm L2' if args.rule else 'alpha-scaled IP'} prune rule), built on "
                 f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L")
+    if args.secondary == "fp16":
+        workload = workload.replace("LVQ-8 primary + LVQ-8 secondary", "LVQ-8 primary + FP16 secondary")
     metric = "QPS at 10-recall@10=0.90, LeanVec vs full-D FP32 graph search; HBM GB/s"
 
     if args.impl == "reference":
@@ -802,7 +809,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
                    "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
-                   "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "projection": args.projection,
+                   "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary, "projection": args.projection,
                    "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),

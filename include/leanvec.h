@@ -204,7 +204,7 @@ typedef struct {
     int32_t D;              /* original dimensionality */
     int32_t d;              /* primary dimensionality (D for the float32 baseline) */
     int32_t primary_bits;   /* 4, 8, or 32 (float32 records) */
-    int32_t secondary_bits; /* 8, or 0 when there is no secondary store */
+    int32_t secondary_bits; /* 8 (LVQ-8), 16 (FP16), or 0 when there is no secondary store */
     int64_t primary_stride;
     int64_t secondary_stride;
     int32_t R;              /* graph max out-degree, 0 when no graph */
@@ -223,9 +223,12 @@ int leanvec_index_buffers(const lv_index *idx, const uint8_t **primary, const fl
 
 /* Encode the database (Sec. 2 "primary vectors" and "secondary vectors"):
  *   primary   = LVQ_{primary_bits}(B x - mu_B), mu_B = mean of B x over the database
- *   secondary = LVQ_{secondary_bits}(x - mu),  mu = mean of x
+ *   secondary = LVQ_8(x - mu), mu = mean of x       (secondary_bits = 8)
+ *             = x rounded to IEEE half precision    (secondary_bits = 16, the FP16 secondaries of
+ *               Sec. 3's experiments: D halves padded to 32 bytes, no constants; the rerank score
+ *               is <q, fp16(x)> accumulated in float32)
  * X: n x D (device), B: d x D (device).  primary_bits in {4, 8};
- * secondary_bits in {8, 0} (0: no secondary store, search cannot rerank).
+ * secondary_bits in {8, 16, 0} (0: no secondary store, search cannot rerank).
  * projection_precision: lv_precision of the B x GEMM.  Replaces any previous
  * store and graph of the index. Synchronises `stream` before returning. */
 int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float *B, int d,

@@ -198,11 +198,14 @@ def _store(kind, dim, lvq: LVQ | None = None, vecs=None):
 def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank: int = 0,
            prim: LVQ | None = None, prim_vecs: np.ndarray | None = None,
            sec: LVQ | None = None, qs: np.ndarray | None = None, max_hops: int = 0,
-           desc: np.ndarray | None = None, want_beam: bool = False, nthreads: int = 0, width: int = 1) -> dict:
+           desc: np.ndarray | None = None, want_beam: bool = False, nthreads: int = 0, width: int = 1,
+           sec_vecs: np.ndarray | None = None) -> dict:
     """Beam search + rerank for all queries (search width `width`: parents expanded
     per round).  qp: m x d_primary (already projected, FP64).  prim: LVQ primary store, or prim_vecs: raw fp32 vectors.  sec/qs: the
-    secondary store and the unreduced queries for the rerank.  desc (m x 4 int32:
-    k, L, r, max_hops) overrides the uniform parameters."""
+    secondary store and the unreduced queries for the rerank; sec_vecs instead of sec: raw
+    secondary vectors (e.g. x rounded to IEEE half, given as their exact float32 values), scored
+    as plain FP64 inner products.  desc (m x 4 int32: k, L, r, max_hops) overrides the uniform
+    parameters."""
     graph = _c(graph, np.int32)
     n, R = graph.shape
     qp = _c(qp, np.float64)
@@ -216,6 +219,11 @@ def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank
     qsp = None
     if sec is not None and rerank != 0:
         ss, keep2 = _store(0, sec.dim, lvq=sec)
+        qs = _c(qs, np.float64)
+        qsp = _p(qs)
+    elif sec_vecs is not None and rerank != 0:
+        sv = _c(sec_vecs, np.float32)
+        ss, keep2 = _store(1, sv.shape[1], vecs=sv)
         qs = _c(qs, np.float64)
         qsp = _p(qs)
     if desc is None:

@@ -30,6 +30,7 @@ int launch_column_mean(const float *X, int64_t n, int dim, float *mean, cudaStre
 int launch_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int bits, uint8_t *rec,
                       cudaStream_t st);
 int launch_fp32_records(const float *X, int64_t n, int dim, uint8_t *rec, int64_t stride, cudaStream_t st);
+int launch_fp16_records(const float *X, int64_t n, int dim, int64_t stride, uint8_t *out, cudaStream_t st);
 int launch_mu2(const float *mean, int dim, float *out, cudaStream_t st);
 int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
                         cudaStream_t st);
@@ -288,20 +289,26 @@ cleanup:
     return rc;
 }
 
-static int set_secondary_impl(lv_index *idx, const float *X, int64_t n, int D, const float *mean, cudaStream_t st) {
+// bits 8: LVQ-8 records of x - mean; bits 16: x rounded to IEEE half (no mean, no constants)
+static int set_secondary_impl(lv_index *idx, const float *X, int64_t n, int D, const float *mean, int bits,
+                              cudaStream_t st) {
     RecGeom sg;
-    rec_geom(D, 8, sg);
+    rec_geom(D, bits, sg);
     int rc = LV_OK;
     drop_secondary(idx);
     LV_TRYC(cudaMalloc(&idx->sec, (size_t)n * sg.stride));
-    LV_TRYC(cudaMalloc(&idx->smean, sizeof(float) * D));
-    if (mean)
-        LV_TRYC(cudaMemcpyAsync(idx->smean, mean, sizeof(float) * D, cudaMemcpyDeviceToDevice, st));
-    else
-        LV_TRY(launch_column_mean(X, n, D, idx->smean, st));
-    LV_TRY(launch_lvq_encode(X, n, D, idx->smean, 8, idx->sec, st));
+    if (bits == 16) {
+        LV_TRY(launch_fp16_records(X, n, D, sg.stride, idx->sec, st));
+    } else {
+        LV_TRYC(cudaMalloc(&idx->smean, sizeof(float) * D));
+        if (mean)
+            LV_TRYC(cudaMemcpyAsync(idx->smean, mean, sizeof(float) * D, cudaMemcpyDeviceToDevice, st));
+        else
+            LV_TRY(launch_column_mean(X, n, D, idx->smean, st));
+        LV_TRY(launch_lvq_encode(X, n, D, idx->smean, 8, idx->sec, st));
+    }
     LV_TRYC(cudaStreamSynchronize(st));
-    idx->sbits = 8;
+    idx->sbits = bits;
     idx->sg = sg;
 cleanup:
     if (rc != LV_OK) drop_secondary(idx);
@@ -325,7 +332,7 @@ int leanvec_set_secondary(lv_index *idx, const float *X, int64_t n, int D, const
     if (n != idx->n || D != idx->D) return fail(LV_ERR_ARG, "set_secondary: n and D must match the primary store");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "set_secondary: cannot select device");
-    return set_secondary_impl(idx, X, n, D, mean, (cudaStream_t)stream);
+    return set_secondary_impl(idx, X, n, D, mean, 8, (cudaStream_t)stream);
 }
 
 int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float *B, int d, int primary_bits,
@@ -334,7 +341,8 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     if (n <= 0 || n >= (int64_t)0x7fffffff) return fail(LV_ERR_ARG, "encode: n must be in [1, 2^31 - 1)");
     if (D <= 0 || d <= 0 || d > D) return fail(LV_ERR_ARG, "encode: need 0 < d <= D");
     if (primary_bits != 4 && primary_bits != 8) return fail(LV_ERR_ARG, "encode: primary_bits must be 4 or 8");
-    if (secondary_bits != 0 && secondary_bits != 8) return fail(LV_ERR_ARG, "encode: secondary_bits must be 0 or 8");
+    if (secondary_bits != 0 && secondary_bits != 8 && secondary_bits != 16)
+        return fail(LV_ERR_ARG, "encode: secondary_bits must be 0, 8 (LVQ-8) or 16 (FP16)");
     if (projection_precision < LV_PREC_FP32 || projection_precision > LV_PREC_FP8)
         return fail(LV_ERR_ARG, "encode: projection precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
     DeviceGuard g(idx->device);
@@ -350,7 +358,7 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
         LV_TRY(launch_project_fp32(X, n, D, B, d, Y, d, st));
     }
     LV_TRY(set_primary_impl(idx, Y, n, d, nullptr, primary_bits, D, st));
-    if (secondary_bits) LV_TRY(set_secondary_impl(idx, X, n, D, nullptr, st));
+    if (secondary_bits) LV_TRY(set_secondary_impl(idx, X, n, D, nullptr, secondary_bits, st));
 cleanup:
     cudaFree(Y);
     if (rc != LV_OK) index_free_stores(idx);
@@ -505,6 +513,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.sec = idx->sec;
     p.sec_stride = idx->sbits ? idx->sg.stride : 0;
     p.sec_chunks = idx->sbits ? idx->sg.code_chunks : 0;
+    p.sec_bits = idx->sbits;
     p.Q = Q;
     p.D = idx->D;
     p.ids = ids;
@@ -532,7 +541,8 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (warps % p.T || warps > 32) return fail(LV_ERR_ARG, "search: warps_per_block must be <= 32 and a multiple of warps_per_query");
     while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
     if ((size_t)(warps / p.T) * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
-    if (idx->sbits && idx->sg.code_chunks + 1 > 64) return fail(LV_ERR_ARG, "search: D > 1008 is not supported by the rerank");
+    if (idx->sbits == 8 && idx->sg.code_chunks + 1 > 64) return fail(LV_ERR_ARG, "search: D > 1008 is not supported by the rerank");
+    if (idx->sbits == 16 && idx->sg.code_chunks > 128) return fail(LV_ERR_ARG, "search: D > 1024 is not supported by the FP16 rerank");
     const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
     if (rerank) {
         p.ldc = p.Lcap;  // r <= L <= Lcap

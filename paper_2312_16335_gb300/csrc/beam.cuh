@@ -38,6 +38,7 @@ struct BeamParams {
     const uint8_t *sec;
     int64_t sec_stride;
     int sec_chunks;
+    int sec_bits;  // 8: LVQ-8 records, 16: IEEE half vectors
     const float *Q;  // unreduced queries m x D
     int D;
     // build mode

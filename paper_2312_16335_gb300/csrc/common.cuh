@@ -58,6 +58,12 @@ inline bool rec_geom(int dim, int bits, RecGeom &g) {
         g.stride = round_up(g.code_bytes + 16, 32);
         return true;
     }
+    if (bits == 16) {  // IEEE half vectors, no constants
+        g.code_bytes = (int)round_up((int64_t)dim * 2, 16);
+        g.code_chunks = g.code_bytes / 16;
+        g.stride = round_up((int64_t)dim * 2, 32);
+        return true;
+    }
     if (bits == 32) {
         g.code_bytes = (int)round_up((int64_t)dim * 4, 16);
         g.code_chunks = g.code_bytes / 16;

@@ -1,5 +1,7 @@
 // LVQ encoding (quant() of Sec. 2: LVQ, per-vector scalar quantisation around the
 // dataset mean) and the FP64 column mean.  One warp per vector.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace lv {
@@ -138,6 +140,25 @@ int launch_column_mean(const float *X, int64_t n, int dim, float *mean, cudaStre
     dim3 blk(32, 8), grd((dim + 31) / 32);
     column_mean_kernel<<<grd, blk, 0, st>>>(X, n, dim, mean);
     LV_CHECK_LAUNCH("column_mean_kernel");
+    return LV_OK;
+}
+
+// FP16 secondary records: x rounded to IEEE half (round to nearest even), the padding zeroed.
+__global__ void fp16_record_kernel(const float *__restrict__ X, int64_t n, int dim, int64_t stride,
+                                   uint8_t *__restrict__ out) {
+    const int64_t halves = stride / 2;
+    const int64_t total = n * halves;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / halves, j = t - i * halves;
+        const __half h = j < dim ? __float2half_rn(X[i * dim + j]) : __float2half_rn(0.f);
+        reinterpret_cast<__half *>(out + i * stride)[j] = h;
+    }
+}
+
+int launch_fp16_records(const float *X, int64_t n, int dim, int64_t stride, uint8_t *out, cudaStream_t st) {
+    if (n == 0) return LV_OK;
+    fp16_record_kernel<<<1024, 256, 0, st>>>(X, n, dim, stride, out);
+    LV_CHECK_LAUNCH("fp16_record_kernel");
     return LV_OK;
 }
 

@@ -3,6 +3,8 @@
 // best k are kept).  The beam kernel hands over the top-r ids of every query
 // (BeamParams::cand); here one warp takes one query, scores its r records whole-warp
 // (16-byte coalesced loads of every record) and writes the top k.
+#include <cuda_fp16.h>
+
 #include "beam.cuh"
 
 namespace lv {
@@ -139,6 +141,68 @@ __device__ __forceinline__ void warp_topk(float *S, int *I, int n, int k, int32_
     }
 }
 
+// Rerank scorer for FP16 secondary records (whole warp per record): the unreduced query in
+// float32 registers, lane l holds half chunks l, l + 32, ... (8 halves each; D <= 32 NCW 8); the
+// halves are widened exactly to float32 and accumulated in float32.  4 records per pass.
+template <int NCW>
+struct Fp16SecScorer {
+    static constexpr int U = 4;
+    float q[NCW][8];
+    int CH;
+    const uint8_t *base;
+    int64_t stride;
+
+    __device__ __forceinline__ void setup(const float *qrow, int D, int chunks, const uint8_t *b, int64_t st, float,
+                                          float, int lane) {
+        CH = chunks;
+        base = b;
+        stride = st;
+#pragma unroll
+        for (int t = 0; t < NCW; ++t) {
+            const int c = lane + 32 * t;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j = 8 * c + e;
+                q[t][e] = (c < CH && j < D) ? qrow[j] : 0.f;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
+        for (int b = 0; b < cnt; b += U) {
+            uint4 v[U][NCW];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int id = b + u < cnt ? ids[b + u] : -1;
+                const uint8_t *r = base + (int64_t)(id < 0 ? 0 : id) * stride;
+#pragma unroll
+                for (int t = 0; t < NCW; ++t) {
+                    const int c = lane + 32 * t;
+                    v[u][t] = (c < CH && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int t = 0; t < NCW; ++t) {
+                    const uint32_t w[4] = {v[u][t].x, v[u][t].y, v[u][t].z, v[u][t].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+                        a0 = fmaf(q[t][2 * i], x.x, a0);
+                        a1 = fmaf(q[t][2 * i + 1], x.y, a1);
+                    }
+                }
+                float s = a0 + a1;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+                if (lane == 0 && b + u < cnt) out[b + u] = s;
+            }
+        }
+    }
+};
+
 struct RerankParams {
     const uint8_t *sec;
     int64_t sec_stride;
@@ -159,6 +223,7 @@ struct RerankParams {
 
 constexpr int RR_WARPS = 4;
 
+template <class SS>
 __global__ void __launch_bounds__(32 * RR_WARPS) rerank_kernel(const RerankParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -172,7 +237,7 @@ __global__ void __launch_bounds__(32 * RR_WARPS) rerank_kernel(const RerankParam
         const int32_t *cd = p.cand + qi * p.ldc;
         for (int t = lane; t < nr; t += 32) rI[t] = cd[t];
         __syncwarp();
-        SecIntScorer sc;
+        SS sc;
         const float4 kq = p.qconst[qi];
         sc.setup(p.Q + qi * p.D, p.D, p.sec_chunks, p.sec, p.sec_stride, kq.z, kq.w, lane);
         sc.score(rI, rS, nr, lane);
@@ -186,6 +251,18 @@ __global__ void __launch_bounds__(32 * RR_WARPS) rerank_kernel(const RerankParam
         }
         __syncwarp();
     }
+}
+
+template <class SS>
+static int go_rerank(const RerankParams &p, int num_sms, cudaStream_t st) {
+    const size_t smem = (size_t)RR_WARPS * 2 * sizeof(float) * p.ldc;
+    if (smem > 48 * 1024)
+        LV_CUDA(cudaFuncSetAttribute(rerank_kernel<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t want = (p.m + RR_WARPS - 1) / RR_WARPS;
+    const int64_t grid = std::min<int64_t>(want, (int64_t)num_sms * 64);
+    rerank_kernel<SS><<<(unsigned)std::max<int64_t>(grid, 1), 32 * RR_WARPS, smem, st>>>(p);
+    LV_CHECK_LAUNCH("rerank_kernel");
+    return LV_OK;
 }
 
 int launch_rerank(const BeamParams &bp, int num_sms, cudaStream_t st) {
@@ -205,13 +282,16 @@ int launch_rerank(const BeamParams &bp, int num_sms, cudaStream_t st) {
     p.ids = bp.ids;
     p.scores = bp.scores;
     p.ldo = bp.ldo;
-    const size_t smem = (size_t)RR_WARPS * 2 * sizeof(float) * p.ldc;
-    if (smem > 48 * 1024) LV_CUDA(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t want = (p.m + RR_WARPS - 1) / RR_WARPS;
-    const int64_t grid = std::min<int64_t>(want, (int64_t)num_sms * 64);
-    rerank_kernel<<<(unsigned)std::max<int64_t>(grid, 1), 32 * RR_WARPS, smem, st>>>(p);
-    LV_CHECK_LAUNCH("rerank_kernel");
-    return LV_OK;
+    if (bp.sec_bits == 16) {
+        switch ((p.sec_chunks + 31) / 32) {
+            case 1: return go_rerank<Fp16SecScorer<1>>(p, num_sms, st);
+            case 2: return go_rerank<Fp16SecScorer<2>>(p, num_sms, st);
+            case 3: return go_rerank<Fp16SecScorer<3>>(p, num_sms, st);
+            case 4: return go_rerank<Fp16SecScorer<4>>(p, num_sms, st);
+            default: return fail(LV_ERR_ARG, "rerank: FP16 secondaries longer than 1024 dimensions");
+        }
+    }
+    return go_rerank<SecIntScorer>(p, num_sms, st);
 }
 
 }  // namespace lv

@@ -64,8 +64,10 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search_noalloc: rerank needs a secondary store");
     if (params->projection != LV_PREC_FP32)
         return fail(LV_ERR_ARG, "search_noalloc: only LV_PREC_FP32 projection is available in this build");
-    if (idx->sbits && idx->sg.code_chunks + 1 > 64)
+    if (idx->sbits == 8 && idx->sg.code_chunks + 1 > 64)
         return fail(LV_ERR_ARG, "search_noalloc: D > 1008 is not supported by the rerank");
+    if (idx->sbits == 16 && idx->sg.code_chunks > 128)
+        return fail(LV_ERR_ARG, "search_noalloc: D > 1024 is not supported by the FP16 rerank");
 
     const int cpc = idx->pbits == 8 ? 16 : idx->pbits == 4 ? 32 : 4;
     const int ldq = idx->pg.code_chunks * cpc;
@@ -121,6 +123,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         p.sec = idx->sec;
         p.sec_stride = idx->sbits ? idx->sg.stride : 0;
         p.sec_chunks = idx->sbits ? idx->sg.code_chunks : 0;
+        p.sec_bits = idx->sbits;
         p.Q = Q;
         p.D = idx->D;
         p.ids = ids;

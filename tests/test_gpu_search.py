@@ -133,6 +133,31 @@ def test_warps_per_query_errors(lv, pb):
             idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, width=W, warps_per_query=T, warps_per_block=wpb)
 
 
+def test_fp16_secondary_encode_and_rerank(lv, pb):
+    """FP16 secondaries (secondary_bits = 16): records are x rounded to IEEE half (bit-exact against
+    numpy, padding zero); the rerank over them matches the oracle's FP64 scores of the same halves."""
+    idx = lv.Index(0).encode(t(pb["X"]), t(pb["P"]), 8, 16)
+    inf = idx.info()
+    D = pb["D"]
+    assert inf["secondary_bits"] == 16 and inf["secondary_stride"] == (2 * D + 31) // 32 * 32
+    rec = idx.secondary_records().cpu().numpy()
+    X16 = pb["X"].astype(np.float16)
+    np.testing.assert_array_equal(rec[:, :2 * D].copy().view(np.uint16), X16.view(np.uint16))
+    assert (rec[:, 2 * D:] == 0).all()
+    # the oracle's primaries (same n: the FP16 secondary store stays) and graph
+    idx.set_primary(t(pb["Y"]), t(pb["mu_p"]), pb["bits"], D).set_graph(t(pb["graph"]), pb["entry"])
+    assert idx.info()["secondary_bits"] == 16
+    ids, sc = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48)
+    ref = oracle.search(pb["graph"], pb["entry"], _qp(pb), k=10, L=48, rerank=48, prim=pb["prim"],
+                        sec_vecs=X16.astype(np.float32), qs=pb["Q"].astype(np.float64))
+    ids = ids.cpu().numpy()
+    assert (ids == ref["ids"]).mean() >= 0.99
+    _check_scores(ids, sc.cpu().numpy(), X16.astype(np.float64), pb["Q"].astype(np.float64))
+    # the no-allocation entry point reranks the same way
+    ids2, sc2 = idx.search_noalloc(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48)
+    assert (ids2.cpu().numpy() == ref["ids"]).mean() >= 0.99
+
+
 def test_small_hash_still_exact(lv, pb):
     """A tiny visited cache forgets often; the beam (hence the result) is unchanged."""
     idx = gpu_index(lv, pb)

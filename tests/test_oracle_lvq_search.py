@@ -184,6 +184,26 @@ def test_rerank_uses_secondary_scores(oracle_lib):
     assert res["ids"].shape == (5, 5)
 
 
+def test_rerank_with_raw_secondary_vectors(oracle_lib):
+    """Raw secondary vectors (the FP16 secondaries' exact values): with r = L >= n the result is the
+    brute-force top-k of <q, x16> over all nodes, i.e. numpy on the half-rounded vectors."""
+    rng = np.random.default_rng(16)
+    n, D, d = 100, 24, 5
+    X = workloads.unit_rows(rng.standard_normal((n, D))).astype(np.float32)
+    X16 = X.astype(np.float16).astype(np.float32)  # IEEE round to nearest even, exact widening
+    assert np.abs(X16 - X).max() <= 2.0 ** -11 * np.abs(X).max() * 1.0001
+    P = np.linalg.qr(rng.standard_normal((D, d)))[0].T
+    Yp = (X.astype(np.float64) @ P.T).astype(np.float32)
+    prim = oracle_lib.lvq_encode(Yp, oracle_lib.mean_fp32(Yp), 8)
+    Q = workloads.unit_rows(rng.standard_normal((4, D))).astype(np.float64)
+    res = oracle_lib.search(_connected_graph(n, 4, 3), 0, Q @ P.T, k=6, L=n, rerank=n, prim=prim, sec_vecs=X16, qs=Q)
+    for j in range(4):
+        s = X16.astype(np.float64) @ Q[j]
+        order = np.lexsort((np.arange(n), -s))[:6]
+        np.testing.assert_array_equal(res["ids"][j], order)
+        np.testing.assert_allclose(res["scores"][j], s[order], rtol=0, atol=1e-12)
+
+
 def test_padding_and_max_hops(oracle_lib):
     rng = np.random.default_rng(15)
     n, D = 30, 8
