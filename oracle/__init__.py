@@ -36,7 +36,7 @@ class _Store(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int),
                 ("codes", ctypes.c_void_p), ("delta", ctypes.c_void_p),
                 ("lower", ctypes.c_void_p), ("mean", ctypes.c_void_p),
-                ("vecs", ctypes.c_void_p)]
+                ("vecs", ctypes.c_void_p), ("metric", ctypes.c_int), ("sqnorm", ctypes.c_void_p)]
 
 
 def lib():
@@ -48,22 +48,23 @@ def lib():
         L.orc_lvq_encode.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp]
         L.orc_lvq_decode.argtypes = [vp, vp, vp, vp, i64, i32, vp]
         L.orc_lvq_decode.restype = None
-        L.orc_build_prepare.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp]
-        L.orc_build_score.argtypes = [vp, vp, vp, vp, vp, f32, i32, i64, i64]
+        L.orc_build_prepare.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp]
+        L.orc_build_score.argtypes = [vp, vp, vp, vp, vp, vp, f32, i32, i64, i64]
         L.orc_build_score.restype = f32
         L.orc_search.argtypes = [vp, vp, vp, vp, i64, vp, i64, i32, ctypes.c_int32, vp, i32, vp, vp,
                                  i32, vp, vp, vp, vp, i32, i32]
-        L.orc_bruteforce.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, i32]
+        L.orc_bruteforce.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, i32, i32]
         L.orc_splitmix.argtypes = [u64, u64, u64]
         L.orc_splitmix.restype = u64
         L.orc_random_graph.argtypes = [i64, i32, u64, vp]
         L.orc_random_graph.restype = None
         L.orc_permutation.argtypes = [i64, u64, vp]
         L.orc_permutation.restype = None
-        L.orc_robust_prune.argtypes = [vp, vp, vp, vp, vp, f32, i32, ctypes.c_int32, vp, i32, f32, f32, i32, vp]
-        L.orc_entry_point.argtypes = [vp, i64]
+        L.orc_robust_prune.argtypes = [vp, vp, vp, vp, vp, vp, f32, i32, ctypes.c_int32, vp, i32, f32, f32, i32,
+                                       vp]
+        L.orc_entry_point.argtypes = [vp, vp, i64]
         L.orc_entry_point.restype = ctypes.c_int32
-        L.orc_vamana_build.argtypes = [vp, vp, vp, vp, vp, f32, i32, i64, i32, i32, f32, i32, i32, u64, i32,
+        L.orc_vamana_build.argtypes = [vp, vp, vp, vp, vp, vp, f32, i32, i64, i32, i32, f32, i32, i32, u64, i32,
                                        vp, vp, i32]
         _lib = L
     return _lib
@@ -115,31 +116,44 @@ def mean_fp32(Y: np.ndarray) -> np.ndarray:
     return np.asarray(Y, np.float64).mean(axis=0).astype(np.float32)
 
 
+def sqnorms_fp32(X: np.ndarray) -> np.ndarray:
+    """||x_i||^2 of the original vectors for the L2 metric: squares exact in FP64, summed in FP64,
+    rounded to fp32."""
+    X = np.asarray(X, np.float64)
+    return np.einsum("ij,ij->i", X, X).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # Build-score store (bit-exact FP32 formula over integer sums)
 # --------------------------------------------------------------------------
 class BuildStore:
-    def __init__(self, lvq: LVQ):
+    """metric 0: the build score is <y_a, y_b>; metric 1 (L2): -||y_a - y_b||^2 =
+    2 <y_a, y_b> - (N_a + N_b), N_i = <y_i, y_i>, all in the same fixed FP32 arithmetic."""
+
+    def __init__(self, lvq: LVQ, metric: int = 0):
         self.lvq = lvq
         n, dim = lvq.codes.shape
         self.G = np.empty(n, np.float32)
         self.H = np.empty(n, np.float32)
+        self.N = np.empty(n, np.float32) if metric else None
         mu2 = ctypes.c_float(0.0)
         rc = lib().orc_build_prepare(_p(lvq.codes), _p(lvq.delta), _p(lvq.lower), _p(lvq.mean), n, dim,
-                                     _p(self.G), _p(self.H), ctypes.byref(mu2))
+                                     _p(self.G), _p(self.H), _p(self.N) if metric else None, ctypes.byref(mu2))
         if rc != 0:
             raise ValueError(f"orc_build_prepare failed ({rc})")
         self.mu2 = np.float32(mu2.value)
 
     def _args(self):
         l = self.lvq
-        return (_p(l.codes), _p(l.delta), _p(l.lower), _p(self.G), _p(self.H), float(self.mu2), l.dim)
+        return (_p(l.codes), _p(l.delta), _p(l.lower), _p(self.G), _p(self.H),
+                _p(self.N) if self.N is not None else None, float(self.mu2), l.dim)
 
     def score(self, a: int, b: int) -> np.float32:
         return np.float32(lib().orc_build_score(*self._args(), int(a), int(b)))
 
     def entry(self) -> int:
-        return int(lib().orc_entry_point(_p(self.G), self.G.shape[0]))
+        return int(lib().orc_entry_point(_p(self.G), _p(self.N) if self.N is not None else None,
+                                         self.G.shape[0]))
 
     def robust_prune(self, p: int, pool, alpha: float, R: int, shift: float = 0.0) -> np.ndarray:
         pool = _c(pool, np.int32)
@@ -150,9 +164,11 @@ class BuildStore:
 
 
 def vamana_build(lvq: LVQ, R: int, L_build: int, alpha: float, passes: int, batch: int, seed: int,
-                 nthreads: int = 0, rule: int = 0):
-    """rule 0: drop p' when alpha s(p*,p') >= s(p,p'); rule 1: when alpha s(p*,p') >= s(p,p') + alpha - 1."""
-    bs = BuildStore(lvq)
+                 nthreads: int = 0, rule: int = 0, metric: int = 0):
+    """rule 0: drop p' when alpha s(p*,p') >= s(p,p'); rule 1: when alpha s(p*,p') >= s(p,p') + alpha - 1.
+    metric 1: the L2 build score s = -||y_a - y_b||^2 (rule 0 is then Vamana's alpha d(p*,p') <= d(p,p')
+    on squared distances)."""
+    bs = BuildStore(lvq, metric)
     n = lvq.codes.shape[0]
     graph = np.empty((n, R), np.int32)
     entry = ctypes.c_int32(0)
@@ -182,10 +198,14 @@ def splitmix(seed: int, a: int, b: int) -> int:
 # --------------------------------------------------------------------------
 # Search
 # --------------------------------------------------------------------------
-def _store(kind, dim, lvq: LVQ | None = None, vecs=None):
+def _store(kind, dim, lvq: LVQ | None = None, vecs=None, metric: int = 0, sqnorm=None):
     s = _Store()
-    s.kind, s.dim = kind, dim
+    s.kind, s.dim, s.metric = kind, dim, metric
     keep = []
+    if sqnorm is not None:
+        sqnorm = _c(sqnorm, np.float32)
+        s.sqnorm = _p(sqnorm)
+        keep.append(sqnorm)
     if lvq is not None:
         s.codes, s.delta, s.lower, s.mean = _p(lvq.codes), _p(lvq.delta), _p(lvq.lower), _p(lvq.mean)
         keep.append(lvq)
@@ -199,31 +219,32 @@ def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank
            prim: LVQ | None = None, prim_vecs: np.ndarray | None = None,
            sec: LVQ | None = None, qs: np.ndarray | None = None, max_hops: int = 0,
            desc: np.ndarray | None = None, want_beam: bool = False, nthreads: int = 0, width: int = 1,
-           sec_vecs: np.ndarray | None = None) -> dict:
+           sec_vecs: np.ndarray | None = None, metric: int = 0, sqnorm: np.ndarray | None = None) -> dict:
     """Beam search + rerank for all queries (search width `width`: parents expanded
     per round).  qp: m x d_primary (already projected, FP64).  prim: LVQ primary store, or prim_vecs: raw fp32 vectors.  sec/qs: the
     secondary store and the unreduced queries for the rerank; sec_vecs instead of sec: raw
     secondary vectors (e.g. x rounded to IEEE half, given as their exact float32 values), scored
     as plain FP64 inner products.  desc (m x 4 int32: k, L, r, max_hops) overrides the uniform
-    parameters."""
+    parameters.  metric 1 (L2): scores are 2 <q, x> - ||x||^2 with ||x||^2 = sqnorm (the original
+    vectors' squared norms; raw-vector stores may leave it None: their own norms)."""
     graph = _c(graph, np.int32)
     n, R = graph.shape
     qp = _c(qp, np.float64)
     m = qp.shape[0]
     if prim is not None:
-        ps, keep1 = _store(0, prim.dim, lvq=prim)
+        ps, keep1 = _store(0, prim.dim, lvq=prim, metric=metric, sqnorm=sqnorm)
     else:
         pv = _c(prim_vecs, np.float32)
-        ps, keep1 = _store(1, pv.shape[1], vecs=pv)
+        ps, keep1 = _store(1, pv.shape[1], vecs=pv, metric=metric, sqnorm=sqnorm)
     ss, keep2 = (None, [])
     qsp = None
     if sec is not None and rerank != 0:
-        ss, keep2 = _store(0, sec.dim, lvq=sec)
+        ss, keep2 = _store(0, sec.dim, lvq=sec, metric=metric, sqnorm=sqnorm)
         qs = _c(qs, np.float64)
         qsp = _p(qs)
     elif sec_vecs is not None and rerank != 0:
         sv = _c(sec_vecs, np.float32)
-        ss, keep2 = _store(1, sv.shape[1], vecs=sv)
+        ss, keep2 = _store(1, sv.shape[1], vecs=sv, metric=metric, sqnorm=sqnorm)
         qs = _c(qs, np.float64)
         qsp = _p(qs)
     if desc is None:
@@ -250,14 +271,16 @@ def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank
     return out
 
 
-def bruteforce(X: np.ndarray, Q: np.ndarray, k: int, nthreads: int = 0):
+def bruteforce(X: np.ndarray, Q: np.ndarray, k: int, nthreads: int = 0, metric: int = 0):
+    """Exact top-k by <q, x> (metric 0) or by -||q - x||^2 (metric 1; the scores returned are
+    2 <q, x> - ||x||^2), FP64, ties -> smaller id."""
     X = _c(X, np.float32)
     Q = _c(Q, np.float32)
     n, D = X.shape
     m = Q.shape[0]
     ids = np.empty((m, k), np.int32)
     sc = np.empty((m, k), np.float64)
-    rc = lib().orc_bruteforce(_p(X), n, _p(Q), m, D, k, _p(ids), _p(sc), nthreads)
+    rc = lib().orc_bruteforce(_p(X), n, _p(Q), m, D, k, _p(ids), _p(sc), metric, nthreads)
     if rc != 0:
         raise RuntimeError("orc_bruteforce failed")
     return ids, sc

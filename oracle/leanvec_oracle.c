@@ -20,6 +20,12 @@
  * sequence of FP32 operations on exact integer sums (so that a graph built
  * anywhere is reproducible bit for bit).  Compile with -ffp-contract=off.
  *
+ * Metrics: inner product (the paper's setting), or squared Euclidean distance
+ * ranked through the identity -||q - x||^2 = 2 <q, x> - ||x||^2 - ||q||^2 (the
+ * query's norm is a per-query constant): the "L2 score" of x is 2 <q, x> - ||x||^2,
+ * with <q, x> approximated exactly as for the inner product (Eq. 1) and ||x||^2
+ * the squared norm of the original vector, kept per record.
+ *
  * Parity unpinned: none of the functions below has a printed worked example
  * in the paper; each is pinned by closed forms and brute force in tests/.
  */
@@ -92,12 +98,16 @@ typedef struct {
     const float *lower;
     const float *mean;    /* dim */
     const float *vecs;    /* kind 1: n x dim */
+    int metric;           /* 0 = inner product, 1 = L2 score 2 <q, x> - ||x||^2 */
+    const float *sqnorm;  /* n: ||x_i||^2 of the original vectors (L2; kind 1 may pass NULL) */
 } orc_store;
 
-/* <q, decode(x_i)> in FP64 (decode first, then the plain dot product). */
+/* <q, decode(x_i)> in FP64 (decode first, then the plain dot product); for the
+ * L2 metric 2 <q, decode(x_i)> - ||x_i||^2 (||x_i||^2 from sqnorm, or for raw
+ * vectors without sqnorm the FP64 sum of squares). */
 static double store_score(const orc_store *s, const double *q, int64_t i)
 {
-    double acc = 0.0;
+    double acc = 0.0, nrm = 0.0;
     if (s->kind == 0) {
         const uint8_t *c = s->codes + i * (int64_t)s->dim;
         double l = s->lower[i], dl = s->delta[i];
@@ -105,9 +115,13 @@ static double store_score(const orc_store *s, const double *q, int64_t i)
             acc += q[j] * ((double)s->mean[j] + l + dl * (double)c[j]);
     } else {
         const float *x = s->vecs + i * (int64_t)s->dim;
-        for (int j = 0; j < s->dim; ++j) acc += q[j] * (double)x[j];
+        for (int j = 0; j < s->dim; ++j) {
+            acc += q[j] * (double)x[j];
+            nrm += (double)x[j] * (double)x[j];
+        }
     }
-    return acc;
+    if (!s->metric) return acc;
+    return 2.0 * acc - (s->sqnorm ? (double)s->sqnorm[i] : nrm);
 }
 
 /* ------------------------------------------------------------------ */
@@ -126,13 +140,18 @@ typedef struct {
     const float *lower;
     float *G;      /* n, filled by orc_build_prepare */
     float *H;      /* n */
+    const float *N; /* L2 metric: n self scores <y_i, y_i> (same arithmetic); NULL = inner product */
     float mu2;     /* sum mu^2 as float */
 } orc_bstore;
 
 static const double FIX = 1048576.0; /* 2^20 */
 
+static float bscore_ip(const orc_bstore *b, int64_t a, int64_t c);
+
+/* G, H, mu2 of the build score; N (nullable): the self scores <y_i, y_i> the L2 build
+ * score needs. */
 int orc_build_prepare(const uint8_t *codes, const float *delta, const float *lower,
-                      const float *mean, int64_t n, int dim, float *G, float *H, float *mu2_out)
+                      const float *mean, int64_t n, int dim, float *G, float *H, float *N, float *mu2_out)
 {
     int32_t *mui = (int32_t *)malloc(sizeof(int32_t) * (size_t)dim);
     if (!mui) return -2;
@@ -159,10 +178,14 @@ int orc_build_prepare(const uint8_t *codes, const float *delta, const float *low
         H[i] = delta[i] * (float)s;
     }
     free(mui);
+    if (N) {
+        orc_bstore bs = {dim, codes, delta, lower, G, H, NULL, *mu2_out};
+        for (int64_t i = 0; i < n; ++i) N[i] = bscore_ip(&bs, i, i);
+    }
     return 0;
 }
 
-static float bscore(const orc_bstore *b, int64_t a, int64_t c)
+static float bscore_ip(const orc_bstore *b, int64_t a, int64_t c)
 {
     const uint8_t *ca = b->codes + a * (int64_t)b->dim;
     const uint8_t *cc = b->codes + c * (int64_t)b->dim;
@@ -183,10 +206,20 @@ static float bscore(const orc_bstore *b, int64_t a, int64_t c)
     return s;
 }
 
-float orc_build_score(const uint8_t *codes, const float *delta, const float *lower,
-                      const float *G, const float *H, float mu2, int dim, int64_t a, int64_t b)
+/* inner product: <y_a, y_c>; L2: -||y_a - y_c||^2 = 2 <y_a, y_c> - (N_a + N_c) in FP32
+ * (the sum of the two self scores first, so that the score is symmetric bit for bit) */
+static float bscore(const orc_bstore *b, int64_t a, int64_t c)
 {
-    orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, mu2};
+    const float ip = bscore_ip(b, a, c);
+    if (!b->N) return ip;
+    const float nn = b->N[a] + b->N[c];
+    return 2.0f * ip - nn;
+}
+
+float orc_build_score(const uint8_t *codes, const float *delta, const float *lower,
+                      const float *G, const float *H, const float *N, float mu2, int dim, int64_t a, int64_t b)
+{
+    orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, N, mu2};
     return bscore(&bs, a, b);
 }
 
@@ -350,9 +383,10 @@ int orc_search(const orc_store *prim, const orc_store *sec, const double *qp, co
     return err;
 }
 
-/* Exact top-k by <q, x> in FP64 over the original vectors (ties -> smaller id). */
+/* Exact top-k by <q, x> (metric 0) or by 2 <q, x> - ||x||^2, i.e. by -||q - x||^2 (metric 1),
+ * in FP64 over the original vectors (ties -> smaller id). */
 int orc_bruteforce(const float *X, int64_t n, const float *Q, int64_t m, int D, int k,
-                   int32_t *ids, double *scores, int nthreads)
+                   int32_t *ids, double *scores, int metric, int nthreads)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -371,9 +405,12 @@ int orc_bruteforce(const float *X, int64_t n, const float *Q, int64_t m, int D, 
                 const float *q = Q + qi * (int64_t)D;
                 for (int64_t i = 0; i < n; ++i) {
                     const float *x = X + i * (int64_t)D;
-                    double acc = 0.0;
-                    for (int j = 0; j < D; ++j) acc += (double)q[j] * (double)x[j];
-                    cand_insert(C, &size, k, acc, (int32_t)i);
+                    double acc = 0.0, nrm = 0.0;
+                    for (int j = 0; j < D; ++j) {
+                        acc += (double)q[j] * (double)x[j];
+                        nrm += (double)x[j] * (double)x[j];
+                    }
+                    cand_insert(C, &size, k, metric ? 2.0 * acc - nrm : acc, (int32_t)i);
                 }
                 for (int t = 0; t < k; ++t) {
                     ids[qi * k + t] = t < size ? C[t].id : -1;
@@ -462,10 +499,10 @@ static int robust_prune(const orc_bstore *bs, int32_t p, const int32_t *pool, in
 }
 
 int orc_robust_prune(const uint8_t *codes, const float *delta, const float *lower,
-                     const float *G, const float *H, float mu2, int dim,
+                     const float *G, const float *H, const float *N, float mu2, int dim,
                      int32_t p, const int32_t *pool, int np, float alpha, float shift, int R, int32_t *out)
 {
-    orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, mu2};
+    orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, N, mu2};
     return robust_prune(&bs, p, pool, np, alpha, shift, R, out);
 }
 
@@ -475,12 +512,17 @@ static int cmp_i64(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
-/* entry = argmax_i <mean, y_i> over decoded primaries, i.e. argmax G_i
- * (ties -> smaller id). */
-int32_t orc_entry_point(const float *G, int64_t n)
+/* inner product: entry = argmax_i <mean, y_i> over decoded primaries, i.e. argmax G_i;
+ * L2 (N != NULL): the primary nearest the mean, argmin ||y_i - mean||^2 =
+ * argmax 2 G_i - N_i (FP32); ties -> smaller id. */
+int32_t orc_entry_point(const float *G, const float *N, int64_t n)
 {
     int32_t best = 0;
-    for (int64_t i = 1; i < n; ++i) if (G[i] > G[best]) best = (int32_t)i;
+    float kb = N ? 2.0f * G[0] - N[0] : G[0];
+    for (int64_t i = 1; i < n; ++i) {
+        const float ki = N ? 2.0f * G[i] - N[i] : G[i];
+        if (ki > kb) { best = (int32_t)i; kb = ki; }
+    }
     return best;
 }
 
@@ -498,17 +540,17 @@ int32_t orc_entry_point(const float *G, int64_t n)
  * batch = 1 is the sequential algorithm.  graph: n x R, -1 padded, in/out.
  */
 int orc_vamana_build(const uint8_t *codes, const float *delta, const float *lower,
-                     const float *G, const float *H, float mu2, int dim, int64_t n,
+                     const float *G, const float *H, const float *N, float mu2, int dim, int64_t n,
                      int R, int L_build, float alpha, int passes, int batch, uint64_t seed, int rule,
                      int32_t *graph, int32_t *entry_out, int nthreads)
 {
-    orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, mu2};
+    orc_bstore bs = {dim, codes, delta, lower, (float *)G, (float *)H, N, mu2};
     if (batch < 1 || R < 1 || L_build < 1 || passes < 1) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
     orc_random_graph(n, R, seed, graph);
-    int32_t entry = orc_entry_point(G, n);
+    int32_t entry = orc_entry_point(G, N, n);
     *entry_out = entry;
     int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *snap = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * R);

@@ -75,11 +75,11 @@ def test_robust_prune_invariants(oracle_lib):
         assert out.tolist() == kept
 
 
-def _python_sequential_vamana(oracle_lib, q, R, L, alpha, passes, seed, rule=0):
+def _python_sequential_vamana(oracle_lib, q, R, L, alpha, passes, seed, rule=0, metric=0):
     """Textbook sequential Vamana (one node at a time), written independently of the
     C batch build: greedy search from the entry, prune, add reverse edges and prune
     any neighbour that overflows."""
-    bs = oracle_lib.BuildStore(q)
+    bs = oracle_lib.BuildStore(q, metric)
     n = q.codes.shape[0]
     G = [list(int(u) for u in row if u >= 0) for row in oracle_lib.random_graph(n, R, seed)]
     entry = bs.entry()
@@ -121,11 +121,13 @@ def _python_sequential_vamana(oracle_lib, q, R, L, alpha, passes, seed, rule=0):
     return out, entry
 
 
-@pytest.mark.parametrize("bits,rule,alpha", [(8, 0, 0.95), (4, 0, 0.95), (8, 1, 1.2)])
-def test_batch_one_equals_sequential_vamana(oracle_lib, bits, rule, alpha):
+@pytest.mark.parametrize("bits,rule,alpha,metric", [(8, 0, 0.95, 0), (4, 0, 0.95, 0), (8, 1, 1.2, 0),
+                                                     (8, 0, 1.2, 1), (4, 0, 1.2, 1)])
+def test_batch_one_equals_sequential_vamana(oracle_lib, bits, rule, alpha, metric):
     q = _primaries(oracle_lib, n=70, d=10, bits=bits, seed=22)
-    g, e = oracle_lib.vamana_build(q, R=6, L_build=12, alpha=alpha, passes=2, batch=1, seed=77, rule=rule)
-    g2, e2 = _python_sequential_vamana(oracle_lib, q, 6, 12, alpha, 2, 77, rule=rule)
+    g, e = oracle_lib.vamana_build(q, R=6, L_build=12, alpha=alpha, passes=2, batch=1, seed=77, rule=rule,
+                                   metric=metric)
+    g2, e2 = _python_sequential_vamana(oracle_lib, q, 6, 12, alpha, 2, 77, rule=rule, metric=metric)
     assert e == e2
     np.testing.assert_array_equal(g, g2)
 
