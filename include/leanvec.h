@@ -74,7 +74,15 @@ const char *leanvec_last_error(void);
  * and are NaN when some |mu_j| >= 8.
  * A float32 record (bits = 32, the full-dimensional baseline) is the dim floats
  * zero-padded to a multiple of 32 bytes.
- * Returns the stride in bytes, or a negative lv_status for unsupported bits.
+ * In an index with the L2 metric (leanvec_set_metric) an LVQ record has a second
+ * 16-byte constants chunk at co + 16: float32 {N, ||x||^2, 0, 0}, N = <y, y> of the
+ * decoded record by the build score below (P = sum_j code_j^2, the record paired
+ * with itself) and ||x||^2 the squared norm of the original vector (squares and sum
+ * in FP64, rounded to float32; N when the original vectors are not known; N is 0
+ * in secondary records, which the build does not read); the stride is then co + 32
+ * rounded up to 32 bytes.
+ * Returns the stride in bytes (of an inner-product index), or a negative lv_status
+ * for unsupported bits.
  */
 int64_t leanvec_record_stride(int dim, int bits);
 
@@ -199,6 +207,18 @@ typedef struct lv_index lv_index;
 int leanvec_index_create(lv_index **out, int device);
 int leanvec_index_free(lv_index *idx);
 
+/* Similarity of an index (set before it holds a store; LV_ERR_STATE otherwise):
+ *   LV_METRIC_IP  inner product <q, x> (the paper's setting; the default)
+ *   LV_METRIC_L2  squared Euclidean distance, ranked by the score 2 <q, x> - ||x||^2
+ *                 (= ||q||^2 - ||q - x||^2: the query's norm is a per-query constant).
+ * With L2 the primary score is 2 <A q, decode(primary)> - ||x||^2, the rerank score
+ * 2 <q, decode(secondary)> - ||x||^2 (||x||^2 of the original vector, stored per
+ * record), the float32 baseline and FP16 secondaries use 2 <q, x> - ||x||^2 of their
+ * own values, and the graph build scores -||y_a - y_b||^2 between decoded primaries
+ * (leanvec_build_graph) with the entry point the primary nearest the mean. */
+typedef enum { LV_METRIC_IP = 0, LV_METRIC_L2 = 1 } lv_metric;
+int leanvec_set_metric(lv_index *idx, int metric);
+
 typedef struct {
     int64_t n;              /* database size */
     int32_t D;              /* original dimensionality */
@@ -278,7 +298,11 @@ typedef enum { LV_PRUNE_SCALED = 0, LV_PRUNE_UNIT_L2 = 1 } lv_prune_rule;
  *     unit-norm vectors; the two coincide at alpha = 1) -- then adds the reverse edges by
  *     (target, source) ascending, pruning targets that exceed R;
  *   - pair scores are the exact build score described with the record layout,
- *     so the adjacency is reproducible bit for bit.
+ *     so the adjacency is reproducible bit for bit; with the L2 metric the pair score
+ *     is -||y_a - y_b||^2 = 2 <y_a, y_b> - (N_a + N_b) (float32, the sum of the self
+ *     scores first) and LV_PRUNE_SCALED with alpha > 1 is Vamana's rule on squared
+ *     distances; the entry point is argmax 2 G_i - N_i (the primary nearest the mean)
+ *     instead of argmax G_i.
  * splitmix64(s, a, b) is the SplitMix64 finaliser applied to
  * s + 0x9E3779B97F4A7C15 * (1 + a * 2^32 + b).  R <= 128, L_build <= 512.  If one
  * batch gives a target more new sources than its reverse-edge pool holds (about

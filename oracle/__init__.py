@@ -219,14 +219,16 @@ def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank
            prim: LVQ | None = None, prim_vecs: np.ndarray | None = None,
            sec: LVQ | None = None, qs: np.ndarray | None = None, max_hops: int = 0,
            desc: np.ndarray | None = None, want_beam: bool = False, nthreads: int = 0, width: int = 1,
-           sec_vecs: np.ndarray | None = None, metric: int = 0, sqnorm: np.ndarray | None = None) -> dict:
+           sec_vecs: np.ndarray | None = None, metric: int = 0, sqnorm: np.ndarray | None = None,
+           sec_sqnorm: np.ndarray | None = None) -> dict:
     """Beam search + rerank for all queries (search width `width`: parents expanded
     per round).  qp: m x d_primary (already projected, FP64).  prim: LVQ primary store, or prim_vecs: raw fp32 vectors.  sec/qs: the
     secondary store and the unreduced queries for the rerank; sec_vecs instead of sec: raw
     secondary vectors (e.g. x rounded to IEEE half, given as their exact float32 values), scored
     as plain FP64 inner products.  desc (m x 4 int32: k, L, r, max_hops) overrides the uniform
     parameters.  metric 1 (L2): scores are 2 <q, x> - ||x||^2 with ||x||^2 = sqnorm (the original
-    vectors' squared norms; raw-vector stores may leave it None: their own norms)."""
+    vectors' squared norms) for the primaries and LVQ secondaries; raw-vector secondaries use
+    sec_sqnorm, by default their own norms (raw primaries without sqnorm likewise)."""
     graph = _c(graph, np.int32)
     n, R = graph.shape
     qp = _c(qp, np.float64)
@@ -244,7 +246,7 @@ def search(graph: np.ndarray, entry: int, qp: np.ndarray, k: int, L: int, rerank
         qsp = _p(qs)
     elif sec_vecs is not None and rerank != 0:
         sv = _c(sec_vecs, np.float32)
-        ss, keep2 = _store(1, sv.shape[1], vecs=sv, metric=metric, sqnorm=sqnorm)
+        ss, keep2 = _store(1, sv.shape[1], vecs=sv, metric=metric, sqnorm=sec_sqnorm)
         qs = _c(qs, np.float64)
         qsp = _p(qs)
     if desc is None:

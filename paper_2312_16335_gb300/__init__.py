@@ -22,6 +22,7 @@ __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mea
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
+METRIC_IP, METRIC_L2 = 0, 1
 
 
 def _ptr(t: torch.Tensor | None):
@@ -192,13 +193,17 @@ def fit_ood_gradient(X: torch.Tensor, Q: torch.Tensor, d: int, steps: int = 100,
 class Index:
     """Owns an ``lv_index*`` (stores + graph on one CUDA device)."""
 
-    def __init__(self, device: int | torch.device | None = None):
+    def __init__(self, device: int | torch.device | None = None, metric: int = METRIC_IP):
+        """metric: METRIC_IP (inner product) or METRIC_L2 (squared Euclidean distance, scores
+        2 <q, x> - ||x||^2); see leanvec_set_metric."""
         if device is None:
             device = torch.cuda.current_device()
         self.device = torch.device("cuda", device if isinstance(device, int) else device.index or 0)
         h = ctypes.c_void_p()
         check(lib().leanvec_index_create(ctypes.byref(h), self.device.index))
         self._h = h
+        if metric:
+            check(lib().leanvec_set_metric(self._h, int(metric)))
 
     def close(self):
         if getattr(self, "_h", None):

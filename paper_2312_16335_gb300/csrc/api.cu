@@ -27,8 +27,11 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // kernels of other translation units
 int launch_column_mean(const float *X, int64_t n, int dim, float *mean, cudaStream_t st);
+int launch_lvq_self_norms(uint8_t *rec, int64_t n, int dim, int bits, int64_t stride, int code_bytes, float mu2,
+                          cudaStream_t st);
+int launch_set_sqnorms(uint8_t *rec, int64_t n, int64_t stride, int off, const float *X, int D, cudaStream_t st);
 int launch_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int bits, uint8_t *rec,
-                      cudaStream_t st);
+                      cudaStream_t st, int metric = 0);
 int launch_fp32_records(const float *X, int64_t n, int dim, uint8_t *rec, int64_t stride, cudaStream_t st);
 int launch_fp16_records(const float *X, int64_t n, int dim, int64_t stride, uint8_t *out, cudaStream_t st);
 int launch_mu2(const float *mean, int dim, float *out, cudaStream_t st);
@@ -38,7 +41,7 @@ int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStr
 int launch_query_consts(const float *Qp, int ldq, int d, const float *mu_p, const float *Q, int D,
                         const float *mu_s, int64_t m, float4 *out, cudaStream_t st);
 int launch_graph_sanitize(int32_t *graph, int64_t n, int R, int *status, cudaStream_t st);
-int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int32_t *out,
+int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int metric, int32_t *out,
                         cudaStream_t st);
 int build_graph_impl(lv_index *idx, int R, int L_build, float alpha, int passes, int batch, uint64_t seed,
                      int rule, cudaStream_t st);
@@ -194,6 +197,16 @@ int leanvec_index_free(lv_index *idx) {
     return LV_OK;
 }
 
+int leanvec_set_metric(lv_index *idx, int metric) {
+    if (!idx) return fail(LV_ERR_ARG, "set_metric: null index");
+    if (metric != LV_METRIC_IP && metric != LV_METRIC_L2)
+        return fail(LV_ERR_ARG, "set_metric: metric must be LV_METRIC_IP or LV_METRIC_L2");
+    if (idx->n != 0 && metric != idx->metric)
+        return fail(LV_ERR_STATE, "set_metric: set the metric before the index holds a store");
+    idx->metric = metric;
+    return LV_OK;
+}
+
 int leanvec_index_info(const lv_index *idx, lv_index_info *out) {
     if (!idx || !out) return fail(LV_ERR_ARG, "index_info: null pointer");
     memset(out, 0, sizeof(*out));
@@ -258,7 +271,7 @@ static void drop_secondary(lv_index *idx) {
 static int set_primary_impl(lv_index *idx, const float *Y, int64_t n, int d, const float *mean, int bits, int D,
                             cudaStream_t st) {
     RecGeom pg;
-    rec_geom(d, bits, pg);
+    rec_geom(d, bits, pg, idx->metric);
     float *mu2d = nullptr;
     int rc = LV_OK;
     drop_primary(idx);
@@ -270,10 +283,12 @@ static int set_primary_impl(lv_index *idx, const float *Y, int64_t n, int d, con
         LV_TRYC(cudaMemcpyAsync(idx->pmean, mean, sizeof(float) * d, cudaMemcpyDeviceToDevice, st));
     else
         LV_TRY(launch_column_mean(Y, n, d, idx->pmean, st));
-    LV_TRY(launch_lvq_encode(Y, n, d, idx->pmean, bits, idx->prim, st));
+    LV_TRY(launch_lvq_encode(Y, n, d, idx->pmean, bits, idx->prim, st, idx->metric));
     LV_TRY(launch_mu2(idx->pmean, d, mu2d, st));
     LV_TRYC(cudaMemcpyAsync(&idx->mu2, mu2d, sizeof(float), cudaMemcpyDeviceToHost, st));
     LV_TRYC(cudaStreamSynchronize(st));
+    // L2: self scores N (and ||x||^2 := N until the original vectors are known)
+    if (idx->metric) LV_TRY(launch_lvq_self_norms(idx->prim, n, d, bits, pg.stride, pg.code_bytes, idx->mu2, st));
     idx->n = n;
     idx->d = d;
     idx->D = D;
@@ -293,7 +308,7 @@ cleanup:
 static int set_secondary_impl(lv_index *idx, const float *X, int64_t n, int D, const float *mean, int bits,
                               cudaStream_t st) {
     RecGeom sg;
-    rec_geom(D, bits, sg);
+    rec_geom(D, bits, sg, idx->metric);
     int rc = LV_OK;
     drop_secondary(idx);
     LV_TRYC(cudaMalloc(&idx->sec, (size_t)n * sg.stride));
@@ -305,8 +320,12 @@ static int set_secondary_impl(lv_index *idx, const float *X, int64_t n, int D, c
             LV_TRYC(cudaMemcpyAsync(idx->smean, mean, sizeof(float) * D, cudaMemcpyDeviceToDevice, st));
         else
             LV_TRY(launch_column_mean(X, n, D, idx->smean, st));
-        LV_TRY(launch_lvq_encode(X, n, D, idx->smean, 8, idx->sec, st));
+        LV_TRY(launch_lvq_encode(X, n, D, idx->smean, 8, idx->sec, st, idx->metric));
+        if (idx->metric) LV_TRY(launch_set_sqnorms(idx->sec, n, sg.stride, sg.code_bytes + 20, X, D, st));
     }
+    // L2: the primaries' ||x||^2 from the original vectors too
+    if (idx->metric && idx->prim && idx->pbits != 32)
+        LV_TRY(launch_set_sqnorms(idx->prim, n, idx->pg.stride, idx->pg.code_bytes + 20, X, D, st));
     LV_TRYC(cudaStreamSynchronize(st));
     idx->sbits = bits;
     idx->sg = sg;
@@ -359,6 +378,10 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     }
     LV_TRY(set_primary_impl(idx, Y, n, d, nullptr, primary_bits, D, st));
     if (secondary_bits) LV_TRY(set_secondary_impl(idx, X, n, D, nullptr, secondary_bits, st));
+    if (idx->metric) {  // the primaries' ||x||^2 from X (also without a secondary store)
+        LV_TRY(launch_set_sqnorms(idx->prim, n, idx->pg.stride, idx->pg.code_bytes + 20, X, D, st));
+        LV_TRYC(cudaStreamSynchronize(st));
+    }
 cleanup:
     cudaFree(Y);
     if (rc != LV_OK) index_free_stores(idx);
@@ -411,7 +434,7 @@ int leanvec_set_graph(lv_index *idx, const int32_t *adj, int R, int32_t entry, l
     if (entry < 0) {
         int32_t *e = nullptr;
         LV_CUDA(cudaMalloc(&e, sizeof(int32_t)));
-        rc = launch_entry_argmax(idx->prim, idx->n, idx->pg.stride, idx->pg.code_bytes, e, st);
+        rc = launch_entry_argmax(idx->prim, idx->n, idx->pg.stride, idx->pg.code_bytes, idx->metric, e, st);
         if (rc == LV_OK && cudaMemcpyAsync(&entry, e, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             rc = fail(LV_ERR_CUDA, "set_graph: entry copy failed");
         if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "set_graph: sync failed");
@@ -514,6 +537,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.sec_stride = idx->sbits ? idx->sg.stride : 0;
     p.sec_chunks = idx->sbits ? idx->sg.code_chunks : 0;
     p.sec_bits = idx->sbits;
+    p.metric = idx->metric;
     p.Q = Q;
     p.D = idx->D;
     p.ids = ids;
@@ -535,13 +559,14 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if ((p.T != 1 && p.T != 2 && p.T != 4) || p.W % p.T)
         return fail(LV_ERR_ARG, "search: warps_per_query must be 1, 2 or 4 and divide width");
     p.Rcap = beam_rcap(p.W, p.T, idx->R);
-    const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + 3) / 4;
+    const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
     p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
     int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
     if (warps % p.T || warps > 32) return fail(LV_ERR_ARG, "search: warps_per_block must be <= 32 and a multiple of warps_per_query");
     while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
     if ((size_t)(warps / p.T) * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
-    if (idx->sbits == 8 && idx->sg.code_chunks + 1 > 64) return fail(LV_ERR_ARG, "search: D > 1008 is not supported by the rerank");
+    if (idx->sbits == 8 && idx->sg.code_chunks + 1 + idx->metric > 64)
+        return fail(LV_ERR_ARG, "search: D > 1008 (992 with L2) is not supported by the rerank");
     if (idx->sbits == 16 && idx->sg.code_chunks > 128) return fail(LV_ERR_ARG, "search: D > 1024 is not supported by the FP16 rerank");
     const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
     if (rerank) {
@@ -559,7 +584,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         int ncw = (idx->pg.code_chunks + 31) / 32;
         rc = launch_search_fp32(p, ncw, block, smem, idx->num_sms, st);
     } else {
-        int nc = (idx->pg.code_chunks + 1 + 3) / 4;
+        int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;  // codes + constants chunks over 4 lanes
         rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
                              : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
         if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);

@@ -39,6 +39,7 @@ struct BeamParams {
     int64_t sec_stride;
     int sec_chunks;
     int sec_bits;  // 8: LVQ-8 records, 16: IEEE half vectors
+    int metric;    // 0 inner product, 1 L2 score 2 <q, x> - ||x||^2
     const float *Q;  // unreduced queries m x D
     int D;
     // build mode
@@ -100,7 +101,9 @@ __device__ __forceinline__ int dp4a_uu(uint32_t a, uint32_t b, int c) {
     return d;
 }
 
-template <int NC, int BITS>
+// L2: the score is 2 x (decoded inner product) - ||x||^2, the norm read from the record's second
+// constants chunk (chunk CH + 1)
+template <int NC, int BITS, bool L2 = false>
 struct LvqIntScorer {
     static constexpr int CPC = BITS == 8 ? 16 : 32;  // codes per 16-byte chunk
     static constexpr int V4 = BITS == 8 ? 1 : 2;     // 16-byte limb vectors per limb and chunk
@@ -170,7 +173,7 @@ struct LvqIntScorer {
 #pragma unroll
             for (int t = 0; t < NC; ++t) {
                 const int c = g + 4 * t;
-                v[r][t] = (c <= CH && id >= 0) ? ldg_stream(rec + 16 * c) : make_uint4(0, 0, 0, 0);
+                v[r][t] = (c <= CH + (L2 ? 1 : 0) && id >= 0) ? ldg_stream(rec + 16 * c) : make_uint4(0, 0, 0, 0);
             }
         }
         int sh[P], sm[P], sl[P];
@@ -216,18 +219,22 @@ struct LvqIntScorer {
         for (int r = 0; r < P; ++r) {
             // partial sums of one lane are < 2^24 in magnitude: exact conversions
             float s = fmaf((float)sh[r], 65536.0f, fmaf((float)sm[r], 256.0f, (float)sl[r]));
-            float dl = 0.f, lo = 0.f;
+            float dl = 0.f, lo = 0.f, x2 = 0.f;
 #pragma unroll
-            for (int t = 0; t < NC; ++t)
+            for (int t = 0; t < NC; ++t) {
                 if (g + 4 * t == CH) {
                     dl = __uint_as_float(v[r][t].x);
                     lo = __uint_as_float(v[r][t].y);
                 }
+                if (L2 && g + 4 * t == CH + 1) x2 = __uint_as_float(v[r][t].y);
+            }
             s += __shfl_xor_sync(FULL, s, 1);
             s += __shfl_xor_sync(FULL, s, 2);
             dl = __shfl_sync(FULL, dl, holder);
             lo = __shfl_sync(FULL, lo, holder);
-            if (g == 0 && j[r] < cnt) out[j[r]] = fmaf(dl * scale, s, fmaf(lo, sq, cq));
+            float sc = fmaf(dl * scale, s, fmaf(lo, sq, cq));
+            if (L2) sc = fmaf(2.0f, sc, -__shfl_sync(FULL, x2, (lane & ~3) | ((CH + 1) & 3)));
+            if (g == 0 && j[r] < cnt) out[j[r]] = sc;
         }
     }
 
@@ -243,18 +250,6 @@ struct LvqIntScorer {
 // Build scorer: the query is a database node's own primary record; the pair score is
 // the exact build score (integer sums + a fixed float32 expression, see leanvec.h).
 // --------------------------------------------------------------------------------
-__device__ __forceinline__ float build_pair_score(float mu2, float fdim, float da, float la, float Ga, float Ha,
-                                                  float db, float lb, float Gb, float Hb, int P) {
-    float t1 = __fadd_rn(Ga, Gb);
-    float t2 = __fmul_rn(fdim, __fmul_rn(la, lb));
-    float t3 = __fadd_rn(__fmul_rn(lb, Ha), __fmul_rn(la, Hb));
-    float t4 = __fmul_rn(__fmul_rn(da, db), __int2float_rn(P));
-    float s = __fadd_rn(mu2, t1);
-    s = __fadd_rn(s, t2);
-    s = __fadd_rn(s, t3);
-    return __fadd_rn(s, t4);
-}
-
 // sum of products of the unsigned codes held in two 16-byte chunks (exact)
 template <int BITS>
 __device__ __forceinline__ int code_dot(const uint4 &a, const uint4 &b) {
@@ -278,10 +273,11 @@ __device__ __forceinline__ int code_dot(const uint4 &a, const uint4 &b) {
     return (int)s;
 }
 
-template <int NC, int BITS>
+// L2: the pair score is -||y_a - y_b||^2 from the self scores N (second constants chunk)
+template <int NC, int BITS, bool L2 = false>
 struct BuildScorer {
     uint4 qc[NC];
-    float qd, ql, qG, qH, mu2, fdim;
+    float qd, ql, qG, qH, qN, mu2, fdim;
     int CH;
     const uint8_t *base;
     int64_t stride;
@@ -305,6 +301,7 @@ struct BuildScorer {
         ql = k.y;
         qG = k.z;
         qH = k.w;
+        qN = L2 ? *reinterpret_cast<const float *>(r + 16 * CH + 16) : 0.f;
     }
 
     __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
@@ -320,15 +317,20 @@ struct BuildScorer {
 #pragma unroll
             for (int t = 0; t < NC; ++t) {
                 const int c = g + 4 * t;
-                v0[t] = (c <= CH && id0 >= 0) ? ldg_stream(r0 + 16 * c) : make_uint4(0, 0, 0, 0);
-                v1[t] = (c <= CH && id1 >= 0) ? ldg_stream(r1 + 16 * c) : make_uint4(0, 0, 0, 0);
+                v0[t] = (c <= CH + (L2 ? 1 : 0) && id0 >= 0) ? ldg_stream(r0 + 16 * c) : make_uint4(0, 0, 0, 0);
+                v1[t] = (c <= CH + (L2 ? 1 : 0) && id1 >= 0) ? ldg_stream(r1 + 16 * c) : make_uint4(0, 0, 0, 0);
             }
             int P0 = 0, P1 = 0;
             float4 k0 = make_float4(0, 0, 0, 0), k1 = make_float4(0, 0, 0, 0);
+            float n0 = 0.f, n1 = 0.f;
 #pragma unroll
             for (int t = 0; t < NC; ++t) {
                 P0 += code_dot<BITS>(v0[t], qc[t]);
                 P1 += code_dot<BITS>(v1[t], qc[t]);
+                if (L2 && g + 4 * t == CH + 1) {
+                    n0 = __uint_as_float(v0[t].x);
+                    n1 = __uint_as_float(v1[t].x);
+                }
                 if (g + 4 * t == CH) {
                     k0 = make_float4(__uint_as_float(v0[t].x), __uint_as_float(v0[t].y), __uint_as_float(v0[t].z),
                                      __uint_as_float(v0[t].w));
@@ -348,9 +350,16 @@ struct BuildScorer {
             k1.y = __shfl_sync(FULL, k1.y, holder);
             k1.z = __shfl_sync(FULL, k1.z, holder);
             k1.w = __shfl_sync(FULL, k1.w, holder);
+            float s0 = build_pair_score(mu2, fdim, qd, ql, qG, qH, k0.x, k0.y, k0.z, k0.w, P0);
+            float s1 = build_pair_score(mu2, fdim, qd, ql, qG, qH, k1.x, k1.y, k1.z, k1.w, P1);
+            if (L2) {
+                const int h2 = (lane & ~3) | ((CH + 1) & 3);
+                s0 = l2_from_ip(s0, qN, __shfl_sync(FULL, n0, h2));
+                s1 = l2_from_ip(s1, qN, __shfl_sync(FULL, n1, h2));
+            }
             if (g == 0) {
-                if (j0 < cnt) out[j0] = build_pair_score(mu2, fdim, qd, ql, qG, qH, k0.x, k0.y, k0.z, k0.w, P0);
-                if (j1 < cnt) out[j1] = build_pair_score(mu2, fdim, qd, ql, qG, qH, k1.x, k1.y, k1.z, k1.w, P1);
+                if (j0 < cnt) out[j0] = s0;
+                if (j1 < cnt) out[j1] = s1;
             }
         }
     }
@@ -359,12 +368,12 @@ struct BuildScorer {
 // Build scorer for long records (more code chunks than 4 lanes x 4 chunks hold, e.g. LVQ-8 codes of
 // the unreduced vectors): a whole warp per record, lane l holds chunks l and l + 32 of the node's own
 // record (CH + 1 <= 64); the same exact build score as BuildScorer.  4 records per pass.
-template <int BITS>
+template <int BITS, bool L2 = false>
 struct BuildWarpScorer {
     static constexpr int QBYTES = 0;
     static constexpr int U = 4;
     uint4 qc[2];
-    float qd, ql, qG, qH, mu2, fdim;
+    float qd, ql, qG, qH, qN, mu2, fdim;
     int CH;
     const uint8_t *base;
     int64_t stride;
@@ -386,6 +395,7 @@ struct BuildWarpScorer {
         ql = k.y;
         qG = k.z;
         qH = k.w;
+        qN = L2 ? *reinterpret_cast<const float *>(r + 16 * CH + 16) : 0.f;
     }
 
     __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
@@ -399,7 +409,7 @@ struct BuildWarpScorer {
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     const int c = lane + 32 * t;
-                    v[u][t] = (c <= CH && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
+                    v[u][t] = (c <= CH + (L2 ? 1 : 0) && id >= 0) ? ldg_stream(r + 16 * c) : make_uint4(0, 0, 0, 0);
                 }
             }
 #pragma unroll
@@ -413,7 +423,12 @@ struct BuildWarpScorer {
                 const float kl = __shfl_sync(FULL, __uint_as_float(kv.y), holder);
                 const float kG = __shfl_sync(FULL, __uint_as_float(kv.z), holder);
                 const float kH = __shfl_sync(FULL, __uint_as_float(kv.w), holder);
-                if (lane == 0 && b + u < cnt) out[b + u] = build_pair_score(mu2, fdim, qd, ql, qG, qH, kd, kl, kG, kH, P);
+                float sc = build_pair_score(mu2, fdim, qd, ql, qG, qH, kd, kl, kG, kH, P);
+                if (L2) {
+                    const uint4 nv = ((CH + 1) >> 5) == 0 ? v[u][0] : v[u][1];
+                    sc = l2_from_ip(sc, qN, __shfl_sync(FULL, __uint_as_float(nv.x), (CH + 1) & 31));
+                }
+                if (lane == 0 && b + u < cnt) out[b + u] = sc;
             }
         }
     }
@@ -423,7 +438,8 @@ struct BuildWarpScorer {
 // Whole-warp scorer for long records: float32 vectors (KIND 0, the full-dimensional
 // baseline) or LVQ-8 secondary records (KIND 1, the rerank).  U records per pass.
 // --------------------------------------------------------------------------------
-template <int NCW, int KIND>
+// L2 (float32 records): 2 <q, x> - ||x||^2, the norm summed from the record itself
+template <int NCW, int KIND, bool L2 = false>
 struct WarpScorer {
     static constexpr int CPC = KIND == 0 ? 4 : 16;
     static constexpr int U = KIND == 0 ? (NCW > 4 ? 2 : 4) : 4;
@@ -459,7 +475,7 @@ struct WarpScorer {
     }
 
     __device__ __forceinline__ float dot1(const uint4 (&v)[NCW]) const {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, nn = 0.f;
 #pragma unroll
         for (int t = 0; t < NCW; ++t) {
             if (KIND == 0) {
@@ -467,6 +483,12 @@ struct WarpScorer {
                 a1 = fmaf(q[t][1], __uint_as_float(v[t].y), a1);
                 a2 = fmaf(q[t][2], __uint_as_float(v[t].z), a2);
                 a3 = fmaf(q[t][3], __uint_as_float(v[t].w), a3);
+                if (L2) {
+                    nn = fmaf(__uint_as_float(v[t].x), __uint_as_float(v[t].x), nn);
+                    nn = fmaf(__uint_as_float(v[t].y), __uint_as_float(v[t].y), nn);
+                    nn = fmaf(__uint_as_float(v[t].z), __uint_as_float(v[t].z), nn);
+                    nn = fmaf(__uint_as_float(v[t].w), __uint_as_float(v[t].w), nn);
+                }
             } else {
                 const uint32_t w[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
 #pragma unroll
@@ -478,7 +500,8 @@ struct WarpScorer {
                 }
             }
         }
-        return (a0 + a1) + (a2 + a3);
+        const float ip = (a0 + a1) + (a2 + a3);
+        return L2 ? fmaf(2.0f, ip, -nn) : ip;  // per lane; the warp sum is the score
     }
 
     __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {

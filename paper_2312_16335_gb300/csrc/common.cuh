@@ -39,7 +39,8 @@ int cuda_fail(cudaError_t e, const char *what);
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Record geometry of an LVQ / float32 record (see leanvec.h).
+// Record geometry of an LVQ / float32 record (see leanvec.h).  LVQ records of an L2 index carry a
+// second 16-byte constants chunk {N, ||x||^2, 0, 0} after {delta, lower, G, H}.
 struct RecGeom {
     int dim = 0, bits = 0;
     int code_bytes = 0;   // zero-padded code area (multiple of 16)
@@ -47,7 +48,7 @@ struct RecGeom {
     int64_t stride = 0;
 };
 
-inline bool rec_geom(int dim, int bits, RecGeom &g) {
+inline bool rec_geom(int dim, int bits, RecGeom &g, int metric = 0) {
     if (dim <= 0) return false;
     g.dim = dim;
     g.bits = bits;
@@ -55,7 +56,7 @@ inline bool rec_geom(int dim, int bits, RecGeom &g) {
         int cb = bits == 8 ? dim : (dim + 1) / 2;
         g.code_bytes = (int)round_up(cb, 16);
         g.code_chunks = g.code_bytes / 16;
-        g.stride = round_up(g.code_bytes + 16, 32);
+        g.stride = round_up(g.code_bytes + (metric ? 32 : 16), 32);
         return true;
     }
     if (bits == 16) {  // IEEE half vectors, no constants
@@ -87,6 +88,25 @@ template <int SEL>
 __device__ __forceinline__ float byte_to_float(uint32_t w) {
     uint32_t bits = __byte_perm(w, 0x4B000000u, 0x7540u | SEL);
     return __int_as_float((int)bits) - 8388608.0f;
+}
+
+// The exact build score <y_a, y_b> of two primaries (see leanvec.h): integer sums P and the
+// per-record terms combined by one fixed sequence of float32 operations (no FMA).
+__device__ __forceinline__ float build_pair_score(float mu2, float fdim, float da, float la, float Ga, float Ha,
+                                                  float db, float lb, float Gb, float Hb, int P) {
+    float t1 = __fadd_rn(Ga, Gb);
+    float t2 = __fmul_rn(fdim, __fmul_rn(la, lb));
+    float t3 = __fadd_rn(__fmul_rn(lb, Ha), __fmul_rn(la, Hb));
+    float t4 = __fmul_rn(__fmul_rn(da, db), __int2float_rn(P));
+    float s = __fadd_rn(mu2, t1);
+    s = __fadd_rn(s, t2);
+    s = __fadd_rn(s, t3);
+    return __fadd_rn(s, t4);
+}
+
+// L2 build score -||y_a - y_b||^2 = 2 <y_a, y_b> - (N_a + N_b), N = self scores (symmetric)
+__device__ __forceinline__ float l2_from_ip(float ip, float Na, float Nb) {
+    return __fsub_rn(__fmul_rn(2.0f, ip), __fadd_rn(Na, Nb));
 }
 
 __device__ __forceinline__ bool key_better(float sa, int ia, float sb, int ib) {

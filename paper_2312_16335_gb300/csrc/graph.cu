@@ -55,14 +55,17 @@ __global__ void graph_sanitize_kernel(int32_t *g, int64_t n, int R, int *status)
     }
 }
 
-// argmax_i G_i (ties -> smaller id): G is the third float of the record constants.
-__global__ void entry_partial_kernel(const uint8_t *rec, int64_t n, int64_t stride, int cb, float *bg, int *bi) {
+// argmax_i G_i (ties -> smaller id): G is the third float of the record constants; with the L2
+// metric argmax_i 2 G_i - N_i (the primary nearest the mean; N = first float of the second chunk).
+__global__ void entry_partial_kernel(const uint8_t *rec, int64_t n, int64_t stride, int cb, int metric, float *bg,
+                                     int *bi) {
     __shared__ float sg[256];
     __shared__ int si[256];
     float best = -INFINITY;
     int bid = 0x7fffffff;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float gv = *reinterpret_cast<const float *>(rec + i * stride + cb + 8);
+        if (metric) gv = __fsub_rn(__fmul_rn(2.0f, gv), *reinterpret_cast<const float *>(rec + i * stride + cb + 16));
         if (entry_better(gv, (int)i, best, bid) || bid == 0x7fffffff) {
             if (!isnan(gv) || bid == 0x7fffffff) {
                 best = isnan(gv) ? -INFINITY : gv;
@@ -140,8 +143,8 @@ __global__ void random_graph_kernel(int32_t *g, int64_t n, int R, uint64_t seed,
 }
 
 // --------------------------------------------------------------- RobustPrune
-// Pair score of two records held in shared memory (exact build score).
-template <int BITS>
+// Pair score of two records held in shared memory (exact build score; L2: -||y_a - y_b||^2).
+template <int BITS, bool L2>
 __device__ __forceinline__ float smem_pair_score(const uint8_t *ra, const uint8_t *rb, int CH, int cb, float mu2,
                                                  float fdim) {
     int P = 0;
@@ -149,7 +152,9 @@ __device__ __forceinline__ float smem_pair_score(const uint8_t *ra, const uint8_
         P += code_dot<BITS>(*reinterpret_cast<const uint4 *>(ra + 16 * c), *reinterpret_cast<const uint4 *>(rb + 16 * c));
     const float4 ka = *reinterpret_cast<const float4 *>(ra + cb);
     const float4 kb = *reinterpret_cast<const float4 *>(rb + cb);
-    return build_pair_score(mu2, fdim, ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w, P);
+    const float ip = build_pair_score(mu2, fdim, ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w, P);
+    if (!L2) return ip;
+    return l2_from_ip(ip, *reinterpret_cast<const float *>(ra + cb + 16), *reinterpret_cast<const float *>(rb + cb + 16));
 }
 
 struct PruneParams {
@@ -157,6 +162,7 @@ struct PruneParams {
     int64_t stride;  // record stride (multiple of 32)
     int CH, cb, dim;
     float mu2, alpha, shift;
+    int metric;  // 1: L2 pair scores -||y_a - y_b||^2
     int R, PMAX;
     int64_t n;
     int32_t *graph;        // n x R
@@ -176,7 +182,7 @@ struct PruneParams {
 // MODE 0: pool = beam (minus p) u old out-list of p; output to newl[t].
 // MODE 1: pool = current out-list of u + its new sources (ascending, not present);
 //         pruned only when it exceeds R; output to graph[u].
-template <int BITS, int MODE>
+template <int BITS, int MODE, bool L2>
 __global__ void __launch_bounds__(128) prune_kernel(const PruneParams pp) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int stride = (int)pp.stride;
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(128) prune_kernel(const PruneParams pp) {
     __syncthreads();
     const float fdim = (float)pp.dim;
     for (int i = tid; i < np; i += blockDim.x) {
-        psc[i] = smem_pair_score<BITS>(prec, recs + (size_t)i * stride, pp.CH, pp.cb, pp.mu2, fdim);
+        psc[i] = smem_pair_score<BITS, L2>(prec, recs + (size_t)i * stride, pp.CH, pp.cb, pp.mu2, fdim);
         dead[i] = 0;
     }
     __syncthreads();
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(128) prune_kernel(const PruneParams pp) {
             for (int q = pos + 1 + tid; q < np; q += blockDim.x) {
                 const int j = ord[q];
                 if (dead[j]) continue;
-                const float s = smem_pair_score<BITS>(ri, recs + (size_t)j * stride, pp.CH, pp.cb, pp.mu2, fdim);
+                const float s = smem_pair_score<BITS, L2>(ri, recs + (size_t)j * stride, pp.CH, pp.cb, pp.mu2, fdim);
                 if (__fmul_rn(pp.alpha, s) >= __fadd_rn(psc[j], pp.shift)) dead[j] = 1;
             }
         }
@@ -435,14 +441,14 @@ int launch_graph_sanitize(int32_t *graph, int64_t n, int R, int *status, cudaStr
     return LV_OK;
 }
 
-int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int32_t *out,
+int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int metric, int32_t *out,
                         cudaStream_t st) {
     const int nb = 256;
     float *bg = nullptr;
     int *bi = nullptr;
     LV_CUDA(cudaMallocAsync((void **)&bg, sizeof(float) * nb, st));
     LV_CUDA(cudaMallocAsync((void **)&bi, sizeof(int) * nb, st));
-    entry_partial_kernel<<<nb, 256, 0, st>>>(rec, n, stride, code_bytes, bg, bi);
+    entry_partial_kernel<<<nb, 256, 0, st>>>(rec, n, stride, code_bytes, metric, bg, bi);
     entry_final_kernel<<<1, 256, 0, st>>>(bg, bi, nb, out);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(bg, st);
@@ -454,21 +460,26 @@ int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_
 // ------------------------------------------------------------------ driver
 static int prune_smem(int PMAX, int64_t stride) { return (int)(PMAX * (stride + 17) + stride + 16); }
 
-template <int BITS>
-static int launch_prune(const PruneParams &pp, int mode, unsigned grid, cudaStream_t st) {
+template <int BITS, bool L2>
+static int launch_prune_m(const PruneParams &pp, int mode, unsigned grid, cudaStream_t st) {
     const int sm = prune_smem(pp.PMAX, pp.stride);
     if (grid == 0) return LV_OK;
     if (mode == 0) {
-        auto k = prune_kernel<BITS, 0>;
+        auto k = prune_kernel<BITS, 0, L2>;
         LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
         k<<<grid, 128, sm, st>>>(pp);
     } else {
-        auto k = prune_kernel<BITS, 1>;
+        auto k = prune_kernel<BITS, 1, L2>;
         LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
         k<<<grid, 128, sm, st>>>(pp);
     }
     LV_CHECK_LAUNCH("prune_kernel");
     return LV_OK;
+}
+
+template <int BITS>
+static int launch_prune(const PruneParams &pp, int mode, unsigned grid, cudaStream_t st) {
+    return pp.metric ? launch_prune_m<BITS, true>(pp, mode, grid, st) : launch_prune_m<BITS, false>(pp, mode, grid, st);
 }
 
 int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int batch, uint64_t seed, int rule,
@@ -525,7 +536,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     // initial graph, entry point, order
     random_graph_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(idx->graph, n, R, seed, idx->status);
     LV_CHECK_LAUNCH("random_graph_kernel");
-    rc = launch_entry_argmax(idx->prim, n, idx->pg.stride, idx->pg.code_bytes, ent_d, st);
+    rc = launch_entry_argmax(idx->prim, n, idx->pg.stride, idx->pg.code_bytes, idx->metric, ent_d, st);
     if (rc) return rc;
     int32_t entry = 0;
     LV_CUDA(cudaMemcpyAsync(&entry, ent_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -552,6 +563,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     bp.entry = entry;
     bp.uni = make_int4(Lb, Lb, 0, 0);
     bp.mu2 = idx->mu2;
+    bp.metric = idx->metric;
     bp.ids = bid;
     bp.scores = bsc;
     bp.ldo = Lb;
@@ -571,7 +583,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     int warps = 8;
     while (warps > 1 && (size_t)warps * bp.warp_smem > 227 * 1024) warps >>= 1;
     const size_t bsmem = (size_t)warps * bp.warp_smem;
-    const int nc = (idx->pg.code_chunks + 1 + 3) / 4;
+    const int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
 
     PruneParams pp;
     memset(&pp, 0, sizeof(pp));
@@ -581,6 +593,7 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     pp.cb = idx->pg.code_bytes;
     pp.dim = idx->d;
     pp.mu2 = idx->mu2;
+    pp.metric = idx->metric;
     pp.R = R;
     pp.PMAX = PMAX;
     pp.n = n;

@@ -6,6 +6,7 @@
 struct lv_index {
     int device = 0;
     int num_sms = 0;
+    int metric = 0;  // LV_METRIC_IP or LV_METRIC_L2
     int64_t n = 0;
     int D = 0, d = 0;
     int pbits = 0, sbits = 0;

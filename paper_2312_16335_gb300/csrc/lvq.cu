@@ -162,10 +162,74 @@ int launch_fp16_records(const float *X, int64_t n, int dim, int64_t stride, uint
     return LV_OK;
 }
 
+// L2 index: the second constants chunk {N, ||x||^2, 0, 0} of LVQ records.  N = <y, y> by the build
+// score's own arithmetic (the sum of squared codes and the record's constants, see leanvec.h); the
+// squared norm defaults to N until the original vectors set it (set_sqnorm_kernel).  One warp per
+// record.
+template <int BITS>
+__global__ void lvq_self_norm_kernel(uint8_t *__restrict__ rec, int64_t n, int64_t stride, int code_bytes, int dim,
+                                     float mu2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    uint8_t *r = rec + i * stride;
+    int P = 0;
+    for (int b = lane; b < code_bytes; b += 32) {
+        const uint32_t v = r[b];
+        if (BITS == 8)
+            P += (int)(v * v);
+        else
+            P += (int)((v & 15u) * (v & 15u) + (v >> 4) * (v >> 4));
+    }
+    for (int o = 16; o; o >>= 1) P += __shfl_xor_sync(FULL, P, o);
+    if (lane == 0) {
+        const float4 k = *reinterpret_cast<const float4 *>(r + code_bytes);
+        const float N = build_pair_score(mu2, (float)dim, k.x, k.y, k.z, k.w, k.x, k.y, k.z, k.w, P);
+        *reinterpret_cast<float4 *>(r + code_bytes + 16) = make_float4(N, N, 0.f, 0.f);
+    }
+}
+
+// ||x_i||^2 of the original vectors (squares exact in FP64, FP64 sum, rounded to float32) into the
+// float at byte offset `off` of every record.  One warp per vector.
+__global__ void set_sqnorm_kernel(uint8_t *__restrict__ rec, int64_t n, int64_t stride, int off,
+                                  const float *__restrict__ X, int D) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < D; j += 32) {
+        const double x = (double)X[i * (int64_t)D + j];
+        s += x * x;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) *reinterpret_cast<float *>(rec + i * stride + off) = (float)s;
+}
+
+int launch_lvq_self_norms(uint8_t *rec, int64_t n, int dim, int bits, int64_t stride, int code_bytes, float mu2,
+                          cudaStream_t st) {
+    if (n == 0) return LV_OK;
+    const int wpb = 8;
+    const int64_t blocks = (n + wpb - 1) / wpb;
+    if (bits == 8)
+        lvq_self_norm_kernel<8><<<(unsigned)blocks, wpb * 32, 0, st>>>(rec, n, stride, code_bytes, dim, mu2);
+    else
+        lvq_self_norm_kernel<4><<<(unsigned)blocks, wpb * 32, 0, st>>>(rec, n, stride, code_bytes, dim, mu2);
+    LV_CHECK_LAUNCH("lvq_self_norm_kernel");
+    return LV_OK;
+}
+
+int launch_set_sqnorms(uint8_t *rec, int64_t n, int64_t stride, int off, const float *X, int D, cudaStream_t st) {
+    if (n == 0) return LV_OK;
+    const int wpb = 8;
+    set_sqnorm_kernel<<<(unsigned)((n + wpb - 1) / wpb), wpb * 32, 0, st>>>(rec, n, stride, off, X, D);
+    LV_CHECK_LAUNCH("set_sqnorm_kernel");
+    return LV_OK;
+}
+
 int launch_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int bits,
-                      uint8_t *rec, cudaStream_t st) {
+                      uint8_t *rec, cudaStream_t st, int metric) {
     RecGeom g;
-    if (!rec_geom(dim, bits, g) || bits == 32) return fail(LV_ERR_ARG, "lvq_encode: bits must be 4 or 8");
+    if (!rec_geom(dim, bits, g, metric) || bits == 32) return fail(LV_ERR_ARG, "lvq_encode: bits must be 4 or 8");
     if (n == 0) return LV_OK;
     const int wpb = 8;
     int64_t blocks = (n + wpb - 1) / wpb;

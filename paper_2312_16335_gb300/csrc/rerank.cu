@@ -15,6 +15,7 @@ namespace lv {
 // error bound as LvqIntScorer, with D in place of d).  Lane l holds code chunks l and
 // l + 32 (D <= 1008); 4 records per pass.
 // --------------------------------------------------------------------------------
+template <bool L2 = false>
 struct SecIntScorer {
     static constexpr int NCW = 2, U = 4;
     uint32_t qh[NCW][4], qm[NCW][4], ql[NCW][4];
@@ -62,7 +63,7 @@ struct SecIntScorer {
     }
 
     __device__ __forceinline__ void score(const int *ids, float *out, int cnt, int lane) const {
-        const int tot = CH + 1;
+        const int tot = CH + 1 + (L2 ? 1 : 0);
         const int holder = CH & 31, tslot = CH >> 5;
         for (int b = 0; b < cnt; b += U) {
             uint4 v[U][NCW];
@@ -101,7 +102,12 @@ struct SecIntScorer {
                     }
                 dl = __shfl_sync(FULL, dl, holder);
                 lo = __shfl_sync(FULL, lo, holder);
-                if (lane == 0 && b + u < cnt) out[b + u] = fmaf(dl * scale, s, fmaf(lo, s0, c0));
+                float sc = fmaf(dl * scale, s, fmaf(lo, s0, c0));
+                if (L2) {  // the original vector's squared norm: second constants chunk
+                    const uint4 nv = ((CH + 1) >> 5) == 0 ? v[u][0] : v[u][1];
+                    sc = fmaf(2.0f, sc, -__shfl_sync(FULL, __uint_as_float(nv.y), (CH + 1) & 31));
+                }
+                if (lane == 0 && b + u < cnt) out[b + u] = sc;
             }
         }
     }
@@ -144,7 +150,7 @@ __device__ __forceinline__ void warp_topk(float *S, int *I, int n, int k, int32_
 // Rerank scorer for FP16 secondary records (whole warp per record): the unreduced query in
 // float32 registers, lane l holds half chunks l, l + 32, ... (8 halves each; D <= 32 NCW 8); the
 // halves are widened exactly to float32 and accumulated in float32.  4 records per pass.
-template <int NCW>
+template <int NCW, bool L2 = false>
 struct Fp16SecScorer {
     static constexpr int U = 4;
     float q[NCW][8];
@@ -183,7 +189,7 @@ struct Fp16SecScorer {
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                float a0 = 0.f, a1 = 0.f;
+                float a0 = 0.f, a1 = 0.f, nn = 0.f;
 #pragma unroll
                 for (int t = 0; t < NCW; ++t) {
                     const uint32_t w[4] = {v[u][t].x, v[u][t].y, v[u][t].z, v[u][t].w};
@@ -192,9 +198,11 @@ struct Fp16SecScorer {
                         const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
                         a0 = fmaf(q[t][2 * i], x.x, a0);
                         a1 = fmaf(q[t][2 * i + 1], x.y, a1);
+                        if (L2) nn = fmaf(x.y, x.y, fmaf(x.x, x.x, nn));
                     }
                 }
                 float s = a0 + a1;
+                if (L2) s = fmaf(2.0f, s, -nn);  // 2 <q, x16> - ||x16||^2, summed over the warp below
 #pragma unroll
                 for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
                 if (lane == 0 && b + u < cnt) out[b + u] = s;
@@ -265,6 +273,20 @@ static int go_rerank(const RerankParams &p, int num_sms, cudaStream_t st) {
     return LV_OK;
 }
 
+template <bool L2>
+static int launch_rerank_m(const BeamParams &bp, const RerankParams &p, int num_sms, cudaStream_t st) {
+    if (bp.sec_bits == 16) {
+        switch ((p.sec_chunks + 31) / 32) {
+            case 1: return go_rerank<Fp16SecScorer<1, L2>>(p, num_sms, st);
+            case 2: return go_rerank<Fp16SecScorer<2, L2>>(p, num_sms, st);
+            case 3: return go_rerank<Fp16SecScorer<3, L2>>(p, num_sms, st);
+            case 4: return go_rerank<Fp16SecScorer<4, L2>>(p, num_sms, st);
+            default: return fail(LV_ERR_ARG, "rerank: FP16 secondaries longer than 1024 dimensions");
+        }
+    }
+    return go_rerank<SecIntScorer<L2>>(p, num_sms, st);
+}
+
 int launch_rerank(const BeamParams &bp, int num_sms, cudaStream_t st) {
     RerankParams p;
     p.sec = bp.sec;
@@ -282,16 +304,8 @@ int launch_rerank(const BeamParams &bp, int num_sms, cudaStream_t st) {
     p.ids = bp.ids;
     p.scores = bp.scores;
     p.ldo = bp.ldo;
-    if (bp.sec_bits == 16) {
-        switch ((p.sec_chunks + 31) / 32) {
-            case 1: return go_rerank<Fp16SecScorer<1>>(p, num_sms, st);
-            case 2: return go_rerank<Fp16SecScorer<2>>(p, num_sms, st);
-            case 3: return go_rerank<Fp16SecScorer<3>>(p, num_sms, st);
-            case 4: return go_rerank<Fp16SecScorer<4>>(p, num_sms, st);
-            default: return fail(LV_ERR_ARG, "rerank: FP16 secondaries longer than 1024 dimensions");
-        }
-    }
-    return go_rerank<SecIntScorer>(p, num_sms, st);
+    if (bp.metric) return launch_rerank_m<true>(bp, p, num_sms, st);
+    return launch_rerank_m<false>(bp, p, num_sms, st);
 }
 
 }  // namespace lv

@@ -4,9 +4,9 @@
 
 namespace lv {
 
-template <int NCW, int WT>
+template <int NCW, int WT, bool L2>
 static int go_w(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
-    auto k = beam_kernel<WarpScorer<NCW, 0>, false, false, WT>;
+    auto k = beam_kernel<WarpScorer<NCW, 0, L2>, false, false, WT>;
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
@@ -23,9 +23,14 @@ static int go_w(const BeamParams &p, int block, size_t smem, int num_sms, cudaSt
 template <int NCW>
 static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
     // widths 1 and 2 get their own instantiations (fixed-trip parent loops); 3 and 4 the generic one
-    if (p.W == 1) return go_w<NCW, 1>(p, block, smem, num_sms, st);
-    if (p.W == 2) return go_w<NCW, 2>(p, block, smem, num_sms, st);
-    return go_w<NCW, 0>(p, block, smem, num_sms, st);
+    if (p.metric) {
+        if (p.W == 1) return go_w<NCW, 1, true>(p, block, smem, num_sms, st);
+        if (p.W == 2) return go_w<NCW, 2, true>(p, block, smem, num_sms, st);
+        return go_w<NCW, 0, true>(p, block, smem, num_sms, st);
+    }
+    if (p.W == 1) return go_w<NCW, 1, false>(p, block, smem, num_sms, st);
+    if (p.W == 2) return go_w<NCW, 2, false>(p, block, smem, num_sms, st);
+    return go_w<NCW, 0, false>(p, block, smem, num_sms, st);
 }
 
 int launch_search_fp32(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st) {

@@ -3,9 +3,9 @@
 
 namespace lv {
 
-template <int NC, int WT>
+template <int NC, int WT, bool L2>
 static int go_w(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
-    auto k = beam_kernel<LvqIntScorer<NC, 4>, false, true, WT>;
+    auto k = beam_kernel<LvqIntScorer<NC, 4, L2>, false, true, WT>;
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
@@ -22,9 +22,14 @@ static int go_w(const BeamParams &p, int block, size_t smem, int num_sms, cudaSt
 template <int NC>
 static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
     // widths 1 and 2 get their own instantiations (fixed-trip parent loops); 3 and 4 the generic one
-    if (p.W == 1) return go_w<NC, 1>(p, block, smem, num_sms, st);
-    if (p.W == 2) return go_w<NC, 2>(p, block, smem, num_sms, st);
-    return go_w<NC, 0>(p, block, smem, num_sms, st);
+    if (p.metric) {
+        if (p.W == 1) return go_w<NC, 1, true>(p, block, smem, num_sms, st);
+        if (p.W == 2) return go_w<NC, 2, true>(p, block, smem, num_sms, st);
+        return go_w<NC, 0, true>(p, block, smem, num_sms, st);
+    }
+    if (p.W == 1) return go_w<NC, 1, false>(p, block, smem, num_sms, st);
+    if (p.W == 2) return go_w<NC, 2, false>(p, block, smem, num_sms, st);
+    return go_w<NC, 0, false>(p, block, smem, num_sms, st);
 }
 
 int launch_search_lvq4(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st) {

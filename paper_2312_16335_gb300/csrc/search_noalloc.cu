@@ -64,7 +64,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search_noalloc: rerank needs a secondary store");
     if (params->projection != LV_PREC_FP32)
         return fail(LV_ERR_ARG, "search_noalloc: only LV_PREC_FP32 projection is available in this build");
-    if (idx->sbits == 8 && idx->sg.code_chunks + 1 > 64)
+    if (idx->sbits == 8 && idx->sg.code_chunks + 1 + idx->metric > 64)
         return fail(LV_ERR_ARG, "search_noalloc: D > 1008 is not supported by the rerank");
     if (idx->sbits == 16 && idx->sg.code_chunks > 128)
         return fail(LV_ERR_ARG, "search_noalloc: D > 1024 is not supported by the FP16 rerank");
@@ -124,6 +124,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         p.sec_stride = idx->sbits ? idx->sg.stride : 0;
         p.sec_chunks = idx->sbits ? idx->sg.code_chunks : 0;
         p.sec_bits = idx->sbits;
+        p.metric = idx->metric;
         p.Q = Q;
         p.D = idx->D;
         p.ids = ids;
@@ -158,7 +159,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             break;
         }
         p.Rcap = beam_rcap(p.W, p.T, idx->R);
-        const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + 3) / 4;
+        const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
         p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
         int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
         if (warps % p.T || warps > 32) {
@@ -187,7 +188,7 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         if (idx->pbits == 32) {
             rc = launch_search_fp32(p, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, st);
         } else {
-            const int nc = (idx->pg.code_chunks + 1 + 3) / 4;
+            const int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
             rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
                                  : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
             if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
