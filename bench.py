@@ -49,9 +49,9 @@ TRAFFIC_RECORDS = [
     {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 148, "width": 2, "hash": 0,
      "projection": "bf16", "alpha": 1.02, "rule": 1, "bytes": 3271060992 + 10185216 + 1106905856 + 252160},
     # the default: the same rule on a graph built on full-D LVQ-8 codes, L = 120: beam 2.733 GB + 8.8 MB,
-    # rerank 0.893 GB + 0.31 MB
-    {"src_sha1": "4e2ac9ceadbe546c30cb2a438a18dcf7d48e6ac1", "n": 1_000_000, "m": 10_000, "L": 120, "width": 2, "hash": 0, "projection": "bf16",
-     "alpha": 1.02, "rule": 1, "graph": "full", "bytes": 2732890112 + 8800256 + 892947712 + 306944},
+    # rerank 0.893 GB + 1.2 MB
+    {"src_sha1": "9ea3355bc525640bcd5ba8c54cfb9beac141d1aa", "n": 1_000_000, "m": 10_000, "L": 120, "width": 2, "hash": 0, "projection": "bf16",
+     "alpha": 1.02, "rule": 1, "graph": "full", "bytes": 2733314560 + 8754688 + 893092608 + 1217024},
 ]
 
 
@@ -141,14 +141,17 @@ class Clocks:
                 "samples": len(mhz)}
 
 
-def ground_truth(X: torch.Tensor, Q: torch.Tensor, k: int = 10, chunk: int = 131072) -> torch.Tensor:
-    """Exact top-k inner products (float32 on the GPU, TF32 off; ties -> smaller id)."""
+def ground_truth(X: torch.Tensor, Q: torch.Tensor, k: int = 10, chunk: int = 131072, l2: bool = False) -> torch.Tensor:
+    """Exact top-k inner products, or with l2 the k nearest in Euclidean distance (largest
+    2 <q, x> - ||x||^2); float32 on the GPU, TF32 off."""
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     best_s = torch.full((Q.shape[0], k), -float("inf"), device=Q.device)
     best_i = torch.full((Q.shape[0], k), -1, dtype=torch.int64, device=Q.device)
     for s in range(0, X.shape[0], chunk):
         S = Q @ X[s:s + chunk].T
+        if l2:
+            S = 2 * S - (X[s:s + chunk].double() ** 2).sum(1).float()[None, :]
         v, i = torch.topk(S, k, dim=1)
         cs = torch.cat([best_s, v], 1)
         ci = torch.cat([best_i, i + s], 1)
@@ -566,6 +569,80 @@ def bench_buildstudy(args, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_l2(args, dev):
+    """Euclidean workload shaped like gist-960-1M (Table 1: D = 960, Euclidean, d = 160): the
+    anisotropic mixture without normalisation (norms vary with the component), 10k ID queries,
+    ground truth = the 10 nearest in L2.  One graph, built in an L2 index on full-D LVQ-8 codes with
+    Vamana's rule on squared distances (alpha-scaled, alpha = 1.2 as the paper sets for L2); then
+    the LeanVec search (LVQ-8 primaries of d dims + LVQ-8 secondaries, scores 2 <Aq, y> - ||x||^2,
+    rerank 2 <q, x> - ||x||^2) and the full-D FP32 search, each at the smallest grid L with
+    recall@10 >= 0.90."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    t0 = time.time()
+    X, Q, _ = workloads.make_workload_torch("anisotropic", args.n, args.m, args.D, args.components, cfg=4,
+                                            device=dev, normalize=False)
+    torch.cuda.synchronize()
+    nrm = X.norm(dim=1)
+    log(f"data {tuple(X.shape)} queries {tuple(Q.shape)} in {time.time() - t0:.1f}s; ||x|| mean "
+        f"{float(nrm.mean()):.2f} sd {float(nrm.std()):.2f}")
+    t0 = time.time()
+    sub = torch.from_numpy(workloads.subsample_rows(args.n, min(args.n, 100_000), cfg=4)).to(dev)
+    A = lv.leanvec_fit_id(X.index_select(0, sub).contiguous(), args.d)
+    idx = lv.Index(dev.index, metric=lv.METRIC_L2).encode(
+        X, A, primary_bits=8, secondary_bits=16 if args.secondary == "fp16" else 8)
+    torch.cuda.synchronize()
+    t_enc = time.time() - t0
+    t0 = time.time()
+    gi = lv.Index(dev.index, metric=lv.METRIC_L2)
+    if args.graph == "full":
+        gi.set_primary(X, None, 8, args.D)
+    else:
+        gi = idx
+    gi.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
+                   seed=workloads.SEED_GRAPH + 4)
+    clamped = False
+    try:
+        gi.sync_status()
+    except lv.LeanVecError as e:  # reverse-edge pool clamp: the build completed, some reverse edges dropped
+        if e.code != -4:
+            raise
+        clamped = True
+    graph, entry = gi.get_graph()
+    if gi is not idx:
+        idx.set_graph(graph, entry)
+        del gi
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    log(f"fit+encode {t_enc:.2f}s build {t_build:.2f}s")
+    base = lv.Index(dev.index, metric=lv.METRIC_L2).encode_fp32(X).set_graph(graph, entry)
+    truth = ground_truth(X, Q, 10, l2=True)
+    truth_ip = ground_truth(X, Q, 10)
+    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
+    res = {"mean_degree": float((graph >= 0).sum(1).float().mean()),
+           "ip_top10_overlap": recall_at(truth_ip, truth, 10)}
+    for arm, fn in (("leanvec", lambda L: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=proj)),
+                    ("fp32", lambda L: base.search(Q, None, k=10, L=L, width=args.width))):
+        L, trace = calibrate(lambda L: fn(L)[0], truth, 10)
+        a = {"L_for_0.90": L, "recall_trace": trace[-3:]}
+        if L:
+            nst = max(5, args.steps // 5)
+            ms, _ = time_steps(lambda ev: fn(L), nst, 3)
+            a["qps"] = args.m * nst / (ms / 1e3)
+        res[arm] = a
+        log(f"{arm}: {a}")
+    out = {"metric": "QPS at 10-recall@10 = 0.90 under the Euclidean distance, LeanVec vs full-D FP32 graph search",
+           "workload": f"l2-{args.n // 1000}k-{args.D} (gist-960-1M shape): anisotropic Gaussian mixture "
+                       f"({args.components} components, i^-1 spectrum), not normalised; {args.m} ID queries; "
+                       f"LeanVec-ID d={args.d}, LVQ-8 primary + {'FP16' if args.secondary == 'fp16' else 'LVQ-8'} secondary; graph R={args.R}, "
+                       f"L_build={args.L_build}, alpha={args.alpha} (rule {args.rule}), batch {args.batch}, built in an L2 index on "
+                       f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L",
+           "build_seconds": t_build, "encode_seconds": t_enc, "reverse_pool_clamped": clamped, "results": res,
+           "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def bench_dsweep(args, dev):
     """Target-d selection on the id-1M-768 workload: one graph (the id workload's, see --graph), then
     for each primary dimension d the LeanVec-ID projection of that size, its primaries and
@@ -618,16 +695,20 @@ def main():
     ap.add_argument("--components", type=int, default=1000)
     ap.add_argument("--R", type=int, default=64)
     ap.add_argument("--L_build", type=int, default=128)
-    ap.add_argument("--alpha", type=float, default=1.02)
+    ap.add_argument("--alpha", type=float, default=None,
+                    help="RobustPrune alpha (default 1.02; 1.2 for the l2 workload)")
     ap.add_argument("--secondary", default="lvq8", choices=["lvq8", "fp16"],
                     help="id workload: LVQ-8 secondaries (the configured encoding) or FP16 ones (the paper's "
                          "default in its experiments)")
     ap.add_argument("--graph", default="full", choices=["full", "primary"],
                     help="id workload: build the shared graph on LVQ-8 codes of the unreduced vectors (full, the "
                          "paper's setting for its search comparisons) or on the d-dim primaries")
-    ap.add_argument("--rule", type=int, default=1,
-                    help="RobustPrune rule: 0 alpha-scaled similarity, 1 Vamana's L2 rule on unit-norm vectors")
-    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--rule", type=int, default=None,
+                    help="RobustPrune rule: 0 alpha-scaled similarity, 1 Vamana's L2 rule on unit-norm vectors "
+                         "(default 1; 0 for the l2 workload, whose build scores are negative squared distances)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="build batch (default 65536; 16384 for the l2 workload, whose 992-byte records leave "
+                         "room for a smaller reverse-edge pool per target)")
     ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -635,20 +716,31 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
-    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy"],
+    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy",
+                                                      "l2"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
                          "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
                          "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph; "
-                         "buildstudy: graph build on primaries vs on full-D LVQ-8 codes")
+                         "buildstudy: graph build on primaries vs on full-D LVQ-8 codes; "
+                         "l2: Euclidean 1M x 960 (gist-960-1M shape), LeanVec vs FP32 at recall 0.90")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
     sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
              "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
-             "buildstudy": (1_000_000, 10_000)}[args.workload]
+             "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000)}[args.workload]
     args.n = args.n or sizes[0]
     args.m = args.m or sizes[1]
+    l2 = args.workload == "l2"
+    if args.alpha is None:
+        args.alpha = 1.2 if l2 else 1.02
+    if args.rule is None:
+        args.rule = 0 if l2 else 1
+    if args.batch is None:
+        args.batch = 16384 if l2 else 65536
+    if l2 and "--D" not in sys.argv:
+        args.D = 960
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -672,6 +764,9 @@ def main():
         return
     if args.workload == "buildstudy":
         bench_buildstudy(args, dev)
+        return
+    if args.workload == "l2":
+        bench_l2(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "

@@ -5,7 +5,8 @@ t2i/laion/wit/rqa (out-of-distribution queries); none of those files exist here,
 so every input is drawn from a seeded Gaussian mixture with the same n, D,
 similarity (inner product on unit-norm vectors) and the ID/OOD query structure.
 
-This module only draws random numbers and unit-normalises them. It holds none
+This module only draws random numbers and unit-normalises them (or, for the
+Euclidean workloads, leaves the mixture draws raw). It holds none
 of the method's arithmetic (no projection, quantisation, search or fitting) and
 is the one module that both the CUDA path's tests/bench and the CPU oracle
 consume.
@@ -83,9 +84,10 @@ class Mixture:
         return out
 
 
-    def sample_torch(self, n: int, seed: int, device, chunk: int = 131072):
+    def sample_torch(self, n: int, seed: int, device, chunk: int = 131072, normalize: bool = True):
         """Same recipe drawn with torch's generator on `device` (for the million-scale
-        workloads; deterministic for a given device type and torch version)."""
+        workloads; deterministic for a given device type and torch version).  normalize=False
+        keeps the raw mixture draws (the Euclidean workloads)."""
         import torch
         g = torch.Generator(device=device)
         g.manual_seed(int(seed))
@@ -101,7 +103,7 @@ class Mixture:
             if basis is not None:
                 z = (z * sq) @ basis
             x = means[comp] + self.sigma * z
-            out[s:e] = x / x.norm(dim=1, keepdim=True).clamp_min(1e-30)
+            out[s:e] = x / x.norm(dim=1, keepdim=True).clamp_min(1e-30) if normalize else x
         return out
 
 
@@ -180,19 +182,20 @@ def workload_ood(n: int = 1_000_000, m: int = 10_000, D: int = 512, components: 
 
 
 def make_workload_torch(kind: str, n: int, m: int, D: int, components: int, cfg: int, device,
-                        sigma: float = 0.3, ood: bool = False, m_learn: int | None = None):
-    """make_workload drawn on a CUDA device (float32 tensors X, Q, Q_learn)."""
+                        sigma: float = 0.3, ood: bool = False, m_learn: int | None = None, normalize: bool = True):
+    """make_workload drawn on a CUDA device (float32 tensors X, Q, Q_learn); normalize=False for the
+    Euclidean workloads (raw mixture draws)."""
     import torch
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
         mix = (isotropic_mixture(D, components, sigma, SEED_DATABASE + cfg) if kind == "isotropic"
                else anisotropic_mixture(D, components, sigma, SEED_DATABASE + cfg))
-        X = mix.sample_torch(n, SEED_DATABASE + cfg + 1, device)
+        X = mix.sample_torch(n, SEED_DATABASE + cfg + 1, device, normalize=normalize)
         qmix = ood_query_mixture(mix, SEED_TEST_QUERIES + cfg + 7) if ood else mix
-        Q = qmix.sample_torch(m, SEED_TEST_QUERIES + cfg, device)
+        Q = qmix.sample_torch(m, SEED_TEST_QUERIES + cfg, device, normalize=normalize)
         ml = m if m_learn is None else m_learn
-        Ql = qmix.sample_torch(ml, SEED_LEARN_QUERIES + cfg, device)
+        Ql = qmix.sample_torch(ml, SEED_LEARN_QUERIES + cfg, device, normalize=normalize)
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     return X, Q, Ql
