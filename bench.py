@@ -643,6 +643,118 @@ def bench_l2(args, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_kernels(args, dev):
+    """The offline and auxiliary kernels of the path, each timed alone through its C-ABI call
+    (CUDA events on the launching stream, warm-up first) and set against its roofline:
+    second moments and projections (tcgen05 GEMMs), LVQ encode and column mean (HBM), FP64
+    Jacobi eigh, LeanVec-ID / -OOD fits, the pair loss forward + backward (CUDA-core FP32)."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    hbm, hbm_src = peaks()
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(pk.get("bf16_tflops", 1900.0))
+    src = "measured" if "bf16_tflops" in pk else "fallback"
+    # CUDA-core FP32 peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (nominal; nothing measures it here)
+    fp32_cc = 152 * 128 * 2 * 2.07e9 / 1e12
+
+    def timed(fn, reps):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3  # seconds per call
+
+    res = {}
+
+    def tensor_row(name, flops, t, peak, unit_peak_src):
+        res[name] = {"seconds": t, "bound": "tensor", "achieved_tflops": flops / t / 1e12, "peak_tflops": peak,
+                     "frac": flops / t / 1e12 / peak, "peak_source": unit_peak_src}
+        log(name, res[name])
+
+    def hbm_row(name, nbytes, t):
+        res[name] = {"seconds": t, "bound": "hbm", "achieved_gbs": nbytes / t / 1e9, "peak_gbs": hbm,
+                     "frac": nbytes / t / 1e9 / hbm, "algorithmic_bytes": nbytes, "peak_source": hbm_src}
+        log(name, res[name])
+
+    n, D, d = args.n, args.D, args.d
+    X, Q, Ql = workloads.make_workload_torch("anisotropic", n, args.m, D, args.components, cfg=2, device=dev)
+    torch.cuda.synchronize()
+    # a13: second moments K = sum x x^T (bf16 operands, tcgen05, FP32 accumulation)
+    for ns in (100_000, n):
+        Xs = X[:ns]
+        t = timed(lambda: lv.leanvec_second_moment(Xs, precision=lv.PREC_BF16), 5)
+        tensor_row(f"second_moment_bf16_{ns // 1000}k_x_{D}", 2.0 * ns * D * D, t, bf16, src)
+    t = timed(lambda: lv.leanvec_second_moment(X[:100_000], precision=lv.PREC_FP32), 3)
+    res[f"second_moment_fp32_100k_x_{D}"] = {"seconds": t, "tflops": 2.0 * 100_000 * D * D / t / 1e12,
+                                             "bound": "fp32 CUDA cores", "peak_tflops_nominal": fp32_cc}
+    log("second_moment_fp32", res[f"second_moment_fp32_100k_x_{D}"])
+    # a1 / a11: projections x -> B x of the database (and q -> A q of a search batch)
+    A = lv.leanvec_fit_id(X[:100_000], d)
+    ldy = (d + 15) // 16 * 16
+    for prec, tag in ((lv.PREC_BF16, "bf16"), (lv.PREC_FP8, "fp8"), (lv.PREC_FP32, "fp32")):
+        t = timed(lambda: lv.leanvec_project(X, A, ldy=ldy, precision=prec), 5)
+        # algorithmic bytes: read X (float32), write Y (float32); the GEMM itself is 2 n D d flops
+        hbm_row(f"project_{tag}_{n // 1000}k_{D}_to_{d}", 4.0 * n * D + 4.0 * n * ldy, t)
+        res[f"project_{tag}_{n // 1000}k_{D}_to_{d}"]["tflops"] = 2.0 * n * D * d / t / 1e12
+    for prec, tag in ((lv.PREC_BF16, "bf16"), (lv.PREC_FP8, "fp8")):
+        t = timed(lambda: lv.leanvec_project(Q, A, ldy=ldy, precision=prec), 20)
+        hbm_row(f"project_{tag}_queries_{Q.shape[0] // 1000}k_{D}_to_{d}", 4.0 * Q.shape[0] * (D + ldy), t)
+    # a11: column mean and LVQ-8 encode of the full-D vectors (secondaries)
+    mu = lv.leanvec_column_mean(X)
+    t = timed(lambda: lv.leanvec_column_mean(X), 5)
+    hbm_row(f"column_mean_{n // 1000}k_{D}", 4.0 * n * D, t)
+    stride = lv.leanvec_record_stride(D, 8)
+    t = timed(lambda: lv.leanvec_lvq_encode(X, mu, 8), 5)
+    hbm_row(f"lvq8_encode_{n // 1000}k_{D}", 4.0 * n * D + float(n) * stride, t)
+    Y = lv.leanvec_project(X, A, ldy=d, precision=lv.PREC_FP32)
+    muy = lv.leanvec_column_mean(Y)
+    t = timed(lambda: lv.leanvec_lvq_encode(Y, muy, 8), 5)
+    hbm_row(f"lvq8_encode_{n // 1000}k_{d}", 4.0 * n * d + float(n) * lv.leanvec_record_stride(d, 8), t)
+    del Y
+    # a14: FP64 Jacobi eigh of a D x D second moment; LeanVec-ID fit end to end
+    K = lv.leanvec_second_moment(X[:100_000], precision=lv.PREC_FP32).double()
+    t = timed(lambda: lv.leanvec_eigh(K), 1)
+    res[f"eigh_fp64_{D}"] = {"seconds": t}
+    log("eigh", res[f"eigh_fp64_{D}"])
+    t = timed(lambda: lv.leanvec_fit_id(X[:100_000], d, precision=lv.PREC_BF16), 1)
+    res[f"fit_id_bf16_100k_{D}_to_{d}"] = {"seconds": t}
+    log("fit_id", res[f"fit_id_bf16_100k_{D}_to_{d}"])
+    # a14 / a15 on the OOD shape: 100k database samples, 10k learning queries, D = 512, d = 128
+    Xo, _, Qo = workloads.make_workload_torch("anisotropic", 100_000, 1000, 512, args.components, cfg=3, device=dev,
+                                              ood=True, m_learn=10_000)
+    for meth, tag in ((lv.FIT_FW, "fw"), (lv.FIT_ES, "es")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, rep = lv.leanvec_fit_ood(Xo, Qo, 128, method=meth)
+        torch.cuda.synchronize()
+        res[f"fit_ood_{tag}_100k_10k_512_to_128"] = {"seconds": time.perf_counter() - t0,
+                                                      "iterations": rep["iterations"]}
+        log(tag, res[f"fit_ood_{tag}_100k_10k_512_to_128"])
+    Ai = lv.leanvec_fit_id(Xo, 128)
+    pair_flops = 2.0 * Qo.shape[0] * Xo.shape[0] * (512 + 128)  # q^T x and (A q)^T (B x) per pair
+    t = timed(lambda: lv.leanvec_ood_loss_fwd(Ai, Ai, Qo, Xo), 2)
+    res["pair_loss_fwd_10k_x_100k_512_128"] = {"seconds": t, "tflops": pair_flops / t / 1e12,
+                                               "bound": "fp32 CUDA cores", "peak_tflops_nominal": fp32_cc,
+                                               "frac_nominal": pair_flops / t / 1e12 / fp32_cc}
+    log("loss fwd", res["pair_loss_fwd_10k_x_100k_512_128"])
+    t = timed(lambda: lv.leanvec_ood_loss_bwd(Ai, Ai, Qo, Xo), 2)
+    res["pair_loss_bwd_10k_x_100k_512_128"] = {"seconds": t}
+    log("loss bwd", res["pair_loss_bwd_10k_x_100k_512_128"])
+    out = {"metric": "offline / auxiliary kernels through the C ABI: seconds per call and the fraction of each "
+                     "kernel's roofline (tensor: bf16 peak " + src + ", fp8 = 2x bf16; hbm: copy peak " + hbm_src + ")",
+           "workload": f"id-{n // 1000}k-{D} (anisotropic mixture, unit norm), d = {d}; OOD fits on 100k x 512 "
+                       f"database samples and 10k learning queries, d = 128",
+           "results": res, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def bench_dsweep(args, dev):
     """Target-d selection on the id-1M-768 workload: one graph (the id workload's, see --graph), then
     for each primary dimension d the LeanVec-ID projection of that size, its primaries and
@@ -717,19 +829,21 @@ def main():
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
     ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy",
-                                                      "l2"],
+                                                      "l2", "kernels"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
                          "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
                          "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph; "
                          "buildstudy: graph build on primaries vs on full-D LVQ-8 codes; "
-                         "l2: Euclidean 1M x 960 (gist-960-1M shape), LeanVec vs FP32 at recall 0.90")
+                         "l2: Euclidean 1M x 960 (gist-960-1M shape), LeanVec vs FP32 at recall 0.90; "
+                         "kernels: the offline / auxiliary kernels alone against their rooflines")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
     sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
              "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
-             "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000)}[args.workload]
+             "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000),
+             "kernels": (1_000_000, 10_000)}[args.workload]
     args.n = args.n or sizes[0]
     args.m = args.m or sizes[1]
     l2 = args.workload == "l2"
@@ -767,6 +881,9 @@ def main():
         return
     if args.workload == "l2":
         bench_l2(args, dev)
+        return
+    if args.workload == "kernels":
+        bench_kernels(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "

@@ -51,6 +51,16 @@ typedef enum {
 /* Message for the last failing call on this thread ("" if none). */
 const char *leanvec_last_error(void);
 
+/* Scratch memory.  The temporaries of the offline calls (operand copies of the
+ * tensor-core GEMMs, split-K partials, eigen-solver and fit buffers) come from one
+ * stream-ordered memory pool per device owned by the library, which keeps freed
+ * blocks for reuse instead of returning them to the driver.  This call returns the
+ * unused blocks of `device`'s pool to the driver (blocks freed by work still in
+ * flight are returned once a later call finds them idle; synchronise first to
+ * release everything).  LV_ERR_ARG for a negative ordinal; LV_OK when the device
+ * has no pool yet. */
+int leanvec_trim_scratch(int device);
+
 /* ------------------------------------------------------------------------ */
 /* Record layout                                                            */
 /* ------------------------------------------------------------------------ */

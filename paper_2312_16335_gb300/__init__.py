@@ -18,7 +18,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "SearchGraph", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "SearchGraph", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
@@ -43,6 +43,13 @@ def _f32(t: torch.Tensor) -> torch.Tensor:
     if t.dtype != torch.float32:
         raise TypeError("expected float32")
     return t.contiguous()
+
+
+def leanvec_trim_scratch(device: int | torch.device | None = None) -> None:
+    """Return the unused blocks of the library's scratch pool on `device` to the driver."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device("cuda", device) \
+        if isinstance(device, int) else device
+    check(lib().leanvec_trim_scratch(dev.index))
 
 
 def leanvec_record_stride(dim: int, bits: int) -> int:

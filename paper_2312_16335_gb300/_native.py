@@ -46,6 +46,7 @@ class LVFitReport(ctypes.Structure):
 # (name, restype, argtypes) for every symbol of include/leanvec.h
 SIGNATURES = {
     "leanvec_last_error": (ctypes.c_char_p, []),
+    "leanvec_trim_scratch": (ctypes.c_int, [ctypes.c_int]),
     "leanvec_record_stride": (c_i64, [c_i32, c_i32]),
     "leanvec_column_mean": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp]),
     "leanvec_lvq_encode": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp, c_vp]),

@@ -49,6 +49,7 @@ int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float 
                  size_t *ws_bytes, int *status, cudaStream_t st);
 int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                 size_t *ws_bytes, int *status, cudaStream_t st);
+size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d);
 // tensor-core projection with bf16 or e4m3 (per-row scaled) operands
 static int project_tc(int prec, const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                       size_t *ws_bytes, int *status, cudaStream_t st) {
@@ -142,20 +143,20 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
     if (n == 0) return LV_OK;
     cudaStream_t st = (cudaStream_t)stream;
     void *ws = nullptr;
-    size_t wsb = 0;
+    size_t wsb = project_tc_ws_bytes(precision, n, D, d);
     int *status = nullptr;
     int h_status = 0;
-    int rc = LV_OK;
-    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return fail(LV_ERR_OOM, "project: allocation failed");
-    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "project: memset failed");
+    int rc = tmp_alloc((void **)&status, sizeof(int), st);
+    if (rc == LV_OK) rc = tmp_alloc(&ws, wsb, st);
+    if (rc == LV_OK && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+        rc = fail(LV_ERR_CUDA, "project: memset failed");
     if (rc == LV_OK) rc = project_tc(precision, X, n, D, P, d, Y, ldy, &ws, &wsb, status, st);
     if (rc == LV_OK && cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = fail(LV_ERR_CUDA, "project: status copy failed");
     if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "project: sync failed");
     if (rc == LV_OK && h_status) rc = fail(LV_ERR_TIMEOUT, "project: a tensor-core pipeline wait timed out");
-    cudaStreamSynchronize(st);
-    cudaFree(ws);
-    cudaFree(status);
+    tmp_free(ws, st);
+    tmp_free(status, st);
     return rc;
 }
 
@@ -276,7 +277,7 @@ static int set_primary_impl(lv_index *idx, const float *Y, int64_t n, int d, con
     int rc = LV_OK;
     drop_primary(idx);
     if (idx->n != n) drop_secondary(idx);
-    LV_TRYC(cudaMalloc(&mu2d, sizeof(float)));
+    LV_TRY(tmp_alloc((void **)&mu2d, sizeof(float), st));
     LV_TRYC(cudaMalloc(&idx->prim, (size_t)n * pg.stride));
     LV_TRYC(cudaMalloc(&idx->pmean, sizeof(float) * d));
     if (mean)
@@ -295,7 +296,7 @@ static int set_primary_impl(lv_index *idx, const float *Y, int64_t n, int d, con
     idx->pbits = bits;
     idx->pg = pg;
 cleanup:
-    cudaFree(mu2d);
+    tmp_free(mu2d, st);
     if (rc != LV_OK) {
         drop_primary(idx);
         drop_secondary(idx);
@@ -370,7 +371,7 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     float *Y = nullptr;
     int rc = LV_OK;
     index_free_stores(idx);
-    LV_TRYC(cudaMalloc(&Y, sizeof(float) * (size_t)n * d));
+    LV_TRY(tmp_alloc((void **)&Y, sizeof(float) * (size_t)n * d, st));
     if (projection_precision != LV_PREC_FP32) {
         LV_TRY(project_tc(projection_precision, X, n, D, B, d, Y, d, &idx->bws, &idx->bws_bytes, idx->status, st));
     } else {
@@ -383,7 +384,7 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
         LV_TRYC(cudaStreamSynchronize(st));
     }
 cleanup:
-    cudaFree(Y);
+    tmp_free(Y, st);
     if (rc != LV_OK) index_free_stores(idx);
     return rc;
 }
@@ -433,12 +434,13 @@ int leanvec_set_graph(lv_index *idx, const int32_t *adj, int R, int32_t entry, l
     if (rc != LV_OK) return rc;
     if (entry < 0) {
         int32_t *e = nullptr;
-        LV_CUDA(cudaMalloc(&e, sizeof(int32_t)));
+        rc = tmp_alloc((void **)&e, sizeof(int32_t), st);
+        if (rc != LV_OK) return rc;
         rc = launch_entry_argmax(idx->prim, idx->n, idx->pg.stride, idx->pg.code_bytes, idx->metric, e, st);
         if (rc == LV_OK && cudaMemcpyAsync(&entry, e, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             rc = fail(LV_ERR_CUDA, "set_graph: entry copy failed");
         if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "set_graph: sync failed");
-        cudaFree(e);
+        tmp_free(e, st);
         if (rc != LV_OK) return rc;
     }
     idx->R = R;

@@ -25,6 +25,10 @@ void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
+// scratch memory from the library's stream-ordered pool (pool.cu)
+int tmp_alloc(void **p, size_t bytes, cudaStream_t st);
+void tmp_free(void *p, cudaStream_t st);
+
 #define LV_CUDA(call)                                              \
     do {                                                           \
         cudaError_t _e = (call);                                   \

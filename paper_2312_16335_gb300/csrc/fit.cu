@@ -136,6 +136,57 @@ __global__ void jacobi_cols_kernel(double *__restrict__ A, double *__restrict__ 
     vr[q] = k.y * a + k.x * b;
 }
 
+// One whole round in one kernel: block i owns the pair (p, q) = rr_pair(r, i) and writes rows
+// p and q of J^T A J (its own rotation mixes the two rows, then every pair's rotation mixes
+// the columns of both rows) and rows p and q of V J.  The pairs partition the indices, so
+// the blocks touch disjoint rows; the arithmetic is the row pass followed by the column pass
+// of the two kernels above, with coalesced row accesses only.
+__global__ void __launch_bounds__(256) jacobi_round_kernel(double *__restrict__ A, double *__restrict__ V, int Dp,
+                                                           int r, const double2 *__restrict__ cs) {
+    extern __shared__ double rows_sm[];
+    double *rp = rows_sm, *rq = rows_sm + Dp, *vp = rows_sm + 2 * Dp, *vq = rows_sm + 3 * Dp;
+    int p, q;
+    rr_pair(r, blockIdx.x, Dp, p, q);
+    const double2 k = cs[blockIdx.x];
+    double *Ap = A + (int64_t)p * Dp, *Aq = A + (int64_t)q * Dp;
+    double *Vp = V + (int64_t)p * Dp, *Vq = V + (int64_t)q * Dp;
+    for (int j = threadIdx.x; j < Dp; j += blockDim.x) {
+        const double a = Ap[j], b = Aq[j];
+        rp[j] = k.x * a - k.y * b;
+        rq[j] = k.y * a + k.x * b;
+        vp[j] = Vp[j];
+        vq[j] = Vq[j];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Dp / 2; t += blockDim.x) {
+        int pp, qq;
+        rr_pair(r, t, Dp, pp, qq);
+        const double2 kk = cs[t];
+        double a = rp[pp], b = rp[qq];
+        rp[pp] = kk.x * a - kk.y * b;
+        rp[qq] = kk.y * a + kk.x * b;
+        a = rq[pp];
+        b = rq[qq];
+        rq[pp] = kk.x * a - kk.y * b;
+        rq[qq] = kk.y * a + kk.x * b;
+        a = vp[pp];
+        b = vp[qq];
+        vp[pp] = kk.x * a - kk.y * b;
+        vp[qq] = kk.y * a + kk.x * b;
+        a = vq[pp];
+        b = vq[qq];
+        vq[pp] = kk.x * a - kk.y * b;
+        vq[qq] = kk.y * a + kk.x * b;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < Dp; j += blockDim.x) {
+        Ap[j] = rp[j];
+        Aq[j] = rq[j];
+        Vp[j] = vp[j];
+        Vq[j] = vq[j];
+    }
+}
+
 // out[0] = sum of squared off-diagonal entries, out[1] = sum of squared diagonal entries
 __global__ void jacobi_offnorm_kernel(const double *__restrict__ A, int Dp, double *__restrict__ out) {
     __shared__ double so[256], sd[256];
@@ -238,13 +289,47 @@ int eigh_impl(const double *K, int D, int nout, double *evals, double *evecs, cu
     std::vector<int> order(Dp);
     double host_acc[2];
     int sweep = 0;
-    if (cudaMalloc(&A, sizeof(double) * Dp * Dp) != cudaSuccess || cudaMalloc(&V, sizeof(double) * Dp * Dp) != cudaSuccess ||
-        cudaMalloc(&acc, 2 * sizeof(double)) != cudaSuccess || cudaMalloc(&cs, sizeof(double2) * Dp / 2) != cudaSuccess ||
-        cudaMalloc(&idx_d, sizeof(int) * Dp) != cudaSuccess || cudaMalloc(&dg, sizeof(double) * Dp) != cudaSuccess) {
+    bool fused = (size_t)Dp * 32 <= 200 * 1024;  // four rows of Dp doubles in shared memory
+    cudaGraphExec_t sweep_exec = nullptr;
+    auto launch_sweep = [&](cudaStream_t s) {
+        for (int r = 0; r < Dp - 1; ++r) {
+            jacobi_rot_kernel<<<(Dp / 2 + 127) / 128, 128, 0, s>>>(A, Dp, r, cs);
+            if (fused) {
+                jacobi_round_kernel<<<Dp / 2, 256, (size_t)Dp * 32, s>>>(A, V, Dp, r, cs);
+            } else {
+                jacobi_rows_kernel<<<dim3((Dp + 127) / 128, Dp / 2), 128, 0, s>>>(A, Dp, r, cs);
+                jacobi_cols_kernel<<<dim3((Dp + 127) / 128, Dp / 2), 128, 0, s>>>(A, V, Dp, r, cs);
+            }
+        }
+    };
+    if (tmp_alloc((void **)&A, sizeof(double) * Dp * Dp, st) || tmp_alloc((void **)&V, sizeof(double) * Dp * Dp, st) ||
+        tmp_alloc((void **)&acc, 2 * sizeof(double), st) || tmp_alloc((void **)&cs, sizeof(double2) * Dp / 2, st) ||
+        tmp_alloc((void **)&idx_d, sizeof(int) * Dp, st) || tmp_alloc((void **)&dg, sizeof(double) * Dp, st)) {
         rc = fail(LV_ERR_OOM, "eigh: allocation failed");
         goto done;
     }
     pad_copy_kernel<<<(unsigned)(((int64_t)Dp * Dp + 255) / 256), 256, 0, st>>>(K, D, A, V, Dp);
+    // one sweep = Dp - 1 rounds of (rotation angles, fused round); captured once into a CUDA
+    // graph (launched per sweep), else launched directly
+    if (fused && Dp * 32 > 48 * 1024 &&
+        cudaFuncSetAttribute(jacobi_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Dp * 32) != cudaSuccess) {
+        cudaGetLastError();
+        fused = false;
+    }
+    {
+        cudaStream_t cap = nullptr;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            launch_sweep(cap);
+            if (cudaStreamEndCapture(cap, &graph) != cudaSuccess ||
+                cudaGraphInstantiate(&sweep_exec, graph, 0) != cudaSuccess)
+                sweep_exec = nullptr;
+        }
+        cudaGetLastError();  // a failed capture falls back to direct launches
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    }
     for (sweep = 0; sweep < 40; ++sweep) {
         cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
         jacobi_offnorm_kernel<<<128, 256, 0, st>>>(A, Dp, acc);
@@ -255,10 +340,13 @@ int eigh_impl(const double *K, int D, int nout, double *evals, double *evecs, cu
         }
         const double tot = host_acc[0] + host_acc[1];
         if (!(host_acc[0] > 1e-28 * tot) || tot == 0.0) break;
-        for (int r = 0; r < Dp - 1; ++r) {
-            jacobi_rot_kernel<<<(Dp / 2 + 127) / 128, 128, 0, st>>>(A, Dp, r, cs);
-            jacobi_rows_kernel<<<dim3((Dp + 127) / 128, Dp / 2), 128, 0, st>>>(A, Dp, r, cs);
-            jacobi_cols_kernel<<<dim3((Dp + 127) / 128, Dp / 2), 128, 0, st>>>(A, V, Dp, r, cs);
+        if (sweep_exec) {
+            if (cudaGraphLaunch(sweep_exec, st) != cudaSuccess) {
+                rc = fail(LV_ERR_CUDA, "eigh: sweep graph launch failed");
+                goto done;
+            }
+        } else {
+            launch_sweep(st);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -284,13 +372,17 @@ int eigh_impl(const double *K, int D, int nout, double *evals, double *evecs, cu
         }
     }
 done:
+    if (sweep_exec) {
+        cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(sweep_exec);
+    }
     if (sweeps_out) *sweeps_out = sweep;
-    cudaFree(A);
-    cudaFree(V);
-    cudaFree(acc);
-    cudaFree(cs);
-    cudaFree(idx_d);
-    cudaFree(dg);
+    tmp_free(A, st);
+    tmp_free(V, st);
+    tmp_free(acc, st);
+    tmp_free(cs, st);
+    tmp_free(idx_d, st);
+    tmp_free(dg, st);
     return rc;
 }
 
@@ -320,14 +412,14 @@ int leanvec_second_moment(const float *X, int64_t n, int D, float *K, int precis
     if (precision != LV_PREC_BF16) return fail(LV_ERR_ARG, "second_moment: precision must be LV_PREC_FP32 or LV_PREC_BF16");
     cudaStream_t st = (cudaStream_t)stream;
     int *status = nullptr, h = 0;
-    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return fail(LV_ERR_OOM, "second_moment: allocation failed");
+    if (tmp_alloc((void **)&status, sizeof(int), st)) return fail(LV_ERR_OOM, "second_moment: allocation failed");
     int rc = cudaMemsetAsync(status, 0, sizeof(int), st) == cudaSuccess ? LV_OK : fail(LV_ERR_CUDA, "memset failed");
     if (rc == LV_OK) rc = second_moment_bf16(X, n, D, K, status, st);
     if (rc == LV_OK && cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = fail(LV_ERR_CUDA, "second_moment: status copy failed");
     if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "second_moment: sync failed");
     if (rc == LV_OK && h) rc = fail(LV_ERR_TIMEOUT, "second_moment: a tensor-core pipeline wait timed out");
-    cudaFree(status);
+    tmp_free(status, st);
     return rc;
 }
 
@@ -344,8 +436,8 @@ int leanvec_fit_id(const float *X, int64_t n, int D, int d, float *A_out, float 
     float *K = nullptr;
     double *K64 = nullptr, *P = nullptr;
     int rc = LV_OK;
-    if (cudaMalloc(&K, sizeof(float) * D * D) != cudaSuccess || cudaMalloc(&K64, sizeof(double) * D * D) != cudaSuccess ||
-        cudaMalloc(&P, sizeof(double) * (size_t)d * D) != cudaSuccess) {
+    if (tmp_alloc((void **)&K, sizeof(float) * D * D, st) || tmp_alloc((void **)&K64, sizeof(double) * D * D, st) ||
+        tmp_alloc((void **)&P, sizeof(double) * (size_t)d * D, st)) {
         rc = fail(LV_ERR_OOM, "fit_id: allocation failed");
     }
     if (rc == LV_OK) rc = leanvec_second_moment(X, n, D, K, precision, stream);
@@ -356,9 +448,9 @@ int leanvec_fit_id(const float *X, int64_t n, int D, int d, float *A_out, float 
         if (cudaMemcpyAsync(B_out, A_out, sizeof(float) * (size_t)d * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             rc = fail(LV_ERR_CUDA, "fit_id: copy failed");
     if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "fit_id: sync failed");
-    cudaFree(K);
-    cudaFree(K64);
-    cudaFree(P);
+    tmp_free(K, st);
+    tmp_free(K64, st);
+    tmp_free(P, st);
     return rc;
 }
 

@@ -399,6 +399,17 @@ int launch_cast_transpose_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *
 
 int ensure_ws(void **p, size_t *have, size_t want);
 
+// workspace bytes of project_bf16 (prec LV_PREC_BF16) or project_fp8 (LV_PREC_FP8)
+size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d) {
+    if (prec == LV_PREC_FP8) {
+        const int ldx = (int)round_up(D, 16);
+        return round_up((int64_t)n * ldx, 256) + round_up((int64_t)d * ldx, 256) + round_up(4 * n, 256) +
+               round_up(4 * (int64_t)d, 256);
+    }
+    const int ldx = (int)round_up(D, 8);
+    return round_up((int64_t)n * ldx * 2, 256) + round_up((int64_t)d * ldx * 2, 256);
+}
+
 // Y (n x ldy) = X P^T with bf16 operands on the tensor cores; columns d..ldy-1 zeroed.
 // The bf16 copies of X and P live in the caller's workspace (*ws, grown as needed).
 int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
@@ -444,13 +455,12 @@ int second_moment_bf16(const float *X, int64_t n, int D, float *K, int *status, 
     __nv_bfloat16 *Xt = nullptr;
     float *work = nullptr;
     int rc = LV_OK;
-    if (cudaMallocAsync((void **)&Xt, (size_t)D * ldt * 2, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&work, sizeof(float) * (size_t)splits * D * D, st) != cudaSuccess)
+    if (tmp_alloc((void **)&Xt, (size_t)D * ldt * 2, st) || tmp_alloc((void **)&work, sizeof(float) * (size_t)splits * D * D, st))
         rc = fail(LV_ERR_OOM, "second_moment: allocation failed");
     if (rc == LV_OK) rc = launch_cast_transpose_bf16(X, n, D, Xt, ldt, st);
     if (rc == LV_OK) rc = gemm_bf16_tc(Xt, D, ldt, Xt, D, ldt, n, K, D, splits, work, status, st);
-    if (Xt) cudaFreeAsync(Xt, st);
-    if (work) cudaFreeAsync(work, st);
+    tmp_free(Xt, st);
+    tmp_free(work, st);
     return rc;
 }
 

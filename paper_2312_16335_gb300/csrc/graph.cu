@@ -446,13 +446,17 @@ int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_
     const int nb = 256;
     float *bg = nullptr;
     int *bi = nullptr;
-    LV_CUDA(cudaMallocAsync((void **)&bg, sizeof(float) * nb, st));
-    LV_CUDA(cudaMallocAsync((void **)&bi, sizeof(int) * nb, st));
+    int rc = tmp_alloc((void **)&bg, sizeof(float) * nb, st);
+    if (rc == LV_OK) rc = tmp_alloc((void **)&bi, sizeof(int) * nb, st);
+    if (rc) {
+        tmp_free(bg, st);
+        return rc;
+    }
     entry_partial_kernel<<<nb, 256, 0, st>>>(rec, n, stride, code_bytes, metric, bg, bi);
     entry_final_kernel<<<1, 256, 0, st>>>(bg, bi, nb, out);
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(bg, st);
-    cudaFreeAsync(bi, st);
+    tmp_free(bg, st);
+    tmp_free(bi, st);
     if (e != cudaSuccess) return cuda_fail(e, "entry kernels");
     return LV_OK;
 }

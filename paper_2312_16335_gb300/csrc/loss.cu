@@ -190,24 +190,24 @@ struct PairWork {
 
 static int pair_prepare(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
                         int d, PairWork &w, bool grads, cudaStream_t st) {
-    if (cudaMalloc(&w.Qp, sizeof(float) * (size_t)m * d) != cudaSuccess ||
-        cudaMalloc(&w.Xp, sizeof(float) * (size_t)n * d) != cudaSuccess ||
-        cudaMalloc(&w.part, sizeof(double) * (size_t)((m + PT - 1) / PT)) != cudaSuccess)
+    if (tmp_alloc((void **)&w.Qp, sizeof(float) * (size_t)m * d, st) ||
+        tmp_alloc((void **)&w.Xp, sizeof(float) * (size_t)n * d, st) ||
+        tmp_alloc((void **)&w.part, sizeof(double) * (size_t)((m + PT - 1) / PT), st))
         return fail(LV_ERR_OOM, "ood_loss: allocation failed");
-    if (grads && (cudaMalloc(&w.U, sizeof(float) * (size_t)m * d) != cudaSuccess ||
-                  cudaMalloc(&w.V, sizeof(float) * (size_t)n * d) != cudaSuccess))
+    if (grads && (tmp_alloc((void **)&w.U, sizeof(float) * (size_t)m * d, st) ||
+                  tmp_alloc((void **)&w.V, sizeof(float) * (size_t)n * d, st)))
         return fail(LV_ERR_OOM, "ood_loss: allocation failed");
     int rc = launch_project_fp32(Q, m, D, A, d, w.Qp, d, st);
     if (rc) return rc;
     return launch_project_fp32(X, n, D, B, d, w.Xp, d, st);
 }
 
-static void pair_free(PairWork &w) {
-    cudaFree(w.Qp);
-    cudaFree(w.Xp);
-    cudaFree(w.U);
-    cudaFree(w.V);
-    cudaFree(w.part);
+static void pair_free(PairWork &w, cudaStream_t st) {
+    tmp_free(w.Qp, st);
+    tmp_free(w.Xp, st);
+    tmp_free(w.U, st);
+    tmp_free(w.V, st);
+    tmp_free(w.part, st);
 }
 
 }  // namespace lv
@@ -240,7 +240,7 @@ int leanvec_ood_loss_fwd(const float *A, const float *B, const float *Q, int64_t
         for (double v : part) s += v;  // fixed order
         *loss = s / ((double)n * (double)m);
     }
-    pair_free(w);
+    pair_free(w, st);
     return rc;
 }
 
@@ -263,7 +263,7 @@ int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t
         if (e != cudaSuccess) rc = cuda_fail(e, "ood_loss_bwd kernels");
     }
     if (rc == LV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "ood_loss_bwd: sync failed");
-    pair_free(w);
+    pair_free(w, st);
     return rc;
 }
 

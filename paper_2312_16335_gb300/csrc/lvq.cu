@@ -8,21 +8,165 @@ namespace lv {
 
 constexpr double FIX = 1048576.0;  // 2^20: fixed point of the mean in the build score
 
-// Column mean: each block owns 32 columns and sums rows in a fixed order (per-thread
-// strided partial sums reduced in a fixed tree) so the result is deterministic.
-__global__ void column_mean_kernel(const float *__restrict__ X, int64_t n, int dim,
-                                   float *__restrict__ mean) {
-    __shared__ double part[8][33];
-    int col = blockIdx.x * 32 + threadIdx.x;
-    double acc = 0.0;
-    if (col < dim)
-        for (int64_t i = threadIdx.y; i < n; i += 8) acc += (double)X[i * dim + col];
-    part[threadIdx.y][threadIdx.x] = acc;
+// Column mean in FP64, deterministic (a fixed summation order that depends on n and dim
+// only).  Stage 1: block (c, r) sums the rows of chunk r (CM_ROWS rows) for the 4 x 32
+// columns of tile c, each warp a strided subset of the rows (float4 loads along the row when
+// the rows are 16-byte aligned), the 8 warps combined in order; stage 2 adds the chunks in
+// order and rounds the mean to float32.
+constexpr int CM_ROWS = 2048, CM_COLS = 128;
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) column_sum_kernel(const float *__restrict__ X, int64_t n, int dim,
+                                                         double *__restrict__ part) {
+    __shared__ double red[8][CM_COLS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * CM_COLS + 4 * lane;
+    const int64_t r0 = (int64_t)blockIdx.y * CM_ROWS, r1 = min(n, r0 + CM_ROWS);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (VEC) {
+        if (c0 < dim)
+            for (int64_t i = r0 + warp; i < r1; i += 8) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(X + i * dim + c0));
+                a0 += (double)v.x;
+                a1 += (double)v.y;
+                a2 += (double)v.z;
+                a3 += (double)v.w;
+            }
+    } else {
+        for (int64_t i = r0 + warp; i < r1; i += 8) {
+            const float *row = X + i * dim;
+            if (c0 < dim) a0 += (double)row[c0];
+            if (c0 + 1 < dim) a1 += (double)row[c0 + 1];
+            if (c0 + 2 < dim) a2 += (double)row[c0 + 2];
+            if (c0 + 3 < dim) a3 += (double)row[c0 + 3];
+        }
+    }
+    red[warp][4 * lane] = a0;
+    red[warp][4 * lane + 1] = a1;
+    red[warp][4 * lane + 2] = a2;
+    red[warp][4 * lane + 3] = a3;
     __syncthreads();
-    if (threadIdx.y == 0 && col < dim) {
+    if (threadIdx.x < CM_COLS) {
+        const int c = blockIdx.x * CM_COLS + threadIdx.x;
         double s = 0.0;
-        for (int t = 0; t < 8; ++t) s += part[t][threadIdx.x];
-        mean[col] = (float)(s / (double)n);
+        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        if (c < dim) part[(int64_t)blockIdx.y * dim + c] = s;
+    }
+}
+
+__global__ void column_mean_final_kernel(const double *__restrict__ part, int chunks, int64_t n, int dim,
+                                         float *__restrict__ mean) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= dim) return;
+    double s = 0.0;
+    for (int r = 0; r < chunks; ++r) s += part[(int64_t)r * dim + c];
+    mean[c] = (float)(s / (double)n);
+}
+
+// LVQ encode with 16-byte loads (dim % 4 == 0, 16-byte aligned rows): one warp per vector, a
+// persistent grid; lane l holds the float4 chunks l, l + 32, .. (at most KMAX) of v - mean in
+// registers between the min/max pass and the code pass.  The fixed-point mean (mui = mean_i
+// 2^20, exact for |mean_i| < 8) and its sums are computed once per block in shared memory.
+// Same arithmetic as lvq_encode_kernel, so the records are bit-identical.
+template <int BITS, int KMAX>
+__global__ void __launch_bounds__(256) lvq_encode_vec_kernel(const float *__restrict__ V, int64_t n, int dim,
+                                                             const float *__restrict__ mean, uint8_t *__restrict__ rec,
+                                                             int64_t stride, int code_bytes) {
+    extern __shared__ uint8_t sm_raw[];
+    float *smean = reinterpret_cast<float *>(sm_raw);
+    int *smi = reinterpret_cast<int *>(smean + dim);
+    __shared__ long long s_mu;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) {
+        s_mu = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    long long pmu = 0;
+    int bad = 0;
+    for (int j = threadIdx.x; j < dim; j += blockDim.x) {
+        const float mj = mean[j];
+        if (!(fabsf(mj) < 8.0f)) bad = 1;
+        const long long mi = __double2ll_rn((double)mj * FIX);
+        smean[j] = mj;
+        smi[j] = (int)mi;  // only read when every |mean_j| < 8 (then |mi| < 2^23)
+        pmu += mi;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long *>(&s_mu), (unsigned long long)pmu);
+    if (bad) atomicOr(&s_bad, 1);
+    __syncthreads();
+    const bool mean_ok = !s_bad;
+    const long long smu = s_mu;
+    const int lane = threadIdx.x & 31;
+    const int nc = dim >> 2;  // float4 chunks per vector
+    const float levels = (float)((1 << BITS) - 1);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const float4 *v4 = reinterpret_cast<const float4 *>(V + i * dim);
+        float4 x[KMAX];
+        float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int c = lane + 32 * k;
+            if (c < nc) {
+                const float4 v = __ldg(v4 + c);
+                const float4 m = *reinterpret_cast<const float4 *>(smean + 4 * c);
+                x[k] = make_float4(__fsub_rn(v.x, m.x), __fsub_rn(v.y, m.y), __fsub_rn(v.z, m.z), __fsub_rn(v.w, m.w));
+                lo = fminf(fminf(lo, fminf(x[k].x, x[k].y)), fminf(x[k].z, x[k].w));
+                hi = fmaxf(fmaxf(hi, fmaxf(x[k].x, x[k].y)), fmaxf(x[k].z, x[k].w));
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+        }
+        const float delta = __fdiv_rn(__fsub_rn(hi, lo), levels);
+        uint8_t *r = rec + i * stride;
+        long long msum = 0;
+        int csum = 0;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int c = lane + 32 * k;
+            if (c < nc) {
+                const float xs[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+                uint32_t cw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t q = 0;
+                    if (delta > 0.0f) {
+                        float t = __fdiv_rn(__fsub_rn(xs[e], lo), delta);
+                        float f = floorf(__fadd_rn(t, 0.5f));
+                        f = fminf(fmaxf(f, 0.0f), levels);
+                        q = (uint32_t)f;
+                    }
+                    cw[e] = q;
+                    msum += (long long)(smi[4 * c + e] * (int)q);
+                    csum += (int)q;
+                }
+                if (BITS == 8)
+                    *reinterpret_cast<uint32_t *>(r + 4 * c) = cw[0] | (cw[1] << 8) | (cw[2] << 16) | (cw[3] << 24);
+                else
+                    *reinterpret_cast<uint16_t *>(r + 2 * c) =
+                        (uint16_t)(cw[0] | (cw[1] << 4) | (cw[2] << 8) | (cw[3] << 12));
+            }
+        }
+        // zero the code padding (whole 16-bit units: the code bytes end on an even offset)
+        const int used = BITS == 8 ? dim : dim / 2;
+        for (int b = used + 2 * lane; b < code_bytes; b += 64) *reinterpret_cast<uint16_t *>(r + b) = 0;
+        for (int o = 16; o; o >>= 1) {
+            msum += __shfl_xor_sync(FULL, msum, o);
+            csum += __shfl_xor_sync(FULL, csum, o);
+        }
+        if (lane == 0) {
+            const float inv = (float)(1.0 / FIX);
+            float mu1 = __fmul_rn(__ll2float_rn(smu), inv);
+            float mf = __fmul_rn(__ll2float_rn(msum), inv);
+            float G = __fadd_rn(__fmul_rn(lo, mu1), __fmul_rn(delta, mf));
+            float H = __fmul_rn(delta, __int2float_rn(csum));
+            if (!mean_ok) G = H = __int_as_float(0x7fc00000);
+            *reinterpret_cast<float4 *>(r + code_bytes) = make_float4(delta, lo, G, H);
+        }
+        for (int64_t t = code_bytes + 16 + 4 * lane; t < stride; t += 128) *reinterpret_cast<uint32_t *>(r + t) = 0u;
     }
 }
 
@@ -137,9 +281,21 @@ __global__ void mu2_kernel(const float *__restrict__ mean, int dim, float *__res
 }
 
 int launch_column_mean(const float *X, int64_t n, int dim, float *mean, cudaStream_t st) {
-    dim3 blk(32, 8), grd((dim + 31) / 32);
-    column_mean_kernel<<<grd, blk, 0, st>>>(X, n, dim, mean);
-    LV_CHECK_LAUNCH("column_mean_kernel");
+    if (n <= 0 || dim <= 0) return LV_OK;
+    const int64_t chunks = (n + CM_ROWS - 1) / CM_ROWS;
+    if (chunks >= 65536) return fail(LV_ERR_ARG, "column_mean: more than 2^27 rows");
+    double *part = nullptr;
+    int rc = tmp_alloc((void **)&part, sizeof(double) * (size_t)chunks * dim, st);
+    if (rc) return rc;
+    dim3 grd((unsigned)((dim + CM_COLS - 1) / CM_COLS), (unsigned)chunks);
+    if (dim % 4 == 0 && ((uintptr_t)X & 15) == 0)
+        column_sum_kernel<true><<<grd, 256, 0, st>>>(X, n, dim, part);
+    else
+        column_sum_kernel<false><<<grd, 256, 0, st>>>(X, n, dim, part);
+    column_mean_final_kernel<<<(dim + 127) / 128, 128, 0, st>>>(part, (int)chunks, n, dim, mean);
+    cudaError_t e = cudaGetLastError();
+    tmp_free(part, st);
+    if (e != cudaSuccess) return cuda_fail(e, "column mean kernels");
     return LV_OK;
 }
 
@@ -233,6 +389,28 @@ int launch_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int
     if (n == 0) return LV_OK;
     const int wpb = 8;
     int64_t blocks = (n + wpb - 1) / wpb;
+    const int nc = dim / 4;
+    if (dim % 4 == 0 && ((uintptr_t)V & 15) == 0 && nc <= 32 * 8) {
+        int dev = 0, sms = 0;
+        LV_CUDA(cudaGetDevice(&dev));
+        LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const size_t smem = (size_t)dim * 8;
+        const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)sms * 8);
+        auto go = [&](auto kern) -> int {
+            if (smem > 48 * 1024) LV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<grid, wpb * 32, smem, st>>>(V, n, dim, mean, rec, g.stride, g.code_bytes);
+            LV_CHECK_LAUNCH("lvq_encode_vec_kernel");
+            return LV_OK;
+        };
+        if (bits == 8) {
+            if (nc <= 64) return go(lvq_encode_vec_kernel<8, 2>);
+            if (nc <= 128) return go(lvq_encode_vec_kernel<8, 4>);
+            return go(lvq_encode_vec_kernel<8, 8>);
+        }
+        if (nc <= 64) return go(lvq_encode_vec_kernel<4, 2>);
+        if (nc <= 128) return go(lvq_encode_vec_kernel<4, 4>);
+        return go(lvq_encode_vec_kernel<4, 8>);
+    }
     if (bits == 8)
         lvq_encode_kernel<8><<<(unsigned)blocks, wpb * 32, 0, st>>>(V, n, dim, mean, rec, g.stride, g.code_bytes);
     else

@@ -342,9 +342,9 @@ int leanvec_spectral_clip(float *A, int d, int D, lv_stream_t stream) {
     const size_t dD = (size_t)d * D, dd = (size_t)d * d;
     double *A64 = nullptr, *G = nullptr, *ev = nullptr, *U = nullptr, *W = nullptr, *R = nullptr;
     int rc = LV_OK;
-    if (cudaMalloc(&A64, 8 * dD) != cudaSuccess || cudaMalloc(&G, 8 * dd) != cudaSuccess ||
-        cudaMalloc(&ev, 8 * (size_t)d) != cudaSuccess || cudaMalloc(&U, 8 * dd) != cudaSuccess ||
-        cudaMalloc(&W, 8 * dd) != cudaSuccess || cudaMalloc(&R, 8 * dD) != cudaSuccess)
+    if (tmp_alloc((void **)&A64, 8 * dD, st) || tmp_alloc((void **)&G, 8 * dd, st) ||
+        tmp_alloc((void **)&ev, 8 * (size_t)d, st) || tmp_alloc((void **)&U, 8 * dd, st) ||
+        tmp_alloc((void **)&W, 8 * dd, st) || tmp_alloc((void **)&R, 8 * dD, st))
         rc = fail(LV_ERR_OOM, "spectral_clip: allocation failed");
     if (rc == LV_OK) {
         f32_to_f64_k<<<(unsigned)((dD + 255) / 256), 256, 0, st>>>(A, (int64_t)dD, A64);
@@ -365,12 +365,12 @@ int leanvec_spectral_clip(float *A, int d, int D, lv_stream_t stream) {
         f64_to_f32_k<<<(unsigned)((dD + 255) / 256), 256, 0, st>>>(R, (int64_t)dD, A);
         if (cudaStreamSynchronize(st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "spectral_clip: sync failed");
     }
-    cudaFree(A64);
-    cudaFree(G);
-    cudaFree(ev);
-    cudaFree(U);
-    cudaFree(W);
-    cudaFree(R);
+    tmp_free(A64, st);
+    tmp_free(G, st);
+    tmp_free(ev, st);
+    tmp_free(U, st);
+    tmp_free(W, st);
+    tmp_free(R, st);
     return rc;
 }
 
@@ -392,7 +392,7 @@ int leanvec_fit_ood(const float *X, int64_t n, const float *Q, int64_t m, int D,
     const size_t DD = (size_t)D * D, dD = (size_t)d * D, dd = (size_t)d * d;
     std::vector<void *> allocs;
     auto alloc = [&](void **p, size_t bytes) -> bool {
-        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        if (tmp_alloc(p, bytes, st) != LV_OK) return false;
         allocs.push_back(*p);
         return true;
     };
@@ -535,7 +535,7 @@ done:
         rep->loss_trace = trace;
         rep->trace_capacity = cap;
     }
-    for (void *p : allocs) cudaFree(p);
+    for (void *p : allocs) tmp_free(p, st);
     return rc;
 }
 
