@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -64,10 +65,11 @@ def beam_src_sha1() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(args, L):
+def recorded_traffic(args, L, max_hops=0):
     sha = beam_src_sha1()
     for r in TRAFFIC_RECORDS:
         if (r["src_sha1"] == sha and r["n"] == args.n and r["m"] == args.m and r["L"] == L and
+                r.get("max_hops", 0) == max_hops and
                 r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection and
                 r.get("alpha") == args.alpha and r.get("rule") == args.rule and
                 r.get("graph", "primary") == getattr(args, "graph", "primary") and
@@ -181,6 +183,62 @@ def calibrate(search_fn, truth, k):
     return chosen, trace
 
 
+HOP_FACTORS = (0.0, 1.5, 1.33, 1.2, 1.1, 1.0)
+
+
+def hop_limit(c, L):
+    """The expansion budget max_hops = ceil(c L) of hop factor c (0: no limit)."""
+    return 0 if not c else int(math.ceil(c * L - 1e-9))
+
+
+def calibrate_budget(search_fn, time_fn, truth, k, factors=HOP_FACTORS):
+    """Early termination by an expansion budget (the query descriptor's max_hops): for each hop
+    factor c, the smallest grid L with recall@k >= 0.90 under max_hops = ceil(c L), timed; returns
+    (L, max_hops, recall, table) of the fastest.  search_fn(L, mh) -> ids; time_fn(L, mh) -> QPS."""
+    table = []
+    for c in factors:
+        L, trace = calibrate(lambda L: search_fn(L, hop_limit(c, L)), truth, k)
+        if L is None:
+            table.append({"hop_factor": c, "L": None, "recall_trace": trace[-2:]})
+            continue
+        mh = hop_limit(c, L)
+        table.append({"hop_factor": c, "L": L, "max_hops": mh, "recall": dict(trace)[L], "qps": time_fn(L, mh),
+                      "recall_trace": trace[-2:]})
+    ok = [t for t in table if t.get("qps")]
+    if not ok:
+        return None, 0, None, table
+    best = max(ok, key=lambda t: t["qps"])
+    return best["L"], best["max_hops"], best["recall"], table
+
+
+def qps_of(fn, m):
+    """QPS of search fn(L, mh) over 5 timed calls after 2 untimed ones."""
+    def q(L, mh):
+        ms, _ = time_steps(lambda ev: fn(L, mh), 5, 2)
+        return m * 5 / (ms / 1e3)
+    return q
+
+
+def choose_config(args, S, proj, k=10):
+    """The id workload's LeanVec search configuration: --L/--max-hops when given, else the fastest
+    (L, max_hops) of the hop-budget calibration (recall@k >= 0.90).  Returns (L, mh, recall, table)."""
+    idx, Q, A, truth = S["idx"], S["Q"], S["A"], S["truth"]
+
+    def lv_search(L, mh):
+        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash,
+                          projection=proj)
+
+    if args.L:
+        return args.L, args.max_hops, recall_at(lv_search(args.L, args.max_hops)[0], truth, k), []
+    factors = HOP_FACTORS if args.hop_factor is None else (args.hop_factor,)
+    L, mh, rec, table = calibrate_budget(lambda L, mh: lv_search(L, mh)[0], qps_of(lv_search, Q.shape[0]), truth, k,
+                                         factors)
+    if L is None:
+        L, mh = L_GRID[-1], 0
+        rec = recall_at(lv_search(L, mh)[0], truth, k)
+    return L, mh, rec, table
+
+
 def replica_throughput(total_ms, units_per_step, steps, device=None):
     """Whole-job throughput of N independent replicas (one per rank, no data exchange): every rank
     timed the same number of steps; the job lasts as long as the slowest rank (max over ranks) and
@@ -278,7 +336,7 @@ def oracle_prepare(S):
                 truth=S["truth"].cpu().numpy())
 
 
-def cpu_oracle_sample(O, L, budget_s, nthreads=0):
+def cpu_oracle_sample(O, L, budget_s, nthreads=0, max_hops=0):
     """Time the CPU oracle (C, OpenMP over queries) on a bounded query sample."""
     import oracle
     cores = nthreads or os.cpu_count()
@@ -287,14 +345,15 @@ def cpu_oracle_sample(O, L, budget_s, nthreads=0):
     while True:
         t0 = time.perf_counter()
         r = oracle.search(O["g"], O["entry"], O["qp"][:m], k=10, L=L, rerank=L, prim=O["prim"], sec=O["sec"],
-                          qs=Qh[:m], nthreads=cores)
+                          qs=Qh[:m], nthreads=cores, max_hops=max_hops)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or m >= Qh.shape[0]:
             break
         m = min(Qh.shape[0], int(m * max(2.0, budget_s / 2 / max(dt, 1e-3))))
     rec = oracle.recall(r["ids"], O["truth"][:m], 10)
     return {"value": m / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {m} of {Qh.shape[0]} queries, same graph/projection, L = rerank = {L}, k = 10",
+            "sample": f"first {m} of {Qh.shape[0]} queries, same graph/projection, L = rerank = {L}, "
+                      f"max_hops = {max_hops or 'none'}, k = 10",
             "recall_at_10": rec, "seconds": dt, "scored_per_query": float(r["scored"].mean()),
             "hops_per_query": float(r["hops"].mean())}
 
@@ -822,6 +881,10 @@ def main():
                     help="build batch (default 65536; 16384 for the l2 workload, whose 992-byte records leave "
                          "room for a smaller reverse-edge pool per target)")
     ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
+    ap.add_argument("--max-hops", type=int, default=0, help="expansion budget with --L (0: none)")
+    ap.add_argument("--hop-factor", type=float, default=None,
+                    help="id workload: only this hop factor c (max_hops = ceil(c L); 0 = no budget) instead of "
+                         "calibrating over %s" % (HOP_FACTORS,))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hash", type=int, default=0, help="visited-cache slots per query (0 = library default)")
@@ -897,16 +960,14 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        S = setup(args, dev)
-        L = args.L
-        if not L:
-            L, _ = calibrate(lambda L: S["idx"].search(S["Q"], S["A"], k=10, L=L, rerank=L)[0], S["truth"], 10)
-            L = L or L_GRID[-1]
+        S = setup(args, dev, with_base=False)
+        proj = S["lv"].PREC_BF16 if args.projection == "bf16" else S["lv"].PREC_FP32
+        L, mh, _, _ = choose_config(args, S, proj)
         vals = []
         cb = None
         O = oracle_prepare(S)
         for i in range(args.warmup + args.steps):
-            r = cpu_oracle_sample(O, L, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
+            r = cpu_oracle_sample(O, L, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)), max_hops=mh)
             if i >= args.warmup:
                 vals.append(r["value"])
                 cb = r
@@ -915,7 +976,7 @@ def main():
         out = {"impl": "reference", "metric": metric, "value": v, "unit": "queries/s", "n_gpus": 1,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": workload, "L": L, "impl_note": "CPU oracle on the host cores"},
+               "config": {"workload": workload, "L": L, "max_hops": mh, "impl_note": "CPU oracle on the host cores"},
                "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                                              "d2h_bytes_per_step": 0}}
         print(json.dumps(out), flush=True)
@@ -941,26 +1002,26 @@ def main():
     ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
     sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
 
-    # -- choose L for recall 0.90 (untimed)
-    if args.L:
-        L, trace = args.L, []
-        rec = recall_at(idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, hash_slots=args.hash)[0], truth, k)
-        trace = [(L, rec)]
-    else:
-        L, trace = calibrate(lambda L: idx.search(Q, A, k=k, L=L, rerank=L, width=args.width,
-                                                  hash_slots=args.hash, projection=proj)[0], truth, k)
-        if L is None:
-            L = L_GRID[-1]
-    rec = dict(trace)[L]
-    Lb, trace_b = calibrate(lambda L: base.search(Q, None, k=k, L=L, width=args.width)[0], truth, k)
+    # -- choose L (and the expansion budget) for recall 0.90 (untimed)
+    def lv_search(L, mh, **kw):
+        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash,
+                          projection=proj, **kw)
+
+    def base_search(L, mh, **kw):
+        return base.search(Q, None, k=k, L=L, max_hops=mh, width=args.width, **kw)
+
+    L, mh, rec, hop_table = choose_config(args, S, proj)
+    factors = HOP_FACTORS if args.hop_factor is None else (args.hop_factor,)
+    Lb, mhb, rec_b, hop_table_b = calibrate_budget(lambda L, mh: base_search(L, mh)[0], qps_of(base_search, m),
+                                                   truth, k, factors)
     if Lb is None:
-        Lb = L_GRID[-1]
-    rec_b = dict(trace_b)[Lb]
-    log(f"LeanVec L={L} recall={rec:.4f}  trace={trace}")
-    log(f"FP32   L={Lb} recall={rec_b:.4f}  trace={trace_b}")
+        Lb, mhb = L_GRID[-1], 0
+        rec_b = recall_at(base_search(Lb, mhb)[0], truth, k)
+    log(f"LeanVec L={L} max_hops={mh} recall={rec:.4f}  table={hop_table}")
+    log(f"FP32   L={Lb} max_hops={mhb} recall={rec_b:.4f}  table={hop_table_b}")
 
     # -- per-query work (untimed run with counters)
-    _, _, st = idx.search(Q, A, k=k, L=L, rerank=L, stats=True, hash_slots=args.hash, width=args.width, projection=proj)
+    _, _, st = lv_search(L, mh, stats=True)
     hops = float(st[:, 0].double().mean())
     scored = float(st[:, 1].double().mean())
     inf = idx.info()
@@ -968,7 +1029,7 @@ def main():
         L * inf["secondary_stride"] + args.D * 4 + k * 8
 
     def step(ev):
-        idx.search(Q, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), events=ev, hash_slots=args.hash, width=args.width, projection=proj)
+        lv_search(L, mh, out=(ids_buf, sc_buf), events=ev)
 
     if world > 1:
         torch.distributed.barrier()
@@ -988,7 +1049,8 @@ def main():
 
     def step_e2e(ev):
         Qd.copy_(Qh, non_blocking=True)
-        idx.search(Qd, A, k=k, L=L, rerank=L, out=(ids_buf, sc_buf), hash_slots=args.hash, width=args.width, projection=proj)
+        idx.search(Qd, A, k=k, L=L, rerank=L, max_hops=mh, out=(ids_buf, sc_buf), hash_slots=args.hash,
+                   width=args.width, projection=proj)
         ids_h.copy_(ids_buf, non_blocking=True)
         sc_h.copy_(sc_buf, non_blocking=True)
 
@@ -998,17 +1060,16 @@ def main():
     # -- full-dimensional float32 baseline on the same graph
     ids_b = torch.empty((m, k), dtype=torch.int32, device=dev)
     sc_b = torch.empty((m, k), dtype=torch.float32, device=dev)
-    base_ms, _ = time_steps(lambda ev: base.search(Q, None, k=k, L=Lb, out=(ids_b, sc_b), width=args.width),
-                            max(5, args.steps // 2), 2)
+    base_ms, _ = time_steps(lambda ev: base_search(Lb, mhb, out=(ids_b, sc_b)), max(5, args.steps // 2), 2)
     qps_b = m * max(5, args.steps // 2) / (base_ms / 1e3)
-    _, _, stb = base.search(Q, None, k=k, L=Lb, stats=True, width=args.width)
+    _, _, stb = base_search(Lb, mhb, stats=True)
     bytes_b = args.D * 4 + float(stb[:, 0].double().mean()) * inf["R"] * 4 + \
         float(stb[:, 1].double().mean()) * lv.leanvec_record_stride(args.D, 32) + k * 8
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_oracle_sample(oracle_prepare(S), L, args.cpu_budget)
+            cpu = cpu_oracle_sample(oracle_prepare(S), L, args.cpu_budget, max_hops=mh)
         except Exception as e:  # the GPU result stands without the CPU leg
             cpu = {"error": repr(e)}
 
@@ -1020,7 +1081,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u8 LVQ codes decoded to f32)",
         "data": "synthetic",
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
-                   "rerank": L, "recall_at_10": rec, "recall_trace": trace, "R": args.R,
+                   "rerank": L, "max_hops": mh, "recall_at_10": rec, "hop_budget_table": hop_table, "R": args.R,
                    "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary, "projection": args.projection,
                    "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
@@ -1030,12 +1091,12 @@ def main():
                 "d2h_bytes_per_step": m * k * 8},
         "gpu_launches": (6 if args.projection == "bf16" else 4) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L),
+                     "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L, mh),
                      "kernel": "beam_kernel<LvqIntScorer<3,8>,search> + rerank_kernel",
                      "kernel_ms": kern_avg, "bytes_per_query": bytes_q, "hops_per_query": hops,
                      "scored_per_query": scored, "peak_kind": peak_kind},
-        "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "recall_at_10": rec_b,
-                          "recall_trace": trace_b, "bytes_per_query": bytes_b,
+        "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "max_hops": mhb, "recall_at_10": rec_b,
+                          "hop_budget_table": hop_table_b, "bytes_per_query": bytes_b,
                           "speedup_leanvec": qps / world / qps_b},
         "cpu_baseline": cpu,
         "clocks": ck,

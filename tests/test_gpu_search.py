@@ -84,6 +84,22 @@ def test_ids_match_oracle(lv, pb, L, r):
     assert np.all(st[:, 1] >= 1)
 
 
+@pytest.mark.parametrize("W,mh", [(1, 20), (2, 25), (2, 36), (4, 30), (3, 31)])
+def test_expansion_budget_matches_oracle(lv, pb, W, mh):
+    """max_hops below the unlimited search's hop count (about 50 here): the last round is cut to
+    the remaining budget on both sides, so the beams, the reranked ids and the hop counts agree."""
+    idx = gpu_index(lv, pb)
+    ref = oracle.search(pb["graph"], pb["entry"], _qp(pb), k=10, L=48, rerank=48, prim=pb["prim"], sec=pb["sec"],
+                        qs=pb["Q"].astype(np.float64), width=W, max_hops=mh)
+    assert ref["hops"].max() <= mh and (ref["hops"] == mh).mean() > 0.5  # the budget binds
+    ids, sc, st = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48, width=W, max_hops=mh, stats=True)
+    ids = ids.cpu().numpy()
+    assert (ids == ref["ids"]).mean() >= 0.99
+    hops = st[:, 0].cpu().numpy()
+    assert hops.max() <= mh
+    assert np.abs(hops - ref["hops"]).mean() <= 0.5
+
+
 @pytest.mark.parametrize("W", [2, 4])
 def test_search_width_matches_oracle(lv, pb, W):
     """Expanding the W best unexpanded members per round: same result as the oracle's
