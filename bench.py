@@ -49,10 +49,14 @@ TRAFFIC_RECORDS = [
     # the default graph (unit-L2 rule, alpha 1.02) at its L for 0.90: beam 3.271 GB + 10.2 MB, rerank 1.107 GB + 0.25 MB
     {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 148, "width": 2, "hash": 0,
      "projection": "bf16", "alpha": 1.02, "rule": 1, "bytes": 3271060992 + 10185216 + 1106905856 + 252160},
-    # the default: the same rule on a graph built on full-D LVQ-8 codes, L = 120: beam 2.733 GB + 8.8 MB,
-    # rerank 0.893 GB + 1.2 MB
+    # the same rule on a graph built on full-D LVQ-8 codes, L = 120: beam 2.733 GB + 8.8 MB, rerank 0.893 GB + 1.2 MB
     {"src_sha1": "9ea3355bc525640bcd5ba8c54cfb9beac141d1aa", "n": 1_000_000, "m": 10_000, "L": 120, "width": 2, "hash": 0, "projection": "bf16",
      "alpha": 1.02, "rule": 1, "graph": "full", "bytes": 2733314560 + 8754688 + 893092608 + 1217024},
+    # the default: that graph with the expansion budget max_hops = L, L = 128: beam 2.455 GB + 8.3 MB,
+    # rerank 0.954 GB + 1.2 MB
+    {"src_sha1": "9ea3355bc525640bcd5ba8c54cfb9beac141d1aa", "n": 1_000_000, "m": 10_000, "L": 128, "max_hops": 128,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
+     "bytes": 2454921216 + 8330752 + 954114560 + 1157888},
 ]
 
 
@@ -183,7 +187,7 @@ def calibrate(search_fn, truth, k):
     return chosen, trace
 
 
-HOP_FACTORS = (0.0, 1.5, 1.33, 1.2, 1.1, 1.0)
+HOP_FACTORS = (0.0, 1.5, 1.33, 1.2, 1.1, 1.0, 0.9, 0.8)
 
 
 def hop_limit(c, L):
@@ -230,7 +234,7 @@ def choose_config(args, S, proj, k=10):
 
     if args.L:
         return args.L, args.max_hops, recall_at(lv_search(args.L, args.max_hops)[0], truth, k), []
-    factors = HOP_FACTORS if args.hop_factor is None else (args.hop_factor,)
+    factors = HOP_FACTORS if args.hop_sweep else (args.hop_factor,)
     L, mh, rec, table = calibrate_budget(lambda L, mh: lv_search(L, mh)[0], qps_of(lv_search, Q.shape[0]), truth, k,
                                          factors)
     if L is None:
@@ -882,9 +886,12 @@ def main():
                          "room for a smaller reverse-edge pool per target)")
     ap.add_argument("--L", type=int, default=0, help="fixed beam width (skips the recall sweep)")
     ap.add_argument("--max-hops", type=int, default=0, help="expansion budget with --L (0: none)")
-    ap.add_argument("--hop-factor", type=float, default=None,
-                    help="id workload: only this hop factor c (max_hops = ceil(c L); 0 = no budget) instead of "
-                         "calibrating over %s" % (HOP_FACTORS,))
+    ap.add_argument("--hop-factor", type=float, default=1.0,
+                    help="id workload: expansion budget max_hops = ceil(c L) for hop factor c (0 = no budget); "
+                         "both arms, L calibrated for recall 0.90 under it")
+    ap.add_argument("--hop-sweep", action="store_true",
+                    help="id workload: calibrate every hop factor of %s and keep the fastest (both arms)"
+                         % (HOP_FACTORS,))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hash", type=int, default=0, help="visited-cache slots per query (0 = library default)")
@@ -990,14 +997,17 @@ def main():
     if args.profile:
         L = args.L or 64
         for _ in range(args.warmup):
-            idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, hash_slots=args.hash, projection=proj)
+            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash,
+                       projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
-            idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, hash_slots=args.hash, projection=proj)
+            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash,
+                       projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"profile": True, "L": L, "n": args.n, "m": m, "steps": args.steps}), flush=True)
+        print(json.dumps({"profile": True, "L": L, "max_hops": args.max_hops, "n": args.n, "m": m,
+                          "steps": args.steps}), flush=True)
         return
     ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
     sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
@@ -1011,7 +1021,7 @@ def main():
         return base.search(Q, None, k=k, L=L, max_hops=mh, width=args.width, **kw)
 
     L, mh, rec, hop_table = choose_config(args, S, proj)
-    factors = HOP_FACTORS if args.hop_factor is None else (args.hop_factor,)
+    factors = HOP_FACTORS if args.hop_sweep else (args.hop_factor,)
     Lb, mhb, rec_b, hop_table_b = calibrate_budget(lambda L, mh: base_search(L, mh)[0], qps_of(base_search, m),
                                                    truth, k, factors)
     if Lb is None:

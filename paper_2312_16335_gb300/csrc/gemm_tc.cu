@@ -255,6 +255,23 @@ __global__ void cast_bf16_kernel(const float *__restrict__ X, int64_t n, int D, 
     Y[t] = __float2bfloat16_rn(c < D ? X[r * D + c] : 0.f);
 }
 
+// The same with 16-byte accesses (D % 8 == 0, ldo == D, 16-byte aligned X and Y): each thread
+// converts 8 consecutive floats (two float4 loads) into one 16-byte store.
+__global__ void cast_bf16_vec_kernel(const float *__restrict__ X, int64_t total8, __nv_bfloat16 *__restrict__ Y) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total8; t += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(X) + 2 * t);
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(X) + 2 * t + 1);
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(a.z, a.w);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(b.x, b.y), h3 = __floats2bfloat162_rn(b.z, b.w);
+        uint4 o;
+        o.x = *reinterpret_cast<const uint32_t *>(&h0);
+        o.y = *reinterpret_cast<const uint32_t *>(&h1);
+        o.z = *reinterpret_cast<const uint32_t *>(&h2);
+        o.w = *reinterpret_cast<const uint32_t *>(&h3);
+        reinterpret_cast<uint4 *>(Y)[t] = o;
+    }
+}
+
 // float32 rows -> e4m3 rows (n x ldo bytes, zero-padded) with per-row scale max|row| / 448;
 // one warp per row
 __global__ void cast_e4m3_kernel(const float *__restrict__ X, int64_t n, int D, uint8_t *__restrict__ Y, int ldo,
@@ -289,6 +306,37 @@ __global__ void cast_transpose_bf16_kernel(const float *__restrict__ X, int64_t 
         const int c = c0 + i;
         const int64_t r = r0 + threadIdx.x;
         if (c < D && r < ldo) Y[(int64_t)c * ldo + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+    }
+}
+
+// float32 X (n x D) -> bf16 X^T (D x ldo) with 64 x 64 tiles, 16-byte loads and stores
+// (D % 4 == 0, ldo % 8 == 0, 16-byte aligned X and Y); rows n..ldo-1 of the output are zero.
+__global__ void __launch_bounds__(256) cast_transpose_bf16_vec_kernel(const float *__restrict__ X, int64_t n, int D,
+                                                                      __nv_bfloat16 *__restrict__ Y, int64_t ldo) {
+    __shared__ __align__(16) __nv_bfloat16 tile[64][72];  // [column of X][row of X], 16-byte padded rows
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = t / 16 + 16 * i, c4 = t % 16;
+        const int64_t gr = r0 + r;
+        const int gc = c0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gr < n && gc < D) v = __ldg(reinterpret_cast<const float4 *>(X + gr * D + gc));
+        tile[4 * c4 + 0][r] = __float2bfloat16_rn(v.x);
+        tile[4 * c4 + 1][r] = __float2bfloat16_rn(v.y);
+        tile[4 * c4 + 2][r] = __float2bfloat16_rn(v.z);
+        tile[4 * c4 + 3][r] = __float2bfloat16_rn(v.w);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int c = t / 8 + 32 * j, ch = t % 8;
+        const int gc = c0 + c;
+        const int64_t gr = r0 + 8 * ch;
+        if (gc < D && gr < ldo)
+            *reinterpret_cast<uint4 *>(Y + (int64_t)gc * ldo + gr) = *reinterpret_cast<const uint4 *>(&tile[c][8 * ch]);
     }
 }
 
@@ -384,6 +432,13 @@ int gemm_bf16_tc(const __nv_bfloat16 *A, int64_t M, int64_t lda, const __nv_bflo
 }
 
 int launch_cast_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *Y, int ldo, cudaStream_t st) {
+    if (D % 8 == 0 && ldo == D && ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0) {
+        const int64_t total8 = n * D / 8;
+        const unsigned grid = (unsigned)std::min<int64_t>((total8 + 255) / 256, 152 * 16);
+        if (total8 > 0) cast_bf16_vec_kernel<<<grid, 256, 0, st>>>(X, total8, Y);
+        LV_CHECK_LAUNCH("cast_bf16_vec_kernel");
+        return LV_OK;
+    }
     const int64_t tot = n * ldo;
     cast_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, n, D, Y, ldo);
     LV_CHECK_LAUNCH("cast_bf16_kernel");
@@ -391,6 +446,12 @@ int launch_cast_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *Y, int ldo
 }
 
 int launch_cast_transpose_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *Y, int64_t ldo, cudaStream_t st) {
+    if (D % 4 == 0 && ldo % 8 == 0 && ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0) {
+        dim3 grd((unsigned)((ldo + 63) / 64), (unsigned)((D + 63) / 64));
+        cast_transpose_bf16_vec_kernel<<<grd, 256, 0, st>>>(X, n, D, Y, ldo);
+        LV_CHECK_LAUNCH("cast_transpose_bf16_vec_kernel");
+        return LV_OK;
+    }
     dim3 grd((unsigned)((ldo + 31) / 32), (unsigned)((D + 31) / 32));
     cast_transpose_bf16_kernel<<<grd, dim3(32, 8), 0, st>>>(X, n, D, Y, ldo);
     LV_CHECK_LAUNCH("cast_transpose_bf16_kernel");

@@ -23,8 +23,11 @@ def lv():
 
 
 @pytest.mark.parametrize("n,D,d,ldy", [(300, 128, 32, 32), (1000, 768, 160, 160), (77, 200, 64, 80),
-                                       (5000, 512, 128, 128), (129, 64, 16, 16), (1, 768, 160, 176)])
+                                       (5000, 512, 128, 128), (129, 64, 16, 16), (1, 768, 160, 176),
+                                       (50, 100, 16, 16), (333, 77, 8, 8)])
 def test_projection_bf16(lv, n, D, d, ldy):
+    """D % 8 == 0 casts 8 floats per thread with 16-byte accesses; D = 100 and 77 take the
+    element-wise cast into padded rows."""
     rng = np.random.default_rng(n + D + d)
     X = rng.standard_normal((n, D)).astype(np.float32)
     P = rng.standard_normal((d, D)).astype(np.float32)
@@ -37,8 +40,10 @@ def test_projection_bf16(lv, n, D, d, ldy):
     assert np.abs(Y[:, :d] - ref).max() > 0
 
 
-@pytest.mark.parametrize("n,D", [(1000, 64), (20000, 768), (3001, 200)])
+@pytest.mark.parametrize("n,D", [(1000, 64), (20000, 768), (3001, 200), (3001, 100), (517, 77)])
 def test_second_moment_bf16(lv, n, D):
+    """D % 4 == 0 transposes 64 x 64 tiles with 16-byte accesses (ragged row and column tiles for
+    n = 3001, D = 100); D = 77 takes the element-wise transposing cast."""
     rng = np.random.default_rng(n * 7 + D)
     X = rng.standard_normal((n, D)).astype(np.float32)
     K = lv.leanvec_second_moment(t(X), precision=lv.PREC_BF16).cpu().numpy().astype(np.float64)
