@@ -100,9 +100,11 @@ int64_t leanvec_record_stride(int dim, int bits);
 /* Stand-alone kernels on caller-owned device buffers                        */
 /* ------------------------------------------------------------------------ */
 
-/* Column mean of X (n x dim, device) accumulated in FP64 in a fixed order and
- * rounded to float32 into mean (dim, device).  The dataset mean around which
- * LVQ quantises (Sec. 2 cites LVQ for quant()). */
+/* Column mean of X (n x dim, device) rounded to float32 into mean (dim, device),
+ * accumulated in a fixed order (so repeated calls agree bit for bit): per chunk of
+ * 2048 rows in compensated float32 (each addition's rounding error carried in a
+ * second float32, TwoSum: about 44 significant bits), the chunks in FP64.  The
+ * dataset mean around which LVQ quantises (Sec. 2 cites LVQ for quant()). */
 int leanvec_column_mean(const float *X, int64_t n, int dim, float *mean, lv_stream_t stream);
 
 /* LVQ-encode the n rows of V (n x dim, device) around mean (dim, device) into

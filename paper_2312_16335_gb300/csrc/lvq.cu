@@ -8,12 +8,26 @@ namespace lv {
 
 constexpr double FIX = 1048576.0;  // 2^20: fixed point of the mean in the build score
 
-// Column mean in FP64, deterministic (a fixed summation order that depends on n and dim
-// only).  Stage 1: block (c, r) sums the rows of chunk r (CM_ROWS rows) for the 4 x 32
-// columns of tile c, each warp a strided subset of the rows (float4 loads along the row when
-// the rows are 16-byte aligned), the 8 warps combined in order; stage 2 adds the chunks in
-// order and rounds the mean to float32.
+// Column mean, deterministic (a fixed summation order that depends on n and dim only).
+// Stage 1: block (c, r) sums the rows of chunk r (CM_ROWS rows) for the 4 x 32 columns of tile
+// c, each warp a strided subset of the rows (float4 loads along the row when the rows are
+// 16-byte aligned) in compensated float32 (Knuth's TwoSum keeps each addition's rounding
+// error in a second float32: about 44 significant bits, FP64 being a slow pipe here); the
+// warps' (sum, error) pairs are combined in FP64 in order; stage 2 adds the chunks in FP64
+// in order and rounds the mean to float32.
 constexpr int CM_ROWS = 2048, CM_COLS = 128;
+
+struct Comp {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float bb = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb));
+        s = t;
+        e = __fadd_rn(e, err);
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
 
 template <bool VEC>
 __global__ void __launch_bounds__(256) column_sum_kernel(const float *__restrict__ X, int64_t n, int dim,
@@ -22,29 +36,29 @@ __global__ void __launch_bounds__(256) column_sum_kernel(const float *__restrict
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = blockIdx.x * CM_COLS + 4 * lane;
     const int64_t r0 = (int64_t)blockIdx.y * CM_ROWS, r1 = min(n, r0 + CM_ROWS);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    Comp a0, a1, a2, a3;
     if (VEC) {
         if (c0 < dim)
             for (int64_t i = r0 + warp; i < r1; i += 8) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(X + i * dim + c0));
-                a0 += (double)v.x;
-                a1 += (double)v.y;
-                a2 += (double)v.z;
-                a3 += (double)v.w;
+                a0.add(v.x);
+                a1.add(v.y);
+                a2.add(v.z);
+                a3.add(v.w);
             }
     } else {
         for (int64_t i = r0 + warp; i < r1; i += 8) {
             const float *row = X + i * dim;
-            if (c0 < dim) a0 += (double)row[c0];
-            if (c0 + 1 < dim) a1 += (double)row[c0 + 1];
-            if (c0 + 2 < dim) a2 += (double)row[c0 + 2];
-            if (c0 + 3 < dim) a3 += (double)row[c0 + 3];
+            if (c0 < dim) a0.add(row[c0]);
+            if (c0 + 1 < dim) a1.add(row[c0 + 1]);
+            if (c0 + 2 < dim) a2.add(row[c0 + 2]);
+            if (c0 + 3 < dim) a3.add(row[c0 + 3]);
         }
     }
-    red[warp][4 * lane] = a0;
-    red[warp][4 * lane + 1] = a1;
-    red[warp][4 * lane + 2] = a2;
-    red[warp][4 * lane + 3] = a3;
+    red[warp][4 * lane] = a0.value();
+    red[warp][4 * lane + 1] = a1.value();
+    red[warp][4 * lane + 2] = a2.value();
+    red[warp][4 * lane + 3] = a3.value();
     __syncthreads();
     if (threadIdx.x < CM_COLS) {
         const int c = blockIdx.x * CM_COLS + threadIdx.x;
