@@ -1099,7 +1099,9 @@ def main():
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
                 "d2h_bytes_per_step": m * k * 8},
-        "gpu_launches": (6 if args.projection == "bf16" else 4) * args.steps,
+        # per step: bf16 -> cast of A + fused float32-input projection GEMM, fp32 -> projection GEMM;
+        # then the query constants, the beam kernel and the rerank kernel
+        "gpu_launches": (5 if args.projection == "bf16" else 4) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L, mh),
                      "kernel": "beam_kernel<LvqIntScorer<3,8>,search> + rerank_kernel",

@@ -49,7 +49,7 @@ int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float 
                  size_t *ws_bytes, int *status, cudaStream_t st);
 int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                 size_t *ws_bytes, int *status, cudaStream_t st);
-size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d);
+size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X);
 // tensor-core projection with bf16 or e4m3 (per-row scaled) operands
 static int project_tc(int prec, const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                       size_t *ws_bytes, int *status, cudaStream_t st) {
@@ -143,7 +143,7 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
     if (n == 0) return LV_OK;
     cudaStream_t st = (cudaStream_t)stream;
     void *ws = nullptr;
-    size_t wsb = project_tc_ws_bytes(precision, n, D, d);
+    size_t wsb = project_tc_ws_bytes(precision, n, D, d, X);
     int *status = nullptr;
     int h_status = 0;
     int rc = tmp_alloc((void **)&status, sizeof(int), st);

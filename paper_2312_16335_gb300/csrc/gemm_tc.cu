@@ -200,30 +200,46 @@ __global__ void __launch_bounds__(128, 1)
     bool ok = nkb > 0 && mbar_wait(accum, 0) && !*abort_flag;
     if (nkb > 0 && !ok && threadIdx.x == 0) atomicOr(p.status, ST_TIMEOUT);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
     if (ok) {
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(addr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < p.M) {
-                const int col0 = n0 + c0;
-                float *dst = p.partial ? p.partial + ((int64_t)blockIdx.z * p.M + row) * p.N + col0
-                                       : p.C + (int64_t)row * p.ldc + col0;
-                const float rs = p.row_scale ? p.row_scale[row] : 1.f;
+        // each warp moves its 32 rows through a 32 x 33 float slab in the (now idle) stage memory,
+        // 32 columns at a time, so that every global store instruction writes one 128-byte row
+        // segment
+        float *slab = reinterpret_cast<float *>(base) + warp * 32 * 33;
+        const int row0 = m0 + warp * 32;
+        for (int c0 = 0; c0 < BN; c0 += 32) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (col0 + j < p.N) {
-                        float v = __uint_as_float(r[j]);
-                        if (p.row_scale) v *= rs * p.col_scale[col0 + j];
-                        dst[j] = v;
-                    }
+            for (int h = 0; h < 2; ++h) {
+                const int cc = c0 + 16 * h;
+                uint32_t r[16];
+                if (cc < BN) {
+                    const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc;
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(addr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) slab[lane * 33 + 16 * h + j] = cc < BN ? __uint_as_float(r[j]) : 0.f;
             }
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+            const float cs = (p.row_scale && col < p.N) ? p.col_scale[col] : 1.f;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = row0 + rr;
+                if (row < p.M && c0 + lane < BN && col < p.N) {
+                    float v = slab[rr * 33 + lane];
+                    if (p.row_scale) v *= p.row_scale[row] * cs;
+                    if (p.partial)
+                        p.partial[((int64_t)blockIdx.z * p.M + row) * p.N + col] = v;
+                    else
+                        p.C[(int64_t)row * p.ldc + col] = v;
+                }
+            }
+            __syncwarp();
         }
     } else if (nkb > 0 && warp == 0 && lane == 0) {
         // drain: wait (bounded) for the copies this CTA may still have in flight
@@ -233,6 +249,273 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Projection Y = X P^T with X read as float32 and converted to bf16 inside the kernel (no bf16
+// copy of X in HBM), P as a bf16 copy loaded by TMA.  Persistent: CTA c takes the 128-row tiles
+// c, c + G, ...; the accumulator is double-buffered in tensor memory so that the epilogue of one
+// tile overlaps the main loop of the next.
+//   warp 9    : lane 0 streams the float32 X blocks (128 rows x 64 columns, 32 KB, no swizzle)
+//               by TMA into a 3-deep staging ring
+//   warps 4-7 : converters, 128 threads: per K block, 8 chunks of 8 floats each read from the
+//               staging buffer -> 8 bf16 -> one 16-byte store at the 128-byte-swizzle position
+//               (row r, chunk c) -> r * 128 + ((c ^ (r & 7)) << 4) of the operand stage, the
+//               layout TMA would write; the first converter thread also starts the TMA of the
+//               stage's P tile
+//   warp 8    : TMEM allocation; lane 0 issues tcgen05.mma (M 128, N BN, K 16) and the commits
+//   warps 0-3 : epilogue, warp w owns TMEM lanes (= tile rows) 32w .. 32w + 31
+// Barriers: sfull[t] (X block bytes), sempty[t] (128 converter arrivals), full[s] (128 converter
+// arrivals + the P tile's bytes), empty[s] (MMA commit), tfull[b] (MMA commit after a tile),
+// tempty[b] (128 epilogue arrivals).  Every wait is bounded.
+constexpr int PF_THREADS = 320, PF_XSTAGES = 3;
+constexpr uint32_t PF_XBYTES = 128 * 64 * 4;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_tx_only(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+struct PfParams {
+    int M, K, N, BN;  // N = d (<= 256), BN = round_up(N, 16)
+    int stages;       // operand stages (2 or 3)
+    float *Y;         // M x ldy float32; columns N .. ldy-1 written with zeros
+    int ldy;
+    int *status;
+};
+
+__global__ void __launch_bounds__(PF_THREADS, 1)
+    proj_f32in_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tb,
+                      const PfParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int BN = p.BN, PS = p.stages;
+    const uint32_t a_bytes = TC_BM * 128, b_bytes = (uint32_t)BN * 128;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    uint8_t *xstage = base + PS * stage_bytes;  // PF_XSTAGES x 32 KB
+    uint64_t *full = reinterpret_cast<uint64_t *>(xstage + PF_XSTAGES * PF_XBYTES);
+    uint64_t *empty = full + 4;
+    uint64_t *sfull = empty + 4;
+    uint64_t *sempty = sfull + PF_XSTAGES;
+    uint64_t *tfull = sempty + PF_XSTAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = (p.M + TC_BM - 1) / TC_BM;
+    const int nkb = (p.K + 63) / 64;
+    const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int64_t total = (int64_t)my_tiles * nkb;  // this CTA's K blocks, g = 0 .. total - 1
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PS; ++s) {
+            mbar_init(full + s, 128);
+            mbar_init(empty + s, 1);
+        }
+        for (int t = 0; t < PF_XSTAGES; ++t) {
+            mbar_init(sfull + t, 1);
+            mbar_init(sempty + t, 128);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull + b, 1);
+            mbar_init(tempty + b, 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 9) {
+        // ---- X producer
+        if (lane == 0) {
+            for (int64_t g = 0; g < total; ++g) {
+                const int t = (int)(g % PF_XSTAGES);
+                const int64_t w = g / PF_XSTAGES;
+                if (w > 0 && !mbar_wait(sempty + t, (uint32_t)((w - 1) & 1))) {
+                    *abort_flag = 1;
+                    atomicOr(p.status, ST_TIMEOUT);
+                }
+                if (*abort_flag) {
+                    // drain: the copies already started must land before the CTA exits
+                    for (int64_t q = std::max<int64_t>(0, g - PF_XSTAGES); q < g; ++q)
+                        mbar_wait(sfull + (int)(q % PF_XSTAGES), (uint32_t)((q / PF_XSTAGES) & 1));
+                    break;
+                }
+                const int tile = (int)blockIdx.x + (int)(g / nkb) * (int)gridDim.x;
+                mbar_expect_tx(sfull + t, PF_XBYTES);
+                tma_load_2d(xstage + (size_t)t * PF_XBYTES, &tx, (int)(g % nkb) * 64, tile * TC_BM, sfull + t);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4 && warp < 8) {
+        // ---- converters
+        const int ct = threadIdx.x - 128;
+        for (int64_t g = 0; g < total; ++g) {
+            const int t = (int)(g % PF_XSTAGES);
+            const int s = (int)(g % PS);
+            const int64_t u = g / PS;
+            bool ok = !*abort_flag && mbar_wait(sfull + t, (uint32_t)((g / PF_XSTAGES) & 1));
+            float4 v[16];
+            if (ok) {
+                const uint8_t *xs = xstage + (size_t)t * PF_XBYTES;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int ci = ct + 128 * j;
+                    const int r = ci >> 3, c = ci & 7;
+                    const float4 *src = reinterpret_cast<const float4 *>(xs + r * 256 + 32 * c);
+                    v[2 * j] = src[0];
+                    v[2 * j + 1] = src[1];
+                }
+            }
+            mbar_arrive(sempty + t);  // the staging block is in registers (or abandoned)
+            if (ok && u > 0) ok = mbar_wait(empty + s, (uint32_t)((u - 1) & 1));
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            uint8_t *sa = base + s * stage_bytes;
+            if (ct == 0) {
+                mbar_tx_only(full + s, b_bytes);
+                tma_load_2d(sa + a_bytes, &tb, (int)(g % nkb) * 64, 0, full + s);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int ci = ct + 128 * j;
+                const int r = ci >> 3, c = ci & 7;
+                uint4 o;
+                o.x = pack_bf16x2(v[2 * j].x, v[2 * j].y);
+                o.y = pack_bf16x2(v[2 * j].z, v[2 * j].w);
+                o.z = pack_bf16x2(v[2 * j + 1].x, v[2 * j + 1].y);
+                o.w = pack_bf16x2(v[2 * j + 1].z, v[2 * j + 1].w);
+                *reinterpret_cast<uint4 *>(sa + r * 128 + ((c ^ (r & 7)) << 4)) = o;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full + s);
+        }
+    } else if (warp == 8) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tc<0>(TC_BM, BN);
+            int64_t g = 0;
+            for (int tc = 0; tc < my_tiles && !*abort_flag; ++tc) {
+                const int b = tc & 1, v = tc >> 1;
+                if (v > 0 && !mbar_wait(tempty + b, (uint32_t)((v - 1) & 1))) {
+                    *abort_flag = 1;
+                    atomicOr(p.status, ST_TIMEOUT);
+                    break;
+                }
+                const uint32_t acc_addr = tmem + (uint32_t)(b * 256);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % PS);
+                    if (!mbar_wait(full + s, (uint32_t)((g / PS) & 1)) || *abort_flag) {
+                        *abort_flag = 1;
+                        atomicOr(p.status, ST_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    uint8_t *sa = base + s * stage_bytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t ad = sdesc(sa + 32 * k);
+                        const uint64_t bd = sdesc(sa + a_bytes + 32 * k);
+                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\t"
+                            "setp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(empty + s))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(tfull + b))
+                             : "memory");
+            }
+            // every MMA this thread issued has completed once `drain` flips
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(drain))
+                         : "memory");
+            if (!mbar_wait(drain, 0)) atomicOr(p.status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: tile row = TMEM lane; each warp moves its 32 rows through a 32 x 33
+        // float slab in shared memory, 32 columns at a time, so that every global store
+        // instruction writes one whole 128-byte row segment
+        float *slab = reinterpret_cast<float *>(tmem_slot + 2) + warp * 32 * 33;
+        for (int tc = 0; tc < my_tiles; ++tc) {
+            const int tile = (int)blockIdx.x + tc * (int)gridDim.x;
+            const int b = tc & 1, v = tc >> 1;
+            const bool ok = !*abort_flag && mbar_wait(tfull + b, (uint32_t)(v & 1));
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row0 = tile * TC_BM + warp * 32;
+            for (int c0 = 0; c0 < p.ldy; c0 += 32) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = c0 + 16 * h;
+                    uint32_t r[16];
+                    if (cc < BN) {
+                        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + cc);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                              "=r"(r[14]), "=r"(r[15])
+                            : "r"(addr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        slab[lane * 33 + 16 * h + j] = (cc + j < p.N) ? __uint_as_float(r[j]) : 0.f;
+                }
+                __syncwarp();
+                const int col = c0 + lane;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = row0 + rr;
+                    if (row < p.M && col < p.ldy) p.Y[(int64_t)row * p.ldy + col] = slab[rr * 33 + lane];
+                }
+                __syncwarp();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(tempty + b);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 8)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // sum of the split-K partials in a fixed order
@@ -460,21 +743,81 @@ int launch_cast_transpose_bf16(const float *X, int64_t n, int D, __nv_bfloat16 *
 
 int ensure_ws(void **p, size_t *have, size_t want);
 
+// the fp32-input projection kernel applies: 16-byte aligned rows of X, d <= 256
+static bool proj_fused_ok(const float *X, int D, int d) {
+    return D % 4 == 0 && ((uintptr_t)X & 15) == 0 && d >= 1 && d <= 256;
+}
+
 // workspace bytes of project_bf16 (prec LV_PREC_BF16) or project_fp8 (LV_PREC_FP8)
-size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d) {
+size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X) {
     if (prec == LV_PREC_FP8) {
         const int ldx = (int)round_up(D, 16);
         return round_up((int64_t)n * ldx, 256) + round_up((int64_t)d * ldx, 256) + round_up(4 * n, 256) +
                round_up(4 * (int64_t)d, 256);
     }
     const int ldx = (int)round_up(D, 8);
+    if (proj_fused_ok(X, D, d)) return round_up((int64_t)d * ldx * 2, 256);
     return round_up((int64_t)n * ldx * 2, 256) + round_up((int64_t)d * ldx * 2, 256);
 }
 
+static int project_bf16_fused(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
+                              void **ws, size_t *ws_bytes, int *status, cudaStream_t st) {
+    const int ldx = (int)round_up(D, 8);
+    int rc = ensure_ws(ws, ws_bytes, round_up((int64_t)d * ldx * 2, 256));
+    if (rc) return rc;
+    __nv_bfloat16 *Pb = reinterpret_cast<__nv_bfloat16 *>(*ws);
+    rc = launch_cast_bf16(P, d, D, Pb, ldx, st);
+    if (rc) return rc;
+    const int BN = (int)round_up(d, 16);
+    CUtensorMap tb, tx;
+    rc = make_map(&tb, Pb, d, D, ldx, BN, 2);
+    if (rc) return rc;
+    {
+        // X as float32 blocks of 128 rows x 64 columns (256-byte rows, no swizzle); rows >= n
+        // and columns >= D read as zeros
+        auto fn = encode_fn();
+        if (!fn) return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled unavailable");
+        cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)n};
+        cuuint64_t strides[1] = {(cuuint64_t)D * 4};
+        cuuint32_t box[2] = {64, (cuuint32_t)TC_BM};
+        cuuint32_t es[2] = {1, 1};
+        if (fn(&tx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled failed for the float32 operand");
+    }
+    PfParams pp;
+    pp.M = (int)n;
+    pp.K = D;
+    pp.N = d;
+    pp.BN = BN;
+    pp.Y = Y;
+    pp.ldy = ldy;
+    pp.status = status;
+    // fixed: the X staging ring, barriers and flags (256), the epilogue slabs (4 x 32 x 33 floats),
+    // alignment slack (1024)
+    const size_t stage = (size_t)(TC_BM + BN) * 128,
+                 fixed = (size_t)PF_XSTAGES * PF_XBYTES + 256 + 4 * 32 * 33 * 4 + 1024;
+    pp.stages = 3 * stage + fixed <= 227 * 1024 ? 3 : 2;
+    const size_t sm = pp.stages * stage + fixed;
+    int dev = 0, sms = 0;
+    LV_CUDA(cudaGetDevice(&dev));
+    LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = (n + TC_BM - 1) / TC_BM;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);
+    LV_CUDA(cudaFuncSetAttribute(proj_f32in_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    proj_f32in_kernel<<<grid, PF_THREADS, sm, st>>>(tx, tb, pp);
+    LV_CHECK_LAUNCH("proj_f32in_kernel");
+    return LV_OK;
+}
+
 // Y (n x ldy) = X P^T with bf16 operands on the tensor cores; columns d..ldy-1 zeroed.
-// The bf16 copies of X and P live in the caller's workspace (*ws, grown as needed).
+// X is converted to bf16 inside the GEMM when its rows are 16-byte aligned; otherwise the bf16
+// copies of X and P live in the caller's workspace (*ws, grown as needed).
 int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                  size_t *ws_bytes, int *status, cudaStream_t st) {
+    if (n >= (int64_t)1 << 31) return fail(LV_ERR_ARG, "tcgen05 GEMM: sizes too large");
+    if (proj_fused_ok(X, D, d)) return project_bf16_fused(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st);
     const int ldx = (int)round_up(D, 8);
     const size_t xb = round_up((int64_t)n * ldx * 2, 256), pb = round_up((int64_t)d * ldx * 2, 256);
     int rc = ensure_ws(ws, ws_bytes, xb + pb);

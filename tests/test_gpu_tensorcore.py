@@ -24,10 +24,13 @@ def lv():
 
 @pytest.mark.parametrize("n,D,d,ldy", [(300, 128, 32, 32), (1000, 768, 160, 160), (77, 200, 64, 80),
                                        (5000, 512, 128, 128), (129, 64, 16, 16), (1, 768, 160, 176),
-                                       (50, 100, 16, 16), (333, 77, 8, 8)])
+                                       (50, 100, 16, 16), (333, 77, 8, 8), (100000, 256, 64, 72),
+                                       (40000, 132, 256, 256), (3000, 64, 1, 4)])
 def test_projection_bf16(lv, n, D, d, ldy):
-    """D % 8 == 0 casts 8 floats per thread with 16-byte accesses; D = 100 and 77 take the
-    element-wise cast into padded rows."""
+    """D % 4 == 0: X is converted to bf16 inside the persistent GEMM (n = 100000 and 40000 give
+    every CTA several 128-row tiles, so both tensor-memory accumulators and the stage ring wrap;
+    D = 132 leaves a ragged K block, d = 1 and 256 the extreme widths); D = 77 takes the cast into
+    a bf16 copy first."""
     rng = np.random.default_rng(n + D + d)
     X = rng.standard_normal((n, D)).astype(np.float32)
     P = rng.standard_normal((d, D)).astype(np.float32)
