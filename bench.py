@@ -52,11 +52,16 @@ TRAFFIC_RECORDS = [
     # the same rule on a graph built on full-D LVQ-8 codes, L = 120: beam 2.733 GB + 8.8 MB, rerank 0.893 GB + 1.2 MB
     {"src_sha1": "9ea3355bc525640bcd5ba8c54cfb9beac141d1aa", "n": 1_000_000, "m": 10_000, "L": 120, "width": 2, "hash": 0, "projection": "bf16",
      "alpha": 1.02, "rule": 1, "graph": "full", "bytes": 2733314560 + 8754688 + 893092608 + 1217024},
-    # the default: that graph with the expansion budget max_hops = L, L = 128: beam 2.455 GB + 8.3 MB,
+    # that graph with the expansion budget max_hops = L, L = 128, one launch each: beam 2.455 GB + 8.3 MB,
     # rerank 0.954 GB + 1.2 MB
     {"src_sha1": "9ea3355bc525640bcd5ba8c54cfb9beac141d1aa", "n": 1_000_000, "m": 10_000, "L": 128, "max_hops": 128,
      "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
      "bytes": 2454921216 + 8330752 + 954114560 + 1157888},
+    # the default: the same, 7296 + 2704 queries as two sub-batches on two streams (four launches):
+    # beam 1.698 GB + 0.508 GB read, rerank 0.688 GB + 0.255 GB read, 9.8 MB written in all
+    {"src_sha1": "d570e3e1d2fda9ca3c092fe3121669cb1dd17e74", "n": 1_000_000, "m": 10_000, "L": 128, "max_hops": 128,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
+     "bytes": 3148564224 + 9814016},
 ]
 
 
@@ -1032,6 +1037,7 @@ def main():
 
     # -- per-query work (untimed run with counters)
     _, _, st = lv_search(L, mh, stats=True)
+    launches = idx.info()["last_search_kernels"]
     hops = float(st[:, 0].double().mean())
     scored = float(st[:, 1].double().mean())
     inf = idx.info()
@@ -1099,9 +1105,9 @@ def main():
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
                 "d2h_bytes_per_step": m * k * 8},
-        # per step: bf16 -> cast of A + fused float32-input projection GEMM, fp32 -> projection GEMM;
-        # then the query constants, the beam kernel and the rerank kernel
-        "gpu_launches": (5 if args.projection == "bf16" else 4) * args.steps,
+        # per step, as the library counts them: the projection (bf16: cast of A + the float32-input
+        # GEMM), the query constants, then the beam and rerank kernels of each sub-batch
+        "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L, mh),
                      "kernel": "beam_kernel<LvqIntScorer<3,8>,search> + rerank_kernel",

@@ -242,7 +242,7 @@ typedef struct {
     int32_t R;              /* graph max out-degree, 0 when no graph */
     int32_t entry;          /* search entry point, -1 when no graph */
     float mu2;              /* build-score constant sum_j (mui_j 2^-20)^2 */
-    int32_t reserved;
+    int32_t last_search_kernels; /* kernels the last leanvec_search call launched (0 before any) */
 } lv_index_info;
 
 int leanvec_index_info(const lv_index *idx, lv_index_info *out);
@@ -364,7 +364,13 @@ typedef struct {
  * unreduced query and the best k written, sorted by score (ties -> smaller id), to
  * ids/scores (m x ldo, device); the rest of each row (fewer than k reachable
  * candidates, or k < ldo) is filled with -1 / -inf.  Reported scores are the
- * decoded inner products (secondary after rerank, primary otherwise). */
+ * decoded inner products (secondary after rerank, primary otherwise).
+ * Streams: the work is ordered after `stream`'s earlier work and `stream`'s later
+ * work waits for all of it.  With rerank and m above one wave of the beam kernel's
+ * resident query slots (and not a multiple of it), the queries past the last whole
+ * wave run as a second launch on a stream of the index's own, forked from and joined
+ * back to `stream` by events (this also holds inside a CUDA-graph capture of
+ * `stream`); results do not depend on it.  Calls on one index are not thread-safe. */
 int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
                    const lv_search_params *params, const lv_query_desc *desc,
                    int32_t *ids, float *scores, int ldo, lv_search_stats *stats,

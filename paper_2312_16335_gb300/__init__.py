@@ -230,7 +230,7 @@ class Index:
     def info(self) -> dict:
         inf = LVIndexInfo()
         check(lib().leanvec_index_info(self._h, ctypes.byref(inf)))
-        return {f: getattr(inf, f) for f, _ in LVIndexInfo._fields_ if f != "reserved"}
+        return {f: getattr(inf, f) for f, _ in LVIndexInfo._fields_}
 
     def buffers(self) -> dict:
         ptrs = [ctypes.c_void_p() for _ in range(5)]

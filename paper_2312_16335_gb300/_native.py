@@ -29,7 +29,7 @@ class LVSearchParams(ctypes.Structure):
 class LVIndexInfo(ctypes.Structure):
     _fields_ = [("n", c_i64), ("D", c_i32), ("d", c_i32), ("primary_bits", c_i32),
                 ("secondary_bits", c_i32), ("primary_stride", c_i64), ("secondary_stride", c_i64),
-                ("R", c_i32), ("entry", c_i32), ("mu2", c_f32), ("reserved", c_i32)]
+                ("R", c_i32), ("entry", c_i32), ("mu2", c_f32), ("last_search_kernels", c_i32)]
 
 
 class LVFitOpts(ctypes.Structure):

@@ -50,6 +50,7 @@ int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float 
 int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                 size_t *ws_bytes, int *status, cudaStream_t st);
 size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X);
+bool project_bf16_fused_ok(const float *X, int D, int d);
 // tensor-core projection with bf16 or e4m3 (per-row scaled) operands
 static int project_tc(int prec, const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                       size_t *ws_bytes, int *status, cudaStream_t st) {
@@ -194,6 +195,9 @@ int leanvec_index_free(lv_index *idx) {
     cudaFree(idx->ws_c);
     cudaFree(idx->ws_cand);
     cudaFree(idx->bws);
+    if (idx->aux) cudaStreamDestroy(idx->aux);
+    if (idx->ev_fork) cudaEventDestroy(idx->ev_fork);
+    if (idx->ev_join) cudaEventDestroy(idx->ev_join);
     delete idx;
     return LV_OK;
 }
@@ -221,6 +225,7 @@ int leanvec_index_info(const lv_index *idx, lv_index_info *out) {
     out->R = idx->R;
     out->entry = idx->entry;
     out->mu2 = idx->mu2;
+    out->last_search_kernels = idx->last_kernels;
     return LV_OK;
 }
 
@@ -506,6 +511,12 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (rc) return rc;
     rc = ensure_ws((void **)&idx->ws_c, &idx->ws_c_bytes, sizeof(float4) * (size_t)m);
     if (rc) return rc;
+    idx->last_kernels = 0;
+    // kernels of the projection: padding copy / float32 GEMM: 1; bf16 with float32 X converted in
+    // the GEMM: cast of A + GEMM; otherwise casts of Q and A + GEMM
+    const int proj_kernels = idx->pbits == 32 || params->projection == LV_PREC_FP32 ? 1
+                             : params->projection == LV_PREC_BF16 && project_bf16_fused_ok(Q, idx->D, idx->d) ? 2
+                                                                                                                : 3;
     if (idx->pbits == 32) {
         rc = launch_pad_rows(Q, m, idx->D, idx->ws_q, ldq, st);
     } else if (params->projection != LV_PREC_FP32) {
@@ -548,6 +559,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.stats = reinterpret_cast<int2 *>(stats);
     p.status = idx->status;
     p.work = idx->status + 1;
+    p.slots = nullptr;
     p.Lcap = (int)round_up(u.L, 32);
     int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(4 * u.L)));
     if (hs & (hs - 1)) return fail(LV_ERR_ARG, "search: hash_slots must be a power of two");
@@ -578,20 +590,64 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         p.cand = idx->ws_cand;
         p.cand_n = idx->ws_cand + (size_t)m * p.ldc;
     }
-    LV_CUDA(cudaMemsetAsync(p.work, 0, sizeof(int), st));
+    LV_CUDA(cudaMemsetAsync(p.work, 0, 2 * sizeof(int), st));  // the work counters of both sub-batches
     const size_t smem = (size_t)(warps / p.T) * p.warp_smem;
     const int block = warps * 32;
-    if (params->event_begin) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_begin, st));
-    if (idx->pbits == 32) {
-        int ncw = (idx->pg.code_chunks + 31) / 32;
-        rc = launch_search_fp32(p, ncw, block, smem, idx->num_sms, st);
-    } else {
-        int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;  // codes + constants chunks over 4 lanes
-        rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
-                             : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
-        if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
+    auto beam = [&](const BeamParams &q, cudaStream_t s) -> int {
+        if (idx->pbits == 32) return launch_search_fp32(q, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, s);
+        const int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;  // codes + constants chunks over 4 lanes
+        return idx->pbits == 8 ? launch_search_lvq8(q, nc, block, smem, idx->num_sms, s)
+                               : launch_search_lvq4(q, nc, block, smem, idx->num_sms, s);
+    };
+    // Sub-batches: with rerank, the queries beyond the last whole wave of resident query slots
+    // (slots = blocks per SM x SMs x queries per block) form a second batch launched on a second
+    // stream.  The first batch's waves end together; its rerank then runs beside the second
+    // batch's partial wave instead of after it.  Every query is computed exactly as in one launch.
+    int64_t mA = m;
+    if (rerank) {
+        int64_t slots = 0;
+        BeamParams q = p;
+        q.slots = &slots;
+        rc = beam(q, st);
+        if (rc) return rc;
+        if (slots > 0 && m > slots && m % slots) mA = m / slots * slots;
     }
-    if (rc) return rc;
+    if (mA < m && !idx->aux) {
+        LV_CUDA(cudaStreamCreateWithFlags(&idx->aux, cudaStreamNonBlocking));
+        LV_CUDA(cudaEventCreateWithFlags(&idx->ev_fork, cudaEventDisableTiming));
+        LV_CUDA(cudaEventCreateWithFlags(&idx->ev_join, cudaEventDisableTiming));
+    }
+    idx->last_kernels = proj_kernels + 1 + (mA == m ? 1 : 2) * (rerank ? 2 : 1);
+    if (params->event_begin) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_begin, st));
+    if (mA == m) {
+        rc = beam(p, st);
+        if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
+        if (rc) return rc;
+    } else {
+        BeamParams pa = p, pb = p;
+        pa.m = mA;
+        pb.m = m - mA;
+        pb.qp = p.qp + mA * ldq;
+        pb.qconst = p.qconst + mA;
+        if (p.desc) pb.desc = p.desc + mA;
+        pb.Q = p.Q + mA * p.D;
+        pb.ids = p.ids + mA * ldo;
+        pb.scores = p.scores + mA * ldo;
+        if (p.stats) pb.stats = p.stats + mA;
+        pb.cand = p.cand + mA * p.ldc;
+        pb.cand_n = p.cand_n + mA;
+        pb.work = p.work + 1;
+        LV_CUDA(cudaEventRecord(idx->ev_fork, st));
+        LV_CUDA(cudaStreamWaitEvent(idx->aux, idx->ev_fork, 0));
+        rc = beam(pa, st);
+        if (!rc) rc = beam(pb, idx->aux);
+        if (!rc) rc = launch_rerank(pa, idx->num_sms, st);
+        if (!rc) rc = launch_rerank(pb, idx->num_sms, idx->aux);
+        // join even after a failed launch, so that the caller's stream orders after the second one
+        LV_CUDA(cudaEventRecord(idx->ev_join, idx->aux));
+        LV_CUDA(cudaStreamWaitEvent(st, idx->ev_join, 0));
+        if (rc) return rc;
+    }
     if (params->event_end) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_end, st));
     return LV_OK;
 }

@@ -66,6 +66,8 @@ struct BeamParams {
     int W;      // search width: parents expanded per round (1..4, W * R <= 256)
     int T;      // warps per query (1, 2 or 4; divides W); Rcap = T * (W / T * R rounded up to 32)
     int warp_smem;  // shared bytes of one query (one team of T warps)
+    int64_t *slots;  // host side: when set, the search launchers report the query slots one
+                     // launch keeps resident (blocks per SM x SMs x teams per block) and launch nothing
 };
 
 constexpr int WMAX = 4;

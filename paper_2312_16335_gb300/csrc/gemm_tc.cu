@@ -747,6 +747,7 @@ int ensure_ws(void **p, size_t *have, size_t want);
 static bool proj_fused_ok(const float *X, int D, int d) {
     return D % 4 == 0 && ((uintptr_t)X & 15) == 0 && d >= 1 && d <= 256;
 }
+bool project_bf16_fused_ok(const float *X, int D, int d) { return proj_fused_ok(X, D, d); }
 
 // workspace bytes of project_bf16 (prec LV_PREC_BF16) or project_fp8 (LV_PREC_FP8)
 size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X) {

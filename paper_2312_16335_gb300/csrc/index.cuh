@@ -30,6 +30,10 @@ struct lv_index {
     // build workspace
     void *bws = nullptr;
     size_t bws_bytes = 0;
+    // second stream of the search's sub-batch, and its fork / join events (created on first use)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int last_kernels = 0;  // kernels launched by the last search call
 };
 
 namespace lv {

@@ -12,6 +12,10 @@ static int go_w(const BeamParams &p, int block, size_t smem, int num_sms, cudaSt
     LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
     if (per_sm < 1) return fail(LV_ERR_CAPACITY, "search: beam/visited capacity does not fit in shared memory");
     const int teams = block / 32 / p.T;  // queries served at once by one block
+    if (p.slots) {
+        *p.slots = (int64_t)per_sm * num_sms * teams;
+        return LV_OK;
+    }
     int64_t want = (p.m + teams - 1) / teams;
     int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
     k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);

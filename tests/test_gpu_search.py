@@ -286,3 +286,30 @@ def test_cuda_graph_replay_and_autotune(lv, pb):
         torch.cuda.synchronize()
         assert torch.equal(ids, eager[0])
         assert torch.equal(sc, eager[1])
+
+
+def test_sub_batches_match_small_batches(lv):
+    """m = 12000 is above one wave of resident query slots and not a multiple of it: the queries
+    past the last whole wave run as a second launch on a second stream.  Every query is computed
+    independently, so ids, scores and counters equal those of batches of 100 (one launch each),
+    also when the search is captured in a CUDA graph; and the ids agree with the oracle."""
+    sub = small_problem(oracle, n=3000, D=64, d=16, m=12000, seed=11)
+    idx = gpu_index(lv, sub)
+    Q, P = t(sub["Q"]), t(sub["P"])
+    ids, sc, st = idx.search(Q, P, k=10, L=48, rerank=48, width=2, stats=True)
+    # fp32 projection, query constants, then beam + rerank for each of the two sub-batches
+    assert idx.info()["last_search_kernels"] == 1 + 1 + 2 * 2
+    parts = [idx.search(Q[s:s + 100].contiguous(), P, k=10, L=48, rerank=48, width=2, stats=True)
+             for s in range(0, 12000, 100)]
+    assert idx.info()["last_search_kernels"] == 1 + 1 + 2
+    torch.testing.assert_close(ids, torch.cat([p[0] for p in parts]), rtol=0, atol=0)
+    torch.testing.assert_close(sc, torch.cat([p[1] for p in parts]), rtol=0, atol=0)
+    torch.testing.assert_close(st, torch.cat([p[2] for p in parts]), rtol=0, atol=0)
+    g = lv.SearchGraph(idx, Q, P, k=10, L=48, rerank=48, width=2)
+    gi, gs = g.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(gi, ids, rtol=0, atol=0)
+    torch.testing.assert_close(gs, sc, rtol=0, atol=0)
+    ref = oracle.search(sub["graph"], sub["entry"], _qp(sub), k=10, L=48, rerank=48, prim=sub["prim"],
+                        sec=sub["sec"], qs=sub["Q"].astype(np.float64), width=2)
+    assert (ids.cpu().numpy() == ref["ids"]).mean() >= 0.99
