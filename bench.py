@@ -823,6 +823,79 @@ def bench_kernels(args, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_samples(args, dev):
+    """Sample sizes of the fit (the paper's appendix study): on the ood-1M-512 workload, the
+    second moments, the LeanVec-OOD projections (Frank-Wolfe A, B; eigenvector search P) and the
+    LeanVec-ID projection are learned once from the full learning sets (1M database vectors,
+    10k learning queries) and again from the first n_s rows of each (the rows are independent
+    draws of the mixture, so these are uniform samples); reported are
+    the relative Frobenius errors of n_s^-1 K and of the projectors A^T A, B^T B, P^T P against the
+    full-set ones, and the exhaustive-search recall@10 of <A q, B x> on 10k held-out OOD test
+    queries (ground truth: exact inner products) for each sample size."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    n, m, D, d = args.n, args.m, 512, 128
+    X, Q, Ql = workloads.make_workload_torch("anisotropic", n, m, D, 1000, cfg=3, device=dev, ood=True, m_learn=m)
+    truth = ground_truth(X, Q, 10)
+
+    def rel(a, b):
+        return float((a.double() - b.double()).norm() / b.double().norm())
+
+    def projector(M):
+        M = M.double()
+        return M.T @ M
+
+    def bf_recall(A, B):
+        """recall@10 of the exhaustive search by <A q, B x> (float32 projections by the library)"""
+        qa = lv.leanvec_project(Q, A)
+        best_s = torch.full((Q.shape[0], 10), -float("inf"), device=dev)
+        best_i = torch.full((Q.shape[0], 10), -1, dtype=torch.int64, device=dev)
+        for s0 in range(0, n, 131072):
+            xb = lv.leanvec_project(X[s0:s0 + 131072].contiguous(), B)
+            S = qa @ xb.T
+            v, i = torch.topk(S, 10, dim=1)
+            cs, ci = torch.cat([best_s, v], 1), torch.cat([best_i, i + s0], 1)
+            o = torch.topk(cs, 10, dim=1)
+            best_s, best_i = o.values, torch.gather(ci, 1, o.indices)
+        return recall_at(best_i, truth, 10)
+
+    def fit_all(nx, nq):
+        Xs, Qs = X[:nx].contiguous(), Ql[:nq].contiguous()  # rows are i.i.d. draws: the first rows are a sample
+        KX = lv.leanvec_second_moment(Xs, precision=lv.PREC_BF16) / nx
+        KQ = lv.leanvec_second_moment(Qs, precision=lv.PREC_BF16) / nq
+        A, B, rf = lv.leanvec_fit_ood(Xs, Qs, d, method=lv.FIT_FW, precision=lv.PREC_BF16)
+        P, _, re = lv.leanvec_fit_ood(Xs, Qs, d, method=lv.FIT_ES, precision=lv.PREC_BF16)
+        I = lv.leanvec_fit_id(Xs, d, precision=lv.PREC_BF16)
+        return dict(KX=KX, KQ=KQ, A=A, B=B, P=P, I=I, fw_iters=rf["iterations"], es_beta=re["beta"])
+
+    t0 = time.time()
+    full = fit_all(n, m)
+    log(f"full-set fit {time.time() - t0:.1f}s")
+    ref = {k: projector(full[k]) for k in ("A", "B", "P", "I")}
+    res = {"full": {"recall_fw": bf_recall(full["A"], full["B"]), "recall_es": bf_recall(full["P"], full["P"]),
+                    "recall_id": bf_recall(full["I"], full["I"]), "fw_iterations": full["fw_iters"],
+                    "es_beta": full["es_beta"]}}
+    log(f"full: {res['full']}")
+    for ns in (D, 2 * D, 4 * D, 8 * D, 10_000, 100_000, 1_000_000):
+        nx, nq = min(ns, n), min(ns, m)
+        f = fit_all(nx, nq)
+        r = {"n_x": nx, "n_q": nq,
+             "err_KQ": rel(f["KQ"], full["KQ"]), "err_KX": rel(f["KX"], full["KX"]),
+             "err_AtA": rel(projector(f["A"]), ref["A"]), "err_BtB": rel(projector(f["B"]), ref["B"]),
+             "err_PtP": rel(projector(f["P"]), ref["P"]), "err_ID": rel(projector(f["I"]), ref["I"]),
+             "recall_fw": bf_recall(f["A"], f["B"]), "recall_es": bf_recall(f["P"], f["P"]),
+             "recall_id": bf_recall(f["I"], f["I"]), "fw_iterations": f["fw_iters"], "es_beta": f["es_beta"]}
+        res[ns] = r
+        log(f"n_s={ns}: {r}")
+    out = {"metric": "relative Frobenius errors of the sample second moments and learned projectors, and the "
+                     "exhaustive-search recall@10 of <A q, B x>, vs the learning sample size n_s",
+           "workload": f"ood-{n // 1000}k-512: {m} learning + {m} held-out OOD queries, d = {d}; full sets = "
+                       f"{n} database vectors and {m} learning queries; n_s rows of each (queries capped at {m})",
+           "results": res, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def bench_dsweep(args, dev):
     """Target-d selection on the id-1M-768 workload: one graph (the id workload's, see --graph), then
     for each primary dimension d the LeanVec-ID projection of that size, its primaries and
@@ -904,21 +977,22 @@ def main():
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
     ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy",
-                                                      "l2", "kernels"],
+                                                      "l2", "kernels", "samples"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
                          "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
                          "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph; "
                          "buildstudy: graph build on primaries vs on full-D LVQ-8 codes; "
                          "l2: Euclidean 1M x 960 (gist-960-1M shape), LeanVec vs FP32 at recall 0.90; "
-                         "kernels: the offline / auxiliary kernels alone against their rooflines")
+                         "kernels: the offline / auxiliary kernels alone against their rooflines; "
+                         "samples: fit sample-size study (second moments, projectors, exhaustive-search recall)")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
     sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
              "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
              "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000),
-             "kernels": (1_000_000, 10_000)}[args.workload]
+             "kernels": (1_000_000, 10_000), "samples": (1_000_000, 10_000)}[args.workload]
     args.n = args.n or sizes[0]
     args.m = args.m or sizes[1]
     l2 = args.workload == "l2"
@@ -959,6 +1033,9 @@ def main():
         return
     if args.workload == "kernels":
         bench_kernels(args, dev)
+        return
+    if args.workload == "samples":
+        bench_samples(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
