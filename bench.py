@@ -897,9 +897,11 @@ def bench_samples(args, dev):
 
 
 def bench_dsweep(args, dev):
-    """Target-d selection on the id-1M-768 workload: one graph (the id workload's, see --graph), then
-    for each primary dimension d the LeanVec-ID projection of that size, its primaries and
-    secondaries, the smallest grid L with recall@10 >= 0.90 (rerank = L) and the QPS there."""
+    """Target-d selection on the id-1M-768 workload through the library's autotuner
+    (autotune_target_d): one graph (the id workload's, see --graph), then for each primary
+    dimension d the LeanVec-ID projection of that size (100k-row sample), its primaries and
+    secondaries, the smallest L with recall@10 >= 0.90 (rerank = L, max_hops = ceil(c L) for
+    the hop factor c) and the QPS there."""
     S = setup(args, dev, with_base=False)
     lv, X, Q, truth = S["lv"], S["X"], S["Q"], S["truth"]
     graph, entry = S["graph"], S["entry"]
@@ -907,30 +909,23 @@ def bench_dsweep(args, dev):
     sub = torch.from_numpy(workloads.subsample_rows(args.n, min(args.n, 100_000), cfg=2)).to(dev)
     Xs = X.index_select(0, sub).contiguous()
     proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
-    res = {}
-    for d in (64, 96, 128, 160, 192, 224, 240):
-        A = lv.leanvec_fit_id(Xs, d)
-        idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8).set_graph(graph, entry)
-        L, trace = calibrate(lambda L: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width,
-                                                  projection=proj)[0], truth, 10)
-        r = {"L_for_0.90": L, "recall_trace": trace[-3:]}
-        if L:
-            nst = max(5, args.steps // 5)
-            ms, _ = time_steps(lambda ev: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=proj),
-                               nst, 2)
-            _, _, st = idx.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=proj, stats=True)
-            r.update(qps=args.m * nst / (ms / 1e3), hops=float(st[:, 0].float().mean()),
-                     scored=float(st[:, 1].float().mean()), primary_stride=idx.info()["primary_stride"])
-        res[d] = r
+
+    def fit(_, d):
+        P = lv.leanvec_fit_id(Xs, d)
+        return P, P
+
+    tune = lv.autotune_target_d(X, Q, truth, graph, entry, ds=(64, 96, 128, 160, 192, 224, 240), k=10,
+                                target=TARGET, L_grid=tuple(L_GRID), fit=fit, width=args.width, projection=proj,
+                                hop_factor=args.hop_factor)
+    res = {r["d"]: {k: v for k, v in r.items() if k != "A"} for r in tune["table"]}
+    for d, r in res.items():
         log(f"d={d}: {r}")
-        del idx
-        torch.cuda.empty_cache()
-    ok = {d: r for d, r in res.items() if r.get("qps")}
-    best = max(ok, key=lambda d: ok[d]["qps"]) if ok else None
+    best = tune["best"]["d"] if tune["best"] else None
     out = {"metric": "QPS at 10-recall@10 = 0.90 vs the primary dimension d (one graph, built on "
                      + ("full-D LVQ-8 codes)" if args.graph == "full" else "the d = 160 primaries)"),
            "workload": f"id-{args.n // 1000}k-{args.D}, {args.m} ID queries, LeanVec-ID LVQ-8 primaries of d dims "
-                       f"+ LVQ-8 secondaries, width {args.width}, {args.projection} projection",
+                       f"+ LVQ-8 secondaries, width {args.width}, {args.projection} projection, "
+                       f"max_hops = ceil({args.hop_factor} L)",
            "results": res, "best_d": best, "data": "synthetic"}
     print(json.dumps(out), flush=True)
 

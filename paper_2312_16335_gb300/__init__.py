@@ -18,7 +18,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "SearchGraph", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "autotune_target_d", "SearchGraph", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
@@ -394,6 +394,63 @@ def autotune(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, k: int, L:
             table.append({"warps_per_block": w, "hash_slots": h, "ms": ms})
             if best is None or ms < best["ms"]:
                 best = table[-1]
+    return {"best": best, "table": table}
+
+
+def _recall(ids: torch.Tensor, truth: torch.Tensor, k: int) -> float:
+    a = ids[:, :k].long()
+    hit = (a.unsqueeze(2) == truth[:, :k].long().unsqueeze(1)).any(dim=2) & (a >= 0)
+    return float(hit.float().sum().item()) / (k * ids.shape[0])
+
+
+def autotune_target_d(X: torch.Tensor, Q: torch.Tensor, truth: torch.Tensor, graph: torch.Tensor, entry: int,
+                      ds=(64, 96, 128, 160, 192, 224, 256), k: int = 10, target: float = 0.90,
+                      L_grid=(16, 24, 32, 48, 64, 80, 96, 112, 128, 144, 160, 192, 224, 256, 320, 384, 448, 512),
+                      fit=None, primary_bits: int = 8, secondary_bits: int = 8, width: int = 2,
+                      projection: int = PREC_BF16, hop_factor: float = 0.0, reps: int = 5) -> dict:
+    """Target dimensionality d (the paper picks, per dataset, the d of highest QPS at the target
+    accuracy on a fixed graph, App. D.2): for each d of `ds`, learn the projection with `fit(X, d)`
+    (default: LeanVec-ID on X), encode X, search the validation queries Q on the given graph for
+    the smallest L of `L_grid` whose recall@k against `truth` (m x k ids of the exact neighbours,
+    computed by the caller) reaches `target`, with max_hops = ceil(hop_factor L) (0: none), and
+    time that search with CUDA events.  Returns {"best": entry of the fastest d, "table": [...]};
+    an entry holds d, L, max_hops, recall, qps and the projection A (for LeanVec-ID A = B)."""
+    import math
+    fit = fit or (lambda X_, d_: (lambda P: (P, P))(leanvec_fit_id(X_, d_, precision=PREC_BF16)))
+    dev = X.device
+    m = Q.shape[0]
+    table, best = [], None
+    for d in ds:
+        if d > X.shape[1]:
+            continue
+        A, B = fit(X, d)
+        idx = Index(dev).encode(X, B, primary_bits, secondary_bits, precision=PREC_BF16).set_graph(graph, entry)
+        chosen = None
+        for L in L_grid:
+            if L < k:
+                continue
+            mh = int(math.ceil(hop_factor * L - 1e-9)) if hop_factor else 0
+            r = _recall(idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=width, projection=projection)[0],
+                        truth, k)
+            if r >= target:
+                chosen = (L, mh, r)
+                break
+        row = {"d": d, "L": None, "max_hops": None, "recall": None, "qps": None}
+        if chosen:
+            L, mh, r = chosen
+            run = lambda: idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=width, projection=projection)
+            run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                run()
+            e1.record()
+            torch.cuda.synchronize()
+            row.update(L=L, max_hops=mh, recall=r, qps=m * reps / (e0.elapsed_time(e1) / 1e3), A=A)
+            if best is None or row["qps"] > best["qps"]:
+                best = row
+        table.append(row)
+        idx.close()
     return {"best": best, "table": table}
 
 

@@ -313,3 +313,24 @@ def test_sub_batches_match_small_batches(lv):
     ref = oracle.search(sub["graph"], sub["entry"], _qp(sub), k=10, L=48, rerank=48, prim=sub["prim"],
                         sec=sub["sec"], qs=sub["Q"].astype(np.float64), width=2)
     assert (ids.cpu().numpy() == ref["ids"]).mean() >= 0.99
+
+
+def test_autotune_target_d(lv):
+    """The target-d autotuner: for each d, the smallest L of the grid whose recall@10 reaches the
+    target under the given graph, and the fastest such d; recall checked against the oracle's
+    brute force (the caller's ground truth)."""
+    sub = small_problem(oracle, n=3000, D=64, d=16, m=500, seed=12)
+    truth, _ = oracle.bruteforce(sub["X"], sub["Q"], 10)
+    X, Q = t(sub["X"]), t(sub["Q"])
+    tune = lv.autotune_target_d(X, Q, torch.from_numpy(truth).cuda(), t(sub["graph"]), sub["entry"], ds=(8, 16, 32),
+                                target=0.5, L_grid=(16, 32, 64, 128, 256), projection=lv.PREC_FP32, width=1)
+    assert [r["d"] for r in tune["table"]] == [8, 16, 32]
+    for r in tune["table"]:
+        if r["L"] is not None:
+            assert r["recall"] >= 0.5 and r["qps"] > 0
+    assert tune["best"] is not None and tune["best"]["qps"] == max(r["qps"] or 0 for r in tune["table"])
+    # the reported recall is that of the search at the chosen L, recomputed here
+    b = tune["best"]
+    idx = lv.Index(0).encode(X, b["A"], 8, 8, precision=lv.PREC_BF16).set_graph(t(sub["graph"]), sub["entry"])
+    ids = idx.search(Q, b["A"], k=10, L=b["L"], rerank=b["L"], width=1)[0].cpu().numpy()
+    assert abs(oracle.recall(ids, truth, 10) - b["recall"]) < 1e-6
