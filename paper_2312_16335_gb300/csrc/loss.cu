@@ -48,11 +48,10 @@ __device__ __forceinline__ void residual_tile(const float *__restrict__ P, const
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < PK; ++kk) {
-                float a[4], b[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+                // one 16-byte shared load per operand (rows of PT + 4 floats keep them aligned)
+                const float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+                const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+                const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -71,26 +70,32 @@ __device__ __forceinline__ void residual_tile(const float *__restrict__ P, const
     __syncthreads();
 }
 
-// For the row tile of this block (rows of P): loop over all column tiles, accumulate
-//   loss partial (sum r^2, when lossp != NULL) and  Out[rows] += R * Colp  (PT x d).
+// For the row tile blockIdx.x of this block (rows of P): loop over the column tiles of column
+// split blockIdx.y (columns [y cs, (y + 1) cs)), accumulate the loss partial (sum r^2 into
+// lossp[y * gridDim.x + x], when lossp != NULL) and Out_y[rows] = R * Colp over the split
+// (PT x d, split y's partial at Out + y * nr * d).
+template <bool OUT>
 __global__ void __launch_bounds__(256) pair_sweep_kernel(const float *__restrict__ P, const float *__restrict__ Pp,
                                                          int64_t nr, const float *__restrict__ Qm,
                                                          const float *__restrict__ Qp, int64_t nc, int D, int d,
-                                                         double *__restrict__ lossp, float *__restrict__ Out) {
-    __shared__ float As[PK][PT + 4];
-    __shared__ float Bs[PK][PT + 4];
+                                                         int64_t cs, double *__restrict__ lossp,
+                                                         float *__restrict__ Out) {
+    __shared__ __align__(16) float As[PK][PT + 4];
+    __shared__ __align__(16) float Bs[PK][PT + 4];
     __shared__ float Rs[PT][PT + 1];
     __shared__ double red[256];
     const int64_t r0 = (int64_t)blockIdx.x * PT;
     // Out tile accumulators: thread owns rows (threadIdx.x / 16) * 4 + u, cols (threadIdx.x % 16) + 16 w
     const int orow = (threadIdx.x >> 4) * 4, ocol = threadIdx.x & 15;
-    float o[4][DMAX / 16];
+    constexpr int OW = OUT ? DMAX / 16 : 1;  // the loss-only sweep keeps no output accumulators
+    float o[4][OW];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int w = 0; w < DMAX / 16; ++w) o[u][w] = 0.f;
+        for (int w = 0; w < OW; ++w) o[u][w] = 0.f;
     double ls = 0.0;
-    for (int64_t c0 = 0; c0 < nc; c0 += PT) {
+    const int64_t cbeg = (int64_t)blockIdx.y * cs, cend = min(nc, cbeg + cs);
+    for (int64_t c0 = cbeg; c0 < cend; c0 += PT) {
         residual_tile(P, Pp, r0, nr, Qm, Qp, c0, nc, D, d, As, Bs, Rs);
         if (lossp) {
             for (int t = threadIdx.x; t < PT * PT; t += 256) {
@@ -98,17 +103,17 @@ __global__ void __launch_bounds__(256) pair_sweep_kernel(const float *__restrict
                 ls += (double)r * (double)r;
             }
         }
-        if (Out) {
+        if (OUT) {
             // Out[r][c] += sum_k Rs[r][k] * Qp[c0 + k][c]
             for (int k = 0; k < PT; ++k) {
                 const int64_t ck = c0 + k;
-                if (ck >= nc) break;
+                if (ck >= cend) break;
                 const float *qrow = Qp + ck * d;
                 float rv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) rv[u] = Rs[orow + u][k];
 #pragma unroll
-                for (int w = 0; w < DMAX / 16; ++w) {
+                for (int w = 0; w < OW; ++w) {
                     const int c = ocol + 16 * w;
                     if (c < d) {
                         const float q = qrow[c];
@@ -120,15 +125,16 @@ __global__ void __launch_bounds__(256) pair_sweep_kernel(const float *__restrict
         }
         __syncthreads();
     }
-    if (Out) {
+    if (OUT) {
+        float *const Oy = Out + (int64_t)blockIdx.y * nr * d;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t r = r0 + orow + u;
             if (r >= nr) continue;
 #pragma unroll
-            for (int w = 0; w < DMAX / 16; ++w) {
+            for (int w = 0; w < OW; ++w) {
                 const int c = ocol + 16 * w;
-                if (c < d) Out[r * d + c] = o[u][w];
+                if (c < d) Oy[r * d + c] = o[u][w];
             }
         }
     }
@@ -139,13 +145,20 @@ __global__ void __launch_bounds__(256) pair_sweep_kernel(const float *__restrict
             if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
             __syncthreads();
         }
-        if (threadIdx.x == 0) lossp[blockIdx.x] = red[0];
+        if (threadIdx.x == 0) lossp[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
     }
 }
 
-// out (d x D) = scale * M^T Y with M (rows x d), Y (rows x D): column blocks of D, rows looped
-__global__ void __launch_bounds__(256) tgemm_kernel(const float *__restrict__ M, const float *__restrict__ Y, int64_t rows,
-                                                    int d, int D, float scale, float *__restrict__ out) {
+// out_y (d x D) = scale * M^T Y over the rows [y rs, (y + 1) rs) of M (rows x d) and Y (rows x D),
+// y = blockIdx.y (split y's partial at out + y * d * D): column blocks of D, rows looped
+__global__ void __launch_bounds__(256) tgemm_kernel(const float *__restrict__ M, const float *__restrict__ Y,
+                                                    int64_t rows_total, int64_t rs, int d, int D, float scale,
+                                                    float *__restrict__ out) {
+    const int64_t rbeg = (int64_t)blockIdx.y * rs;
+    const int64_t rows = max((int64_t)0, min(rows_total - rbeg, rs));
+    M += rbeg * d;
+    Y += rbeg * D;
+    out += (int64_t)blockIdx.y * d * D;
     const int c = blockIdx.x * 64 + (threadIdx.x & 63);
     const int r0 = (threadIdx.x >> 6);  // 4 row groups of d
     __shared__ float Ms[32][DMAX];
@@ -183,16 +196,40 @@ __global__ void __launch_bounds__(256) tgemm_kernel(const float *__restrict__ M,
     }
 }
 
+// out[i] = sum_y part[y * len + i] for y = 0 .. splits - 1, in that order
+__global__ void split_sum_kernel(const float *__restrict__ part, int splits, int64_t len, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float v = 0.f;
+    for (int y = 0; y < splits; ++y) v += part[(int64_t)y * len + i];
+    out[i] = v;
+}
+
+// splits of a sweep with `tiles` row tiles over `ncols` columns: about 4 blocks per SM in all,
+// each split at least one column tile
+static int sweep_splits(int64_t tiles, int64_t ncols) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (4 * (int64_t)sms + tiles - 1) / tiles;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (ncols + PT - 1) / PT));
+}
+
+static int64_t split_len(int64_t total, int splits, int64_t align) {
+    return ((total + splits - 1) / splits + align - 1) / align * align;
+}
+
 struct PairWork {
     float *Qp = nullptr, *Xp = nullptr, *U = nullptr, *V = nullptr;
+    float *Up = nullptr, *Gp = nullptr;  // split partials of U and of the gradient GEMMs
     double *part = nullptr;
 };
 
 static int pair_prepare(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
                         int d, PairWork &w, bool grads, cudaStream_t st) {
+    const int64_t tiles = (m + PT - 1) / PT;
     if (tmp_alloc((void **)&w.Qp, sizeof(float) * (size_t)m * d, st) ||
         tmp_alloc((void **)&w.Xp, sizeof(float) * (size_t)n * d, st) ||
-        tmp_alloc((void **)&w.part, sizeof(double) * (size_t)((m + PT - 1) / PT), st))
+        tmp_alloc((void **)&w.part, sizeof(double) * (size_t)(tiles * sweep_splits(tiles, n)), st))
         return fail(LV_ERR_OOM, "ood_loss: allocation failed");
     if (grads && (tmp_alloc((void **)&w.U, sizeof(float) * (size_t)m * d, st) ||
                   tmp_alloc((void **)&w.V, sizeof(float) * (size_t)n * d, st)))
@@ -203,6 +240,8 @@ static int pair_prepare(const float *A, const float *B, const float *Q, int64_t 
 }
 
 static void pair_free(PairWork &w, cudaStream_t st) {
+    tmp_free(w.Up, st);
+    tmp_free(w.Gp, st);
     tmp_free(w.Qp, st);
     tmp_free(w.Xp, st);
     tmp_free(w.U, st);
@@ -225,13 +264,15 @@ int leanvec_ood_loss_fwd(const float *A, const float *B, const float *Q, int64_t
     PairWork w;
     int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, false, st);
     const int nb = (int)((m + PT - 1) / PT);
-    std::vector<double> part(nb);
+    const int sp = sweep_splits(nb, n);  // column splits of the database
+    std::vector<double> part((size_t)nb * sp);
     if (rc == LV_OK) {
-        pair_sweep_kernel<<<nb, 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d, w.part, nullptr);
+        pair_sweep_kernel<false><<<dim3(nb, sp), 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d, split_len(n, sp, PT),
+                                                               w.part, nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "pair_sweep_kernel");
     }
-    if (rc == LV_OK && (cudaMemcpyAsync(part.data(), w.part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st) !=
+    if (rc == LV_OK && (cudaMemcpyAsync(part.data(), w.part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st) !=
                             cudaSuccess ||
                         cudaStreamSynchronize(st) != cudaSuccess))
         rc = fail(LV_ERR_CUDA, "ood_loss_fwd: reduction copy failed");
@@ -252,13 +293,31 @@ int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t
     cudaStream_t st = (cudaStream_t)stream;
     PairWork w;
     int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, true, st);
+    // U = R X' (query tiles, the database split in column ranges whose partials are summed in
+    // order), V = R^T Q' (database tiles: rows X, cols Q, residual sign unchanged); the gradient
+    // GEMMs split their rows the same way
+    const int64_t tq = (m + PT - 1) / PT, tx = (n + PT - 1) / PT;
+    const int su = sweep_splits(tq, n), sv = sweep_splits(tx, m);
+    const int cb = (D + 63) / 64;
+    const int sa = sweep_splits(cb, m), sb = sweep_splits(cb, n);
+    if (rc == LV_OK && (tmp_alloc((void **)&w.Up, sizeof(float) * (size_t)std::max(su, sv) * std::max(m, n) * d, st) ||
+                        tmp_alloc((void **)&w.Gp, sizeof(float) * (size_t)std::max(sa, sb) * d * D, st)))
+        rc = fail(LV_ERR_OOM, "ood_loss_bwd: allocation failed");
     if (rc == LV_OK) {
-        // U = R X' (query tiles), V = R^T Q' (database tiles: rows X, cols Q, residual sign unchanged)
-        pair_sweep_kernel<<<(unsigned)((m + PT - 1) / PT), 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d, nullptr, w.U);
-        pair_sweep_kernel<<<(unsigned)((n + PT - 1) / PT), 256, 0, st>>>(X, w.Xp, n, Q, w.Qp, m, D, d, nullptr, w.V);
         const float c = (float)(-2.0 * (double)scale / ((double)n * (double)m));
-        tgemm_kernel<<<(D + 63) / 64, 256, 0, st>>>(w.U, Q, m, d, D, c, gA);
-        tgemm_kernel<<<(D + 63) / 64, 256, 0, st>>>(w.V, X, n, d, D, c, gB);
+        auto sum = [&](const float *part, int splits, int64_t len, float *out) {
+            split_sum_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, splits, len, out);
+        };
+        pair_sweep_kernel<true><<<dim3((unsigned)tq, su), 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d,
+                                                                        split_len(n, su, PT), nullptr, w.Up);
+        sum(w.Up, su, m * d, w.U);
+        pair_sweep_kernel<true><<<dim3((unsigned)tx, sv), 256, 0, st>>>(X, w.Xp, n, Q, w.Qp, m, D, d,
+                                                                        split_len(m, sv, PT), nullptr, w.Up);
+        sum(w.Up, sv, n * d, w.V);
+        tgemm_kernel<<<dim3(cb, sa), 256, 0, st>>>(w.U, Q, m, split_len(m, sa, 32), d, D, c, w.Gp);
+        sum(w.Gp, sa, (int64_t)d * D, gA);
+        tgemm_kernel<<<dim3(cb, sb), 256, 0, st>>>(w.V, X, n, split_len(n, sb, 32), d, D, c, w.Gp);
+        sum(w.Gp, sb, (int64_t)d * D, gB);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "ood_loss_bwd kernels");
     }
