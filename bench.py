@@ -1036,7 +1036,8 @@ def main():
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
                 f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "
                 f"alpha={args.alpha} ({'unit-norm L2' if args.rule else 'alpha-scaled IP'} prune rule), built on "
-                f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L")
+                f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L, "
+                f"{'max_hops=ceil(%g L)' % args.hop_factor if args.hop_factor else 'no expansion budget'}")
     if args.secondary == "fp16":
         workload = workload.replace("LVQ-8 primary + LVQ-8 secondary", "LVQ-8 primary + FP16 secondary")
     metric = "QPS at 10-recall@10=0.90, LeanVec vs full-D FP32 graph search; HBM GB/s"
