@@ -732,7 +732,10 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                             int lo = 0, hi = size;
                             while (lo < hi) {
                                 const int mid = (lo + hi) >> 1;
-                                if (key_better(bS[mid], bI[mid] & ~(int)EXPANDED, s, id))
+                                const float ms = bS[mid];
+                                bool better = ms > s;
+                                if (ms == s) better = (bI[mid] & ~(int)EXPANDED) < id;
+                                if (better)
                                     lo = mid + 1;
                                 else
                                     hi = mid;

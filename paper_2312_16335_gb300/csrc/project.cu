@@ -10,8 +10,8 @@ constexpr int PT_M = 64, PT_N = 64, PT_K = 32;
 __global__ void __launch_bounds__(256) project_fp32_kernel(const float *__restrict__ X, int64_t n, int D,
                                                            const float *__restrict__ P, int d,
                                                            float *__restrict__ Y, int ldy) {
-    __shared__ float As[PT_K][PT_M + 4];
-    __shared__ float Bs[PT_K][PT_N + 4];
+    __shared__ __align__(16) float As[PT_K][PT_M + 4];
+    __shared__ __align__(16) float Bs[PT_K][PT_N + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int64_t row0 = (int64_t)blockIdx.x * PT_M;
     const int col0 = blockIdx.y * PT_N;
@@ -28,11 +28,10 @@ __global__ void __launch_bounds__(256) project_fp32_kernel(const float *__restri
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < PT_K; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+            // one 16-byte shared load per operand (rows of 68 floats keep them aligned)
+            const float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
