@@ -18,7 +18,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "autotune_target_d", "SearchGraph", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "autotune_target_d", "SearchGraph", "HostPipeline", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
@@ -452,6 +452,73 @@ def autotune_target_d(X: torch.Tensor, Q: torch.Tensor, truth: torch.Tensor, gra
         table.append(row)
         idx.close()
     return {"best": best, "table": table}
+
+
+class HostPipeline:
+    """Serving loop for query batches that live in (pinned) host memory: batch i's
+    host-to-device copy runs on a copy stream while batch i - 1 is searched, and its results
+    come back on a second copy stream while batch i + 1 is searched.  Two device buffers of
+    queries and of results alternate; the searches themselves stay in order on one compute
+    stream (they share the index's workspaces).  Every batch is copied in, searched and copied
+    out in full; only the copies of neighbouring batches overlap the search.
+
+        pipe = HostPipeline(index, A, m, D, k=10, L=128, rerank=128, width=2, projection=PREC_BF16)
+        for Qh, ids_h, sc_h in batches:   # pinned host tensors (m x D float32; m x k)
+            pipe.submit(Qh, ids_h, sc_h)
+        pipe.synchronize()                # all results are in the host buffers
+    """
+
+    def __init__(self, index: "Index", A: torch.Tensor | None, m: int, D: int, k: int, L: int, **search_kw):
+        dev = index.device
+        self.index, self.A, self.k, self.L, self.kw = index, A, k, L, search_kw
+        self.Q = [torch.empty((m, D), dtype=torch.float32, device=dev) for _ in range(2)]
+        self.ids = [torch.empty((m, k), dtype=torch.int32, device=dev) for _ in range(2)]
+        self.sc = [torch.empty((m, k), dtype=torch.float32, device=dev) for _ in range(2)]
+        self.s_in = torch.cuda.Stream(device=dev)
+        self.s_cmp = torch.cuda.Stream(device=dev)
+        self.s_out = torch.cuda.Stream(device=dev)
+        self.copied = [torch.cuda.Event() for _ in range(2)]    # queries of slot b are on the device
+        self.searched = [torch.cuda.Event() for _ in range(2)]  # slot b's search is done
+        self.drained = [torch.cuda.Event() for _ in range(2)]   # slot b's results are on the host
+        self.n = 0
+        self.begin()
+
+    def begin(self):
+        """Order the pipeline's next work after the caller's current stream (done at creation)."""
+        cur = torch.cuda.current_stream(self.index.device)
+        for s_ in (self.s_in, self.s_cmp, self.s_out):
+            s_.wait_stream(cur)
+
+    def end(self):
+        """Order the caller's current stream after every submitted batch (no host wait)."""
+        torch.cuda.current_stream(self.index.device).wait_stream(self.s_out)
+
+    def submit(self, Qh: torch.Tensor, ids_h: torch.Tensor, sc_h: torch.Tensor):
+        b = self.n & 1
+        if self.n >= 2:
+            self.s_in.wait_event(self.searched[b])  # slot b's queries were consumed
+        with torch.cuda.stream(self.s_in):
+            self.Q[b].copy_(Qh, non_blocking=True)
+            self.copied[b].record(self.s_in)
+        self.s_cmp.wait_event(self.copied[b])
+        if self.n >= 2:
+            self.s_cmp.wait_event(self.drained[b])  # slot b's previous results left the device
+        with torch.cuda.stream(self.s_cmp):
+            self.index.search(self.Q[b], self.A, k=self.k, L=self.L, out=(self.ids[b], self.sc[b]), **self.kw)
+            self.searched[b].record(self.s_cmp)
+        self.s_out.wait_event(self.searched[b])
+        with torch.cuda.stream(self.s_out):
+            ids_h.copy_(self.ids[b], non_blocking=True)
+            sc_h.copy_(self.sc[b], non_blocking=True)
+            self.drained[b].record(self.s_out)
+        self.n += 1
+
+    def synchronize(self):
+        """Wait for every submitted batch; the host result buffers are then complete (a batch's
+        host buffers must not be changed between its submit and this call)."""
+        for s_ in (self.s_in, self.s_cmp, self.s_out):
+            s_.synchronize()
+        self.end()
 
 
 class SearchGraph:

@@ -334,3 +334,24 @@ def test_autotune_target_d(lv):
     idx = lv.Index(0).encode(X, b["A"], 8, 8, precision=lv.PREC_BF16).set_graph(t(sub["graph"]), sub["entry"])
     ids = idx.search(Q, b["A"], k=10, L=b["L"], rerank=b["L"], width=1)[0].cpu().numpy()
     assert abs(oracle.recall(ids, truth, 10) - b["recall"]) < 1e-6
+
+
+def test_host_pipeline_matches_search(lv, pb):
+    """HostPipeline: pinned host batches in, results out, copies of neighbouring batches
+    overlapping the searches; every batch's host results equal a direct search of it."""
+    idx = gpu_index(lv, pb)
+    P = t(pb["P"])
+    m = 100
+    pipe = lv.HostPipeline(idx, P, m, pb["D"], k=10, L=48, rerank=48, width=2)
+    batches = []
+    for b in range(5):
+        Qh = torch.from_numpy(pb["Q"][(b % 3) * m:(b % 3 + 1) * m]).pin_memory()
+        ids_h = torch.empty((m, 10), dtype=torch.int32).pin_memory()
+        sc_h = torch.empty((m, 10), dtype=torch.float32).pin_memory()
+        pipe.submit(Qh, ids_h, sc_h)
+        batches.append((Qh, ids_h, sc_h))
+    pipe.synchronize()
+    for Qh, ids_h, sc_h in batches:
+        ids, sc = idx.search(Qh.cuda(), P, k=10, L=48, rerank=48, width=2)
+        torch.testing.assert_close(ids_h, ids.cpu(), rtol=0, atol=0)
+        torch.testing.assert_close(sc_h, sc.cpu(), rtol=0, atol=0)
