@@ -416,17 +416,19 @@ def bench_ood(args, dev):
     for name, (A, B, rep) in fits.items():
         ix = lv.Index(dev.index).encode(X, B, 8, 8, precision=lv.PREC_BF16).set_graph(graph, entry)
         per_L = {}
+        hf = args.hop_factor
         for L in (16, 32, 64, 128):
             ids = ix.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=lv.PREC_BF16)[0]
             per_L[L] = recall_at(ids, truth)
-        L90, trace = calibrate(lambda L: ix.search(Q, A, k=10, L=L, rerank=L, width=args.width,
-                                                    projection=lv.PREC_BF16)[0], truth, 10)
+        L90, trace = calibrate(lambda L: ix.search(Q, A, k=10, L=L, rerank=L, max_hops=hop_limit(hf, L),
+                                                    width=args.width, projection=lv.PREC_BF16)[0], truth, 10)
         qps = None
         if L90:
-            ms, _ = time_steps(lambda ev: ix.search(Q, A, k=10, L=L90, rerank=L90, width=args.width,
-                                                    projection=lv.PREC_BF16), 10, 3)
+            ms, _ = time_steps(lambda ev: ix.search(Q, A, k=10, L=L90, rerank=L90, max_hops=hop_limit(hf, L90),
+                                                    width=args.width, projection=lv.PREC_BF16), 10, 3)
             qps = Q.shape[0] * 10 / (ms / 1e3)
-        res[name] = {"recall_at_L": per_L, "L_for_0.90": L90, "qps_at_0.90": qps, "fit": rep}
+        res[name] = {"recall_at_L": per_L, "L_for_0.90": L90, "max_hops": hop_limit(hf, L90) if L90 else None,
+                     "qps_at_0.90": qps, "fit": rep}
         del ix
     out = {"metric": "recall@10 and QPS at 0.90 on shifted (OOD) queries: LeanVec-OOD vs LeanVec-ID",
            "workload": f"ood-{n // 1000}k-512, {m} OOD test queries, {m} learning queries, 100k database samples, d=128",
@@ -694,10 +696,12 @@ def bench_l2(args, dev):
     proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
     res = {"mean_degree": float((graph >= 0).sum(1).float().mean()),
            "ip_top10_overlap": recall_at(truth_ip, truth, 10)}
-    for arm, fn in (("leanvec", lambda L: idx.search(Q, A, k=10, L=L, rerank=L, width=args.width, projection=proj)),
-                    ("fp32", lambda L: base.search(Q, None, k=10, L=L, width=args.width))):
+    hf = args.hop_factor
+    for arm, fn in (("leanvec", lambda L: idx.search(Q, A, k=10, L=L, rerank=L, max_hops=hop_limit(hf, L),
+                                                     width=args.width, projection=proj)),
+                    ("fp32", lambda L: base.search(Q, None, k=10, L=L, max_hops=hop_limit(hf, L), width=args.width))):
         L, trace = calibrate(lambda L: fn(L)[0], truth, 10)
-        a = {"L_for_0.90": L, "recall_trace": trace[-3:]}
+        a = {"L_for_0.90": L, "max_hops": hop_limit(hf, L) if L else None, "recall_trace": trace[-3:]}
         if L:
             nst = max(5, args.steps // 5)
             ms, _ = time_steps(lambda ev: fn(L), nst, 3)
@@ -709,7 +713,8 @@ def bench_l2(args, dev):
                        f"({args.components} components, i^-1 spectrum), not normalised; {args.m} ID queries; "
                        f"LeanVec-ID d={args.d}, LVQ-8 primary + {'FP16' if args.secondary == 'fp16' else 'LVQ-8'} secondary; graph R={args.R}, "
                        f"L_build={args.L_build}, alpha={args.alpha} (rule {args.rule}), batch {args.batch}, built in an L2 index on "
-                       f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L",
+                       f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L, "
+                       f"max_hops=ceil({args.hop_factor} L) (both arms)",
            "build_seconds": t_build, "encode_seconds": t_enc, "reverse_pool_clamped": clamped, "results": res,
            "data": "synthetic"}
     print(json.dumps(out), flush=True)
