@@ -82,7 +82,7 @@ __global__ void column_mean_final_kernel(const double *__restrict__ part, int ch
 // registers between the min/max pass and the code pass.  The fixed-point mean (mui = mean_i
 // 2^20, exact for |mean_i| < 8) and its sums are computed once per block in shared memory.
 // Same arithmetic as lvq_encode_kernel, so the records are bit-identical.
-template <int BITS, int KMAX>
+template <int BITS, int KMAX, int G>
 __global__ void __launch_bounds__(256) lvq_encode_vec_kernel(const float *__restrict__ V, int64_t n, int dim,
                                                              const float *__restrict__ mean, uint8_t *__restrict__ rec,
                                                              int64_t stride, int code_bytes) {
@@ -111,17 +111,23 @@ __global__ void __launch_bounds__(256) lvq_encode_vec_kernel(const float *__rest
     __syncthreads();
     const bool mean_ok = !s_bad;
     const long long smu = s_mu;
-    const int lane = threadIdx.x & 31;
+    // G lanes per vector (32: one warp; 16: two vectors per warp for short vectors)
+    const int lane = threadIdx.x & (G - 1);
     const int nc = dim >> 2;  // float4 chunks per vector
     const float levels = (float)((1 << BITS) - 1);
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const float4 *v4 = reinterpret_cast<const float4 *>(V + i * dim);
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x / G) + (threadIdx.x >> 5) * (32 / G);
+    // every lane of a warp stays in the loop while any of its groups has a vector (shuffles)
+    for (int64_t w0 = g0; w0 < n; w0 += groups) {
+        const int64_t i = w0 + (threadIdx.x & 31) / G;
+        const bool act = i < n;
+        const int64_t ii = act ? i : w0;
+        const float4 *v4 = reinterpret_cast<const float4 *>(V + ii * dim);
         float4 x[KMAX];
         float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int c = lane + 32 * k;
+            const int c = lane + G * k;
             if (c < nc) {
                 const float4 v = __ldg(v4 + c);
                 const float4 m = *reinterpret_cast<const float4 *>(smean + 4 * c);
@@ -130,18 +136,18 @@ __global__ void __launch_bounds__(256) lvq_encode_vec_kernel(const float *__rest
                 hi = fmaxf(fmaxf(hi, fmaxf(x[k].x, x[k].y)), fmaxf(x[k].z, x[k].w));
             }
         }
-        for (int o = 16; o; o >>= 1) {
+        for (int o = G / 2; o; o >>= 1) {
             lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
             hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
         }
         const float delta = __fdiv_rn(__fsub_rn(hi, lo), levels);
-        uint8_t *r = rec + i * stride;
+        uint8_t *r = rec + ii * stride;
         long long msum = 0;
         int csum = 0;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int c = lane + 32 * k;
-            if (c < nc) {
+            const int c = lane + G * k;
+            if (act && c < nc) {
                 const float xs[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
                 uint32_t cw[4];
 #pragma unroll
@@ -166,21 +172,23 @@ __global__ void __launch_bounds__(256) lvq_encode_vec_kernel(const float *__rest
         }
         // zero the code padding (whole 16-bit units: the code bytes end on an even offset)
         const int used = BITS == 8 ? dim : dim / 2;
-        for (int b = used + 2 * lane; b < code_bytes; b += 64) *reinterpret_cast<uint16_t *>(r + b) = 0;
-        for (int o = 16; o; o >>= 1) {
+        if (act)
+            for (int b = used + 2 * lane; b < code_bytes; b += 2 * G) *reinterpret_cast<uint16_t *>(r + b) = 0;
+        for (int o = G / 2; o; o >>= 1) {
             msum += __shfl_xor_sync(FULL, msum, o);
             csum += __shfl_xor_sync(FULL, csum, o);
         }
-        if (lane == 0) {
+        if (act && lane == 0) {
             const float inv = (float)(1.0 / FIX);
             float mu1 = __fmul_rn(__ll2float_rn(smu), inv);
             float mf = __fmul_rn(__ll2float_rn(msum), inv);
-            float G = __fadd_rn(__fmul_rn(lo, mu1), __fmul_rn(delta, mf));
-            float H = __fmul_rn(delta, __int2float_rn(csum));
-            if (!mean_ok) G = H = __int_as_float(0x7fc00000);
-            *reinterpret_cast<float4 *>(r + code_bytes) = make_float4(delta, lo, G, H);
+            float Gt = __fadd_rn(__fmul_rn(lo, mu1), __fmul_rn(delta, mf));
+            float Ht = __fmul_rn(delta, __int2float_rn(csum));
+            if (!mean_ok) Gt = Ht = __int_as_float(0x7fc00000);
+            *reinterpret_cast<float4 *>(r + code_bytes) = make_float4(delta, lo, Gt, Ht);
         }
-        for (int64_t t = code_bytes + 16 + 4 * lane; t < stride; t += 128) *reinterpret_cast<uint32_t *>(r + t) = 0u;
+        if (act)
+            for (int64_t t = code_bytes + 16 + 4 * lane; t < stride; t += 4 * G) *reinterpret_cast<uint32_t *>(r + t) = 0u;
     }
 }
 
@@ -416,14 +424,15 @@ int launch_lvq_encode(const float *V, int64_t n, int dim, const float *mean, int
             LV_CHECK_LAUNCH("lvq_encode_vec_kernel");
             return LV_OK;
         };
+        // short vectors (dim <= 256): two per warp, 16 lanes each
         if (bits == 8) {
-            if (nc <= 64) return go(lvq_encode_vec_kernel<8, 2>);
-            if (nc <= 128) return go(lvq_encode_vec_kernel<8, 4>);
-            return go(lvq_encode_vec_kernel<8, 8>);
+            if (nc <= 64) return go(lvq_encode_vec_kernel<8, 4, 16>);
+            if (nc <= 128) return go(lvq_encode_vec_kernel<8, 4, 32>);
+            return go(lvq_encode_vec_kernel<8, 8, 32>);
         }
-        if (nc <= 64) return go(lvq_encode_vec_kernel<4, 2>);
-        if (nc <= 128) return go(lvq_encode_vec_kernel<4, 4>);
-        return go(lvq_encode_vec_kernel<4, 8>);
+        if (nc <= 64) return go(lvq_encode_vec_kernel<4, 4, 16>);
+        if (nc <= 128) return go(lvq_encode_vec_kernel<4, 4, 32>);
+        return go(lvq_encode_vec_kernel<4, 8, 32>);
     }
     if (bits == 8)
         lvq_encode_kernel<8><<<(unsigned)blocks, wpb * 32, 0, st>>>(V, n, dim, mean, rec, g.stride, g.code_bytes);
