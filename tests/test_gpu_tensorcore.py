@@ -104,3 +104,17 @@ def test_projection_fp8_per_row_scaled(lv, n, D, d):
     err = np.abs(Y - ref) / scale
     assert err.max() <= 2.0 ** -3
     assert err.mean() <= 2e-2
+
+
+def test_scratch_pool_reuse_and_trim(lv):
+    """Repeated offline calls reuse the library's scratch pool (results unchanged) and
+    leanvec_trim_scratch returns its unused blocks without disturbing later calls."""
+    rng = np.random.default_rng(5)
+    X = t(rng.standard_normal((3000, 256)).astype(np.float32))
+    K1 = lv.leanvec_second_moment(X, precision=lv.PREC_BF16)
+    K2 = lv.leanvec_second_moment(X, precision=lv.PREC_BF16)
+    torch.testing.assert_close(K1, K2, rtol=0, atol=0)
+    torch.cuda.synchronize()
+    lv.leanvec_trim_scratch(0)
+    K3 = lv.leanvec_second_moment(X, precision=lv.PREC_BF16)
+    torch.testing.assert_close(K1, K3, rtol=0, atol=0)
