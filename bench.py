@@ -66,6 +66,11 @@ TRAFFIC_RECORDS = [
     {"src_sha1": "5cd3a18943e7fa552c926df8ed848773dac7f10e", "n": 1_000_000, "m": 10_000, "L": 128, "max_hops": 128,
      "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
      "bytes": 3147171584 + 9867776},
+    # the same with the query constants computed in the scorers (no kernel of their own): 3.144 GB
+    # read, 8.1 MB written
+    {"src_sha1": "adabdf5c923b6df5930577829fe01484d40bee83", "n": 1_000_000, "m": 10_000, "L": 128, "max_hops": 128,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
+     "bytes": 3144495360 + 8056832},
 ]
 
 
@@ -1198,7 +1203,7 @@ def main():
                 "d2h_bytes_per_step": m * k * 8, "api": "HostPipeline (pinned host queries in, ids and scores out "
                 "every step; copies of neighbouring steps overlap the search)", "results_match_device": e2e_ok},
         # per step, as the library counts them: the projection (bf16: cast of A + the float32-input
-        # GEMM), the query constants, then the beam and rerank kernels of each sub-batch
+        # GEMM), then the beam and rerank kernels of each sub-batch
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L, mh),

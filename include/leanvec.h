@@ -387,13 +387,13 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
  * the library (held on every GPU that loads the library until the process exits)
  * and calls no cudaMalloc, cudaFree or allocating routine.
  *   - Same arguments, semantics and results as leanvec_search.
- *   - Capacity: 256 + m * 4 * ldq + m * 16 [+ m * 4 * (Lc + 1) when the search
- *     reranks] bytes, each of the three parts rounded up to 256, must fit in
- *     16 MiB, where ldq is the primary dimension rounded up to whole 16-byte code
- *     chunks (d for LVQ-8 with d a multiple of 16) and Lc is params->uniform.L
- *     rounded up to 32 (e.g. m <= 12,900 queries at d = 160, L = 160 with
- *     rerank; m <= 25,000 without); larger batches return LV_ERR_CAPACITY before
- *     anything is launched -- split them.
+ *   - Capacity: 256 + m * 4 * ldq [+ m * 4 * (Lc + 1) when the search reranks]
+ *     bytes, each part rounded up to 256, must fit in 16 MiB, where ldq is the
+ *     primary dimension rounded up to whole 16-byte code chunks (d for LVQ-8 with
+ *     d a multiple of 16) and Lc is params->uniform.L rounded up to 32 (e.g.
+ *     m <= 13,000 queries at d = 160, L = 160 with rerank; m <= 26,000 without);
+ *     larger batches return LV_ERR_CAPACITY before anything is launched -- split
+ *     them.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

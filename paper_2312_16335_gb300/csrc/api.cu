@@ -38,8 +38,6 @@ int launch_mu2(const float *mean, int dim, float *out, cudaStream_t st);
 int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
                         cudaStream_t st);
 int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStream_t st);
-int launch_query_consts(const float *Qp, int ldq, int d, const float *mu_p, const float *Q, int D,
-                        const float *mu_s, int64_t m, float4 *out, cudaStream_t st);
 int launch_graph_sanitize(int32_t *graph, int64_t n, int R, int *status, cudaStream_t st);
 int launch_entry_argmax(const uint8_t *rec, int64_t n, int64_t stride, int code_bytes, int metric, int32_t *out,
                         cudaStream_t st);
@@ -192,7 +190,6 @@ int leanvec_index_free(lv_index *idx) {
     index_free_stores(idx);
     cudaFree(idx->status);
     cudaFree(idx->ws_q);
-    cudaFree(idx->ws_c);
     cudaFree(idx->ws_cand);
     cudaFree(idx->bws);
     if (idx->aux) cudaStreamDestroy(idx->aux);
@@ -509,8 +506,6 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     int ldq = idx->pg.code_chunks * cpc;
     int rc = ensure_ws((void **)&idx->ws_q, &idx->ws_q_bytes, sizeof(float) * (size_t)m * ldq);
     if (rc) return rc;
-    rc = ensure_ws((void **)&idx->ws_c, &idx->ws_c_bytes, sizeof(float4) * (size_t)m);
-    if (rc) return rc;
     idx->last_kernels = 0;
     // kernels of the projection: padding copy / float32 GEMM: 1; bf16 with float32 X converted in
     // the GEMM: cast of A + GEMM; otherwise casts of Q and A + GEMM
@@ -526,9 +521,6 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         rc = launch_project_fp32(Q, m, idx->D, A, idx->d, idx->ws_q, ldq, st);
     }
     if (rc) return rc;
-    rc = launch_query_consts(idx->ws_q, ldq, idx->d, idx->pbits == 32 ? nullptr : idx->pmean, Q, idx->D, idx->smean,
-                             m, idx->ws_c, st);
-    if (rc) return rc;
 
     BeamParams p;
     memset(&p, 0, sizeof(p));
@@ -542,7 +534,8 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.entry = idx->entry;
     p.qp = idx->ws_q;
     p.ldq = ldq;
-    p.qconst = idx->ws_c;
+    p.pmean = idx->pbits == 32 ? nullptr : idx->pmean;
+    p.smean = idx->smean;
     p.desc = reinterpret_cast<const int4 *>(desc);
     p.uni = make_int4(u.k, u.L, idx->sec ? u.rerank : 0, u.max_hops);
     p.m = m;
@@ -617,7 +610,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         LV_CUDA(cudaEventCreateWithFlags(&idx->ev_fork, cudaEventDisableTiming));
         LV_CUDA(cudaEventCreateWithFlags(&idx->ev_join, cudaEventDisableTiming));
     }
-    idx->last_kernels = proj_kernels + 1 + (mA == m ? 1 : 2) * (rerank ? 2 : 1);
+    idx->last_kernels = proj_kernels + (mA == m ? 1 : 2) * (rerank ? 2 : 1);
     if (params->event_begin) LV_CUDA(cudaEventRecord((cudaEvent_t)params->event_begin, st));
     if (mA == m) {
         rc = beam(p, st);
@@ -628,7 +621,6 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         pa.m = mA;
         pb.m = m - mA;
         pb.qp = p.qp + mA * ldq;
-        pb.qconst = p.qconst + mA;
         if (p.desc) pb.desc = p.desc + mA;
         pb.Q = p.Q + mA * p.D;
         pb.ids = p.ids + mA * ldo;

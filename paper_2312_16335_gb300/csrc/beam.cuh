@@ -30,7 +30,8 @@ struct BeamParams {
     // queries
     const float *qp;  // padded queries in the primary space (search mode)
     int ldq;
-    const float4 *qconst;  // (cq, sq, cQ, sQ)
+    const float *pmean;    // primary mean mu_B (prim_dim): cq = <q', mu_B>, sq = sum q' of each query
+    const float *smean;    // secondary mean mu (D): cQ = <q, mu>, sQ = sum q (rerank), or NULL
     const int4 *desc;      // per query (k, L, r, max_hops) or NULL
     int4 uni;
     int64_t m;
@@ -124,10 +125,24 @@ struct LvqIntScorer {
         base = p.prim;
         stride = p.prim_stride;
         const float *row = p.qp + qi * p.ldq;
-        float amax = 0.f;
-        for (int j = lane; j < CH * CPC; j += 32) amax = fmaxf(amax, fabsf(row[j]));
+        // the per-query constants of the decoded inner product: cq = <q', mu_B>, sq = sum q'
+        float amax = 0.f, c = 0.f, s = 0.f;
+        for (int j = lane; j < CH * CPC; j += 32) {
+            const float v = row[j];
+            amax = fmaxf(amax, fabsf(v));
+            if (j < p.prim_dim) {
+                c = fmaf(v, p.pmean[j], c);
+                s += v;
+            }
+        }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+        for (int o = 16; o; o >>= 1) {
+            amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+            c += __shfl_xor_sync(FULL, c, o);
+            s += __shfl_xor_sync(FULL, s, o);
+        }
+        cq = c;
+        sq = s;
         scale = amax > 0.f ? amax / 8388607.0f : 1.0f;
         const float inv = amax > 0.f ? 8388607.0f / amax : 0.f;
         uint32_t *dst = reinterpret_cast<uint32_t *>(qsmem);
@@ -156,9 +171,6 @@ struct LvqIntScorer {
         }
         __syncwarp();
         lq = reinterpret_cast<const uint4 *>(qsmem);
-        float4 k = p.qconst[qi];
-        cq = k.x;
-        sq = k.y;
     }
 
     template <int P>

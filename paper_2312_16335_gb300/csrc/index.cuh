@@ -23,8 +23,6 @@ struct lv_index {
     // search workspace
     float *ws_q = nullptr;
     size_t ws_q_bytes = 0;
-    float4 *ws_c = nullptr;
-    size_t ws_c_bytes = 0;
     int32_t *ws_cand = nullptr;  // rerank hand-off: m x Lcap ids + m counts
     size_t ws_cand_bytes = 0;
     // build workspace

@@ -1,5 +1,4 @@
-// Projection GEMM on the CUDA cores (float32): Y = X P^T (Eq. 1: q -> A q, x -> B x),
-// and the per-query constants of the decoded inner products.
+// Projection GEMM on the CUDA cores (float32): Y = X P^T (Eq. 1: q -> A q, x -> B x).
 #include "common.cuh"
 
 namespace lv {
@@ -57,35 +56,6 @@ __global__ void pad_rows_kernel(const float *__restrict__ X, int64_t n, int D, f
     for (int c = threadIdx.x; c < ldy; c += blockDim.x) Y[r * ldy + c] = c < D ? X[r * D + c] : 0.0f;
 }
 
-// Per query: cq = <q', mu_B>, sq = sum q' (primary), cQ = <q, mu>, sQ = sum q (secondary).
-__global__ void query_consts_kernel(const float *__restrict__ Qp, int ldq, int d, const float *__restrict__ mu_p,
-                                    const float *__restrict__ Q, int D, const float *__restrict__ mu_s,
-                                    int64_t m, float4 *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= m) return;
-    float cq = 0.f, sq = 0.f, cQ = 0.f, sQ = 0.f;
-    if (mu_p)
-        for (int j = lane; j < d; j += 32) {
-            float v = Qp[i * ldq + j];
-            cq = fmaf(v, mu_p[j], cq);
-            sq += v;
-        }
-    if (mu_s)
-        for (int j = lane; j < D; j += 32) {
-            float v = Q[i * D + j];
-            cQ = fmaf(v, mu_s[j], cQ);
-            sQ += v;
-        }
-    for (int o = 16; o; o >>= 1) {
-        cq += __shfl_xor_sync(FULL, cq, o);
-        sq += __shfl_xor_sync(FULL, sq, o);
-        cQ += __shfl_xor_sync(FULL, cQ, o);
-        sQ += __shfl_xor_sync(FULL, sQ, o);
-    }
-    if (lane == 0) out[i] = make_float4(cq, sq, cQ, sQ);
-}
-
 int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
                         cudaStream_t st) {
     if (n == 0) return LV_OK;
@@ -102,12 +72,5 @@ int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStr
     return LV_OK;
 }
 
-int launch_query_consts(const float *Qp, int ldq, int d, const float *mu_p, const float *Q, int D,
-                        const float *mu_s, int64_t m, float4 *out, cudaStream_t st) {
-    if (m == 0) return LV_OK;
-    query_consts_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(Qp, ldq, d, mu_p, Q, D, mu_s, m, out);
-    LV_CHECK_LAUNCH("query_consts_kernel");
-    return LV_OK;
-}
 
 }  // namespace lv

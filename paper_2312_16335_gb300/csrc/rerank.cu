@@ -217,7 +217,7 @@ struct RerankParams {
     int sec_chunks;
     const float *Q;  // unreduced queries m x D
     int D;
-    const float4 *qconst;  // (cq, sq, cQ, sQ); cQ, sQ = the secondary constants
+    const float *smean;    // secondary mean mu (D) or NULL: cQ = <q, mu>, sQ = sum q per query
     const int4 *desc;      // per query (k, L, r, max_hops) or NULL
     int4 uni;
     int64_t m;
@@ -246,8 +246,20 @@ __global__ void __launch_bounds__(32 * RR_WARPS) rerank_kernel(const RerankParam
         for (int t = lane; t < nr; t += 32) rI[t] = cd[t];
         __syncwarp();
         SS sc;
-        const float4 kq = p.qconst[qi];
-        sc.setup(p.Q + qi * p.D, p.D, p.sec_chunks, p.sec, p.sec_stride, kq.z, kq.w, lane);
+        const float *q = p.Q + qi * p.D;
+        float cQ = 0.f, sQ = 0.f;
+        if (p.smean) {
+            for (int j = lane; j < p.D; j += 32) {
+                const float v = q[j];
+                cQ = fmaf(v, p.smean[j], cQ);
+                sQ += v;
+            }
+            for (int o = 16; o; o >>= 1) {
+                cQ += __shfl_xor_sync(FULL, cQ, o);
+                sQ += __shfl_xor_sync(FULL, sQ, o);
+            }
+        }
+        sc.setup(q, p.D, p.sec_chunks, p.sec, p.sec_stride, cQ, sQ, lane);
         sc.score(rI, rS, nr, lane);
         __syncwarp();
         int32_t *oid = p.ids + qi * p.ldo;
@@ -294,7 +306,7 @@ int launch_rerank(const BeamParams &bp, int num_sms, cudaStream_t st) {
     p.sec_chunks = bp.sec_chunks;
     p.Q = bp.Q;
     p.D = bp.D;
-    p.qconst = bp.qconst;
+    p.smean = bp.smean;
     p.desc = bp.desc;
     p.uni = bp.uni;
     p.m = bp.m;

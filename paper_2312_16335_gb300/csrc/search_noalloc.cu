@@ -16,8 +16,6 @@ namespace lv {
 int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
                         cudaStream_t st);
 int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStream_t st);
-int launch_query_consts(const float *Qp, int ldq, int d, const float *mu_p, const float *Q, int D,
-                        const float *mu_s, int64_t m, float4 *out, cudaStream_t st);
 
 // 16 MiB, held by every GPU that loads this library until the process exits.
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
@@ -72,14 +70,13 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     const int cpc = idx->pbits == 8 ? 16 : idx->pbits == 4 ? 32 : 4;
     const int ldq = idx->pg.code_chunks * cpc;
     const size_t q_bytes = round_up((int64_t)sizeof(float) * m * ldq, 256);
-    const size_t c_bytes = round_up((int64_t)sizeof(float4) * m, 256);
     // rerank hand-off (beam kernel -> rerank kernel): m x Lcap ids + m counts
     const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
     const int Lcap = (int)round_up(u.L, 32);
     const size_t r_bytes = rerank ? (size_t)round_up((int64_t)sizeof(int32_t) * m * (Lcap + 1), 256) : 0;
-    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + c_bytes + r_bytes;
+    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + r_bytes;
     if (need > NOALLOC_SCRATCH_BYTES)
-        return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension + 16 [+ 4 * (L rounded up to "
+        return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension [+ 4 * (L rounded up to "
                                      "32) + 4 with rerank]) + 256 bytes (each part rounded up to 256) exceed the "
                                      "16 MiB static scratch; split the batch");
 
@@ -95,13 +92,9 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         if (rc) break;
         int *work = reinterpret_cast<int *>(scratch);
         float *qp = reinterpret_cast<float *>(scratch + NOALLOC_HEADER_BYTES);
-        float4 *qc = reinterpret_cast<float4 *>(scratch + NOALLOC_HEADER_BYTES + q_bytes);
-        int32_t *cand = reinterpret_cast<int32_t *>(scratch + NOALLOC_HEADER_BYTES + q_bytes + c_bytes);
+        int32_t *cand = reinterpret_cast<int32_t *>(scratch + NOALLOC_HEADER_BYTES + q_bytes);
         rc = idx->pbits == 32 ? launch_pad_rows(Q, m, idx->D, qp, ldq, st)
                               : launch_project_fp32(Q, m, idx->D, A, idx->d, qp, ldq, st);
-        if (rc) break;
-        rc = launch_query_consts(qp, ldq, idx->d, idx->pbits == 32 ? nullptr : idx->pmean, Q, idx->D, idx->smean, m,
-                                 qc, st);
         if (rc) break;
 
         BeamParams p;
@@ -116,7 +109,8 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         p.entry = idx->entry;
         p.qp = qp;
         p.ldq = ldq;
-        p.qconst = qc;
+        p.pmean = idx->pbits == 32 ? nullptr : idx->pmean;
+        p.smean = idx->smean;
         p.desc = reinterpret_cast<const int4 *>(desc);
         p.uni = make_int4(u.k, u.L, idx->sec ? u.rerank : 0, u.max_hops);
         p.m = m;
