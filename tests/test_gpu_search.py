@@ -313,6 +313,16 @@ def test_sub_batches_match_small_batches(lv):
     ref = oracle.search(sub["graph"], sub["entry"], _qp(sub), k=10, L=48, rerank=48, prim=sub["prim"],
                         sec=sub["sec"], qs=sub["Q"].astype(np.float64), width=2)
     assert (ids.cpu().numpy() == ref["ids"]).mean() >= 0.99
+    # per-query descriptors (k, L, rerank, max_hops) follow their queries into the second sub-batch
+    rng = np.random.default_rng(3)
+    kk = rng.integers(1, 11, 12000)
+    LL = np.maximum(kk, rng.integers(8, 65, 12000))
+    desc = np.stack([kk, LL, LL, rng.integers(0, 40, 12000)], 1).astype(np.int32)
+    dids, dsc = idx.search(Q, P, k=10, L=64, rerank=64, desc=t(desc), width=2)
+    dparts = [idx.search(Q[s:s + 100].contiguous(), P, k=10, L=64, rerank=64, desc=t(desc[s:s + 100]), width=2)
+              for s in range(0, 12000, 100)]
+    torch.testing.assert_close(dids, torch.cat([p[0] for p in dparts]), rtol=0, atol=0)
+    torch.testing.assert_close(dsc, torch.cat([p[1] for p in dparts]), rtol=0, atol=0)
 
 
 def test_autotune_target_d(lv):
