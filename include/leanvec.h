@@ -367,9 +367,9 @@ typedef struct {
  * decoded inner products (secondary after rerank, primary otherwise).
  * Streams: the work is ordered after `stream`'s earlier work and `stream`'s later
  * work waits for all of it.  With rerank and m above one wave of the beam kernel's
- * resident query slots (and not a multiple of it), the queries past the last whole
- * wave run as a second launch on a stream of the index's own, forked from and joined
- * back to `stream` by events (this also holds inside a CUDA-graph capture of
+ * resident query slots (and not a multiple of it), the queries past 90 % of the last
+ * whole wave run as a second launch on a stream of the index's own, forked from and
+ * joined back to `stream` by events (this also holds inside a CUDA-graph capture of
  * `stream`); results do not depend on it.  Calls on one index are not thread-safe. */
 int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
                    const lv_search_params *params, const lv_query_desc *desc,

@@ -592,10 +592,12 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         return idx->pbits == 8 ? launch_search_lvq8(q, nc, block, smem, idx->num_sms, s)
                                : launch_search_lvq4(q, nc, block, smem, idx->num_sms, s);
     };
-    // Sub-batches: with rerank, the queries beyond the last whole wave of resident query slots
-    // (slots = blocks per SM x SMs x queries per block) form a second batch launched on a second
-    // stream.  The first batch's waves end together; its rerank then runs beside the second
-    // batch's partial wave instead of after it.  Every query is computed exactly as in one launch.
+    // Sub-batches: with rerank and m above one wave of resident query slots (slots = blocks per SM
+    // x SMs x queries per block) and not a multiple of it, the first batch takes the whole waves
+    // but the last 10 % of the last one, the rest forms a second batch launched on a second stream:
+    // the second batch's blocks start as the first one's finish, and the first batch's rerank runs
+    // beside the second batch's partial wave instead of after it.  Every query is computed exactly
+    // as in one launch.
     int64_t mA = m;
     if (rerank) {
         int64_t slots = 0;
@@ -603,7 +605,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         q.slots = &slots;
         rc = beam(q, st);
         if (rc) return rc;
-        if (slots > 0 && m > slots && m % slots) mA = m / slots * slots;
+        if (slots > 0 && m > slots && m % slots) mA = (m / slots - 1) * slots + slots * 9 / 10;
     }
     if (mA < m && !idx->aux) {
         LV_CUDA(cudaStreamCreateWithFlags(&idx->aux, cudaStreamNonBlocking));
