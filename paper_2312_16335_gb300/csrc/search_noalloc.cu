@@ -61,7 +61,8 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         return fail(LV_ERR_ARG, "search_noalloc: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search_noalloc: rerank needs a secondary store");
     if (params->projection != LV_PREC_FP32)
-        return fail(LV_ERR_ARG, "search_noalloc: only LV_PREC_FP32 projection is available in this build");
+        return fail(LV_ERR_ARG, "search_noalloc: the projection must be LV_PREC_FP32 (the tensor-core projections "
+                                "need operand copies in allocated memory)");
     if (idx->sbits == 8 && idx->sg.code_chunks + 1 + idx->metric > 64)
         return fail(LV_ERR_ARG, "search_noalloc: D > 1008 is not supported by the rerank");
     if (idx->sbits == 16 && idx->sg.code_chunks > 128)
