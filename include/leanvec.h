@@ -386,9 +386,13 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
  * size; this variant instead uses one static 16 MiB device array compiled into
  * the library (held on every GPU that loads the library until the process exits)
  * and calls no cudaMalloc, cudaFree or allocating routine.
- *   - Same arguments, semantics and results as leanvec_search.
+ *   - Same arguments, semantics and results as leanvec_search, except that the
+ *     projection must be LV_PREC_FP32, or LV_PREC_BF16 with 16-byte aligned query
+ *     rows (D a multiple of 4: Q is converted inside the GEMM, so only the bf16 copy
+ *     of A needs scratch), and that the batch is one launch (no second stream).
  *   - Capacity: 256 + m * 4 * ldq [+ m * 4 * (Lc + 1) when the search reranks]
- *     bytes, each part rounded up to 256, must fit in 16 MiB, where ldq is the
+ *     [+ 2 d ldx with the bf16 projection, ldx = D rounded up to 8] bytes, each
+ *     part rounded up to 256, must fit in 16 MiB, where ldq is the
  *     primary dimension rounded up to whole 16-byte code chunks (d for LVQ-8 with
  *     d a multiple of 16) and Lc is params->uniform.L rounded up to 32 (e.g.
  *     m <= 13,000 queries at d = 160, L = 160 with rerank; m <= 26,000 without);

@@ -340,11 +340,13 @@ class Index:
 
     def search_noalloc(self, Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
                        max_hops: int = 0, ldo: int | None = None,
-                       out: tuple[torch.Tensor, torch.Tensor] | None = None):
+                       out: tuple[torch.Tensor, torch.Tensor] | None = None, projection: int = PREC_FP32,
+                       width: int = 1):
         """leanvec_search_noalloc: the same search for callers that cannot let the
         library allocate device memory; its scratch is a static 16 MiB device array
         shared by all calls on a device (serialise overlapping calls).  The output
-        tensors are the caller's (pass `out` to reuse preallocated ones)."""
+        tensors are the caller's (pass `out` to reuse preallocated ones).  projection:
+        PREC_FP32 or PREC_BF16 (queries converted inside the tensor-core GEMM)."""
         Q = _f32(Q)
         m = Q.shape[0]
         ldo = k if ldo is None else ldo
@@ -353,7 +355,7 @@ class Index:
             sc = torch.empty((m, ldo), dtype=torch.float32, device=self.device)
         else:
             ids, sc = out
-        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), PREC_FP32, 0, 0, 1, 0, None, None)
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, 0, 0, width, 0, None, None)
         Ac = _f32(A) if A is not None else None
         check(lib().leanvec_search_noalloc(self._h, _ptr(Q), m, _ptr(Ac), ctypes.byref(prm), None, _ptr(ids),
                                            _ptr(sc), ldo, None, _stream(self.device)))

@@ -1,7 +1,7 @@
 // leanvec_search_noalloc: the search of leanvec_search for callers that must not
-// allocate device memory.  Its scratch (the work counter, the projected queries and
-// the per-query constants) lives in one file-scope __device__ array instead of a
-// workspace obtained with cudaMalloc.
+// allocate device memory.  Its scratch (the work counter, the projected queries, the bf16
+// copy of A for the tensor-core projection and the rerank hand-off) lives in one file-scope
+// __device__ array instead of a workspace obtained with cudaMalloc.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -16,6 +16,10 @@ namespace lv {
 int launch_project_fp32(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy,
                         cudaStream_t st);
 int launch_pad_rows(const float *X, int64_t n, int D, float *Y, int ldy, cudaStream_t st);
+bool project_bf16_fused_ok(const float *X, int D, int d);
+size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X);
+int project_bf16(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                 size_t *ws_bytes, int *status, cudaStream_t st);
 
 // 16 MiB, held by every GPU that loads this library until the process exits.
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
@@ -60,9 +64,12 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     if (!desc && (u.k < 1 || u.k > u.L || u.k > ldo || u.rerank < 0 || u.rerank > u.L || u.max_hops < 0))
         return fail(LV_ERR_ARG, "search_noalloc: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search_noalloc: rerank needs a secondary store");
-    if (params->projection != LV_PREC_FP32)
-        return fail(LV_ERR_ARG, "search_noalloc: the projection must be LV_PREC_FP32 (the tensor-core projections "
-                                "need operand copies in allocated memory)");
+    // the bf16 projection converts Q inside the GEMM and needs only a bf16 copy of A (in the
+    // scratch); the other tensor-core paths would need a converted copy of Q
+    const bool bf16 = params->projection == LV_PREC_BF16 && idx->pbits != 32;
+    if (params->projection != LV_PREC_FP32 && !(bf16 && project_bf16_fused_ok(Q, idx->D, idx->d)))
+        return fail(LV_ERR_ARG, "search_noalloc: the projection must be LV_PREC_FP32, or LV_PREC_BF16 with 16-byte "
+                                "aligned query rows (D a multiple of 4)");
     if (idx->sbits == 8 && idx->sg.code_chunks + 1 + idx->metric > 64)
         return fail(LV_ERR_ARG, "search_noalloc: D > 1008 is not supported by the rerank");
     if (idx->sbits == 16 && idx->sg.code_chunks > 128)
@@ -75,11 +82,12 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     const bool rerank = idx->sbits && idx->pbits != 32 && (desc || u.rerank > 0);
     const int Lcap = (int)round_up(u.L, 32);
     const size_t r_bytes = rerank ? (size_t)round_up((int64_t)sizeof(int32_t) * m * (Lcap + 1), 256) : 0;
-    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + r_bytes;
+    const size_t a_bytes = bf16 ? round_up((int64_t)project_tc_ws_bytes(LV_PREC_BF16, m, idx->D, idx->d, Q), 256) : 0;
+    const size_t need = NOALLOC_HEADER_BYTES + q_bytes + r_bytes + a_bytes;
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension [+ 4 * (L rounded up to "
-                                     "32) + 4 with rerank]) + 256 bytes (each part rounded up to 256) exceed the "
-                                     "16 MiB static scratch; split the batch");
+                                     "32) + 4 with rerank]) + 256 [+ 2 d D for a bf16 projection] bytes (each part "
+                                     "rounded up to 256) exceed the 16 MiB static scratch; split the batch");
 
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return fail(LV_ERR_CUDA, "search_noalloc: cudaGetDevice failed");
@@ -94,8 +102,15 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         int *work = reinterpret_cast<int *>(scratch);
         float *qp = reinterpret_cast<float *>(scratch + NOALLOC_HEADER_BYTES);
         int32_t *cand = reinterpret_cast<int32_t *>(scratch + NOALLOC_HEADER_BYTES + q_bytes);
-        rc = idx->pbits == 32 ? launch_pad_rows(Q, m, idx->D, qp, ldq, st)
-                              : launch_project_fp32(Q, m, idx->D, A, idx->d, qp, ldq, st);
+        if (idx->pbits == 32) {
+            rc = launch_pad_rows(Q, m, idx->D, qp, ldq, st);
+        } else if (bf16) {
+            void *ws = scratch + NOALLOC_HEADER_BYTES + q_bytes + r_bytes;
+            size_t wsb = a_bytes;  // large enough: project_bf16 does not grow it
+            rc = project_bf16(Q, m, idx->D, A, idx->d, qp, ldq, &ws, &wsb, idx->status, st);
+        } else {
+            rc = launch_project_fp32(Q, m, idx->D, A, idx->d, qp, ldq, st);
+        }
         if (rc) break;
 
         BeamParams p;

@@ -47,6 +47,21 @@ def test_noalloc_matches_search_on_consecutive_calls(lv):
     idx.sync_status()
 
 
+def test_noalloc_bf16_projection_matches_search(lv):
+    """The bf16 projection (queries converted inside the tensor-core GEMM, the bf16 copy of A in
+    the static scratch) gives the same results as leanvec_search with the same projection, bit
+    for bit; a projection that would need a converted copy of Q is refused."""
+    pb = small_problem(oracle, n=3000, D=64, d=16, m=300, seed=4)
+    idx = gpu_index(lv, pb)
+    Q, P = t(pb["Q"]), t(pb["P"])
+    ref = idx.search(Q, P, k=10, L=40, rerank=40, width=2, projection=lv.PREC_BF16)
+    got = idx.search_noalloc(Q, P, k=10, L=40, rerank=40, width=2, projection=lv.PREC_BF16)
+    torch.testing.assert_close(got[0], ref[0], rtol=0, atol=0)
+    torch.testing.assert_close(got[1], ref[1], rtol=0, atol=0)
+    with pytest.raises(lv.LeanVecError):
+        idx.search_noalloc(Q, P, k=10, L=40, rerank=40, projection=lv.PREC_FP8)
+
+
 def test_noalloc_rejects_batches_beyond_the_static_scratch(lv):
     pb = small_problem(oracle, n=500, D=64, d=16, m=10, seed=2)
     idx = gpu_index(lv, pb)
