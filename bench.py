@@ -822,9 +822,15 @@ def bench_kernels(args, dev):
     Ai = lv.leanvec_fit_id(Xo, 128)
     pair_flops = 2.0 * Qo.shape[0] * Xo.shape[0] * (512 + 128)  # q^T x and (A q)^T (B x) per pair
     t = timed(lambda: lv.leanvec_ood_loss_fwd(Ai, Ai, Qo, Xo), 2)
-    res["pair_loss_fwd_10k_x_100k_512_128"] = {"seconds": t, "tflops": pair_flops / t / 1e12,
-                                               "bound": "fp32 CUDA cores", "peak_tflops_nominal": fp32_cc,
-                                               "frac_nominal": pair_flops / t / 1e12 / fp32_cc}
+    # the forward runs r = qt^T x (qt = q - B^T A q) as three tf32 tensor-core products per pair
+    # (hi/lo splits): 3 x 2 m n D executed flops against the tf32 peak (bf16 measured x 1.1 / 2.25)
+    tf32_peak = bf16 * 1.1 / 2.25
+    exec_flops = 3 * 2.0 * Qo.shape[0] * Xo.shape[0] * 512
+    res["pair_loss_fwd_10k_x_100k_512_128"] = {"seconds": t, "pair_tflops": pair_flops / t / 1e12,
+                                               "bound": "tensor (tf32, three MMAs per product)",
+                                               "executed_tflops": exec_flops / t / 1e12,
+                                               "peak_tflops": tf32_peak, "frac": exec_flops / t / 1e12 / tf32_peak,
+                                               "peak_source": src + " bf16 x nominal tf32/bf16 ratio"}
     log("loss fwd", res["pair_loss_fwd_10k_x_100k_512_128"])
     t = timed(lambda: lv.leanvec_ood_loss_bwd(Ai, Ai, Qo, Xo), 2)
     res["pair_loss_bwd_10k_x_100k_512_128"] = {"seconds": t}

@@ -193,8 +193,13 @@ int leanvec_fit_ood(const float *X, int64_t n, const float *Q, int64_t m, int D,
  * "leanvec_orthonormal" written per pair, Sec. 2.2):
  *   r_ij = q_j^T x_i - (A q_j)^T (B x_i),  L = sum_ij r_ij^2 / (n m)
  * over the m rows of Q (m x D) and the n rows of X (n x D), A, B d x D (all float32,
- * device; d <= 256).  The m x n residuals are recomputed in 64 x 64 tiles, never stored.
- * fwd writes L to *loss (host, FP64 sum of float32 tile partials; synchronises).
+ * device; d <= 256).  The m x n residuals are recomputed in tiles, never stored.
+ * fwd writes L to *loss (host; synchronises).  With D a multiple of 4 it computes
+ * r_ij = qt_j^T x_i with qt_j = q_j - B^T (A q_j) (float32) on the tensor cores:
+ * each operand split into tf32 hi + lo parts, three tf32 products per tile (about 21
+ * bits of the float32 products), 128 x 256 tiles, squares summed in float32 per 16
+ * residuals and in FP64 per CTA, the CTAs' partials in a fixed order; otherwise 64 x 64
+ * float32 CUDA-core tiles with FP64 sums.
  * bwd writes scale * dL/dA and scale * dL/dB (d x D, device):
  *   dL/dA = -2/(nm) sum_ij r_ij (B x_i) q_j^T,  dL/dB = -2/(nm) sum_ij r_ij (A q_j) x_i^T
  * (equal to Eq. "leanvec_gradients" divided by n m).  Synchronises `stream`. */

@@ -518,6 +518,202 @@ __global__ void __launch_bounds__(PF_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------------
+// Sum of squares of R = Qt X^T on the tensor cores (tcgen05.mma kind::tf32): the pair loss of the
+// differentiation form, r_ij = q_j^T x_i - (A q_j)^T (B x_i) = qt_j^T x_i with qt_j = q_j - B^T A q_j
+// computed beforehand, so that the tile products themselves carry no cancellation.  Each operand
+// comes as a tf32 pair (hi = tf32(v), lo = tf32(v - hi), both exact in tf32) and every tile
+// product is hi_a hi_b + hi_a lo_b + lo_a hi_b: three tf32 MMAs that keep about 21 bits of the
+// float32 products (the tf32 unit reads only the top 19 bits of a float; one tf32 product alone is
+// biased by its truncation).  Float32 tiles go from HBM to shared memory by TMA (128-byte swizzle,
+// 32 floats per row) and straight into the MMA.  Persistent over 128 x 256 tiles (query rows x
+// database rows), tiles t = c, c + G, ...; two TMEM accumulators (512 columns) let the epilogue of
+// one tile overlap the main loop of the next.  Rows past m or n are zero-filled by TMA and add
+// nothing.
+//   warp 0, lane 0 : TMA producer (2-stage ring of A hi / lo 128 x 32 and B hi / lo 256 x 32 tiles)
+//   warp 1         : TMEM allocation; lane 0 issues the MMAs (M 128, N 256, K 8) and commits
+//   warps 2-5      : epilogue; warp w reads TMEM lanes 32 (w % 4) ..: sum of squares of its row
+//                    (float32 per 16 columns, then FP64), one FP64 partial per CTA
+constexpr int PL_THREADS = 192, PL_STAGES = 2, PL_BN = 256;
+
+__global__ void __launch_bounds__(PL_THREADS, 1)
+    pair_sq_tf32_kernel(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
+                        const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int m,
+                        int n, int K, double *__restrict__ partial, int *__restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // stage: A hi | A lo | B hi | B lo
+    const uint32_t a_bytes = TC_BM * 128, b_bytes = PL_BN * 128, stage_bytes = 2 * (a_bytes + b_bytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + PL_STAGES * stage_bytes);
+    uint64_t *empty = full + PL_STAGES;
+    uint64_t *tfull = empty + PL_STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    double *red = reinterpret_cast<double *>(base + PL_STAGES * stage_bytes + 256);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = (m + TC_BM - 1) / TC_BM, nt = (n + PL_BN - 1) / PL_BN;
+    const int64_t tiles = (int64_t)mt * nt;
+    const int nkb = (K + 31) / 32;
+    const int my_tiles = (int64_t)blockIdx.x < tiles ? (int)((tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PL_STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull + b, 1);
+            mbar_init(tempty + b, 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    double acc = 0.0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int tc = 0; tc < my_tiles && !*abort_flag; ++tc) {
+                const int64_t tile = blockIdx.x + (int64_t)tc * gridDim.x;
+                const int m0 = (int)(tile / nt) * TC_BM, n0 = (int)(tile % nt) * PL_BN;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % PL_STAGES);
+                    const int64_t u = g / PL_STAGES;
+                    if (u > 0 && !mbar_wait(empty + s, (uint32_t)((u - 1) & 1))) {
+                        *abort_flag = 1;
+                        atomicOr(status, ST_TIMEOUT);
+                        break;
+                    }
+                    uint8_t *sa = base + s * stage_bytes;
+                    mbar_expect_tx(full + s, stage_bytes);
+                    tma_load_2d(sa, &tah, kb * 32, m0, full + s);
+                    tma_load_2d(sa + a_bytes, &tal, kb * 32, m0, full + s);
+                    tma_load_2d(sa + 2 * a_bytes, &tbh, kb * 32, n0, full + s);
+                    tma_load_2d(sa + 2 * a_bytes + b_bytes, &tbl, kb * 32, n0, full + s);
+                }
+            }
+            // the copies in flight land before the CTA ends (bounded waits)
+            for (int64_t q = std::max<int64_t>(0, g - PL_STAGES); q < g; ++q)
+                mbar_wait(full + (int)(q % PL_STAGES), (uint32_t)((q / PL_STAGES) & 1));
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::tf32: A and B format 2 (TF32), D float32, M = 128, N = 256
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PL_BN >> 3) << 17) |
+                                   ((uint32_t)(TC_BM >> 4) << 24);
+            int64_t g = 0;
+            for (int tc = 0; tc < my_tiles && !*abort_flag; ++tc) {
+                const int b = tc & 1, v = tc >> 1;
+                if (v > 0 && !mbar_wait(tempty + b, (uint32_t)((v - 1) & 1))) {
+                    *abort_flag = 1;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+                const uint32_t acc_addr = tmem + (uint32_t)(b * 256);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % PL_STAGES);
+                    if (!mbar_wait(full + s, (uint32_t)((g / PL_STAGES) & 1)) || *abort_flag) {
+                        *abort_flag = 1;
+                        atomicOr(status, ST_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    uint8_t *sa = base + s * stage_bytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // 8 floats (32 bytes) of K per MMA, 4 per 128-byte row
+                        const uint64_t ah = sdesc(sa + 32 * k), al = sdesc(sa + a_bytes + 32 * k);
+                        const uint64_t bh = sdesc(sa + 2 * a_bytes + 32 * k);
+                        const uint64_t bl = sdesc(sa + 2 * a_bytes + b_bytes + 32 * k);
+                        const uint64_t ad[3] = {ah, ah, al}, bd[3] = {bh, bl, bh};
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const uint32_t accf = (kb > 0 || k > 0 || t > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\t"
+                                "setp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+                                "l"(ad[t]), "l"(bd[t]), "r"(idesc), "r"(accf)
+                                : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(empty + s))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(tfull + b))
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(drain))
+                         : "memory");
+            if (!mbar_wait(drain, 0)) atomicOr(status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warps 2..5 cover the TMEM lane quarters 2, 3, 0, 1
+        const int quarter = warp & 3;
+        for (int tc = 0; tc < my_tiles; ++tc) {
+            const int b = tc & 1, v = tc >> 1;
+            const bool ok = !*abort_flag && mbar_wait(tfull + b, (uint32_t)(v & 1));
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int c0 = 0; c0 < PL_BN; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float sq = 0.f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float x = __uint_as_float(r[j]);
+                    sq = fmaf(x, x, sq);
+                }
+                acc += (double)sq;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(tempty + b);
+        }
+    }
+    // one FP64 partial per CTA: the epilogue threads' sums in a fixed order
+    if (warp >= 2) red[threadIdx.x - 64] = acc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 128; ++i) t += red[i];
+        partial[blockIdx.x] = t;
+    }
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // sum of the split-K partials in a fixed order
 __global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, float *__restrict__ C,
                                      int ldc) {
@@ -748,6 +944,66 @@ static bool proj_fused_ok(const float *X, int D, int d) {
     return D % 4 == 0 && ((uintptr_t)X & 15) == 0 && d >= 1 && d <= 256;
 }
 bool project_bf16_fused_ok(const float *X, int D, int d) { return proj_fused_ok(X, D, d); }
+
+// v -> (hi, lo) = (tf32(v), tf32(v - hi)), round to nearest; both are float32 values whose low 13
+// mantissa bits are zero, so the tf32 MMA reads them exactly
+__global__ void tf32_split_kernel(const float *__restrict__ v, int64_t len, float *__restrict__ hi,
+                                  float *__restrict__ lo) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[t];
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+        const float r = __fsub_rn(x, __uint_as_float(h));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+        hi[t] = __uint_as_float(h);
+        lo[t] = __uint_as_float(l);
+    }
+}
+
+int launch_tf32_split(const float *v, int64_t len, float *hi, float *lo, cudaStream_t st) {
+    if (len <= 0) return LV_OK;
+    tf32_split_kernel<<<(unsigned)std::min<int64_t>((len + 255) / 256, 152 * 32), 256, 0, st>>>(v, len, hi, lo);
+    LV_CHECK_LAUNCH("tf32_split_kernel");
+    return LV_OK;
+}
+
+// Sum of squares of Qt X^T (Qt m x K, X n x K, given as tf32 hi / lo pairs: float32, row-major,
+// 16-byte aligned rows, K % 4 == 0) on the tensor cores; writes one FP64 partial per CTA to
+// `partial` (at least *nparts entries: call with partial = NULL to get the count) -- the caller
+// sums them in order.
+int pair_sq_tf32(const float *Qh, const float *Ql, int64_t m, const float *Xh, const float *Xl, int64_t n, int K,
+                 double *partial, int *nparts, int *status, cudaStream_t st) {
+    if (m <= 0 || n <= 0 || K <= 0 || K % 4 || m >= (1ll << 31) || n >= (1ll << 31))
+        return fail(LV_ERR_ARG, "pair_sq_tf32: unsupported sizes");
+    int dev = 0, sms = 0;
+    LV_CUDA(cudaGetDevice(&dev));
+    LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = ((m + TC_BM - 1) / TC_BM) * ((n + PL_BN - 1) / PL_BN);
+    const int grid = (int)std::min<int64_t>(tiles, sms);
+    *nparts = grid;
+    if (!partial) return LV_OK;
+    for (const float *q : {Qh, Ql, Xh, Xl})
+        if ((uintptr_t)q & 15) return fail(LV_ERR_ARG, "pair_sq_tf32: operands must be 16-byte aligned");
+    auto fn = encode_fn();
+    if (!fn) return fail(LV_ERR_CUDA, "pair_sq_tf32: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap tah, tal, tbh, tbl;
+    auto map = [&](CUtensorMap *mp, const float *ptr, int64_t rows, int box_rows) -> bool {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)K * 4};
+        cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+        cuuint32_t es[2] = {1, 1};
+        return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!map(&tah, Qh, m, TC_BM) || !map(&tal, Ql, m, TC_BM) || !map(&tbh, Xh, n, PL_BN) || !map(&tbl, Xl, n, PL_BN))
+        return fail(LV_ERR_CUDA, "pair_sq_tf32: cuTensorMapEncodeTiled failed");
+    const size_t sm = (size_t)PL_STAGES * 2 * (TC_BM + PL_BN) * 128 + 256 + 128 * 8 + 1024;
+    LV_CUDA(cudaFuncSetAttribute(pair_sq_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    pair_sq_tf32_kernel<<<grid, PL_THREADS, sm, st>>>(tah, tal, tbh, tbl, (int)m, (int)n, K, partial, status);
+    LV_CHECK_LAUNCH("pair_sq_tf32_kernel");
+    return LV_OK;
+}
 
 // workspace bytes of project_bf16 (prec LV_PREC_BF16) or project_fp8 (LV_PREC_FP8)
 size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X) {

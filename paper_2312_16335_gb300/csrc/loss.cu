@@ -196,6 +196,24 @@ __global__ void __launch_bounds__(256) tgemm_kernel(const float *__restrict__ M,
     }
 }
 
+int pair_sq_tf32(const float *Qh, const float *Ql, int64_t m, const float *Xh, const float *Xl, int64_t n, int K,
+                 double *partial, int *nparts, int *status, cudaStream_t st);
+int launch_tf32_split(const float *v, int64_t len, float *hi, float *lo, cudaStream_t st);
+
+// Bt (D x d) = B^T for B (d x D)
+__global__ void transpose_kernel(const float *__restrict__ B, int d, int D, float *__restrict__ Bt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)d * D) return;
+    const int i = (int)(t / D), k = (int)(t % D);
+    Bt[(int64_t)k * d + i] = B[t];
+}
+
+// Y -= Z elementwise (float32)
+__global__ void sub_inplace_kernel(float *__restrict__ Y, const float *__restrict__ Z, int64_t len) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < len) Y[t] = Y[t] - Z[t];
+}
+
 // out[i] = sum_y part[y * len + i] for y = 0 .. splits - 1, in that order
 __global__ void split_sum_kernel(const float *__restrict__ part, int splits, int64_t len, float *__restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,6 +279,59 @@ int leanvec_ood_loss_fwd(const float *A, const float *B, const float *Q, int64_t
         return fail(LV_ERR_ARG, "ood_loss_fwd: invalid sizes or null pointer");
     if (d > DMAX) return fail(LV_ERR_ARG, "ood_loss_fwd: d <= 256 is supported");
     cudaStream_t st = (cudaStream_t)stream;
+    if (D % 4 == 0 && m < (1ll << 31) && n < (1ll << 31)) {
+        // tensor-core form: r_ij = qt_j^T x_i with qt_j = q_j - B^T (A q_j) (float32); the tile
+        // products (three tf32 MMAs on hi / lo splits) and their squares summed by tcgen05 MMAs and
+        // the epilogue; FP64 partials summed in order
+        float *Qp = nullptr, *Bt = nullptr, *Qt = nullptr, *QB = nullptr, *Qh = nullptr, *Xh = nullptr,
+              *Xl = nullptr;
+        double *part = nullptr;
+        int *status = nullptr, h = 0, np = 0;
+        int rc = pair_sq_tf32(nullptr, nullptr, m, nullptr, nullptr, n, D, nullptr, &np, nullptr, st);  // count
+        const int64_t np_alloc = std::max(np, 1);
+        if (rc == LV_OK &&
+            (tmp_alloc((void **)&Qp, sizeof(float) * (size_t)m * d, st) ||
+             tmp_alloc((void **)&Bt, sizeof(float) * (size_t)d * D, st) ||
+             tmp_alloc((void **)&Qt, sizeof(float) * (size_t)m * D, st) ||
+             tmp_alloc((void **)&QB, sizeof(float) * (size_t)m * D, st) ||
+             tmp_alloc((void **)&Qh, sizeof(float) * (size_t)m * D, st) ||
+             tmp_alloc((void **)&Xh, sizeof(float) * (size_t)n * D, st) ||
+             tmp_alloc((void **)&Xl, sizeof(float) * (size_t)n * D, st) ||
+             tmp_alloc((void **)&part, sizeof(double) * (size_t)np_alloc, st) ||
+             tmp_alloc((void **)&status, sizeof(int), st)))
+            rc = fail(LV_ERR_OOM, "ood_loss_fwd: allocation failed");
+        if (rc == LV_OK) rc = launch_project_fp32(Q, m, D, A, d, Qp, d, st);  // A q
+        if (rc == LV_OK) {
+            transpose_kernel<<<(unsigned)(((int64_t)d * D + 255) / 256), 256, 0, st>>>(B, d, D, Bt);
+            rc = launch_project_fp32(Qp, m, d, Bt, D, QB, D, st);  // B^T A q
+        }
+        if (rc == LV_OK && cudaMemcpyAsync(Qt, Q, sizeof(float) * (size_t)m * D, cudaMemcpyDeviceToDevice, st) !=
+                               cudaSuccess)
+            rc = fail(LV_ERR_CUDA, "ood_loss_fwd: copy failed");
+        if (rc == LV_OK) {
+            sub_inplace_kernel<<<(unsigned)(((int64_t)m * D + 255) / 256), 256, 0, st>>>(Qt, QB, (int64_t)m * D);
+            if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) rc = fail(LV_ERR_CUDA, "memset failed");
+        }
+        if (rc == LV_OK) rc = launch_tf32_split(Qt, (int64_t)m * D, Qh, QB, st);  // QB now holds the lo part
+        if (rc == LV_OK) rc = launch_tf32_split(X, (int64_t)n * D, Xh, Xl, st);
+        if (rc == LV_OK) rc = pair_sq_tf32(Qh, QB, m, Xh, Xl, n, D, part, &np, status, st);
+        std::vector<double> hp(np_alloc, 0.0);
+        if (rc == LV_OK && (cudaMemcpyAsync(hp.data(), part, sizeof(double) * np, cudaMemcpyDeviceToHost, st) !=
+                                cudaSuccess ||
+                            cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                            cudaStreamSynchronize(st) != cudaSuccess))
+            rc = fail(LV_ERR_CUDA, "ood_loss_fwd: reduction copy failed");
+        if (rc == LV_OK && h) rc = fail(LV_ERR_TIMEOUT, "ood_loss_fwd: a tensor-core pipeline wait timed out");
+        if (rc == LV_OK) {
+            double s = 0.0;
+            for (double v : hp) s += v;  // fixed order
+            *loss = s / ((double)n * (double)m);
+        }
+        for (void *p : {(void *)Qp, (void *)Bt, (void *)Qt, (void *)QB, (void *)Qh, (void *)Xh, (void *)Xl, (void *)part,
+                        (void *)status})
+            tmp_free(p, st);
+        return rc;
+    }
     PairWork w;
     int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, false, st);
     const int nb = (int)((m + PT - 1) / PT);
