@@ -780,7 +780,7 @@ def bench_kernels(args, dev):
     # a1 / a11: projections x -> B x of the database (and q -> A q of a search batch)
     A = lv.leanvec_fit_id(X[:100_000], d)
     ldy = (d + 15) // 16 * 16
-    for prec, tag in ((lv.PREC_BF16, "bf16"), (lv.PREC_FP8, "fp8"), (lv.PREC_FP32, "fp32")):
+    for prec, tag in ((lv.PREC_BF16, "bf16"), (lv.PREC_FP8, "fp8"), (lv.PREC_TF32X3, "tf32x3"), (lv.PREC_FP32, "fp32")):
         t = timed(lambda: lv.leanvec_project(X, A, ldy=ldy, precision=prec), 5)
         # algorithmic bytes: read X (float32), write Y (float32); the GEMM itself is 2 n D d flops
         hbm_row(f"project_{tag}_{n // 1000}k_{D}_to_{d}", 4.0 * n * D + 4.0 * n * ldy, t)

@@ -118,7 +118,10 @@ int leanvec_lvq_encode(const float *V, int64_t n, int dim, const float *mean, in
 typedef enum {
     LV_PREC_FP32 = 0,  /* float32 CUDA-core GEMM, float32 accumulate */
     LV_PREC_BF16 = 1,  /* bf16 operands on the tcgen05 tensor cores, float32 accumulate */
-    LV_PREC_FP8 = 2    /* e4m3 operands with per-row scales, float32 accumulate */
+    LV_PREC_FP8 = 2,   /* e4m3 operands with per-row scales, float32 accumulate */
+    LV_PREC_TF32X3 = 3 /* float32-accurate on the tensor cores: each operand split into tf32
+                          hi + lo, three tf32 products (about 21 bits of every float32 product),
+                          float32 accumulate; needs D % 4 == 0, 16-byte aligned rows, d <= 256 */
 } lv_precision;
 
 /* Y = X P^T: X is n x D, P is d x D, Y is n x ldy with ldy >= d (device); the

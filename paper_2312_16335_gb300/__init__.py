@@ -18,9 +18,9 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "autotune_target_d", "SearchGraph", "HostPipeline", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "autotune_target_d", "SearchGraph", "HostPipeline", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
-PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8, PREC_TF32X3 = 0, 1, 2, 3
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
 METRIC_IP, METRIC_L2 = 0, 1
 

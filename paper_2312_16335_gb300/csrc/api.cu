@@ -50,8 +50,11 @@ int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *
 size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X);
 bool project_bf16_fused_ok(const float *X, int D, int d);
 // tensor-core projection with bf16 or e4m3 (per-row scaled) operands
+int project_tf32x3(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                   size_t *ws_bytes, int *status, cudaStream_t st);
 static int project_tc(int prec, const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
                       size_t *ws_bytes, int *status, cudaStream_t st) {
+    if (prec == LV_PREC_TF32X3) return project_tf32x3(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st);
     return prec == LV_PREC_FP8 ? project_fp8(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st)
                                : project_bf16(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st);
 }
@@ -137,8 +140,8 @@ int leanvec_project(const float *X, int64_t n, int D, const float *P, int d, flo
     if (n < 0 || D <= 0 || d <= 0 || ldy < d || (n > 0 && (!X || !P || !Y)))
         return fail(LV_ERR_ARG, "project: invalid sizes or null pointer");
     if (precision == LV_PREC_FP32) return launch_project_fp32(X, n, D, P, d, Y, ldy, (cudaStream_t)stream);
-    if (precision != LV_PREC_BF16 && precision != LV_PREC_FP8)
-        return fail(LV_ERR_ARG, "project: precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
+    if (precision != LV_PREC_BF16 && precision != LV_PREC_FP8 && precision != LV_PREC_TF32X3)
+        return fail(LV_ERR_ARG, "project: precision must be LV_PREC_FP32, LV_PREC_BF16, LV_PREC_FP8 or LV_PREC_TF32X3");
     if (n == 0) return LV_OK;
     cudaStream_t st = (cudaStream_t)stream;
     void *ws = nullptr;
@@ -365,8 +368,8 @@ int leanvec_encode(lv_index *idx, const float *X, int64_t n, int D, const float 
     if (primary_bits != 4 && primary_bits != 8) return fail(LV_ERR_ARG, "encode: primary_bits must be 4 or 8");
     if (secondary_bits != 0 && secondary_bits != 8 && secondary_bits != 16)
         return fail(LV_ERR_ARG, "encode: secondary_bits must be 0, 8 (LVQ-8) or 16 (FP16)");
-    if (projection_precision < LV_PREC_FP32 || projection_precision > LV_PREC_FP8)
-        return fail(LV_ERR_ARG, "encode: projection precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
+    if (projection_precision < LV_PREC_FP32 || projection_precision > LV_PREC_TF32X3)
+        return fail(LV_ERR_ARG, "encode: projection precision must be an lv_precision value");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "encode: cannot select device");
     cudaStream_t st = (cudaStream_t)stream;
@@ -495,8 +498,8 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     if (!desc && (u.k < 1 || u.k > u.L || u.k > ldo || u.rerank < 0 || u.rerank > u.L || u.max_hops < 0))
         return fail(LV_ERR_ARG, "search: need 1 <= k <= min(L, ldo), 0 <= rerank <= L, max_hops >= 0");
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search: rerank needs a secondary store");
-    if (params->projection < LV_PREC_FP32 || params->projection > LV_PREC_FP8)
-        return fail(LV_ERR_ARG, "search: projection precision must be LV_PREC_FP32, LV_PREC_BF16 or LV_PREC_FP8");
+    if (params->projection < LV_PREC_FP32 || params->projection > LV_PREC_TF32X3)
+        return fail(LV_ERR_ARG, "search: projection precision must be an lv_precision value");
     DeviceGuard g(idx->device);
     if (!g.ok) return fail(LV_ERR_CUDA, "search: cannot select device");
     cudaStream_t st = (cudaStream_t)stream;
@@ -509,7 +512,9 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     idx->last_kernels = 0;
     // kernels of the projection: padding copy / float32 GEMM: 1; bf16 with float32 X converted in
     // the GEMM: cast of A + GEMM; otherwise casts of Q and A + GEMM
+    // (tf32x3: split of A + GEMM)
     const int proj_kernels = idx->pbits == 32 || params->projection == LV_PREC_FP32 ? 1
+                             : params->projection == LV_PREC_TF32X3 ? 2
                              : params->projection == LV_PREC_BF16 && project_bf16_fused_ok(Q, idx->D, idx->d) ? 2
                                                                                                                 : 3;
     if (idx->pbits == 32) {

@@ -714,6 +714,257 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------------
+// Float32-accurate projection Y = X P^T on the tensor cores: every operand is split into tf32
+// hi = tf32(v) and lo = tf32(v - hi) (both exact in tf32) and a tile product is
+// hi_x hi_p + hi_x lo_p + lo_x hi_p, three tcgen05.mma kind::tf32 (about 21 bits of each float32
+// product; float32 accumulation in TMEM).  X stays float32 in HBM: warp 9 streams 128 x 32 blocks
+// by TMA into a 4-deep staging ring, warps 4-7 split them into the hi / lo operand tiles (128-byte
+// swizzle, 32 floats per row: chunk c of row r at r * 128 + ((c ^ (r & 7)) << 4)); P's hi / lo
+// tiles (split once by tf32_split_kernel) come by TMA.  Persistent over 128-row tiles with two TMEM
+// accumulators; the epilogue (warps 0-3) is proj_f32in_kernel's: shared-memory slabs, coalesced
+// row stores, zeros in columns N .. ldy-1.
+constexpr int TX_XSTAGES = 4;
+constexpr uint32_t TX_XBYTES = 128 * 32 * 4;
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    return __uint_as_float(h);
+}
+
+__global__ void __launch_bounds__(PF_THREADS, 1)
+    proj_tf32x3_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tbh,
+                       const __grid_constant__ CUtensorMap tbl, const PfParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int BN = p.BN, PS = p.stages;
+    // operand stage: A hi | A lo | B hi | B lo (one 32-wide K block)
+    const uint32_t a_bytes = TC_BM * 128, b_bytes = (uint32_t)BN * 128;
+    const uint32_t stage_bytes = 2 * (a_bytes + b_bytes);
+    uint8_t *xstage = base + PS * stage_bytes;  // TX_XSTAGES x 16 KB
+    uint64_t *full = reinterpret_cast<uint64_t *>(xstage + TX_XSTAGES * TX_XBYTES);
+    uint64_t *empty = full + 2;
+    uint64_t *sfull = empty + 2;
+    uint64_t *sempty = sfull + TX_XSTAGES;
+    uint64_t *tfull = sempty + TX_XSTAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = (p.M + TC_BM - 1) / TC_BM;
+    const int nkb = (p.K + 31) / 32;
+    const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int64_t total = (int64_t)my_tiles * nkb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PS; ++s) {
+            mbar_init(full + s, 128);
+            mbar_init(empty + s, 1);
+        }
+        for (int t = 0; t < TX_XSTAGES; ++t) {
+            mbar_init(sfull + t, 1);
+            mbar_init(sempty + t, 128);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull + b, 1);
+            mbar_init(tempty + b, 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 9) {
+        // ---- X producer
+        if (lane == 0) {
+            for (int64_t g = 0; g < total; ++g) {
+                const int t = (int)(g % TX_XSTAGES);
+                const int64_t w = g / TX_XSTAGES;
+                if (w > 0 && !mbar_wait(sempty + t, (uint32_t)((w - 1) & 1))) {
+                    *abort_flag = 1;
+                    atomicOr(p.status, ST_TIMEOUT);
+                }
+                if (*abort_flag) {
+                    for (int64_t q = std::max<int64_t>(0, g - TX_XSTAGES); q < g; ++q)
+                        mbar_wait(sfull + (int)(q % TX_XSTAGES), (uint32_t)((q / TX_XSTAGES) & 1));
+                    break;
+                }
+                const int tile = (int)blockIdx.x + (int)(g / nkb) * (int)gridDim.x;
+                mbar_expect_tx(sfull + t, TX_XBYTES);
+                tma_load_2d(xstage + (size_t)t * TX_XBYTES, &tx, (int)(g % nkb) * 32, tile * TC_BM, sfull + t);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4 && warp < 8) {
+        // ---- converters: 128 rows x 8 chunks of 4 floats per K block, 8 chunks per thread
+        const int ct = threadIdx.x - 128;
+        for (int64_t g = 0; g < total; ++g) {
+            const int t = (int)(g % TX_XSTAGES);
+            const int s = (int)(g % PS);
+            const int64_t u = g / PS;
+            bool ok = !*abort_flag && mbar_wait(sfull + t, (uint32_t)((g / TX_XSTAGES) & 1));
+            float4 v[8];
+            if (ok) {
+                const uint8_t *xs = xstage + (size_t)t * TX_XBYTES;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int ci = ct + 128 * j;
+                    v[j] = *reinterpret_cast<const float4 *>(xs + (ci >> 3) * 128 + 16 * (ci & 7));
+                }
+            }
+            mbar_arrive(sempty + t);
+            if (ok && u > 0) ok = mbar_wait(empty + s, (uint32_t)((u - 1) & 1));
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            uint8_t *sa = base + s * stage_bytes;
+            if (ct == 0) {
+                mbar_tx_only(full + s, 2 * b_bytes);
+                tma_load_2d(sa + 2 * a_bytes, &tbh, (int)(g % nkb) * 32, 0, full + s);
+                tma_load_2d(sa + 2 * a_bytes + b_bytes, &tbl, (int)(g % nkb) * 32, 0, full + s);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int ci = ct + 128 * j;
+                const int r = ci >> 3, c = ci & 7;
+                const float x[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+                float hi[4], lo[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    hi[e] = tf32_rna(x[e]);
+                    lo[e] = tf32_rna(__fsub_rn(x[e], hi[e]));
+                }
+                const uint32_t off = r * 128 + ((c ^ (r & 7)) << 4);
+                *reinterpret_cast<float4 *>(sa + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4 *>(sa + a_bytes + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full + s);
+        }
+    } else if (warp == 8) {
+        // ---- MMA issuer: per K block 4 steps of 8 floats, 3 products each
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(TC_BM >> 4) << 24);
+            int64_t g = 0;
+            for (int tc = 0; tc < my_tiles && !*abort_flag; ++tc) {
+                const int b = tc & 1, v = tc >> 1;
+                if (v > 0 && !mbar_wait(tempty + b, (uint32_t)((v - 1) & 1))) {
+                    *abort_flag = 1;
+                    atomicOr(p.status, ST_TIMEOUT);
+                    break;
+                }
+                const uint32_t acc_addr = tmem + (uint32_t)(b * 256);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % PS);
+                    if (!mbar_wait(full + s, (uint32_t)((g / PS) & 1)) || *abort_flag) {
+                        *abort_flag = 1;
+                        atomicOr(p.status, ST_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    uint8_t *sa = base + s * stage_bytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t ah = sdesc(sa + 32 * k), al = sdesc(sa + a_bytes + 32 * k);
+                        const uint64_t bh = sdesc(sa + 2 * a_bytes + 32 * k);
+                        const uint64_t bl = sdesc(sa + 2 * a_bytes + b_bytes + 32 * k);
+                        const uint64_t ad[3] = {ah, ah, al}, bd[3] = {bh, bl, bh};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const uint32_t accf = (kb > 0 || k > 0 || q > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\t"
+                                "setp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+                                "l"(ad[q]), "l"(bd[q]), "r"(idesc), "r"(accf)
+                                : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(empty + s))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(tfull + b))
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(drain))
+                         : "memory");
+            if (!mbar_wait(drain, 0)) atomicOr(p.status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: tile row = TMEM lane; each warp moves its 32 rows through a 32 x 33
+        // float slab in shared memory, 32 columns at a time, so that every global store
+        // instruction writes one whole 128-byte row segment
+        float *slab = reinterpret_cast<float *>(tmem_slot + 2) + warp * 32 * 33;
+        for (int tc = 0; tc < my_tiles; ++tc) {
+            const int tile = (int)blockIdx.x + tc * (int)gridDim.x;
+            const int b = tc & 1, v = tc >> 1;
+            const bool ok = !*abort_flag && mbar_wait(tfull + b, (uint32_t)(v & 1));
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row0 = tile * TC_BM + warp * 32;
+            for (int c0 = 0; c0 < p.ldy; c0 += 32) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = c0 + 16 * h;
+                    uint32_t r[16];
+                    if (cc < BN) {
+                        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + cc);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                              "=r"(r[14]), "=r"(r[15])
+                            : "r"(addr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        slab[lane * 33 + 16 * h + j] = (cc + j < p.N) ? __uint_as_float(r[j]) : 0.f;
+                }
+                __syncwarp();
+                const int col = c0 + lane;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = row0 + rr;
+                    if (row < p.M && col < p.ldy) p.Y[(int64_t)row * p.ldy + col] = slab[rr * 33 + lane];
+                }
+                __syncwarp();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(tempty + b);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 8)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // sum of the split-K partials in a fixed order
 __global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits, int M, int N, float *__restrict__ C,
                                      int ldc) {
@@ -1007,6 +1258,7 @@ int pair_sq_tf32(const float *Qh, const float *Ql, int64_t m, const float *Xh, c
 
 // workspace bytes of project_bf16 (prec LV_PREC_BF16) or project_fp8 (LV_PREC_FP8)
 size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X) {
+    if (prec == LV_PREC_TF32X3) return 2 * round_up((int64_t)d * D * 4, 256);
     if (prec == LV_PREC_FP8) {
         const int ldx = (int)round_up(D, 16);
         return round_up((int64_t)n * ldx, 256) + round_up((int64_t)d * ldx, 256) + round_up(4 * n, 256) +
@@ -1065,6 +1317,61 @@ static int project_bf16_fused(const float *X, int64_t n, int D, const float *P, 
     LV_CUDA(cudaFuncSetAttribute(proj_f32in_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     proj_f32in_kernel<<<grid, PF_THREADS, sm, st>>>(tx, tb, pp);
     LV_CHECK_LAUNCH("proj_f32in_kernel");
+    return LV_OK;
+}
+
+// Y (n x ldy) = X P^T, float32-accurate, on the tensor cores (three tf32 products of hi / lo
+// splits); X is split inside the GEMM (16-byte aligned rows, D % 4 == 0, d <= 256), P's hi / lo
+// copies live in the caller's workspace (*ws, grown as needed); columns d..ldy-1 zeroed.
+int project_tf32x3(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                   size_t *ws_bytes, int *status, cudaStream_t st) {
+    if (!proj_fused_ok(X, D, d)) return fail(LV_ERR_ARG, "tf32x3 projection: needs D % 4 == 0, aligned rows, d <= 256");
+    if (n >= (int64_t)1 << 31) return fail(LV_ERR_ARG, "tf32x3 projection: sizes too large");
+    const size_t pb = round_up((int64_t)d * D * 4, 256);
+    int rc = ensure_ws(ws, ws_bytes, 2 * pb);
+    if (rc) return rc;
+    float *Ph = reinterpret_cast<float *>(*ws);
+    float *Pl = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(*ws) + pb);
+    rc = launch_tf32_split(P, (int64_t)d * D, Ph, Pl, st);
+    if (rc) return rc;
+    const int BN = (int)round_up(d, 16);
+    auto fn = encode_fn();
+    if (!fn) return fail(LV_ERR_CUDA, "tcgen05 GEMM: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap tx, tbh, tbl;
+    auto map = [&](CUtensorMap *mp, const float *ptr, int64_t rows, int box_rows, CUtensorMapSwizzle sw) -> bool {
+        cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)D * 4};
+        cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+        cuuint32_t es[2] = {1, 1};
+        return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!map(&tx, X, n, TC_BM, CU_TENSOR_MAP_SWIZZLE_NONE) || !map(&tbh, Ph, d, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !map(&tbl, Pl, d, BN, CU_TENSOR_MAP_SWIZZLE_128B))
+        return fail(LV_ERR_CUDA, "tf32x3 projection: cuTensorMapEncodeTiled failed");
+    PfParams pp;
+    pp.M = (int)n;
+    pp.K = D;
+    pp.N = d;
+    pp.BN = BN;
+    pp.Y = Y;
+    pp.ldy = ldy;
+    pp.status = status;
+    // stage: A hi, A lo, B hi, B lo of one 32-wide K block; fixed: X staging ring, barriers and
+    // flags, epilogue slabs, alignment slack
+    const size_t stage = (size_t)2 * (TC_BM + BN) * 128,
+                 fixed = (size_t)TX_XSTAGES * TX_XBYTES + 256 + 4 * 32 * 33 * 4 + 1024;
+    pp.stages = 2 * stage + fixed <= 227 * 1024 ? 2 : 1;
+    const size_t sm = pp.stages * stage + fixed;
+    int dev = 0, sms = 0;
+    LV_CUDA(cudaGetDevice(&dev));
+    LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = (n + TC_BM - 1) / TC_BM;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);
+    LV_CUDA(cudaFuncSetAttribute(proj_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    proj_tf32x3_kernel<<<grid, PF_THREADS, sm, st>>>(tx, tbh, tbl, pp);
+    LV_CHECK_LAUNCH("proj_tf32x3_kernel");
     return LV_OK;
 }
 

@@ -118,3 +118,43 @@ def test_scratch_pool_reuse_and_trim(lv):
     lv.leanvec_trim_scratch(0)
     K3 = lv.leanvec_second_moment(X, precision=lv.PREC_BF16)
     torch.testing.assert_close(K1, K3, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("n,D,d,ldy", [(300, 128, 32, 32), (1000, 768, 160, 160), (77, 200, 64, 80),
+                                       (100000, 256, 64, 72), (40000, 132, 256, 256), (3000, 64, 1, 4),
+                                       (1, 768, 160, 176)])
+def test_projection_tf32x3(lv, n, D, d, ldy):
+    """float32-accurate projection on the tensor cores (tf32 hi / lo splits, three products): the
+    FP32 bound 1e-5 ||x|| ||p|| of the CUDA-core path holds, and the error is far below bf16's.
+    n = 100000 / 40000 wrap both TMEM accumulators and the stage rings; d = 256 takes one
+    operand stage (shared memory); D = 132 leaves a ragged K block."""
+    rng = np.random.default_rng(n + 3 * D + d)
+    X = rng.standard_normal((n, D)).astype(np.float32)
+    P = rng.standard_normal((d, D)).astype(np.float32)
+    Y = lv.leanvec_project(t(X), t(P), ldy=ldy, precision=lv.PREC_TF32X3).cpu().numpy()
+    ref = X.astype(np.float64) @ P.T.astype(np.float64)
+    scale = np.linalg.norm(X, axis=1)[:, None] * np.linalg.norm(P, axis=1)[None, :]
+    err = np.abs(Y[:, :d] - ref) / scale
+    assert err.max() <= 1e-5
+    assert err.max() <= 2.0 ** -14
+    assert not Y[:, d:].any()
+
+
+def test_search_and_encode_with_tf32x3_projection(lv):
+    """Search with the tf32x3 query projection agrees with the FP64-projected oracle like the
+    float32 path (>= 99 % of ids); encode with it decodes within delta / 2 + 1e-5 ||x|| ||p||."""
+    pb = small_problem(oracle, n=3000, D=64, d=16, m=300, seed=8)
+    idx = gpu_index(lv, pb)
+    ids, _ = idx.search(t(pb["Q"]), t(pb["P"]), k=10, L=48, rerank=48, projection=lv.PREC_TF32X3)
+    ref = oracle.search(pb["graph"], pb["entry"], pb["Q"].astype(np.float64) @ pb["P"].T.astype(np.float64),
+                        k=10, L=48, rerank=48, prim=pb["prim"], sec=pb["sec"], qs=pb["Q"].astype(np.float64))
+    assert (ids.cpu().numpy() == ref["ids"]).mean() >= 0.99
+    idx2 = lv.Index(0).encode(t(pb["X"]), t(pb["P"]), 8, 8, precision=lv.PREC_TF32X3)
+    idx2.sync_status()
+    from gpu_util import unpack_records
+    codes, delta, lower, _, _, _, _ = unpack_records(idx2.primary_records().cpu().numpy(), 16, 8)
+    mean = idx2.primary_mean().cpu().numpy().astype(np.float64)
+    dec = mean[None, :] + lower[:, None].astype(np.float64) + delta[:, None].astype(np.float64) * codes
+    Yr = pb["X"].astype(np.float64) @ pb["P"].T.astype(np.float64)
+    bound = delta / 2 + 1e-5 * np.linalg.norm(pb["X"], axis=1) * np.linalg.norm(pb["P"], axis=1).max()
+    assert np.all(np.abs(dec - Yr).max(axis=1) <= bound * (1 + 1e-6))
