@@ -729,7 +729,7 @@ def bench_kernels(args, dev):
     """The offline and auxiliary kernels of the path, each timed alone through its C-ABI call
     (CUDA events on the launching stream, warm-up first) and set against its roofline:
     second moments and projections (tcgen05 GEMMs), LVQ encode and column mean (HBM), FP64
-    Jacobi eigh, LeanVec-ID / -OOD fits, the pair loss forward + backward (CUDA-core FP32)."""
+    Jacobi eigh, LeanVec-ID / -OOD fits, the pair loss forward + backward (tf32x3 tensor cores)."""
     from paper_2312_16335_gb300 import build_lib
     build_lib.build()
     import paper_2312_16335_gb300 as lv
@@ -833,7 +833,14 @@ def bench_kernels(args, dev):
                                                "peak_source": src + " bf16 x nominal tf32/bf16 ratio"}
     log("loss fwd", res["pair_loss_fwd_10k_x_100k_512_128"])
     t = timed(lambda: lv.leanvec_ood_loss_bwd(Ai, Ai, Qo, Xo), 2)
-    res["pair_loss_bwd_10k_x_100k_512_128"] = {"seconds": t}
+    # the backward forms R = Qt X^T and contracts it twice (R X', R^T Q'), each in tf32x3 form:
+    # 3 x 2 m n (D + 2 d) executed flops; the final d x D products (float32 CUDA cores) are not counted
+    exec_bwd = 3 * 2.0 * Qo.shape[0] * Xo.shape[0] * (512 + 2 * 128)
+    res["pair_loss_bwd_10k_x_100k_512_128"] = {"seconds": t, "pair_tflops": exec_bwd / 3 / t / 1e12,
+                                               "bound": "tensor (tf32, three MMAs per product)",
+                                               "executed_tflops": exec_bwd / t / 1e12, "peak_tflops": tf32_peak,
+                                               "frac": exec_bwd / t / 1e12 / tf32_peak,
+                                               "peak_source": src + " bf16 x nominal tf32/bf16 ratio"}
     log("loss bwd", res["pair_loss_bwd_10k_x_100k_512_128"])
     out = {"metric": "offline / auxiliary kernels through the C ABI: seconds per call and the fraction of each "
                      "kernel's roofline (tensor: bf16 peak " + src + ", fp8 = 2x bf16; hbm: copy peak " + hbm_src + ")",

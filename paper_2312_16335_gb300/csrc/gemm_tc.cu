@@ -519,27 +519,65 @@ __global__ void __launch_bounds__(PF_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Sum of squares of R = Qt X^T on the tensor cores (tcgen05.mma kind::tf32): the pair loss of the
-// differentiation form, r_ij = q_j^T x_i - (A q_j)^T (B x_i) = qt_j^T x_i with qt_j = q_j - B^T A q_j
-// computed beforehand, so that the tile products themselves carry no cancellation.  Each operand
-// comes as a tf32 pair (hi = tf32(v), lo = tf32(v - hi), both exact in tf32) and every tile
-// product is hi_a hi_b + hi_a lo_b + lo_a hi_b: three tf32 MMAs that keep about 21 bits of the
-// float32 products (the tf32 unit reads only the top 19 bits of a float; one tf32 product alone is
-// biased by its truncation).  Float32 tiles go from HBM to shared memory by TMA (128-byte swizzle,
-// 32 floats per row) and straight into the MMA.  Persistent over 128 x 256 tiles (query rows x
-// database rows), tiles t = c, c + G, ...; two TMEM accumulators (512 columns) let the epilogue of
-// one tile overlap the main loop of the next.  Rows past m or n are zero-filled by TMA and add
-// nothing.
+// C = A B^T in float32-accurate tf32x3 form on the tensor cores (tcgen05.mma kind::tf32), for the
+// differentiation form of the OOD loss.  Each operand comes as a tf32 pair (hi = tf32(v),
+// lo = tf32(v - hi), both exact in tf32) and every tile product is hi_a hi_b + hi_a lo_b + lo_a hi_b:
+// three tf32 MMAs that keep about 21 bits of the float32 products (the tf32 unit reads only the
+// top 19 bits of a float; one tf32 product alone is biased by its truncation).  Float32 tiles go
+// from HBM to shared memory by TMA (128-byte swizzle, 32 floats per row) and straight into the MMA.
+// Persistent over work items = (K split, 128 x 256 tile), items t = c, c + G, ...; two TMEM
+// accumulators (512 columns) let the epilogue of one item overlap the main loop of the next.
+// Rows and K columns past the operands' extents are zero-filled by TMA and add nothing.
 //   warp 0, lane 0 : TMA producer (2-stage ring of A hi / lo 128 x 32 and B hi / lo 256 x 32 tiles)
 //   warp 1         : TMEM allocation; lane 0 issues the MMAs (M 128, N 256, K 8) and commits
-//   warps 2-5      : epilogue; warp w reads TMEM lanes 32 (w % 4) ..: sum of squares of its row
-//                    (float32 per 16 columns, then FP64), one FP64 partial per CTA
-constexpr int PL_THREADS = 192, PL_STAGES = 2, PL_BN = 256;
+//   warps 2-5 (PAIR_SQ) or 2-9 (the others): epilogue; warp w reads TMEM lanes 32 (w % 4) .. (rows
+//                    of C), the 256 columns or, with eight warps, half of them each; by MODE:
+//     PAIR_SQ : sum of squares of its rows (float32 per 16 columns, then FP64), one FP64 partial
+//               per CTA -- the pair loss, with A = Qt (qt_j = q_j - B^T A q_j) and B = X, so that
+//               r_ij = qt_j^T x_i carries no cancellation inside the tile products;
+//     PAIR_R  : the tile as tf32 hi / lo pairs twice: C^T (lanes write consecutive rows of C, so
+//               each column is one coalesced run) and C row-major (through a 32 x 33 shared-memory
+//               slab per warp, one coalesced 128-byte run per row) -- the residual matrix R and
+//               R^T, operands of the two gradient contractions;
+//     PAIR_T  : C^T of split s into out + s * split_stride (float32, pitch ldo), added to what is
+//               there when `accumulate` -- R X' and R^T Q' with the d-wide side as M.
+constexpr int PL_STAGES = 2, PL_BN = 256;
+constexpr int PAIR_SQ = 0, PAIR_R = 1, PAIR_T = 2;
 
-__global__ void __launch_bounds__(PL_THREADS, 1)
-    pair_sq_tf32_kernel(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
-                        const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int m,
-                        int n, int K, double *__restrict__ partial, int *__restrict__ status) {
+struct PairOut {
+    double *partial = nullptr;                                      // PAIR_SQ
+    float *ch = nullptr, *cl = nullptr, *th = nullptr, *tl = nullptr;  // PAIR_R
+    int64_t ldc = 0, ldt = 0;
+    float *out = nullptr;                                           // PAIR_T
+    int64_t ldo = 0, split_stride = 0;
+    int accumulate = 0;
+};
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    return __uint_as_float(h);
+}
+
+// 16 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+}
+
+// epilogue warps: four for the light sum of squares, eight (two per TMEM lane quarter, half the
+// columns each) where the epilogue stores the tile
+template <int MODE>
+constexpr int pair_epi_warps() { return MODE == PAIR_SQ ? 4 : 8; }
+
+template <int MODE>
+__global__ void __launch_bounds__(64 + 32 * pair_epi_warps<MODE>(), 1)
+    pair_tf32_kernel(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
+                     const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M, int N,
+                     int K, int splits, int kps, const PairOut o, int *__restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     // stage: A hi | A lo | B hi | B lo
@@ -551,12 +589,14 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
     uint64_t *drain = tempty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    constexpr int EW = pair_epi_warps<MODE>();
+    // after the barriers: PAIR_SQ's FP64 reduction slots, or the others' 32 x 33 slabs (one per warp)
     double *red = reinterpret_cast<double *>(base + PL_STAGES * stage_bytes + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = (m + TC_BM - 1) / TC_BM, nt = (n + PL_BN - 1) / PL_BN;
-    const int64_t tiles = (int64_t)mt * nt;
+    const int mt = (M + TC_BM - 1) / TC_BM, nt = (N + PL_BN - 1) / PL_BN;
+    const int64_t tiles = (int64_t)mt * nt, items = tiles * splits;
     const int nkb = (K + 31) / 32;
-    const int my_tiles = (int64_t)blockIdx.x < tiles ? (int)((tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+    const int my_items = (int64_t)blockIdx.x < items ? (int)((items - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < PL_STAGES; ++s) {
@@ -565,7 +605,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull + b, 1);
-            mbar_init(tempty + b, 128);
+            mbar_init(tempty + b, 32 * EW);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -585,10 +625,12 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             int64_t g = 0;
-            for (int tc = 0; tc < my_tiles && !*abort_flag; ++tc) {
-                const int64_t tile = blockIdx.x + (int64_t)tc * gridDim.x;
+            for (int it = 0; it < my_items && !*abort_flag; ++it) {
+                const int64_t item = blockIdx.x + (int64_t)it * gridDim.x;
+                const int64_t tile = item % tiles;
                 const int m0 = (int)(tile / nt) * TC_BM, n0 = (int)(tile % nt) * PL_BN;
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int kb0 = (int)(item / tiles) * kps, kb1 = min(nkb, kb0 + kps);
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % PL_STAGES);
                     const int64_t u = g / PL_STAGES;
                     if (u > 0 && !mbar_wait(empty + s, (uint32_t)((u - 1) & 1))) {
@@ -615,8 +657,10 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PL_BN >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
             int64_t g = 0;
-            for (int tc = 0; tc < my_tiles && !*abort_flag; ++tc) {
-                const int b = tc & 1, v = tc >> 1;
+            for (int it = 0; it < my_items && !*abort_flag; ++it) {
+                const int64_t item = blockIdx.x + (int64_t)it * gridDim.x;
+                const int kb0 = (int)(item / tiles) * kps, kb1 = min(nkb, kb0 + kps);
+                const int b = it & 1, v = it >> 1;
                 if (v > 0 && !mbar_wait(tempty + b, (uint32_t)((v - 1) & 1))) {
                     *abort_flag = 1;
                     atomicOr(status, ST_TIMEOUT);
@@ -624,7 +668,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
                 }
                 const uint32_t acc_addr = tmem + (uint32_t)(b * 256);
                 bool ok = true;
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % PL_STAGES);
                     if (!mbar_wait(full + s, (uint32_t)((g / PL_STAGES) & 1)) || *abort_flag) {
                         *abort_flag = 1;
@@ -642,7 +686,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
                         const uint64_t ad[3] = {ah, ah, al}, bd[3] = {bh, bl, bh};
 #pragma unroll
                         for (int t = 0; t < 3; ++t) {
-                            const uint32_t accf = (kb > 0 || k > 0 || t > 0) ? 1u : 0u;
+                            const uint32_t accf = (kb > kb0 || k > 0 || t > 0) ? 1u : 0u;
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\t"
                                 "setp.ne.b32 p, %4, 0;\n\t"
@@ -667,10 +711,13 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warps 2..5 cover the TMEM lane quarters 2, 3, 0, 1
+        // ---- epilogue: warps 2..5 (and 6..9) cover the TMEM lane quarters 2, 3, 0, 1
         const int quarter = warp & 3;
-        for (int tc = 0; tc < my_tiles; ++tc) {
-            const int b = tc & 1, v = tc >> 1;
+        constexpr int NCW = PL_BN / (EW / 4);  // columns per epilogue warp
+        const int cbeg = ((warp - 2) >> 2) * NCW;
+        float *slab = reinterpret_cast<float *>(base + PL_STAGES * stage_bytes + 256) + (warp - 2) * 32 * 33;
+        for (int it = 0; it < my_items; ++it) {
+            const int b = it & 1, v = it >> 1;
             const bool ok = !*abort_flag && mbar_wait(tfull + b, (uint32_t)(v & 1));
             if (!ok) {
                 *abort_flag = 1;
@@ -678,37 +725,91 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int c0 = 0; c0 < PL_BN; c0 += 16) {
-                uint32_t r[16];
-                const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + c0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float sq = 0.f;
+            const int64_t item = blockIdx.x + (int64_t)it * gridDim.x;
+            const int64_t tile = item % tiles;
+            const int m0 = (int)(tile / nt) * TC_BM, n0 = (int)(tile % nt) * PL_BN;
+            const int row0 = m0 + quarter * 32;  // C rows of this warp: row0 .. row0 + 31
+            const int row = row0 + lane;
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+            if (MODE == PAIR_SQ) {
+                for (int c0 = 0; c0 < PL_BN; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tbase + (uint32_t)c0, r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float sq = 0.f;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float x = __uint_as_float(r[j]);
-                    sq = fmaf(x, x, sq);
+                    for (int j = 0; j < 16; ++j) {
+                        const float x = __uint_as_float(r[j]);
+                        sq = fmaf(x, x, sq);
+                    }
+                    acc += (double)sq;
                 }
-                acc += (double)sq;
+            } else {
+                for (int c0 = cbeg; c0 < cbeg + NCW && n0 + c0 < N; c0 += 32) {  // warp-uniform bound
+                    uint32_t r[32];
+                    tmem_ld16(tbase + (uint32_t)c0, r);
+                    tmem_ld16(tbase + (uint32_t)(c0 + 16), r + 16);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int ncols = min(32, N - (n0 + c0));
+                    if (MODE == PAIR_T) {
+                        float *os = o.out + (int64_t)(item / tiles) * o.split_stride;
+                        if (row < M) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (j < ncols) {
+                                    float *p = os + (int64_t)(n0 + c0 + j) * o.ldo + row;
+                                    const float x = __uint_as_float(r[j]);
+                                    *p = o.accumulate ? *p + x : x;
+                                }
+                            }
+                        }
+                    } else {
+                        float hi[32], lo[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float x = __uint_as_float(r[j]);
+                            hi[j] = tf32_rna(x);
+                            lo[j] = tf32_rna(__fsub_rn(x, hi[j]));
+                        }
+                        // C^T: column n0 + c0 + j is row n0 + c0 + j of C^T, the lanes' rows consecutive
+                        if (row < M) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (j < ncols) {
+                                    const int64_t at = (int64_t)(n0 + c0 + j) * o.ldt + row;
+                                    o.th[at] = hi[j];
+                                    o.tl[at] = lo[j];
+                                }
+                            }
+                        }
+                        // C row-major: lane j of the slab's row r is column n0 + c0 + j of row row0 + r
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) slab[lane * 33 + j] = h ? lo[j] : hi[j];
+                            __syncwarp();
+                            float *dst = h ? o.cl : o.ch;
+                            if (lane < ncols) {
+                                for (int rr = 0; rr < 32 && row0 + rr < M; ++rr)
+                                    dst[(int64_t)(row0 + rr) * o.ldc + n0 + c0 + lane] = slab[rr * 33 + lane];
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(tempty + b);
         }
     }
-    // one FP64 partial per CTA: the epilogue threads' sums in a fixed order
-    if (warp >= 2) red[threadIdx.x - 64] = acc;
+    // PAIR_SQ: one FP64 partial per CTA, the epilogue threads' sums in a fixed order
+    if (MODE == PAIR_SQ && warp >= 2) red[threadIdx.x - 64] = acc;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (MODE == PAIR_SQ && threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < 128; ++i) t += red[i];
-        partial[blockIdx.x] = t;
+        o.partial[blockIdx.x] = t;
     }
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
@@ -726,12 +827,6 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
 // row stores, zeros in columns N .. ldy-1.
 constexpr int TX_XSTAGES = 4;
 constexpr uint32_t TX_XBYTES = 128 * 32 * 4;
-
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    return __uint_as_float(h);
-}
 
 __global__ void __launch_bounds__(PF_THREADS, 1)
     proj_tf32x3_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tbh,
@@ -1218,6 +1313,100 @@ int launch_tf32_split(const float *v, int64_t len, float *hi, float *lo, cudaStr
     return LV_OK;
 }
 
+// Y^T as tf32 pairs: hi / lo (cols x ldt, row-major) of Y (rows x cols, row-major), 32 x 32 tiles
+// through shared memory so that both the reads and the writes are coalesced
+__global__ void __launch_bounds__(256) transpose_tf32_split_kernel(const float *__restrict__ Y, int64_t rows,
+                                                                   int cols, float *__restrict__ hi,
+                                                                   float *__restrict__ lo, int64_t ldt) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t r = r0 + i;
+        const int c = c0 + tx;
+        tile[i][tx] = (r < rows && c < cols) ? Y[r * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i;
+        const int64_t r = r0 + tx;
+        if (c < cols && r < rows) {
+            const float x = tile[tx][i];
+            const float h = tf32_rna(x);
+            hi[(int64_t)c * ldt + r] = h;
+            lo[(int64_t)c * ldt + r] = tf32_rna(__fsub_rn(x, h));
+        }
+    }
+}
+
+int launch_transpose_tf32_split(const float *Y, int64_t rows, int cols, float *hi, float *lo, int64_t ldt,
+                                cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return LV_OK;
+    if (ldt < rows || cols > 65535 * 32) return fail(LV_ERR_ARG, "transpose_tf32_split: bad sizes");
+    transpose_tf32_split_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32)), 256, 0, st>>>(
+        Y, rows, cols, hi, lo, ldt);
+    LV_CHECK_LAUNCH("transpose_tf32_split_kernel");
+    return LV_OK;
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+// K blocks per split when K is cut into `splits` ranges, and the number of non-empty ranges
+static int split_kps(int64_t K, int splits, int *used) {
+    const int64_t nkb = (K + 31) / 32;
+    const int64_t kps = (nkb + splits - 1) / splits;
+    *used = (int)((nkb + kps - 1) / kps);
+    return (int)kps;
+}
+
+// C = A B^T (A: M x K, pitch lda; B: N x K, pitch ldb; tf32 hi / lo pairs of float32, row-major,
+// 16-byte aligned rows) with the epilogue MODE; `grid` persistent CTAs over splits x tiles items
+template <int MODE>
+static int pair_tf32_launch(const float *Ah, const float *Al, int64_t M, int64_t lda, const float *Bh,
+                            const float *Bl, int64_t N, int64_t ldb, int64_t K, int splits, const PairOut &o,
+                            int grid, int *status, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0 || M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31) || lda < K ||
+        ldb < K || lda % 4 || ldb % 4 || splits < 1)
+        return fail(LV_ERR_ARG, "tf32x3 pair GEMM: unsupported sizes");
+    for (const float *q : {Ah, Al, Bh, Bl})
+        if ((uintptr_t)q & 15) return fail(LV_ERR_ARG, "tf32x3 pair GEMM: operands must be 16-byte aligned");
+    auto fn = encode_fn();
+    if (!fn) return fail(LV_ERR_CUDA, "tf32x3 pair GEMM: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap tah, tal, tbh, tbl;
+    auto map = [&](CUtensorMap *mp, const float *ptr, int64_t rows, int64_t ld, int box_rows) -> bool {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+        cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+        cuuint32_t es[2] = {1, 1};
+        return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!map(&tah, Ah, M, lda, TC_BM) || !map(&tal, Al, M, lda, TC_BM) || !map(&tbh, Bh, N, ldb, PL_BN) ||
+        !map(&tbl, Bl, N, ldb, PL_BN))
+        return fail(LV_ERR_CUDA, "tf32x3 pair GEMM: cuTensorMapEncodeTiled failed");
+    int used = 0;
+    const int kps = split_kps(K, splits, &used);
+    // stages, barriers and flags, eight epilogue slabs (or the FP64 reduction slots), alignment slack
+    const size_t sm = (size_t)PL_STAGES * 2 * (TC_BM + PL_BN) * 128 + 256 + 8 * 32 * 33 * 4 + 1024;
+    LV_CUDA(cudaFuncSetAttribute(pair_tf32_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    pair_tf32_kernel<MODE><<<grid, 64 + 32 * pair_epi_warps<MODE>(), sm, st>>>(tah, tal, tbh, tbl, (int)M, (int)N, (int)K, used, kps, o,
+                                                         status);
+    LV_CHECK_LAUNCH("pair_tf32_kernel");
+    return LV_OK;
+}
+
+static int64_t pair_items(int64_t M, int64_t N, int splits) {
+    return ((M + TC_BM - 1) / TC_BM) * ((N + PL_BN - 1) / PL_BN) * splits;
+}
+
 // Sum of squares of Qt X^T (Qt m x K, X n x K, given as tf32 hi / lo pairs: float32, row-major,
 // 16-byte aligned rows, K % 4 == 0) on the tensor cores; writes one FP64 partial per CTA to
 // `partial` (at least *nparts entries: call with partial = NULL to get the count) -- the caller
@@ -1226,34 +1415,75 @@ int pair_sq_tf32(const float *Qh, const float *Ql, int64_t m, const float *Xh, c
                  double *partial, int *nparts, int *status, cudaStream_t st) {
     if (m <= 0 || n <= 0 || K <= 0 || K % 4 || m >= (1ll << 31) || n >= (1ll << 31))
         return fail(LV_ERR_ARG, "pair_sq_tf32: unsupported sizes");
-    int dev = 0, sms = 0;
-    LV_CUDA(cudaGetDevice(&dev));
-    LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t tiles = ((m + TC_BM - 1) / TC_BM) * ((n + PL_BN - 1) / PL_BN);
-    const int grid = (int)std::min<int64_t>(tiles, sms);
+    const int sms = sm_count();
+    if (sms <= 0) return fail(LV_ERR_CUDA, "pair_sq_tf32: no device");
+    const int grid = (int)std::min<int64_t>(pair_items(m, n, 1), sms);
     *nparts = grid;
     if (!partial) return LV_OK;
-    for (const float *q : {Qh, Ql, Xh, Xl})
-        if ((uintptr_t)q & 15) return fail(LV_ERR_ARG, "pair_sq_tf32: operands must be 16-byte aligned");
-    auto fn = encode_fn();
-    if (!fn) return fail(LV_ERR_CUDA, "pair_sq_tf32: cuTensorMapEncodeTiled unavailable");
-    CUtensorMap tah, tal, tbh, tbl;
-    auto map = [&](CUtensorMap *mp, const float *ptr, int64_t rows, int box_rows) -> bool {
-        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-        cuuint64_t strides[1] = {(cuuint64_t)K * 4};
-        cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
-        cuuint32_t es[2] = {1, 1};
-        return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-    };
-    if (!map(&tah, Qh, m, TC_BM) || !map(&tal, Ql, m, TC_BM) || !map(&tbh, Xh, n, PL_BN) || !map(&tbl, Xl, n, PL_BN))
-        return fail(LV_ERR_CUDA, "pair_sq_tf32: cuTensorMapEncodeTiled failed");
-    const size_t sm = (size_t)PL_STAGES * 2 * (TC_BM + PL_BN) * 128 + 256 + 128 * 8 + 1024;
-    LV_CUDA(cudaFuncSetAttribute(pair_sq_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    pair_sq_tf32_kernel<<<grid, PL_THREADS, sm, st>>>(tah, tal, tbh, tbl, (int)m, (int)n, K, partial, status);
-    LV_CHECK_LAUNCH("pair_sq_tf32_kernel");
-    return LV_OK;
+    PairOut o;
+    o.partial = partial;
+    return pair_tf32_launch<PAIR_SQ>(Qh, Ql, m, K, Xh, Xl, n, K, K, 1, o, grid, status, st);
+}
+
+// C = A B^T (M x N) stored as tf32 pairs twice: C row-major in ch / cl (pitch ldc) and C^T in
+// th / tl (N x M, pitch ldt)
+int pair_r_tf32(const float *Ah, const float *Al, int64_t M, int64_t lda, const float *Bh, const float *Bl, int64_t N,
+                int64_t ldb, int64_t K, float *ch, float *cl, int64_t ldc, float *th, float *tl, int64_t ldt,
+                int *status, cudaStream_t st) {
+    if (!ch || !cl || !th || !tl || ldc < N || ldt < M) return fail(LV_ERR_ARG, "pair_r_tf32: bad output");
+    const int sms = sm_count();
+    if (sms <= 0) return fail(LV_ERR_CUDA, "pair_r_tf32: no device");
+    PairOut o;
+    o.ch = ch;
+    o.cl = cl;
+    o.th = th;
+    o.tl = tl;
+    o.ldc = ldc;
+    o.ldt = ldt;
+    const int grid = (int)std::min<int64_t>(pair_items(M, N, 1), sms);
+    return pair_tf32_launch<PAIR_R>(Ah, Al, M, lda, Bh, Bl, N, ldb, K, 1, o, grid, status, st);
+}
+
+// K splits for gemm_t_tf32 of an M x N output over K: at least four 32-wide K blocks per split and
+// about four to eight work items per SM, the count whose last wave of items is fullest (ties: fewer
+// splits); the value is the number of partial slots the call writes
+int gemm_t_tf32_splits(int64_t M, int64_t N, int64_t K) {
+    const int64_t sms = std::max(1, sm_count());
+    const int64_t tiles = pair_items(M, N, 1), nkb = (K + 31) / 32;
+    const int64_t lo = std::max<int64_t>(1, std::min<int64_t>((4 * sms + tiles - 1) / tiles, nkb / 4));
+    const int64_t hi = std::max<int64_t>(lo, std::min<int64_t>((8 * sms + tiles - 1) / tiles, nkb / 4));
+    int best = 1;
+    double best_eff = -1.0;
+    for (int64_t s = lo; s <= hi; ++s) {
+        int used = 0;
+        split_kps(K, (int)s, &used);
+        const int64_t items = tiles * used, waves = (items + sms - 1) / sms;
+        const double eff = (double)items / (double)(waves * sms);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = used;
+        }
+    }
+    return best;
+}
+
+// C = A B^T over K in `splits` ranges (gemm_t_tf32_splits' count); split s writes C^T (N x M,
+// pitch ldo) to out + s * split_stride, added to what is there when `accumulate`
+int gemm_t_tf32(const float *Ah, const float *Al, int64_t M, int64_t lda, const float *Bh, const float *Bl, int64_t N,
+                int64_t ldb, int64_t K, float *out, int64_t ldo, int64_t split_stride, int accumulate, int splits,
+                int *status, cudaStream_t st) {
+    if (!out || ldo < M) return fail(LV_ERR_ARG, "gemm_t_tf32: bad output");
+    const int sms = sm_count();
+    if (sms <= 0) return fail(LV_ERR_CUDA, "gemm_t_tf32: no device");
+    int used = 0;
+    split_kps(K, splits, &used);
+    PairOut o;
+    o.out = out;
+    o.ldo = ldo;
+    o.split_stride = split_stride;
+    o.accumulate = accumulate;
+    const int grid = (int)std::min<int64_t>(pair_items(M, N, used), sms);
+    return pair_tf32_launch<PAIR_T>(Ah, Al, M, lda, Bh, Bl, N, ldb, K, splits, o, grid, status, st);
 }
 
 // workspace bytes of project_bf16 (prec LV_PREC_BF16) or project_fp8 (LV_PREC_FP8)

@@ -3,11 +3,14 @@
 //   r_ij = q_j^T x_i - (A q_j)^T (B x_i),   L = sum_ij r_ij^2 / (n m)
 //   dL/dA = -2/(nm) sum_ij r_ij (B x_i) q_j^T = -2/(nm) (R X')^T Q
 //   dL/dB = -2/(nm) sum_ij r_ij (A q_j) x_i^T = -2/(nm) (R^T Q')^T X
-// with Q' = Q A^T (m x d), X' = X B^T (n x d) and R (m x n) the residual matrix.  R is
-// never stored: 64 x 64 pair tiles are recomputed from Q, X, Q', X' (float32 CUDA-core
-// tiles; the residual is a small difference of two inner products, which bf16 / tf32
-// operands would swamp).  One kernel walks the database tiles for each query tile
-// (loss, U = R X'), another the query tiles for each database tile (V = R^T Q').
+// with Q' = Q A^T (m x d), X' = X B^T (n x d) and R (m x n) the residual matrix.
+// D % 4 == 0 (the tensor-core form): r_ij = qt_j^T x_i with qt_j = q_j - B^T A q_j formed first in
+// float32, so that no tile product carries the cancellation, and every product over pairs runs in
+// tf32x3 form (hi / lo splits, three tf32 MMAs, float32-accurate): the loss as a fused sum of
+// squares, the gradients through R kept per chunk of database rows (ood_loss_bwd_tc).
+// Other D: R is never stored; 64 x 64 pair tiles are recomputed from Q, X, Q', X' on the CUDA cores
+// in float32 (one kernel walks the database tiles for each query tile: loss, U = R X'; another the
+// query tiles for each database tile: V = R^T Q').
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -199,6 +202,19 @@ __global__ void __launch_bounds__(256) tgemm_kernel(const float *__restrict__ M,
 int pair_sq_tf32(const float *Qh, const float *Ql, int64_t m, const float *Xh, const float *Xl, int64_t n, int K,
                  double *partial, int *nparts, int *status, cudaStream_t st);
 int launch_tf32_split(const float *v, int64_t len, float *hi, float *lo, cudaStream_t st);
+int launch_transpose_tf32_split(const float *Y, int64_t rows, int cols, float *hi, float *lo, int64_t ldt,
+                                cudaStream_t st);
+int pair_r_tf32(const float *Ah, const float *Al, int64_t M, int64_t lda, const float *Bh, const float *Bl, int64_t N,
+                int64_t ldb, int64_t K, float *ch, float *cl, int64_t ldc, float *th, float *tl, int64_t ldt,
+                int *status, cudaStream_t st);
+int gemm_t_tf32_splits(int64_t M, int64_t N, int64_t K);
+bool project_bf16_fused_ok(const float *X, int D, int d);
+size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X);
+int project_tf32x3(const float *X, int64_t n, int D, const float *P, int d, float *Y, int ldy, void **ws,
+                   size_t *ws_bytes, int *status, cudaStream_t st);
+int gemm_t_tf32(const float *Ah, const float *Al, int64_t M, int64_t lda, const float *Bh, const float *Bl, int64_t N,
+                int64_t ldb, int64_t K, float *out, int64_t ldo, int64_t split_stride, int accumulate, int splits,
+                int *status, cudaStream_t st);
 
 // Bt (D x d) = B^T for B (d x D)
 __global__ void transpose_kernel(const float *__restrict__ B, int d, int D, float *__restrict__ Bt) {
@@ -214,13 +230,14 @@ __global__ void sub_inplace_kernel(float *__restrict__ Y, const float *__restric
     if (t < len) Y[t] = Y[t] - Z[t];
 }
 
-// out[i] = sum_y part[y * len + i] for y = 0 .. splits - 1, in that order
-__global__ void split_sum_kernel(const float *__restrict__ part, int splits, int64_t len, float *__restrict__ out) {
+// out[i] = scale * sum_y part[y * len + i] for y = 0 .. splits - 1, in that order
+__global__ void split_sum_kernel(const float *__restrict__ part, int splits, int64_t len, float *__restrict__ out,
+                                 float scale) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
     float v = 0.f;
     for (int y = 0; y < splits; ++y) v += part[(int64_t)y * len + i];
-    out[i] = v;
+    out[i] = scale * v;
 }
 
 // splits of a sweep with `tiles` row tiles over `ncols` columns: about 4 blocks per SM in all,
@@ -265,6 +282,137 @@ static void pair_free(PairWork &w, cudaStream_t st) {
     tmp_free(w.U, st);
     tmp_free(w.V, st);
     tmp_free(w.part, st);
+}
+
+// Gradients on the tensor cores (D % 4 == 0), every contraction in tf32x3 form (float32 accurate):
+//   Q' = Q A^T, Qt = Q - Q' B (so that r_ij = qt_j^T x_i), X' = X B^T;
+//   per chunk of database rows [c0, c0 + nc): R_c = Qt X_c^T (m x nc) kept as tf32 hi / lo pairs,
+//   row-major and transposed; U += R_c X'_c and V_c = R_c^T Q' with the d-wide side as M and K
+//   split over the SMs (partial slots summed in order afterwards);
+//   dL/dA = c U^T Q, dL/dB = c V^T X the same way (D-wide side as M, K = m or n), c = -2 scale / (n m).
+// R and R^T of one chunk take at most 4 GiB of scratch, so any n runs in bounded memory.
+static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
+                           int d, float scale, float *gA, float *gB, cudaStream_t st) {
+    const int64_t ldm = round_up(m, 4), ldn = round_up(n, 4);
+    int64_t nc = ((int64_t)1 << 32) / (16 * ldm);
+    nc = std::min<int64_t>(std::max<int64_t>(256, nc / 256 * 256), n);
+    const int64_t ldr = round_up(nc, 4);
+    const int su = gemm_t_tf32_splits(d, m, nc), sv = gemm_t_tf32_splits(d, nc, m);
+    const int sa = gemm_t_tf32_splits(D, d, m), sb = gemm_t_tf32_splits(D, d, n);
+    const bool proj_tc = project_bf16_fused_ok(X, D, d);
+    float *Qp = nullptr, *Bt = nullptr, *QB = nullptr, *Qt = nullptr, *Qth = nullptr, *Xh = nullptr, *Xl = nullptr,
+          *Xp = nullptr, *XpTh = nullptr, *XpTl = nullptr, *QpTh = nullptr, *QpTl = nullptr, *Rh = nullptr,
+          *Rl = nullptr, *RTh = nullptr, *RTl = nullptr, *Up = nullptr, *Vp = nullptr, *U = nullptr, *V = nullptr,
+          *Pw = nullptr, *Gp = nullptr;
+    int *status = nullptr, h = 0;
+    int rc = LV_OK;
+    auto grab = [&](float **p, int64_t count) {
+        if (rc == LV_OK && tmp_alloc((void **)p, sizeof(float) * (size_t)count, st))
+            rc = fail(LV_ERR_OOM, "ood_loss_bwd: allocation failed");
+    };
+    const size_t pw_bytes = proj_tc ? project_tc_ws_bytes(LV_PREC_TF32X3, n, D, d, X) : 0;
+    grab(&Qp, m * d);
+    grab(&Bt, (int64_t)d * D);
+    grab(&QB, m * D);
+    grab(&Qt, m * D);
+    grab(&Qth, m * D);
+    grab(&Xh, n * D);
+    grab(&Xl, n * D);
+    grab(&Xp, n * d);
+    grab(&XpTh, d * ldn);
+    grab(&XpTl, d * ldn);
+    grab(&QpTh, d * ldm);
+    grab(&QpTl, d * ldm);
+    grab(&Rh, m * ldr);
+    grab(&Rl, m * ldr);
+    grab(&RTh, nc * ldm);
+    grab(&RTl, nc * ldm);
+    grab(&Up, su * m * d);
+    grab(&Vp, sv * n * d);
+    grab(&U, m * d);
+    grab(&V, n * d);
+    grab(&Pw, (int64_t)(pw_bytes + 3) / 4);
+    if (rc == LV_OK && tmp_alloc((void **)&status, sizeof(int), st))
+        rc = fail(LV_ERR_OOM, "ood_loss_bwd: allocation failed");
+    if (rc == LV_OK && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+        rc = fail(LV_ERR_CUDA, "ood_loss_bwd: memset failed");
+    if (rc == LV_OK) rc = launch_project_fp32(Q, m, D, A, d, Qp, d, st);  // Q'
+    if (rc == LV_OK) {
+        transpose_kernel<<<(unsigned)(((int64_t)d * D + 255) / 256), 256, 0, st>>>(B, d, D, Bt);
+        rc = launch_project_fp32(Qp, m, d, Bt, D, QB, D, st);  // Q' B
+    }
+    if (rc == LV_OK &&
+        cudaMemcpyAsync(Qt, Q, sizeof(float) * (size_t)m * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        rc = fail(LV_ERR_CUDA, "ood_loss_bwd: copy failed");
+    if (rc == LV_OK) {
+        sub_inplace_kernel<<<(unsigned)(((int64_t)m * D + 255) / 256), 256, 0, st>>>(Qt, QB, (int64_t)m * D);
+        rc = launch_tf32_split(Qt, m * D, Qth, QB, st);  // QB now holds Qt's lo part
+    }
+    if (rc == LV_OK) rc = launch_tf32_split(X, n * D, Xh, Xl, st);
+    if (rc == LV_OK) {  // X'
+        if (proj_tc) {
+            void *ws = Pw;
+            size_t have = pw_bytes;
+            rc = project_tf32x3(X, n, D, B, d, Xp, d, &ws, &have, status, st);
+        } else {
+            rc = launch_project_fp32(X, n, D, B, d, Xp, d, st);
+        }
+    }
+    if (rc == LV_OK) rc = launch_transpose_tf32_split(Xp, n, d, XpTh, XpTl, ldn, st);
+    if (rc == LV_OK) rc = launch_transpose_tf32_split(Qp, m, d, QpTh, QpTl, ldm, st);
+    for (int64_t c0 = 0; rc == LV_OK && c0 < n; c0 += nc) {
+        const int64_t nk = std::min(nc, n - c0);
+        rc = pair_r_tf32(Qth, QB, m, D, Xh + c0 * D, Xl + c0 * D, nk, D, D, Rh, Rl, ldr, RTh, RTl, ldm, status, st);
+        if (rc == LV_OK)  // U (m x d) += R_c X'_c: M = d, N = m, K = nk
+            rc = gemm_t_tf32(XpTh + c0, XpTl + c0, d, ldn, Rh, Rl, m, ldr, nk, Up, d, m * d, c0 > 0, su, status, st);
+        if (rc == LV_OK)  // V rows c0 .. c0 + nk: M = d, N = nk, K = m
+            rc = gemm_t_tf32(QpTh, QpTl, d, ldm, RTh, RTl, nk, ldm, m, Vp + c0 * d, d, n * d, 0, sv, status, st);
+    }
+    auto sum = [&](const float *part, int splits, int64_t len, float *out, float sc) {
+        split_sum_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, splits, len, out, sc);
+    };
+    if (rc == LV_OK) {
+        sum(Up, su, m * d, U, 1.f);
+        sum(Vp, sv, n * d, V, 1.f);
+    }
+    // the gradient products reuse the chunk buffers' memory: Q^T, U^T, X^T, V^T as tf32 pairs
+    for (float *p : {Rh, Rl, RTh, RTl, Up, Vp}) tmp_free(p, st);
+    Rh = Rl = RTh = RTl = Up = Vp = nullptr;
+    float *QTh = nullptr, *QTl = nullptr, *UTh = nullptr, *UTl = nullptr, *XTh = nullptr, *XTl = nullptr,
+          *VTh = nullptr, *VTl = nullptr;
+    grab(&QTh, D * ldm);
+    grab(&QTl, D * ldm);
+    grab(&UTh, d * ldm);
+    grab(&UTl, d * ldm);
+    grab(&XTh, D * ldn);
+    grab(&XTl, D * ldn);
+    grab(&VTh, d * ldn);
+    grab(&VTl, d * ldn);
+    grab(&Gp, (int64_t)std::max(sa, sb) * d * D);
+    const float c = (float)(-2.0 * (double)scale / ((double)n * (double)m));
+    if (rc == LV_OK) rc = launch_transpose_tf32_split(Q, m, D, QTh, QTl, ldm, st);
+    if (rc == LV_OK) rc = launch_transpose_tf32_split(U, m, d, UTh, UTl, ldm, st);
+    if (rc == LV_OK)  // (Q^T U)^T = U^T Q: M = D, N = d, K = m
+        rc = gemm_t_tf32(QTh, QTl, D, ldm, UTh, UTl, d, ldm, m, Gp, D, (int64_t)d * D, 0, sa, status, st);
+    if (rc == LV_OK) sum(Gp, sa, (int64_t)d * D, gA, c);
+    if (rc == LV_OK) rc = launch_transpose_tf32_split(X, n, D, XTh, XTl, ldn, st);
+    if (rc == LV_OK) rc = launch_transpose_tf32_split(V, n, d, VTh, VTl, ldn, st);
+    if (rc == LV_OK)  // V^T X: M = D, N = d, K = n
+        rc = gemm_t_tf32(XTh, XTl, D, ldn, VTh, VTl, d, ldn, n, Gp, D, (int64_t)d * D, 0, sb, status, st);
+    if (rc == LV_OK) sum(Gp, sb, (int64_t)d * D, gB, c);
+    if (rc == LV_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "ood_loss_bwd kernels");
+    }
+    if (rc == LV_OK && (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        rc = fail(LV_ERR_CUDA, "ood_loss_bwd: sync failed");
+    if (rc == LV_OK && h) rc = fail(LV_ERR_TIMEOUT, "ood_loss_bwd: a tensor-core pipeline wait timed out");
+    for (float *p : {Qp, Bt, QB, Qt, Qth, Xh, Xl, Xp, XpTh, XpTl, QpTh, QpTl, U, V, Pw, Gp, QTh, QTl, UTh, UTl, XTh,
+                     XTl, VTh, VTl})
+        tmp_free(p, st);
+    tmp_free(status, st);
+    return rc;
 }
 
 }  // namespace lv
@@ -362,6 +510,7 @@ int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t
         return fail(LV_ERR_ARG, "ood_loss_bwd: invalid sizes or null pointer");
     if (d > DMAX) return fail(LV_ERR_ARG, "ood_loss_bwd: d <= 256 is supported");
     cudaStream_t st = (cudaStream_t)stream;
+    if (D % 4 == 0 && m < (1ll << 31) && n < (1ll << 31)) return ood_loss_bwd_tc(A, B, Q, m, X, n, D, d, scale, gA, gB, st);
     PairWork w;
     int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, true, st);
     // U = R X' (query tiles, the database split in column ranges whose partials are summed in
@@ -377,7 +526,7 @@ int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t
     if (rc == LV_OK) {
         const float c = (float)(-2.0 * (double)scale / ((double)n * (double)m));
         auto sum = [&](const float *part, int splits, int64_t len, float *out) {
-            split_sum_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, splits, len, out);
+            split_sum_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, splits, len, out, 1.f);
         };
         pair_sweep_kernel<true><<<dim3((unsigned)tq, su), 256, 0, st>>>(Q, w.Qp, m, X, w.Xp, n, D, d,
                                                                         split_len(n, su, PT), nullptr, w.Up);

@@ -75,8 +75,11 @@ def test_line_search_and_bf16_second_moments(lv, data):
     assert f == pytest.approx(ref["loss"][-1], rel=2e-2)
 
 
-@pytest.mark.parametrize("m,n,D,d", [(70, 130, 24, 5), (300, 1000, 64, 16), (129, 257, 200, 64)])
+@pytest.mark.parametrize("m,n,D,d", [(70, 130, 24, 5), (300, 1000, 64, 16), (129, 257, 200, 64),
+                                     (1000, 5000, 128, 40), (257, 3000, 256, 160), (100, 300, 30, 7)])
 def test_pair_loss_forward_backward(lv, m, n, D, d):
+    """D % 4 == 0 takes the tensor-core form (tf32x3 products; 1000 x 5000 splits the gradient
+    contractions over K, d = 160 gives them two 128-row tiles); D = 30 the CUDA-core form."""
     rng = np.random.default_rng(m + n)
     Q = (rng.standard_normal((m, D)) / np.sqrt(D)).astype(np.float32)
     X = (rng.standard_normal((n, D)) / np.sqrt(D)).astype(np.float32)
@@ -91,6 +94,25 @@ def test_pair_loss_forward_backward(lv, m, n, D, d):
     # equals the closed-form gradient built from K_Q, K_X (Eq. leanvec_gradients) / (n m)
     tA, tB = fit.ood_grads(A, B, fit.second_moment(Q), fit.second_moment(X))
     np.testing.assert_allclose(gA.cpu().numpy(), tA / (n * m), rtol=0, atol=1e-4 * np.abs(tA / (n * m)).max())
+
+
+def test_pair_loss_backward_in_chunks(lv):
+    """20000 queries x 30000 database rows: R and R^T of 6e8 pairs exceed the 4 GiB chunk budget,
+    so the gradients run over three chunks of database rows (U accumulated across them).  Checked
+    against the closed-form gradients built from K_Q and K_X in FP64 (Eq. leanvec_gradients / (n m))."""
+    m, n, D, d = 20000, 30000, 64, 24
+    rng = np.random.default_rng(17)
+    Q = (rng.standard_normal((m, D)) / np.sqrt(D)).astype(np.float32)
+    X = (rng.standard_normal((n, D)) / np.sqrt(D)).astype(np.float32)
+    A = (rng.standard_normal((d, D)) / np.sqrt(D)).astype(np.float32)
+    B = (rng.standard_normal((d, D)) / np.sqrt(D)).astype(np.float32)
+    gA, gB = lv.leanvec_ood_loss_bwd(t(A), t(B), t(Q), t(X))
+    KQ, KX = fit.second_moment(Q), fit.second_moment(X)
+    tA, tB = fit.ood_grads(A, B, KQ, KX)
+    np.testing.assert_allclose(gA.cpu().numpy(), tA / (n * m), rtol=0, atol=1e-4 * np.abs(tA / (n * m)).max())
+    np.testing.assert_allclose(gB.cpu().numpy(), tB / (n * m), rtol=0, atol=1e-4 * np.abs(tB / (n * m)).max())
+    L = lv.leanvec_ood_loss_fwd(t(A), t(B), t(Q), t(X))
+    assert L == pytest.approx(fit.ood_loss(A, B, KQ, KX) / (n * m), rel=1e-5)
 
 
 def test_autograd_function_and_gradient_optimiser(lv, data):
