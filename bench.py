@@ -725,6 +725,53 @@ def bench_l2(args, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_loss(args, dev):
+    """The differentiation form alone (Sec. 2.2 problem "leanvec_orthonormal", Eq. "leanvec_gradients"
+    per pair): the pair loss forward and backward over 10^4 learning queries x 10^5 database samples,
+    D = 512, d = 128 (10^9 pairs), `steps` of each after `warmup`, timed with CUDA events; the timed
+    calls sit inside an NVTX range 'timed' for launch lists."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(pk.get("bf16_tflops", 1900.0))
+    src = "measured" if "bf16_tflops" in pk else "fallback"
+    tf32_peak = bf16 * 1.1 / 2.25
+    Xo, _, Qo = workloads.make_workload_torch("anisotropic", 100_000, 1000, 512, args.components, cfg=3, device=dev,
+                                              ood=True, m_learn=10_000)
+    Ai = lv.leanvec_fit_id(Xo, 128)
+    m, n, D, d = Qo.shape[0], Xo.shape[0], 512, 128
+    for _ in range(max(1, args.warmup)):
+        lv.leanvec_ood_loss_fwd(Ai, Ai, Qo, Xo)
+        lv.leanvec_ood_loss_bwd(Ai, Ai, Qo, Xo)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf = tb = 0.0
+    for _ in range(args.steps):
+        torch.cuda.nvtx.range_push("timed")
+        ev[0].record()
+        L = lv.leanvec_ood_loss_fwd(Ai, Ai, Qo, Xo)
+        ev[1].record()
+        lv.leanvec_ood_loss_bwd(Ai, Ai, Qo, Xo)
+        ev[2].record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        tf += ev[0].elapsed_time(ev[1]) / 1e3
+        tb += ev[1].elapsed_time(ev[2]) / 1e3
+    tf /= args.steps
+    tb /= args.steps
+    ex_f, ex_b = 3 * 2.0 * m * n * D, 3 * 2.0 * m * n * (D + 2 * d)
+    out = {"metric": "pair loss forward / backward, seconds per call (tf32x3 tensor cores)", "data": "synthetic",
+           "workload": "ood-100k-512: 10^4 learning queries x 10^5 database samples, d = 128, A = B = LeanVec-ID",
+           "steps": args.steps, "warmup": args.warmup, "loss": L,
+           "forward": {"seconds": tf, "executed_tflops": ex_f / tf / 1e12, "frac": ex_f / tf / 1e12 / tf32_peak},
+           "backward": {"seconds": tb, "executed_tflops": ex_b / tb / 1e12, "frac": ex_b / tb / 1e12 / tf32_peak},
+           "bound": "tensor (tf32, three MMAs per product)", "peak_tflops": tf32_peak,
+           "peak_source": src + " bf16 x nominal tf32/bf16 ratio"}
+    print(json.dumps(out), flush=True)
+
+
 def bench_kernels(args, dev):
     """The offline and auxiliary kernels of the path, each timed alone through its C-ABI call
     (CUDA events on the launching stream, warm-up first) and set against its roofline:
@@ -999,7 +1046,7 @@ def main():
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
     ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy",
-                                                      "l2", "kernels", "samples"],
+                                                      "l2", "kernels", "samples", "loss"],
                     help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
                          "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
@@ -1007,14 +1054,15 @@ def main():
                          "buildstudy: graph build on primaries vs on full-D LVQ-8 codes; "
                          "l2: Euclidean 1M x 960 (gist-960-1M shape), LeanVec vs FP32 at recall 0.90; "
                          "kernels: the offline / auxiliary kernels alone against their rooflines; "
-                         "samples: fit sample-size study (second moments, projectors, exhaustive-search recall)")
+                         "samples: fit sample-size study (second moments, projectors, exhaustive-search recall); "
+                         "loss: the pair loss forward / backward of the differentiation form alone")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
     sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
              "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
              "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000),
-             "kernels": (1_000_000, 10_000), "samples": (1_000_000, 10_000)}[args.workload]
+             "kernels": (1_000_000, 10_000), "samples": (1_000_000, 10_000), "loss": (100_000, 10_000)}[args.workload]
     args.n = args.n or sizes[0]
     args.m = args.m or sizes[1]
     l2 = args.workload == "l2"
@@ -1058,6 +1106,9 @@ def main():
         return
     if args.workload == "samples":
         bench_samples(args, dev)
+        return
+    if args.workload == "loss":
+        bench_loss(args, dev)
         return
     workload = (f"id-{args.n // 1000}k-{args.D}: anisotropic Gaussian mixture ({args.components} components, "
                 f"i^-1 spectrum), unit norm, inner product; {args.m} ID queries; LeanVec-ID d={args.d}, "
