@@ -196,8 +196,9 @@ int leanvec_fit_ood(const float *X, int64_t n, const float *Q, int64_t m, int D,
  * "leanvec_orthonormal" written per pair, Sec. 2.2):
  *   r_ij = q_j^T x_i - (A q_j)^T (B x_i),  L = sum_ij r_ij^2 / (n m)
  * over the m rows of Q (m x D) and the n rows of X (n x D), A, B d x D (all float32,
- * device; d <= 256).  The m x n residuals are recomputed in tiles, never stored.
- * fwd writes L to *loss (host; synchronises).  With D a multiple of 4 it computes
+ * device; d <= 256).
+ * fwd writes L to *loss (host; synchronises); the residuals are never stored.  With D a
+ * multiple of 4 it computes
  * r_ij = qt_j^T x_i with qt_j = q_j - B^T (A q_j) (float32) on the tensor cores:
  * each operand split into tf32 hi + lo parts, three tf32 products per tile (about 21
  * bits of the float32 products), 128 x 256 tiles, squares summed in float32 per 16
@@ -205,7 +206,15 @@ int leanvec_fit_ood(const float *X, int64_t n, const float *Q, int64_t m, int D,
  * float32 CUDA-core tiles with FP64 sums.
  * bwd writes scale * dL/dA and scale * dL/dB (d x D, device):
  *   dL/dA = -2/(nm) sum_ij r_ij (B x_i) q_j^T,  dL/dB = -2/(nm) sum_ij r_ij (A q_j) x_i^T
- * (equal to Eq. "leanvec_gradients" divided by n m).  Synchronises `stream`. */
+ * (equal to Eq. "leanvec_gradients" divided by n m).  With D a multiple of 4, on the
+ * tensor cores in the same tf32x3 form: R = [r_ij] (m x chunk) is formed per chunk of
+ * database rows and kept, as tf32 hi / lo pairs row-major and transposed, in at most
+ * 4 GiB of library scratch; U = R X' (X' = X B^T) and V = R^T Q' (Q' = Q A^T) are split-K
+ * contractions over it, U accumulated across chunks in chunk order; dL/dA = c U^T Q and
+ * dL/dB = c V^T X likewise; every partial sum is combined in a fixed order (the result is
+ * deterministic).  Otherwise float32 CUDA-core pair tiles, recomputed per use.  Returns
+ * LV_ERR_OOM when the scratch cannot be had and LV_ERR_TIMEOUT when a tensor-core pipeline
+ * wait gave up.  Synchronises `stream`. */
 int leanvec_ood_loss_fwd(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n,
                          int D, int d, double *loss, lv_stream_t stream);
 int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n,
