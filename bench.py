@@ -727,9 +727,9 @@ def bench_l2(args, dev):
 
 def bench_loss(args, dev):
     """The differentiation form alone (Sec. 2.2 problem "leanvec_orthonormal", Eq. "leanvec_gradients"
-    per pair): the pair loss forward and backward over 10^4 learning queries x 10^5 database samples,
-    D = 512, d = 128 (10^9 pairs), `steps` of each after `warmup`, timed with CUDA events; the timed
-    calls sit inside an NVTX range 'timed' for launch lists."""
+    per pair): the pair loss forward and backward over --m learning queries x --n database samples
+    (default 10^4 x 10^5, 10^9 pairs), D = 512, d = 128, `steps` of each after `warmup`, timed with
+    CUDA events; the timed calls sit inside an NVTX range 'timed' for launch lists."""
     from paper_2312_16335_gb300 import build_lib
     build_lib.build()
     import paper_2312_16335_gb300 as lv
@@ -738,8 +738,8 @@ def bench_loss(args, dev):
     bf16 = float(pk.get("bf16_tflops", 1900.0))
     src = "measured" if "bf16_tflops" in pk else "fallback"
     tf32_peak = bf16 * 1.1 / 2.25
-    Xo, _, Qo = workloads.make_workload_torch("anisotropic", 100_000, 1000, 512, args.components, cfg=3, device=dev,
-                                              ood=True, m_learn=10_000)
+    Xo, _, Qo = workloads.make_workload_torch("anisotropic", args.n, 1000, 512, args.components, cfg=3, device=dev,
+                                              ood=True, m_learn=args.m)
     Ai = lv.leanvec_fit_id(Xo, 128)
     m, n, D, d = Qo.shape[0], Xo.shape[0], 512, 128
     for _ in range(max(1, args.warmup)):
@@ -763,7 +763,8 @@ def bench_loss(args, dev):
     tb /= args.steps
     ex_f, ex_b = 3 * 2.0 * m * n * D, 3 * 2.0 * m * n * (D + 2 * d)
     out = {"metric": "pair loss forward / backward, seconds per call (tf32x3 tensor cores)", "data": "synthetic",
-           "workload": "ood-100k-512: 10^4 learning queries x 10^5 database samples, d = 128, A = B = LeanVec-ID",
+           "workload": f"ood-{n // 1000}k-512: {m} learning queries x {n} database samples, d = 128, "
+                       "A = B = LeanVec-ID",
            "steps": args.steps, "warmup": args.warmup, "loss": L,
            "forward": {"seconds": tf, "executed_tflops": ex_f / tf / 1e12, "frac": ex_f / tf / 1e12 / tf32_peak},
            "backward": {"seconds": tb, "executed_tflops": ex_b / tb / 1e12, "frac": ex_b / tb / 1e12 / tf32_peak},
