@@ -568,6 +568,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t *r) {
         : "r"(addr));
 }
 
+// Tile t -> (m0, n0): groups of PAIR_GROUP row tiles, column-major inside a group, so that the CTAs
+// running at one time share a few A row tiles and each B column tile is read by up to PAIR_GROUP of
+// them close together (B re-read mt / PAIR_GROUP times from DRAM instead of up to mt times once the
+// L2 is busy with the stores of the R epilogue); the last group may hold fewer rows.
+constexpr int PAIR_GROUP = 16;
+__device__ __forceinline__ void pair_tile(int64_t tile, int mt, int nt, int &m0, int &n0) {
+    const int64_t per = (int64_t)PAIR_GROUP * nt;
+    const int64_t g = tile / per, r = tile % per;
+    const int gm = (int)min((int64_t)PAIR_GROUP, (int64_t)mt - g * PAIR_GROUP);
+    m0 = (int)((g * PAIR_GROUP + r % gm) * TC_BM);
+    n0 = (int)((r / gm) * PL_BN);
+}
+
 // epilogue warps: four for the light sum of squares, eight (two per TMEM lane quarter, half the
 // columns each) where the epilogue stores the tile
 template <int MODE>
@@ -627,8 +640,8 @@ __global__ void __launch_bounds__(64 + 32 * pair_epi_warps<MODE>(), 1)
             int64_t g = 0;
             for (int it = 0; it < my_items && !*abort_flag; ++it) {
                 const int64_t item = blockIdx.x + (int64_t)it * gridDim.x;
-                const int64_t tile = item % tiles;
-                const int m0 = (int)(tile / nt) * TC_BM, n0 = (int)(tile % nt) * PL_BN;
+                int m0, n0;
+                pair_tile(item % tiles, mt, nt, m0, n0);
                 const int kb0 = (int)(item / tiles) * kps, kb1 = min(nkb, kb0 + kps);
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % PL_STAGES);
@@ -726,8 +739,8 @@ __global__ void __launch_bounds__(64 + 32 * pair_epi_warps<MODE>(), 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int64_t item = blockIdx.x + (int64_t)it * gridDim.x;
-            const int64_t tile = item % tiles;
-            const int m0 = (int)(tile / nt) * TC_BM, n0 = (int)(tile % nt) * PL_BN;
+            int m0, n0;
+            pair_tile(item % tiles, mt, nt, m0, n0);
             const int row0 = m0 + quarter * 32;  // C rows of this warp: row0 .. row0 + 31
             const int row = row0 + lane;
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
