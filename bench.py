@@ -398,7 +398,7 @@ def bench_ood(args, dev):
         rep = {k: v for k, v in rep.items() if k != "loss_trace"}
         rep["seconds"] = time.time() - t0
         fits[name] = (A, B, rep)
-    # differentiation form: one forward + backward over 10k x 100k pairs (recomputed tiles)
+    # differentiation form: one forward + backward over 10k x 100k pairs (tf32x3 tensor cores)
     Ap = torch.nn.Parameter(fits["id"][0].clone())
     Bp = torch.nn.Parameter(fits["id"][1].clone())
     torch.cuda.synchronize()
@@ -410,7 +410,8 @@ def bench_ood(args, dev):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     mm, nn_ = Ql.shape[0], Xs.shape[0]
-    flops = 3 * (2 * mm * nn_ * D + 2 * mm * nn_ * d) + 2 * (2 * mm * nn_ * d)  # fwd + 2 sweeps + U, V
+    # executed tf32 flops: forward 3 x 2 m n D, backward 3 x 2 m n (D + 2 d) (R, then R X' and R^T Q')
+    flops = 3 * 2 * mm * nn_ * D + 3 * 2 * mm * nn_ * (D + 2 * d)
     diff = {"seconds": min(times[1:]), "pairs": mm * nn_, "tflops": flops / min(times[1:]) / 1e12}
     # one graph (built on the ID primaries), primaries swapped per projection
     idx = lv.Index(dev.index).encode(X, fits["id"][1], 8, 8, precision=lv.PREC_BF16)
