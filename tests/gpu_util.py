@@ -59,3 +59,23 @@ def gpu_index(lv, pb):
     idx.set_secondary(t(pb["X"]), t(pb["mu_s"]))
     idx.set_graph(t(pb["graph"]), pb["entry"])
     return idx
+
+
+def encode_parallel(oracle, Y, mu, bits, parts=16):
+    """oracle.lvq_encode over row blocks on threads (the oracle's C call releases the GIL): the
+    same codes and constants as one call, for the full-size stores."""
+    from concurrent.futures import ThreadPoolExecutor
+    n, dim = Y.shape
+    codes = np.empty((n, dim), np.uint8)
+    delta = np.empty(n, np.float32)
+    lower = np.empty(n, np.float32)
+    bounds = np.linspace(0, n, parts + 1).astype(np.int64)
+
+    def one(i):
+        a, b = bounds[i], bounds[i + 1]
+        e = oracle.lvq_encode(Y[a:b], mu, bits)
+        codes[a:b], delta[a:b], lower[a:b] = e.codes, e.delta, e.lower
+
+    with ThreadPoolExecutor(parts) as ex:
+        list(ex.map(one, range(parts)))
+    return oracle.LVQ(codes, delta, lower, np.ascontiguousarray(mu, np.float32), bits)

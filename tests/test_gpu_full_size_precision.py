@@ -10,15 +10,13 @@ by the oracle one by one.  With the FP32 query projection the ids must agree ele
 with the benchmark's e4m3 projection (per-row scales, up to 2^-3 of ||q|| ||a|| per coordinate) the
 walk is no longer the FP64 oracle's, so the answers are checked for what still holds exactly: each
 returned score is the rerank score of its id, scores are sorted and ids distinct."""
-from concurrent.futures import ThreadPoolExecutor
-
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads
-from gpu_util import t
+from gpu_util import encode_parallel, t
 from oracle import fit
 
 pytestmark = pytest.mark.gpu
@@ -32,24 +30,6 @@ SAMPLE = 48
 def lv():
     import paper_2312_16335_gb300 as lv
     return lv
-
-
-def _encode_parallel(Y, mu, bits, parts=16):
-    """oracle.lvq_encode over row blocks on threads (the oracle's C call releases the GIL)."""
-    n, dim = Y.shape
-    codes = np.empty((n, dim), np.uint8)
-    delta = np.empty(n, np.float32)
-    lower = np.empty(n, np.float32)
-    bounds = np.linspace(0, n, parts + 1).astype(np.int64)
-
-    def one(i):
-        a, b = bounds[i], bounds[i + 1]
-        e = oracle.lvq_encode(Y[a:b], mu, bits)
-        codes[a:b], delta[a:b], lower[a:b] = e.codes, e.delta, e.lower
-
-    with ThreadPoolExecutor(parts) as ex:
-        list(ex.map(one, range(parts)))
-    return oracle.LVQ(codes, delta, lower, np.ascontiguousarray(mu, np.float32), bits)
 
 
 @pytest.fixture(scope="module")
@@ -72,8 +52,8 @@ def problem():
         sy += Y[s:s + 500_000].astype(np.float64).sum(axis=0)
     mu_s = (sx / N).astype(np.float32)
     mu_p = (sy / N).astype(np.float32)
-    prim = _encode_parallel(Y, mu_p, 4)
-    sec = _encode_parallel(X, mu_s, 8)
+    prim = encode_parallel(oracle, Y, mu_p, 4)
+    sec = encode_parallel(oracle, X, mu_s, 8)
     graph = oracle.random_graph(N, R, 5004)
     return dict(X=X, Q=Q, P=P, Y=Y, mu_p=mu_p, mu_s=mu_s, prim=prim, sec=sec, graph=graph, entry=0)
 

@@ -8,15 +8,13 @@ search over the FP64 second moments of a 10^5-row database sample and the 10^4 l
 the projected database in FP64 rounded to float32, the FP64 means, the LVQ stores and its
 SplitMix64 random 64-regular graph.  Sampled queries are searched by the oracle one by one with
 their own descriptors and compared element by element with the GPU's answers."""
-from concurrent.futures import ThreadPoolExecutor
-
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads
-from gpu_util import t
+from gpu_util import encode_parallel, t
 from oracle import fit
 
 pytestmark = pytest.mark.gpu
@@ -29,24 +27,6 @@ SAMPLE = 96
 def lv():
     import paper_2312_16335_gb300 as lv
     return lv
-
-
-def _encode_parallel(Y, mu, bits, parts=16):
-    """oracle.lvq_encode over row blocks on threads (the oracle's C call releases the GIL)."""
-    n, dim = Y.shape
-    codes = np.empty((n, dim), np.uint8)
-    delta = np.empty(n, np.float32)
-    lower = np.empty(n, np.float32)
-    bounds = np.linspace(0, n, parts + 1).astype(np.int64)
-
-    def one(i):
-        a, b = bounds[i], bounds[i + 1]
-        e = oracle.lvq_encode(Y[a:b], mu, bits)
-        codes[a:b], delta[a:b], lower[a:b] = e.codes, e.delta, e.lower
-
-    with ThreadPoolExecutor(parts) as ex:
-        list(ex.map(one, range(parts)))
-    return oracle.LVQ(codes, delta, lower, np.ascontiguousarray(mu, np.float32), bits)
 
 
 @pytest.fixture(scope="module")
@@ -69,8 +49,8 @@ def problem():
         sy += Y[s:s + 500_000].astype(np.float64).sum(axis=0)
     mu_s = (sx / N).astype(np.float32)
     mu_p = (sy / N).astype(np.float32)
-    prim = _encode_parallel(Y, mu_p, 8)
-    sec = _encode_parallel(X, mu_s, 8)
+    prim = encode_parallel(oracle, Y, mu_p, 8)
+    sec = encode_parallel(oracle, X, mu_s, 8)
     graph = oracle.random_graph(N, R, 5005)
     kl = workloads.uneven_batch(M, seed=workloads.SEED_TEST_QUERIES + 55)
     desc = np.stack([kl[:, 0], kl[:, 1], kl[:, 1], np.zeros(M, np.int32)], 1).astype(np.int32)

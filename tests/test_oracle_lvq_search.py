@@ -222,3 +222,17 @@ def test_recall_definition(oracle_lib):
     found = np.array([[1, 2, 3, 4], [5, 6, -1, -1]])
     truth = np.array([[4, 3, 9, 8], [5, 6, 7, 8]])
     assert oracle_lib.recall(found, truth, 4) == pytest.approx((2 + 2) / 8)
+
+
+def test_encode_parallel_equals_one_call(oracle_lib):
+    """The threaded block encode the full-size GPU tests use for the oracle's stores gives the
+    codes and constants of one oracle call (blocks of unequal length, both widths)."""
+    from gpu_util import encode_parallel
+    rng = np.random.default_rng(21)
+    Y = rng.standard_normal((1003, 37)).astype(np.float32)
+    mu = Y.astype(np.float64).mean(axis=0).astype(np.float32)
+    for bits in (4, 8):
+        one = oracle_lib.lvq_encode(Y, mu, bits)
+        par = encode_parallel(oracle_lib, Y, mu, bits, parts=7)
+        assert np.array_equal(one.codes, par.codes)
+        assert np.array_equal(one.delta, par.delta) and np.array_equal(one.lower, par.lower)
