@@ -883,7 +883,7 @@ def bench_kernels(args, dev):
     log("loss fwd", res["pair_loss_fwd_10k_x_100k_512_128"])
     t = timed(lambda: lv.leanvec_ood_loss_bwd(Ai, Ai, Qo, Xo), 2)
     # the backward forms R = Qt X^T and contracts it twice (R X', R^T Q'), each in tf32x3 form:
-    # 3 x 2 m n (D + 2 d) executed flops; the final d x D products (float32 CUDA cores) are not counted
+    # 3 x 2 m n (D + 2 d) executed flops; the final d x D products (3 x 2 (m + n) d D) are not counted
     exec_bwd = 3 * 2.0 * Qo.shape[0] * Xo.shape[0] * (512 + 2 * 128)
     res["pair_loss_bwd_10k_x_100k_512_128"] = {"seconds": t, "pair_tflops": exec_bwd / 3 / t / 1e12,
                                                "bound": "tensor (tf32, three MMAs per product)",
