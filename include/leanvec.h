@@ -264,6 +264,33 @@ typedef struct {
 
 int leanvec_index_info(const lv_index *idx, lv_index_info *out);
 
+/* Index files (the paper has no counterpart; they let a built index be searched again without
+ * re-encoding or rebuilding).  One file holds the metric, the sizes, the primary store with its
+ * mean, the secondary store with its mean (when present), the graph and its entry point.
+ * Layout, little-endian, 96-byte header:
+ *   0  char[8] "LEANVEC" (NUL-terminated)   8  u32 version = 1   12 u32 header bytes = 96
+ *   16 i32 metric  20 i32 D  24 i32 d  28 i32 primary bits (4, 8, 32)  32 i32 secondary bits
+ *      (0, 8, 16)  36 i32 R (0 = no graph)  40 i32 entry (-1 without a graph)  44 f32 mu2
+ *   48 i64 n  56 i64 primary stride  64 i64 secondary stride (0 without secondaries)
+ *   72 24 zero bytes
+ *   96 primary records (n x primary stride bytes), primary mean (d float32; not for float32
+ *      records), secondary records (n x secondary stride bytes), secondary mean (D float32; LVQ-8
+ *      secondaries only), graph (n x R int32)
+ *   then u64 checksum of every preceding byte: 64-bit FNV-1a (offset basis 0xcbf29ce484222325,
+ *   prime 0x100000001b3) applied to the little-endian 64-bit words of the byte stream, the last
+ *   word zero-padded.
+ * leanvec_index_save synchronises `stream`, copies the stores to the host and writes `path`
+ * (LV_ERR_STATE for an index without a store, LV_ERR_ARG when the file cannot be written).
+ * leanvec_index_load reads and validates the whole file first -- magic and version, header
+ * fields against each other, strides against the record geometry, the file size, the checksum,
+ * every graph id in [-1, n) -- and returns LV_ERR_CORRUPT (index unchanged) on any mismatch;
+ * then it replaces the index's stores (and metric) with the file's on the index's device and
+ * synchronises `stream`.  leanvec_index_file_check performs the same validation without a
+ * device and fills `out` (nullable) from the header. */
+int leanvec_index_save(const lv_index *idx, const char *path, lv_stream_t stream);
+int leanvec_index_load(lv_index *idx, const char *path, lv_stream_t stream);
+int leanvec_index_file_check(const char *path, lv_index_info *out);
+
 /* Device pointers to the index's stores (read-only views, owned by the index;
  * valid until the index is freed or re-encoded). Any output may be NULL. */
 int leanvec_index_buffers(const lv_index *idx, const uint8_t **primary, const float **primary_mean,

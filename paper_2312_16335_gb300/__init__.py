@@ -10,6 +10,7 @@ with A q and rerank with the secondaries.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -18,7 +19,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "autotune_target_d", "SearchGraph", "HostPipeline", "leanvec_trim_scratch", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "autotune_target_d", "SearchGraph", "HostPipeline", "leanvec_trim_scratch", "leanvec_index_file_check", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8, PREC_TF32X3 = 0, 1, 2, 3
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
@@ -43,6 +44,14 @@ def _f32(t: torch.Tensor) -> torch.Tensor:
     if t.dtype != torch.float32:
         raise TypeError("expected float32")
     return t.contiguous()
+
+
+def leanvec_index_file_check(path: str) -> dict:
+    """Validate an index file (magic, version, header, strides, size, checksum, graph ids) without a
+    device; returns its header as leanvec_index_info's fields (LeanVecError LV_ERR_CORRUPT if not)."""
+    inf = LVIndexInfo()
+    check(lib().leanvec_index_file_check(os.fsencode(path), ctypes.byref(inf)))
+    return {f: getattr(inf, f) for f, _ in LVIndexInfo._fields_}
 
 
 def leanvec_trim_scratch(device: int | torch.device | None = None) -> None:
@@ -233,6 +242,17 @@ class Index:
         inf = LVIndexInfo()
         check(lib().leanvec_index_info(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in LVIndexInfo._fields_}
+
+    def save(self, path: str) -> "Index":
+        """leanvec_index_save: write the stores, graph and entry point to `path`."""
+        check(lib().leanvec_index_save(self._h, os.fsencode(path), _stream(self.device)))
+        return self
+
+    def load(self, path: str) -> "Index":
+        """leanvec_index_load: replace this index's stores (and metric) with those of `path`,
+        after validating the whole file."""
+        check(lib().leanvec_index_load(self._h, os.fsencode(path), _stream(self.device)))
+        return self
 
     def buffers(self) -> dict:
         ptrs = [ctypes.c_void_p() for _ in range(5)]

@@ -54,6 +54,9 @@ SIGNATURES = {
     "leanvec_index_create": (c_i32, [ctypes.POINTER(c_vp), c_i32]),
     "leanvec_index_free": (c_i32, [c_vp]),
     "leanvec_index_info": (c_i32, [c_vp, ctypes.POINTER(LVIndexInfo)]),
+    "leanvec_index_save": (c_i32, [c_vp, ctypes.c_char_p, c_vp]),
+    "leanvec_index_load": (c_i32, [c_vp, ctypes.c_char_p, c_vp]),
+    "leanvec_index_file_check": (c_i32, [ctypes.c_char_p, ctypes.POINTER(LVIndexInfo)]),
     "leanvec_set_metric": (c_i32, [c_vp, c_i32]),
     "leanvec_index_buffers": (c_i32, [c_vp] + [ctypes.POINTER(c_vp)] * 5),
     "leanvec_encode": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_i32, c_i32, c_i32, c_i32, c_vp]),

@@ -59,19 +59,6 @@ static int project_tc(int prec, const float *X, int64_t n, int D, const float *P
                                : project_bf16(X, n, D, P, d, Y, ldy, ws, ws_bytes, status, st);
 }
 
-// Makes the index's device current for the scope of an API call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess)) ok = true;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 }  // namespace lv
 
 using namespace lv;

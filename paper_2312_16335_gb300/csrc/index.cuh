@@ -35,6 +35,19 @@ struct lv_index {
 };
 
 namespace lv {
+// Makes the index's device current for the scope of an API call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess)) ok = true;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 void index_free_stores(lv_index *idx);
 int ensure_ws(void **p, size_t *have, size_t want);
 }  // namespace lv
