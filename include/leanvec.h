@@ -43,8 +43,8 @@ typedef enum {
     LV_ERR_OOM = -3,       /* device allocation failed */
     LV_ERR_CAPACITY = -4,  /* a per-query size exceeded a compiled/allocated capacity */
     LV_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
-    LV_ERR_CANCELLED = -6,
-    LV_ERR_CORRUPT = -7,   /* malformed input data (e.g. a graph id out of range) */
+    LV_ERR_CANCELLED = -6, /* reserved for a cancellable call; no call of this version returns it */
+    LV_ERR_CORRUPT = -7,   /* malformed input data (a graph id out of range, a damaged index file) */
     LV_ERR_STATE = -8      /* the index lacks what the call needs (no graph, no store) */
 } lv_status;
 
