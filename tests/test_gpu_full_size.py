@@ -7,7 +7,8 @@ of a 10^5-row second moment), the projected database in FP64 rounded to float32,
 the LVQ stores, and the graph (its counter-based SplitMix64 random R-regular graph: a full-size
 Vamana build is out of the oracle's reach in a test, and the search's arithmetic does not depend
 on how the graph was made).  Sampled queries are then searched by the oracle one by one and
-compared element by element with the GPU's answers."""
+compared element by element with the GPU's answers; for the benchmark's bf16 query projection
+the oracle applies the same operand rounding (``oracle.rounding``) before its FP64 projection."""
 import numpy as np
 import pytest
 import torch
@@ -15,7 +16,7 @@ import torch
 import oracle
 import workloads
 from gpu_util import t
-from oracle import fit
+from oracle import fit, rounding
 
 pytestmark = pytest.mark.gpu
 
@@ -87,14 +88,14 @@ def test_id_1m_768_sampled_parity(lv, problem):
         assert np.all(np.abs(sc[qi] - exact) <= bound)
         assert np.all(np.diff(sc[qi]) <= 0)
         assert len(set(ids[qi].tolist())) == K
-    # the benchmark's bf16 query projection moves each primary score by up to about 2^-8 of
-    # ||A q|| ||y||, so the walk and its candidates are no longer those of the FP64 oracle: the
-    # answer sets must still nearly coincide, and every returned score is the exact rerank score
+    # the benchmark's bf16 query projection: the oracle searches with the projection of the same
+    # bf16-rounded operands (computed in FP64), and the ids must agree as for the float32 path
     ids_b, sc_b = idx.search(Qd, Pd, k=K, L=L, rerank=L, max_hops=MAXH, width=W, projection=lv.PREC_BF16)
     idx.sync_status()
     ids_b, sc_b = ids_b.cpu().numpy(), sc_b.cpu().numpy()
-    overlap = np.mean([len(set(ids_b[qi].tolist()) & set(ref["ids"][j].tolist())) / K for j, qi in enumerate(s)])
-    assert overlap >= 0.95
+    ref_b = oracle.search(pb["graph"], pb["entry"], rounding.project(pb["Q"][s], pb["P"], "bf16"), k=K, L=L,
+                          rerank=L, prim=pb["prim"], sec=pb["sec"], qs=Qs, max_hops=MAXH, width=W)
+    assert (ids_b[s] == ref_b["ids"]).mean() >= 0.99
     for j, qi in enumerate(s):
         dec = _decode_rows(pb["sec"], ids_b[qi])
         bound = 1e-4 * np.linalg.norm(Qs[j]) * np.linalg.norm(dec, axis=1)

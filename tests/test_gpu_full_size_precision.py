@@ -7,9 +7,9 @@ The oracle computes every input the GPU search gets: the LeanVec-ID projection (
 of a 10^5-row second moment), the projected database in FP64 rounded to float32, the FP64 means,
 the LVQ-4 / LVQ-8 stores and its SplitMix64 random 64-regular graph.  Sampled queries are searched
 by the oracle one by one.  With the FP32 query projection the ids must agree element by element;
-with the benchmark's e4m3 projection (per-row scales, up to 2^-3 of ||q|| ||a|| per coordinate) the
-walk is no longer the FP64 oracle's, so the answers are checked for what still holds exactly: each
-returned score is the rerank score of its id, scores are sorted and ids distinct."""
+with the benchmark's e4m3 projection (per-row scales) the oracle applies the same operand rounding
+(``oracle.rounding``) before its FP64 projection and the ids must agree likewise; every returned
+score is the exact rerank score of its id, scores are sorted and ids distinct."""
 import numpy as np
 import pytest
 import torch
@@ -17,7 +17,7 @@ import torch
 import oracle
 import workloads
 from gpu_util import encode_parallel, t
-from oracle import fit
+from oracle import fit, rounding
 
 pytestmark = pytest.mark.gpu
 
@@ -92,4 +92,15 @@ def test_precision_10m_768_sampled_parity(lv, problem):
     _check_scores(pb, ids, sc, s, Qs)
     ids8, sc8 = idx.search(Qd, Pd, k=K, L=L, rerank=L, width=W, projection=lv.PREC_FP8)
     idx.sync_status()
-    _check_scores(pb, ids8.cpu().numpy(), sc8.cpu().numpy(), s, Qs)
+    ids8, sc8 = ids8.cpu().numpy(), sc8.cpu().numpy()
+    _check_scores(pb, ids8, sc8, s, Qs)
+    # the e4m3 projection: the oracle searches with the projection of the same per-row scaled
+    # e4m3 operands (computed in FP64), and the ids must agree as for the float32 path
+    ref8 = oracle.search(pb["graph"], pb["entry"], rounding.project(pb["Q"][s], pb["P"], "e4m3"), k=K, L=L,
+                         rerank=L, prim=pb["prim"], sec=pb["sec"], qs=Qs, width=W)
+    assert (ids8[s] == ref8["ids"]).mean() >= 0.99
+    # each e4m3-projected query is within 2e-2 of the unrounded FP64 projection, per coordinate
+    # relative to ||q|| ||a||
+    P64 = pb["P"].astype(np.float64)
+    err = np.abs(rounding.project(pb["Q"][s], pb["P"], "e4m3") - Qs @ P64.T)
+    assert np.all(err <= 2e-2 * np.linalg.norm(Qs, axis=1)[:, None] * np.linalg.norm(P64, axis=1)[None, :])

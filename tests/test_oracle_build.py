@@ -152,3 +152,28 @@ def test_batched_build_invariants_and_quality(oracle_lib):
     truth, _ = oracle_lib.bruteforce(X, Q, 10)
     res = oracle_lib.search(g, entry, Q.astype(np.float64), k=10, L=40, prim_vecs=X)
     assert oracle_lib.recall(res["ids"], truth, 10) >= 0.9
+
+
+def test_ip_entry_is_argmax_of_decoded_primary_dot_mean(oracle_lib):
+    """Inner product: the entry point is argmax_i <mu, decoded y_i> (the primary with the largest
+    inner product with the dataset mean), ties to the smaller id; checked against an independent
+    FP64 argmax of the decoded primaries, including a planted tie."""
+    rng = np.random.default_rng(44)
+    Y = workloads.unit_rows(rng.standard_normal((300, 10)) + np.linspace(0, 2, 10)[None, :])
+    q = oracle_lib.lvq_encode(Y, oracle_lib.mean_fp32(Y), 8)
+    dec = q.decode().astype(np.float64)
+    mu = q.mean.astype(np.float64)
+    v = dec @ mu
+    top2 = np.sort(v)[-2:]
+    assert top2[1] - top2[0] > 1e-4 * np.abs(v).max()  # a unique maximum by a clear margin
+    assert oracle_lib.BuildStore(q).entry() == int(np.argmax(v))
+    assert oracle_lib.BuildStore(q).entry() != int(np.argmin(v))
+    # a tie: the best record copied to a smaller and to a larger id -> the smallest id wins
+    b = int(np.argmax(v))
+    for dup in (0, 299):
+        if dup == b:
+            continue
+        c2, d2, l2 = q.codes.copy(), q.delta.copy(), q.lower.copy()
+        c2[dup], d2[dup], l2[dup] = c2[b], d2[b], l2[b]
+        q2 = oracle_lib.LVQ(c2, d2, l2, q.mean, 8)
+        assert oracle_lib.BuildStore(q2).entry() == min(dup, b)
