@@ -40,8 +40,9 @@ import workloads  # noqa: E402
 L_GRID = [10, 12, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88, 96, 104, 112, 120, 128, 132, 136,
           140, 144, 148, 152, 156, 160, 176, 200, 256, 320, 384, 448, 512]
 
-# DRAM bytes (read + write) of one beam-kernel launch measured with ncu
-# (profiles/beam_kernel_id1m_768.md), valid only for the kernel sources it was taken on.
+# DRAM bytes (read + write) of the search kernels of one search, from one ncu capture of the same
+# configuration (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources
+# it was taken on (the sha1 of beam.cuh, search_lvq8.cu and rerank.cu).
 TRAFFIC_RECORDS = [
     # beam_kernel (3.067 GB read + 10.7 MB written) + rerank_kernel (1.198 GB + 0.15 MB) of one search
     {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 160, "width": 2, "hash": 0,
@@ -341,17 +342,30 @@ def setup(args, dev, with_base=True):
                 t_fit=t_fit, t_enc=t_enc, t_build=t_build)
 
 
-def oracle_prepare(S):
-    """Host copies and the oracle's own LVQ stores of the same vectors and projection."""
+def oracle_prepare(S, projection="bf16"):
+    """Host copies and the oracle's own LVQ stores of the same vectors and projection; the
+    queries projected in FP64 from the operands the GPU's projection multiplies (bf16-rounded
+    for the bf16 projection), so that the oracle walks the same beam."""
     import oracle
+    from oracle import rounding
     X = S["X"].cpu().numpy()
-    A = S["A"].cpu().numpy().astype(np.float64)
+    A32 = S["A"].cpu().numpy()
+    A = A32.astype(np.float64)
     Y = (X.astype(np.float64) @ A.T).astype(np.float32)
     prim = oracle.lvq_encode(Y, oracle.mean_fp32(Y), 8)
     sec = oracle.lvq_encode(X, oracle.mean_fp32(X), 8)
-    Qh = S["Q"].cpu().numpy().astype(np.float64)
-    return dict(prim=prim, sec=sec, g=S["graph"].cpu().numpy(), entry=S["entry"], Qh=Qh, qp=Qh @ A.T,
-                truth=S["truth"].cpu().numpy())
+    Q32 = S["Q"].cpu().numpy()
+    return dict(prim=prim, sec=sec, g=S["graph"].cpu().numpy(), entry=S["entry"], Qh=Q32.astype(np.float64),
+                qp=rounding.project(Q32, A32, projection), truth=S["truth"].cpu().numpy())
+
+
+def method_bytes_per_query(D, d, bits, R, hops, scored, rerank):
+    """Algorithmic bytes of one query of the search: the query (4 D), one graph row per expansion
+    (4 R ids + a 4-byte degree), one primary record per scored node (d bits / 8 code bytes + 8 bytes
+    of constants, rounded up to 32-byte sectors) and one secondary record per reranked candidate
+    (D code bytes + 8 bytes of constants)."""
+    prim = -(-(d * bits // 8 + 8) // 32) * 32
+    return 4 * D + hops * (4 * R + 4) + scored * prim + rerank * (D + 8)
 
 
 def cpu_oracle_sample(O, L, budget_s, nthreads=0, max_hops=0):
@@ -398,6 +412,20 @@ def bench_ood(args, dev):
         rep = {k: v for k, v in rep.items() if k != "loss_trace"}
         rep["seconds"] = time.time() - t0
         fits[name] = (A, B, rep)
+    # the differentiation form's gradient optimiser: Adam on the hand-written pair loss over the
+    # same 10k learning queries x 100k database samples, from LeanVec-ID, spectral-norm projection
+    # after every step; the best iterate of its trace
+    t0 = time.time()
+    A, B, trace = lv.fit_ood_gradient(Xs, Ql, d, steps=args.grad_steps, lr=args.grad_lr, A0=P)
+    torch.cuda.synchronize()
+    fits["ood_grad"] = (A, B, {"seconds": time.time() - t0, "steps": args.grad_steps, "lr": args.grad_lr,
+                               "optimiser": "Adam + spectral-norm projection, best iterate",
+                               "loss_first": trace[0], "loss_best": min(trace), "loss_last": trace[-1],
+                               "best_step": int(np.argmin(trace))})
+    # every projection's loss f(A, B) / (n m) on the learning pairs (the pair loss forward)
+    with torch.no_grad():
+        for name, (A, B, rep) in fits.items():
+            rep["pair_loss"] = float(lv.OODLoss.apply(A.contiguous(), B.contiguous(), Ql, Xs))
     # differentiation form: one forward + backward over 10k x 100k pairs (tf32x3 tensor cores)
     Ap = torch.nn.Parameter(fits["id"][0].clone())
     Bp = torch.nn.Parameter(fits["id"][1].clone())
@@ -436,7 +464,8 @@ def bench_ood(args, dev):
         res[name] = {"recall_at_L": per_L, "L_for_0.90": L90, "max_hops": hop_limit(hf, L90) if L90 else None,
                      "qps_at_0.90": qps, "fit": rep}
         del ix
-    out = {"metric": "recall@10 and QPS at 0.90 on shifted (OOD) queries: LeanVec-OOD vs LeanVec-ID",
+    out = {"metric": "recall@10 and QPS at 0.90 on shifted (OOD) queries: LeanVec-OOD (Frank-Wolfe, eigenvector "
+                     "search, gradient optimiser) vs LeanVec-ID",
            "workload": f"ood-{n // 1000}k-512, {m} OOD test queries, {m} learning queries, 100k database samples, d=128",
            "results": res, "differentiation": diff, "data": "synthetic"}
     print(json.dumps(out), flush=True)
@@ -723,6 +752,137 @@ def bench_l2(args, dev):
                        f"max_hops=ceil({args.hop_factor} L) (both arms)",
            "build_seconds": t_build, "encode_seconds": t_enc, "reverse_pool_clamped": clamped, "results": res,
            "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
+def l2_bandwidth(dev, mb=32, reps=200):
+    """Measured L2 bandwidth: a device copy between two L2-resident buffers (2 x mb MB, far below
+    the L2 size), replayed `reps` times from one CUDA graph so that launch gaps do not count;
+    bytes read + written per second (the best of three replays)."""
+    n = mb * (1 << 20) // 4
+    a = torch.ones(n, device=dev)
+    b = torch.empty_like(a)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            b.copy_(a)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            b.copy_(a)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        gbs = 2 * 4 * n * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+        best = gbs if best is None else max(best, gbs)
+    return best
+
+
+def bench_c1(args, dev):
+    """id-10k-128, the L2-resident configuration: 10k x 128 isotropic mixture (100 components,
+    sigma 0.3, unit norm), 1000 ID queries, LeanVec-ID d = 32 (PCA of the full database), LVQ-8
+    primary + LVQ-8 secondary, GPU-built graph R = 32, L_build = 64, alpha = 0.95 (alpha-scaled
+    rule), k = 10, L = rerank = 50.  The index (about 3 MB) stays in L2, so the roofline is the
+    L2 bandwidth measured in this run, and L2 is flushed (a 256 MB write) before every timed step."""
+    from paper_2312_16335_gb300 import build_lib
+    build_lib.build()
+    import paper_2312_16335_gb300 as lv
+    import oracle
+    n, m, D, d, k, L = 10_000, 1000, 128, 32, 10, 50
+    w = workloads.workload_id_small(n=n, m=m)
+    X, Q = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Q).to(dev)
+    A = lv.leanvec_fit_id(X, d)
+    idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8)
+    idx.build_graph(R=32, L_build=64, alpha=0.95, passes=2, batch=1024, rule=0, seed=workloads.SEED_GRAPH + 1)
+    idx.sync_status()
+    graph, entry = idx.get_graph()
+    truth = ground_truth(X, Q, k)
+    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
+    ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
+    sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def search(ev=None, stats=False):
+        return idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_buf, sc_buf),
+                          events=ev, stats=stats)
+
+    rec = recall_at(search()[0], truth, k)
+    _, _, st = search(stats=True)
+    for _ in range(5):
+        search()
+    times, kern = [], []
+    st_ = torch.cuda.current_stream(dev)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(st_)
+        ev[1].record(st_)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st_)
+        search(ev)
+        e1.record(st_)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kern.append(ev[0].elapsed_time(ev[1]))
+    step_ms = statistics.median(times)
+    kern_ms = statistics.median(kern)
+    # the method's own bytes: the oracle's exact visited counts on the same inputs
+    Xh, Ah = w.X, A.cpu().numpy()
+    Y = (Xh.astype(np.float64) @ Ah.astype(np.float64).T).astype(np.float32)
+    from oracle import rounding
+    prim = oracle.lvq_encode(Y, oracle.mean_fp32(Y), 8)
+    sec = oracle.lvq_encode(Xh, oracle.mean_fp32(Xh), 8)
+    qp = rounding.project(w.Q, Ah, args.projection)
+    t0 = time.perf_counter()
+    r = oracle.search(graph.cpu().numpy(), entry, qp, k=k, L=L, rerank=L, prim=prim, sec=sec,
+                      qs=w.Q.astype(np.float64), width=args.width)
+    cpu_s = time.perf_counter() - t0
+    same = float((ids_buf.cpu().numpy() == r["ids"]).mean())
+    hops_o, scored_o = float(r["hops"].mean()), float(r["scored"].mean())
+    bq = method_bytes_per_query(D, d, 8, 32, hops_o, scored_o, L)
+    l2_gbs = l2_bandwidth(dev)
+    achieved = bq * m / (kern_ms / 1e3) / 1e9
+    # e2e through the C ABI with host buffers (one batch per step)
+    Qh = Q.cpu().pin_memory()
+    ids_h = torch.empty((m, k), dtype=torch.int32).pin_memory()
+    sc_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        idx.search_host(Qh, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_h, sc_h))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        idx.search_host(Qh, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_h, sc_h))
+    e1.record()
+    torch.cuda.synchronize()
+    e2e = m * args.steps / (e0.elapsed_time(e1) / 1e3)
+    out = {"metric": "QPS at k=10, L = rerank = 50 (recall@10 reported), id-10k-128; L2 GB/s",
+           "value": m / (step_ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+           "higher_is_better": True, "dtype": "f32 (u8 LVQ codes decoded to f32)", "data": "synthetic",
+           "config": {"workload": "id-10k-128: isotropic Gaussian mixture (100 components, sigma 0.3), unit norm, "
+                                  "inner product; 1000 ID queries; LeanVec-ID d=32, LVQ-8 primary + LVQ-8 "
+                                  "secondary; GPU-built graph R=32, L_build=64, alpha=0.95 (alpha-scaled rule); "
+                                  "k=10, L=rerank=50, no expansion budget",
+                      "projection": args.projection, "width": args.width,
+                      "l2": "index about 3 MB, L2-resident; L2 flushed (256 MB written) before every timed step"},
+           "recall_at_10": rec, "ids_equal_oracle": same,
+           "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": m * D * 4, "d2h_bytes_per_step": m * k * 8,
+                   "api": "leanvec_search_host (C ABI), one call per step"},
+           "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+                        "kernel": "beam_kernel + rerank_kernel", "kernel_ms": kern_ms, "bytes_per_query": bq,
+                        "hops_per_query": hops_o, "scored_per_query": scored_o,
+                        "gpu_scored_per_query": float(st[:, 1].double().mean()),
+                        "peak_kind": "measured in this run: L2-resident device copy (2 x 32 MB, graph-replayed)",
+                        "note": "1000 queries are one partial wave of the persistent grid's query slots "
+                                "(one warp each): the step is the latency of the longest searches"},
+           "cpu_baseline": {"value": m / cpu_s, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"all {m} queries"}}
     print(json.dumps(out), flush=True)
 
 
@@ -1047,9 +1207,9 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
-    ap.add_argument("--workload", default="id", choices=["id", "ood", "uneven", "precision", "dsweep", "buildstudy",
-                                                      "l2", "kernels", "samples", "loss"],
-                    help="id: the headline 1M x 768 ID workload; ood: the shifted-query 1M x 512 comparison; "
+    ap.add_argument("--workload", default="id", choices=["id", "c1", "ood", "uneven", "precision", "dsweep",
+                                                      "buildstudy", "l2", "kernels", "samples", "loss"],
+                    help="id: the headline 1M x 768 ID workload; c1: the L2-resident 10k x 128 ID configuration; ood: the shifted-query 1M x 512 comparison; "
                          "uneven: 10M x 200 mixed-k / mixed-L batch in one CUDA-graph launch; "
                          "precision: 10M x 768 with FP8 projection and LVQ-4 primaries; "
                          "dsweep: QPS at recall 0.90 vs the primary dimension d on the id workload's graph; "
@@ -1058,10 +1218,12 @@ def main():
                          "kernels: the offline / auxiliary kernels alone against their rooflines; "
                          "samples: fit sample-size study (second moments, projectors, exhaustive-search recall); "
                          "loss: the pair loss forward / backward of the differentiation form alone")
+    ap.add_argument("--grad-steps", type=int, default=100, help="ood workload: Adam steps of the gradient optimiser")
+    ap.add_argument("--grad-lr", type=float, default=1e-2, help="ood workload: Adam learning rate")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
-    sizes = {"id": (1_000_000, 10_000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
+    sizes = {"id": (1_000_000, 10_000), "c1": (10_000, 1000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
              "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
              "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000),
              "kernels": (1_000_000, 10_000), "samples": (1_000_000, 10_000), "loss": (100_000, 10_000)}[args.workload]
@@ -1085,6 +1247,9 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "c1":
+        bench_c1(args, dev)
+        return
     if args.workload == "ood":
         bench_ood(args, dev)
         return
@@ -1188,14 +1353,12 @@ def main():
     log(f"LeanVec L={L} max_hops={mh} recall={rec:.4f}  table={hop_table}")
     log(f"FP32   L={Lb} max_hops={mhb} recall={rec_b:.4f}  table={hop_table_b}")
 
-    # -- per-query work (untimed run with counters)
+    # -- per-query work (untimed run with the kernel's counters)
     _, _, st = lv_search(L, mh, stats=True)
     launches = idx.info()["last_search_kernels"]
     hops = float(st[:, 0].double().mean())
-    scored = float(st[:, 1].double().mean())
+    scored_gpu = float(st[:, 1].double().mean())
     inf = idx.info()
-    bytes_q = (inf["d"] + 4) * 4 + hops * inf["R"] * 4 + scored * inf["primary_stride"] + \
-        L * inf["secondary_stride"] + args.D * 4 + k * 8
 
     def step(ev):
         lv_search(L, mh, out=(ids_buf, sc_buf), events=ev)
@@ -1208,32 +1371,25 @@ def main():
     qps, total_ms = replica_throughput(total_ms, m, args.steps, dev)
     kern_avg = statistics.mean(kern_ms)
     hbm_peak, peak_kind = peaks()
-    achieved = bytes_q * m / (kern_avg / 1e3) / 1e9
 
-    # -- end to end through the C ABI with host buffers
-    Qh = Q.cpu().pin_memory()
-    ids_h = torch.empty((m, k), dtype=torch.int32).pin_memory()
-    sc_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
-
-    # the library's host pipeline: each step copies its queries in, searches and copies the results
-    # out; neighbouring steps' copies overlap the search (two device buffers, copy streams)
-    pipe = lv.HostPipeline(idx, A, m, args.D, k=k, L=L, rerank=L, max_hops=mh, hash_slots=args.hash,
-                           width=args.width, projection=proj)
+    # -- end to end through the C ABI with host buffers: one leanvec_search_host call over
+    # e2e_steps batches of the m queries (pinned host memory), each batch copied in, searched and
+    # its results copied out, the copies of neighbouring batches overlapping the searches
     e2e_steps = max(5, args.steps // 2)
-    for _ in range(3):
-        pipe.submit(Qh, ids_h, sc_h)
-    pipe.synchronize()
+    Qh = Q.cpu().repeat(e2e_steps, 1).pin_memory()
+    ids_h = torch.empty((m * e2e_steps, k), dtype=torch.int32).pin_memory()
+    sc_h = torch.empty((m * e2e_steps, k), dtype=torch.float32).pin_memory()
+    host_kw = dict(k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, projection=proj,
+                   batch=m)
+    idx.search_host(Qh[:2 * m], A, out=(ids_h[:2 * m], sc_h[:2 * m]), **host_kw)  # slots sized, streams made
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    pipe.begin()
-    for _ in range(e2e_steps):
-        pipe.submit(Qh, ids_h, sc_h)
-    pipe.end()
+    idx.search_host(Qh, A, out=(ids_h, sc_h), **host_kw)
     e1.record()
     torch.cuda.synchronize()
     e2e_qps = m * e2e_steps / (e0.elapsed_time(e1) / 1e3)
-    e2e_ok = bool((ids_h.to(dev) == ids_buf).all())  # the host results equal the device-timed step's
+    e2e_ok = bool((ids_h[-m:].to(dev) == ids_buf).all())  # the host results equal the device-timed step's
 
     # -- full-dimensional float32 baseline on the same graph
     ids_b = torch.empty((m, k), dtype=torch.int32, device=dev)
@@ -1241,18 +1397,32 @@ def main():
     base_ms, _ = time_steps(lambda ev: base_search(Lb, mhb, out=(ids_b, sc_b)), max(5, args.steps // 2), 2)
     qps_b = m * max(5, args.steps // 2) / (base_ms / 1e3)
     _, _, stb = base_search(Lb, mhb, stats=True)
-    bytes_b = args.D * 4 + float(stb[:, 0].double().mean()) * inf["R"] * 4 + \
-        float(stb[:, 1].double().mean()) * lv.leanvec_record_stride(args.D, 32) + k * 8
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            cpu = cpu_oracle_sample(oracle_prepare(S), L, args.cpu_budget, max_hops=mh)
-        except Exception as e:  # the GPU result stands without the CPU leg
-            cpu = {"error": repr(e)}
+    bytes_b = args.D * 4 + float(stb[:, 0].double().mean()) * (4 * inf["R"] + 4) + \
+        float(stb[:, 1].double().mean()) * lv.leanvec_record_stride(args.D, 32)
 
     if rank != 0:
         return
+    # -- the CPU oracle on this host's cores (bounded sample), which also gives the method's own
+    # count of scored nodes per query (an exact visited set, the projection's operand rounding
+    # applied), the count the algorithmic bytes use
+    import oracle
+    O = oracle_prepare(S, args.projection)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample(O, L, args.cpu_budget, max_hops=mh)
+        except Exception as e:  # the GPU result stands without the CPU leg
+            cpu = {"error": repr(e)}
+    if cpu and "scored_per_query" in cpu:
+        scored_method, hops_method, method_sample = cpu["scored_per_query"], cpu["hops_per_query"], cpu["sample"]
+    else:
+        ms = min(m, 1000)
+        r = oracle.search(O["g"], O["entry"], O["qp"][:ms], k=k, L=L, rerank=L, prim=O["prim"], sec=O["sec"],
+                          qs=O["Qh"][:ms], max_hops=mh, width=args.width)
+        scored_method, hops_method = float(r["scored"].mean()), float(r["hops"].mean())
+        method_sample = f"first {ms} queries"
+    bytes_q = method_bytes_per_query(args.D, inf["d"], 8, inf["R"], hops_method, scored_method, L)
+    achieved = bytes_q * m / (kern_avg / 1e3) / 1e9
     out = {
         "metric": metric, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -1266,16 +1436,25 @@ def main():
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
-                "d2h_bytes_per_step": m * k * 8, "api": "HostPipeline (pinned host queries in, ids and scores out "
-                "every step; copies of neighbouring steps overlap the search)", "results_match_device": e2e_ok},
+                "d2h_bytes_per_step": m * k * 8, "api": "leanvec_search_host (C ABI): one call over %d batches of "
+                "the %d queries in pinned host memory, each batch copied in, searched and its ids and scores "
+                "copied out, the copies of neighbouring batches overlapping the searches" % (e2e_steps, m),
+                "results_match_device": e2e_ok},
         # per step, as the library counts them: the projection (bf16: cast of A + the float32-input
         # GEMM), then the beam and rerank kernels of each sub-batch
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L, mh),
                      "kernel": "beam_kernel<LvqIntScorer<3,8>,search> + rerank_kernel",
-                     "kernel_ms": kern_avg, "bytes_per_query": bytes_q, "hops_per_query": hops,
-                     "scored_per_query": scored, "peak_kind": peak_kind},
+                     "kernel_ms": kern_avg, "bytes_per_query": bytes_q,
+                     "bytes_model": "4 D + hops (4 R + 4) + scored x %d + rerank x (D + 8)" %
+                                    (-(-(inf["d"] + 8) // 32) * 32),
+                     "hops_per_query": hops_method, "scored_per_query": scored_method,
+                     "scored_counted_by": "the oracle's exact visited set (%s)" % method_sample,
+                     "gpu_scored_per_query": scored_gpu, "gpu_hops_per_query": hops,
+                     "gpu_rescored_bytes_per_query": max(0.0, scored_gpu - scored_method) *
+                                                     (-(-(inf["d"] + 8) // 32) * 32),
+                     "peak_kind": peak_kind},
         "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "max_hops": mhb, "recall_at_10": rec_b,
                           "hop_budget_table": hop_table_b, "bytes_per_query": bytes_b,
                           "speedup_leanvec": qps / world / qps_b},

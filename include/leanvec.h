@@ -285,7 +285,9 @@ int leanvec_index_info(const lv_index *idx, lv_index_info *out);
  * fields against each other, strides against the record geometry, the file size, the checksum,
  * every graph id in [-1, n) -- and returns LV_ERR_CORRUPT (index unchanged) on any mismatch;
  * then it replaces the index's stores (and metric) with the file's on the index's device and
- * synchronises `stream`.  leanvec_index_file_check performs the same validation without a
+ * synchronises `stream`.  Validation holds the whole file in host memory (about 11.6 GB for
+ * 10^7 x 768 with LVQ-4 primaries and LVQ-8 secondaries); a device allocation or copy that fails
+ * after it (LV_ERR_OOM / LV_ERR_CUDA) leaves the index without stores (load again or re-encode).  leanvec_index_file_check performs the same validation without a
  * device and fills `out` (nullable) from the header. */
 int leanvec_index_save(const lv_index *idx, const char *path, lv_stream_t stream);
 int leanvec_index_load(lv_index *idx, const char *path, lv_stream_t stream);
@@ -420,6 +422,29 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
                    int32_t *ids, float *scores, int ldo, lv_search_stats *stats,
                    lv_stream_t stream);
 
+/* leanvec_search over queries and results in HOST memory (Sec. 2 "Search"; the staging is
+ * this library's).  Q is m x D float32 and desc (nullable) m entries in host memory; ids /
+ * scores (m x ldo) are host memory that receives the results.  The m queries are searched in
+ * batches of `batch` rows (batch <= 0 or >= m: one batch); each batch is copied to a device
+ * slot of the index, searched exactly as one leanvec_search call over those rows (same
+ * results), and its results copied back.  Two slots alternate, and the copies run on two copy
+ * streams of the index's own, so that batch i + 1's queries go in and batch i - 1's results
+ * come out while batch i is searched; the searches themselves stay in order on `stream`.
+ *   - Asynchronous like leanvec_search: the copies start after `stream`'s earlier work and
+ *     `stream`'s later work waits for all of them; the host result buffers are complete once
+ *     `stream` has completed (e.g. cudaStreamSynchronize), and Q / desc must stay unchanged
+ *     until then.  Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister) for
+ *     the copies to overlap; pageable memory works but its copies do not overlap.
+ *   - The slots (2 x batch x (4 D + 8 ldo [+ 16]) bytes) are device workspace of the index,
+ *     grown with cudaMalloc on first use at a batch size and kept until the index is freed.
+ *   - params->event_begin / event_end are ignored.  Successive calls on one index must be
+ *     ordered by the caller (the same `stream`, or events), as for leanvec_search.
+ *   - Errors: as leanvec_search (arguments are checked per batch before its launches); a
+ *     failure stops issuing batches, and `stream` still waits for the copies issued. */
+int leanvec_search_host(lv_index *idx, const float *Q, int64_t m, const float *A,
+                        const lv_search_params *params, const lv_query_desc *desc,
+                        int32_t *ids, float *scores, int ldo, int64_t batch, lv_stream_t stream);
+
 /* leanvec_search without device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc while they serve
  * queries -- hosts whose device memory is owned by their own pool allocator and
@@ -430,10 +455,11 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A,
  * size; this variant instead uses one static 16 MiB device array compiled into
  * the library (held on every GPU that loads the library until the process exits)
  * and calls no cudaMalloc, cudaFree or allocating routine.
- *   - Same arguments, semantics and results as leanvec_search, except that the
- *     projection must be LV_PREC_FP32, or LV_PREC_BF16 with 16-byte aligned query
- *     rows (D a multiple of 4: Q is converted inside the GEMM, so only the bf16 copy
- *     of A needs scratch), and that the batch is one launch (no second stream).
+ *   - Same arguments, semantics and results as leanvec_search, except that for an LVQ
+ *     index the projection must be LV_PREC_FP32, or LV_PREC_BF16 with 16-byte aligned
+ *     query rows (D a multiple of 4: Q is converted inside the GEMM, so only the bf16
+ *     copy of A needs scratch) -- a float32 index ignores the projection, as
+ *     leanvec_search does -- and that the batch is one launch (no second stream).
  *   - Capacity: 256 + m * 4 * ldq [+ m * 4 * (Lc + 1) when the search reranks]
  *     [+ 2 d ldx with the bf16 projection, ldx = D rounded up to 8] bytes, each
  *     part rounded up to 256, must fit in 16 MiB, where ldq is the

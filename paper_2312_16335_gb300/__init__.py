@@ -19,7 +19,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "autotune_target_d", "SearchGraph", "HostPipeline", "leanvec_trim_scratch", "leanvec_index_file_check", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "autotune_target_d", "SearchGraph", "leanvec_trim_scratch", "leanvec_index_file_check", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8, PREC_TF32X3 = 0, 1, 2, 3
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
@@ -31,6 +31,17 @@ def _ptr(t: torch.Tensor | None):
         return None
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t: torch.Tensor | None):
+    """Pointer to a contiguous host (CPU) tensor."""
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
@@ -187,25 +198,33 @@ def fit_ood_gradient(X: torch.Tensor, Q: torch.Tensor, d: int, steps: int = 100,
                      A0: torch.Tensor | None = None, B0: torch.Tensor | None = None, log=None):
     """A gradient optimiser for LeanVec-OOD beside Frank-Wolfe: Adam on the pair loss
     (OODLoss, hand-written fwd/bwd) with a projection onto the spectral-norm ball after
-    every step (the relaxed problem "leanvec").  Starts from LeanVec-ID unless A0/B0 given."""
+    every step (the relaxed problem "leanvec").  Starts from LeanVec-ID unless A0/B0 given.
+    Returns the iterate with the lowest loss seen (Adam's steps do not decrease the loss
+    monotonically once the projection is active), and the loss of every iterate."""
     if A0 is None:
         A0 = leanvec_fit_id(X, d)
     A = torch.nn.Parameter(A0.clone().contiguous())
     B = torch.nn.Parameter((A0 if B0 is None else B0).clone().contiguous())
     opt = torch.optim.Adam([A, B], lr=lr)
     trace = []
-    for _ in range(steps):
+    best = (float("inf"), None, None)
+    for _ in range(steps + 1):
         opt.zero_grad()
         loss = OODLoss.apply(A, B, Q, X)
+        cur = float(loss.detach())
+        trace.append(cur)
+        if log:
+            log(cur)
+        if cur < best[0]:
+            best = (cur, A.detach().clone(), B.detach().clone())
+        if len(trace) > steps:  # the last entry is the loss of the final iterate
+            break
         loss.backward()
         opt.step()
         with torch.no_grad():
             leanvec_spectral_clip(A.data)
             leanvec_spectral_clip(B.data)
-        trace.append(float(loss))
-        if log:
-            log(trace[-1])
-    return A.detach(), B.detach(), trace
+    return best[1], best[2], trace
 
 
 class Index:
@@ -360,15 +379,43 @@ class Index:
                                    ldo, _ptr(st), _stream(self.device)))
         return (ids, sc, st) if stats else (ids, sc)
 
+    def search_host(self, Qh: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
+                    max_hops: int = 0, desc: torch.Tensor | None = None, ldo: int | None = None,
+                    out: tuple[torch.Tensor, torch.Tensor] | None = None, batch: int = 0,
+                    projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0, width: int = 1,
+                    warps_per_query: int = 0):
+        """leanvec_search_host: queries Qh (m x D float32) and the results in host memory (use
+        pinned tensors, ``.pin_memory()``, for the copies to overlap the searches); searched in
+        batches of `batch` rows (0 = one batch), each exactly as ``search`` over those rows.
+        desc: optional (m, 4) int32 host tensor of per-query (k, L, rerank, max_hops).  The
+        results are complete once the current stream has completed."""
+        Qh = _f32(Qh)
+        m = Qh.shape[0]
+        ldo = k if ldo is None else ldo
+        if out is None:
+            ids = torch.empty((m, ldo), dtype=torch.int32).pin_memory()
+            sc = torch.empty((m, ldo), dtype=torch.float32).pin_memory()
+        else:
+            ids, sc = out
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width,
+                             warps_per_query, None, None)
+        if desc is not None:
+            desc = desc.to(dtype=torch.int32).contiguous()
+        Ac = _f32(A) if A is not None else None
+        check(lib().leanvec_search_host(self._h, _hptr(Qh), m, _ptr(Ac), ctypes.byref(prm), _hptr(desc), _hptr(ids),
+                                        _hptr(sc), ldo, batch, _stream(self.device)))
+        return ids, sc
+
     def search_noalloc(self, Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
                        max_hops: int = 0, ldo: int | None = None,
                        out: tuple[torch.Tensor, torch.Tensor] | None = None, projection: int = PREC_FP32,
-                       width: int = 1):
+                       width: int = 1, desc: torch.Tensor | None = None):
         """leanvec_search_noalloc: the same search for callers that cannot let the
         library allocate device memory; its scratch is a static 16 MiB device array
         shared by all calls on a device (serialise overlapping calls).  The output
         tensors are the caller's (pass `out` to reuse preallocated ones).  projection:
-        PREC_FP32 or PREC_BF16 (queries converted inside the tensor-core GEMM)."""
+        PREC_FP32 or PREC_BF16 (queries converted inside the tensor-core GEMM).  desc:
+        optional (m, 4) int32 CUDA tensor of per-query (k, L, rerank, max_hops)."""
         Q = _f32(Q)
         m = Q.shape[0]
         ldo = k if ldo is None else ldo
@@ -378,8 +425,10 @@ class Index:
         else:
             ids, sc = out
         prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, 0, 0, width, 0, None, None)
+        if desc is not None:
+            desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None
-        check(lib().leanvec_search_noalloc(self._h, _ptr(Q), m, _ptr(Ac), ctypes.byref(prm), None, _ptr(ids),
+        check(lib().leanvec_search_noalloc(self._h, _ptr(Q), m, _ptr(Ac), ctypes.byref(prm), _ptr(desc), _ptr(ids),
                                            _ptr(sc), ldo, None, _stream(self.device)))
         return ids, sc
 
@@ -476,73 +525,6 @@ def autotune_target_d(X: torch.Tensor, Q: torch.Tensor, truth: torch.Tensor, gra
         table.append(row)
         idx.close()
     return {"best": best, "table": table}
-
-
-class HostPipeline:
-    """Serving loop for query batches that live in (pinned) host memory: batch i's
-    host-to-device copy runs on a copy stream while batch i - 1 is searched, and its results
-    come back on a second copy stream while batch i + 1 is searched.  Two device buffers of
-    queries and of results alternate; the searches themselves stay in order on one compute
-    stream (they share the index's workspaces).  Every batch is copied in, searched and copied
-    out in full; only the copies of neighbouring batches overlap the search.
-
-        pipe = HostPipeline(index, A, m, D, k=10, L=128, rerank=128, width=2, projection=PREC_BF16)
-        for Qh, ids_h, sc_h in batches:   # pinned host tensors (m x D float32; m x k)
-            pipe.submit(Qh, ids_h, sc_h)
-        pipe.synchronize()                # all results are in the host buffers
-    """
-
-    def __init__(self, index: "Index", A: torch.Tensor | None, m: int, D: int, k: int, L: int, **search_kw):
-        dev = index.device
-        self.index, self.A, self.k, self.L, self.kw = index, A, k, L, search_kw
-        self.Q = [torch.empty((m, D), dtype=torch.float32, device=dev) for _ in range(2)]
-        self.ids = [torch.empty((m, k), dtype=torch.int32, device=dev) for _ in range(2)]
-        self.sc = [torch.empty((m, k), dtype=torch.float32, device=dev) for _ in range(2)]
-        self.s_in = torch.cuda.Stream(device=dev)
-        self.s_cmp = torch.cuda.Stream(device=dev)
-        self.s_out = torch.cuda.Stream(device=dev)
-        self.copied = [torch.cuda.Event() for _ in range(2)]    # queries of slot b are on the device
-        self.searched = [torch.cuda.Event() for _ in range(2)]  # slot b's search is done
-        self.drained = [torch.cuda.Event() for _ in range(2)]   # slot b's results are on the host
-        self.n = 0
-        self.begin()
-
-    def begin(self):
-        """Order the pipeline's next work after the caller's current stream (done at creation)."""
-        cur = torch.cuda.current_stream(self.index.device)
-        for s_ in (self.s_in, self.s_cmp, self.s_out):
-            s_.wait_stream(cur)
-
-    def end(self):
-        """Order the caller's current stream after every submitted batch (no host wait)."""
-        torch.cuda.current_stream(self.index.device).wait_stream(self.s_out)
-
-    def submit(self, Qh: torch.Tensor, ids_h: torch.Tensor, sc_h: torch.Tensor):
-        b = self.n & 1
-        if self.n >= 2:
-            self.s_in.wait_event(self.searched[b])  # slot b's queries were consumed
-        with torch.cuda.stream(self.s_in):
-            self.Q[b].copy_(Qh, non_blocking=True)
-            self.copied[b].record(self.s_in)
-        self.s_cmp.wait_event(self.copied[b])
-        if self.n >= 2:
-            self.s_cmp.wait_event(self.drained[b])  # slot b's previous results left the device
-        with torch.cuda.stream(self.s_cmp):
-            self.index.search(self.Q[b], self.A, k=self.k, L=self.L, out=(self.ids[b], self.sc[b]), **self.kw)
-            self.searched[b].record(self.s_cmp)
-        self.s_out.wait_event(self.searched[b])
-        with torch.cuda.stream(self.s_out):
-            ids_h.copy_(self.ids[b], non_blocking=True)
-            sc_h.copy_(self.sc[b], non_blocking=True)
-            self.drained[b].record(self.s_out)
-        self.n += 1
-
-    def synchronize(self):
-        """Wait for every submitted batch; the host result buffers are then complete (a batch's
-        host buffers must not be changed between its submit and this call)."""
-        for s_ in (self.s_in, self.s_cmp, self.s_out):
-            s_.synchronize()
-        self.end()
 
 
 class SearchGraph:

@@ -69,6 +69,8 @@ SIGNATURES = {
     "leanvec_search": (c_i32, [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(LVSearchParams), c_vp, c_vp, c_vp,
                                c_i32, c_vp, c_vp]),
     "leanvec_sync_status": (c_i32, [c_vp, c_vp]),
+    "leanvec_search_host": (c_i32, [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(LVSearchParams), c_vp, c_vp, c_vp,
+                                    c_i32, c_i64, c_vp]),
     "leanvec_search_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(LVSearchParams), c_vp, c_vp, c_vp,
                                        c_i32, c_vp, c_vp]),
     "leanvec_second_moment": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp]),

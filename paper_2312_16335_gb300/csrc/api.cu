@@ -185,6 +185,7 @@ int leanvec_index_free(lv_index *idx) {
     if (idx->aux) cudaStreamDestroy(idx->aux);
     if (idx->ev_fork) cudaEventDestroy(idx->ev_fork);
     if (idx->ev_join) cudaEventDestroy(idx->ev_join);
+    host_slots_free(idx);
     delete idx;
     return LV_OK;
 }

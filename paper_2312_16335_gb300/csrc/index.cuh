@@ -32,6 +32,18 @@ struct lv_index {
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int last_kernels = 0;  // kernels launched by the last search call
+    // leanvec_search_host: two device staging slots (queries, descriptors, results), the copy
+    // streams and the events that order them (created on first use)
+    struct HostSlots {
+        float *q[2] = {nullptr, nullptr};
+        lv_query_desc *desc[2] = {nullptr, nullptr};
+        int32_t *ids[2] = {nullptr, nullptr};
+        float *sc[2] = {nullptr, nullptr};
+        size_t qb[2] = {0, 0}, db[2] = {0, 0}, ib[2] = {0, 0}, sb[2] = {0, 0};
+        cudaStream_t s_in = nullptr, s_out = nullptr;
+        cudaEvent_t start = nullptr, done = nullptr;
+        cudaEvent_t copied[2] = {nullptr, nullptr}, searched[2] = {nullptr, nullptr}, drained[2] = {nullptr, nullptr};
+    } hs;
 };
 
 namespace lv {
@@ -49,5 +61,6 @@ struct DeviceGuard {
 };
 
 void index_free_stores(lv_index *idx);
+void host_slots_free(lv_index *idx);
 int ensure_ws(void **p, size_t *have, size_t want);
 }  // namespace lv

@@ -66,8 +66,11 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     if (u.rerank > 0 && !desc && !idx->sec) return fail(LV_ERR_STATE, "search_noalloc: rerank needs a secondary store");
     // the bf16 projection converts Q inside the GEMM and needs only a bf16 copy of A (in the
     // scratch); the other tensor-core paths would need a converted copy of Q
+    // (a float32 index ignores the projection, as leanvec_search does)
     const bool bf16 = params->projection == LV_PREC_BF16 && idx->pbits != 32;
-    if (params->projection != LV_PREC_FP32 && !(bf16 && project_bf16_fused_ok(Q, idx->D, idx->d)))
+    if (params->projection < LV_PREC_FP32 || params->projection > LV_PREC_TF32X3)
+        return fail(LV_ERR_ARG, "search_noalloc: projection precision must be an lv_precision value");
+    if (idx->pbits != 32 && params->projection != LV_PREC_FP32 && !(bf16 && project_bf16_fused_ok(Q, idx->D, idx->d)))
         return fail(LV_ERR_ARG, "search_noalloc: the projection must be LV_PREC_FP32, or LV_PREC_BF16 with 16-byte "
                                 "aligned query rows (D a multiple of 4)");
     if (idx->sbits == 8 && idx->sg.code_chunks + 1 + idx->metric > 64)
@@ -86,8 +89,9 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
     const size_t need = NOALLOC_HEADER_BYTES + q_bytes + r_bytes + a_bytes;
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(LV_ERR_CAPACITY, "search_noalloc: m * (4 * padded primary dimension [+ 4 * (L rounded up to "
-                                     "32) + 4 with rerank]) + 256 [+ 2 d D for a bf16 projection] bytes (each part "
-                                     "rounded up to 256) exceed the 16 MiB static scratch; split the batch");
+                                     "32) + 4 with rerank]) + 256 [+ 2 d (D rounded up to 8) for a bf16 "
+                                     "projection] bytes (each part rounded up to 256) exceed the 16 MiB static "
+                                     "scratch; split the batch");
 
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return fail(LV_ERR_CUDA, "search_noalloc: cudaGetDevice failed");
@@ -194,7 +198,10 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         }
         const size_t smem = (size_t)(warps / p.T) * p.warp_smem;
         const int block = warps * 32;
-        if (params->event_begin) cudaEventRecord((cudaEvent_t)params->event_begin, st);
+        if (params->event_begin && (e = cudaEventRecord((cudaEvent_t)params->event_begin, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "search_noalloc: cudaEventRecord(event_begin)");
+            break;
+        }
         if (idx->pbits == 32) {
             rc = launch_search_fp32(p, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, st);
         } else {
@@ -204,7 +211,10 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
         }
         if (rc) break;
-        if (params->event_end) cudaEventRecord((cudaEvent_t)params->event_end, st);
+        if (params->event_end && (e = cudaEventRecord((cudaEvent_t)params->event_end, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "search_noalloc: cudaEventRecord(event_end)");
+            break;
+        }
     } while (0);
     if (prev >= 0 && prev != idx->device) cudaSetDevice(prev);
     return rc;

@@ -130,8 +130,32 @@ def test_autograd_function_and_gradient_optimiser(lv, data):
     assert float(loss.detach()) == pytest.approx(ref_L, rel=1e-5)
     np.testing.assert_allclose(A.grad.cpu().numpy(), ref_gA, rtol=0, atol=1e-4 * np.abs(ref_gA).max())
     A1, B1, trace = lv.fit_ood_gradient(Xt, Qt, d, steps=30, lr=5e-3)
-    assert trace[-1] < trace[0]
+    assert min(trace) < trace[0] and len(trace) == 31
     assert fit.op_norm(A1.cpu().numpy()) <= 1 + 1e-4
+
+
+def test_gradient_optimiser_against_frank_wolfe(lv, data):
+    """The differentiation form's optimiser on the small shifted-query mixture: Adam on the
+    hand-written pair loss (100 steps, lr 1e-2, from LeanVec-ID, projected onto the spectral-norm
+    ball) ends with a loss f(A, B) / (n m) -- FP64 trace form from K_Q, K_X -- no larger than
+    Frank-Wolfe's (Algorithm 1, alpha 0.5, relative-change stop 1e-3) and at least 10 % below
+    LeanVec-ID's; the iterate returned is the best one of its loss trace."""
+    X, Q, KX, KQ = data
+    d = 12
+    n, m = X.shape[0], Q.shape[0]
+    Xt, Qt = t(X), t(Q)
+    Afw, Bfw, _ = lv.leanvec_fit_ood(Xt, Qt, d, method=lv.FIT_FW, alpha=0.5, tol=1e-3)
+    Ag, Bg, trace = lv.fit_ood_gradient(Xt, Qt, d, steps=100, lr=1e-2)
+    P = lv.leanvec_fit_id(Xt, d)
+
+    def f(A, B):
+        return fit.ood_loss(A.cpu().numpy().astype(np.float64), B.cpu().numpy().astype(np.float64), KQ, KX) / (n * m)
+
+    l_fw, l_g, l_id = f(Afw, Bfw), f(Ag, Bg), f(P, P)
+    assert l_g <= l_fw, (l_g, l_fw)
+    assert l_g <= 0.9 * l_id, (l_g, l_id)
+    assert min(trace) == pytest.approx(l_g, rel=1e-4)
+    assert fit.op_norm(Ag.cpu().numpy()) <= 1 + 1e-4 and fit.op_norm(Bg.cpu().numpy()) <= 1 + 1e-4
 
 
 def test_spectral_clip(lv):

@@ -346,22 +346,44 @@ def test_autotune_target_d(lv):
     assert abs(oracle.recall(ids, truth, 10) - b["recall"]) < 1e-6
 
 
-def test_host_pipeline_matches_search(lv, pb):
-    """HostPipeline: pinned host batches in, results out, copies of neighbouring batches
-    overlapping the searches; every batch's host results equal a direct search of it."""
+@pytest.mark.parametrize("batch", [0, 70, 300])
+def test_search_host_matches_search(lv, pb, batch):
+    """leanvec_search_host: pinned host queries in, host results out, in batches of `batch` rows
+    (a ragged last batch at 70; one batch at 0 and 300) with the copies of neighbouring batches
+    on the index's copy streams; the results equal a device search of each batch, bit for bit,
+    and the oracle's ids; a second call reuses the staging slots."""
     idx = gpu_index(lv, pb)
     P = t(pb["P"])
-    m = 100
-    pipe = lv.HostPipeline(idx, P, m, pb["D"], k=10, L=48, rerank=48, width=2)
-    batches = []
-    for b in range(5):
-        Qh = torch.from_numpy(pb["Q"][(b % 3) * m:(b % 3 + 1) * m]).pin_memory()
-        ids_h = torch.empty((m, 10), dtype=torch.int32).pin_memory()
-        sc_h = torch.empty((m, 10), dtype=torch.float32).pin_memory()
-        pipe.submit(Qh, ids_h, sc_h)
-        batches.append((Qh, ids_h, sc_h))
-    pipe.synchronize()
-    for Qh, ids_h, sc_h in batches:
-        ids, sc = idx.search(Qh.cuda(), P, k=10, L=48, rerank=48, width=2)
-        torch.testing.assert_close(ids_h, ids.cpu(), rtol=0, atol=0)
-        torch.testing.assert_close(sc_h, sc.cpu(), rtol=0, atol=0)
+    Qh = torch.from_numpy(pb["Q"]).pin_memory()
+    m = Qh.shape[0]
+    for _ in range(2):
+        ids_h, sc_h = idx.search_host(Qh, P, k=10, L=48, rerank=48, width=2, batch=batch)
+        torch.cuda.synchronize()
+        bt = batch or m
+        for q0 in range(0, m, bt):
+            ids, sc = idx.search(t(pb["Q"][q0:q0 + bt]), P, k=10, L=48, rerank=48, width=2)
+            torch.testing.assert_close(ids_h[q0:q0 + bt], ids.cpu(), rtol=0, atol=0)
+            torch.testing.assert_close(sc_h[q0:q0 + bt], sc.cpu(), rtol=0, atol=0)
+    idx.sync_status()
+    ref = oracle.search(pb["graph"], pb["entry"], _qp(pb), k=10, L=48, rerank=48, prim=pb["prim"], sec=pb["sec"],
+                        qs=pb["Q"].astype(np.float64), width=2)
+    assert (ids_h.numpy() == ref["ids"]).mean() >= 0.99
+
+
+def test_search_host_descriptors(lv, pb):
+    """Per-query descriptors from host memory across batch boundaries: the same results as the
+    device search with the same descriptors."""
+    idx = gpu_index(lv, pb)
+    P = t(pb["P"])
+    m = pb["Q"].shape[0]
+    rng = np.random.default_rng(12)
+    L = rng.integers(12, 64, m).astype(np.int32)
+    k = np.minimum(rng.choice([1, 5, 10], m), L).astype(np.int32)
+    desc = np.stack([k, L, L, np.zeros(m, np.int32)], axis=1).astype(np.int32)
+    ids_h, sc_h = idx.search_host(torch.from_numpy(pb["Q"]).pin_memory(), P, k=10, L=64, ldo=10,
+                                  desc=torch.from_numpy(desc), batch=128, width=2)
+    torch.cuda.synchronize()
+    ids, sc = idx.search(t(pb["Q"]), P, k=10, L=64, ldo=10, desc=t(desc), width=2)
+    torch.testing.assert_close(ids_h, ids.cpu(), rtol=0, atol=0)
+    torch.testing.assert_close(sc_h, sc.cpu(), rtol=0, atol=0)
+    idx.sync_status()

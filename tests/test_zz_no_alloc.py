@@ -70,3 +70,50 @@ def test_noalloc_rejects_batches_beyond_the_static_scratch(lv):
     with pytest.raises(lv.LeanVecError) as e:
         idx.search_noalloc(Q, t(pb["P"]), k=5, L=16, rerank=16)
     assert e.value.code == -4 and "16 MiB" in str(e.value)
+
+
+def test_noalloc_float32_index_and_descriptors(lv):
+    """A float32 (full-dimensional) index, whose padded queries go to the static scratch, and an
+    uneven batch of per-query descriptors: the same results as leanvec_search; a float32 index
+    ignores the projection, as leanvec_search does."""
+    import numpy as np
+    pb = small_problem(oracle, n=3000, D=64, d=16, m=300, seed=6)
+    Q, P = t(pb["Q"]), t(pb["P"])
+    base = lv.Index(0).encode_fp32(t(pb["X"])).set_graph(t(pb["graph"]), pb["entry"])
+    ref = base.search(Q, None, k=10, L=40, width=2)
+    for prec in (lv.PREC_FP32, lv.PREC_BF16):
+        got = base.search_noalloc(Q, None, k=10, L=40, width=2, projection=prec)
+        torch.testing.assert_close(got[0], ref[0], rtol=0, atol=0)
+        torch.testing.assert_close(got[1], ref[1], rtol=0, atol=0)
+    idx = gpu_index(lv, pb)
+    rng = np.random.default_rng(3)
+    m = Q.shape[0]
+    k = rng.choice([1, 5, 10], m)
+    L = np.maximum(rng.integers(10, 64, m), k)
+    r = np.minimum(L, rng.integers(0, 48, m))
+    desc = t(np.stack([k, L, r, np.zeros(m, int)], 1).astype(np.int32))
+    ref = idx.search(Q, P, k=10, L=64, rerank=64, desc=desc, ldo=10, width=2)
+    for _ in range(2):
+        got = idx.search_noalloc(Q, P, k=10, L=64, rerank=64, desc=desc, ldo=10, width=2)
+        torch.testing.assert_close(got[0], ref[0], rtol=0, atol=0)
+        torch.testing.assert_close(got[1], ref[1], rtol=0, atol=0)
+    idx.sync_status()
+
+
+def test_noalloc_allocates_no_device_memory(lv):
+    """The entry point's promise: after a first call (which loads the kernels and looks up the
+    scratch array's address), calls with more queries and a wider beam leave the device's free
+    memory unchanged (the outputs are preallocated by the caller)."""
+    pb = small_problem(oracle, n=3000, D=64, d=16, m=300, seed=7)
+    idx = gpu_index(lv, pb)
+    Q, P = t(pb["Q"]), t(pb["P"])
+    ids = torch.empty((300, 10), dtype=torch.int32, device="cuda")
+    sc = torch.empty((300, 10), dtype=torch.float32, device="cuda")
+    idx.search_noalloc(Q[:50], P, k=10, L=24, rerank=24, width=2, out=(ids[:50], sc[:50]))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for m, L in ((300, 64), (300, 128), (120, 96)):
+        idx.search_noalloc(Q[:m], P, k=10, L=L, rerank=L, width=2, out=(ids[:m], sc[:m]))
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    idx.sync_status()
