@@ -829,6 +829,365 @@ __global__ void __launch_bounds__(64 + 32 * pair_epi_warps<MODE>(), 1)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Gradient contraction of the pair loss with the residual tiles recomputed, never stored
+// (Eq. "leanvec_gradients" written per pair, Sec. 2.2):
+//   O[r][:] = sum_c (sum_k Rows[r][k] Cols[c][k]) C[c][:]      (r over a row tile of 128, c over
+// column blocks of 128), i.e. U = R X' (Rows = Qt, Cols = X, C = X') or V = R^T Q' (Rows = X,
+// Cols = Qt, C = Q'), R = Qt X^T.  Per (row tile, column block):
+//   MMA1: S = Rows Cols^T over K = D in bf16x3 form (bf16 hi / lo splits of the float32 operands,
+//         hi hi + hi lo + lo hi: kind::f16 MMAs with float32 accumulation in TMEM; the dropped lo lo
+//         term and the split remainders are ~2^-17 relative, unbiased);
+//   epilogue warps: S (TMEM) -> tf32 hi / lo pair P_hi (in place) and P_lo (TMEM), so that
+//   MMA2: O += P C over K = 128 in tf32x3 form with A read from TMEM (kind::tf32) and B = C^T
+//         (d x 128, tf32 hi / lo) by TMA.
+// S is double-buffered in TMEM (two 128-column buffers), P_lo and the O accumulator take the other
+// 256 columns: MMA1 of the next block runs while the epilogue splits this one.  Work items are
+// (row tile, range of column blocks); an item's O is written to its split's partial slot.
+//   warp 0 lane 0: TMA producer, 3-stage ring of 64 KB stages (MMA1: Rows hi / lo 128 x 64 bf16,
+//                  Cols hi / lo 128 x 64 bf16; MMA2: C^T hi / lo, two 32-column blocks each)
+//   warp 1: TMEM (512 columns); lane 0 issues MMA1 of block t + 1 before MMA2 of block t
+//   warps 2-9: epilogue (warp w: TMEM lanes 32 (w % 4) ..; columns 64 ((w - 2) / 4) .. + 63)
+// Every wait is bounded: a time-out sets the status word's TIMEOUT bit and the kernel drains.
+constexpr int PFL_STAGES = 3;
+constexpr uint32_t PFL_STAGE_BYTES = 65536;
+constexpr int PFL_EPI_WARPS = 8;
+constexpr int PFL_BC = 128;  // columns per block (the K of MMA2)
+
+struct PflParams {
+    int M, N, K, d, dn;  // rows, columns, inner dimension, d, d rounded up to 16 (MMA2's N)
+    int cblocks, cbps, splits;
+    float *out;          // partial[split][M][d]
+    int *status;
+};
+
+// 32 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *r) {
+    tmem_ld16(addr, r);
+    tmem_ld16(addr + 16, r + 16);
+}
+
+// 16 consecutive TMEM columns of this warp's 32 lanes <- r
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            addr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(64 + 32 * PFL_EPI_WARPS, 1)
+    pair_flash_kernel(const __grid_constant__ CUtensorMap trh, const __grid_constant__ CUtensorMap trl,
+                      const __grid_constant__ CUtensorMap tch, const __grid_constant__ CUtensorMap tcl,
+                      const __grid_constant__ CUtensorMap tth, const __grid_constant__ CUtensorMap ttl,
+                      const PflParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + PFL_STAGES * PFL_STAGE_BYTES);
+    uint64_t *empty = full + PFL_STAGES;
+    uint64_t *sfull = empty + PFL_STAGES;  // [2] MMA1 of block t done (buffer t & 1)
+    uint64_t *pready = sfull + 2;          // [2] P_hi / P_lo of block t written (256 arrivals)
+    uint64_t *m2done = pready + 2;         // MMA2 of a block done (one completion per block)
+    uint64_t *odone = m2done + 1;          // the last MMA2 of an item done (one per item)
+    uint64_t *ofree = odone + 1;           // O read out (256 arrivals, one completion per item)
+    uint64_t *drain = ofree + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = (p.M + TC_BM - 1) / TC_BM;
+    const int64_t items = (int64_t)mt * p.splits;
+    const int nkb = (p.K + 63) / 64;  // MMA1 stages per block
+    const int my_items = (int64_t)blockIdx.x < items ? (int)((items - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+    constexpr uint32_t HALF = 16384;  // 128 rows x 128 bytes: one operand tile of a stage
+    const uint32_t ct_box = (uint32_t)p.dn * 128;  // one C^T box (dn rows x 32 floats)
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PFL_STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(sfull + b, 1);
+            mbar_init(pready + b, 32 * PFL_EPI_WARPS);
+        }
+        mbar_init(m2done, 1);
+        mbar_init(odone, 1);
+        mbar_init(ofree, 32 * PFL_EPI_WARPS);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    // TMEM columns: S / P_hi buffers 0 and 128, P_lo 256, O 384
+    auto item_range = [&](int it, int &r0, int &c0, int &c1, int &split) {
+        const int64_t item = blockIdx.x + (int64_t)it * gridDim.x;
+        const int rt = (int)(item % mt);
+        split = (int)(item / mt);
+        r0 = rt * TC_BM;
+        c0 = split * p.cbps;
+        c1 = min(p.cblocks, c0 + p.cbps);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0;
+            bool ok = true;
+            auto acquire = [&](int64_t gg) -> uint8_t * {
+                const int s = (int)(gg % PFL_STAGES);
+                const int64_t u = gg / PFL_STAGES;
+                if (u > 0 && !mbar_wait(empty + s, (uint32_t)((u - 1) & 1))) return nullptr;
+                return base + s * PFL_STAGE_BYTES;
+            };
+            auto load_ct = [&](int cb) -> bool {  // MMA2's operands of block cb: two stages
+                for (int h = 0; h < 2; ++h, ++g) {
+                    uint8_t *sa = acquire(g);
+                    if (!sa || *abort_flag) return false;
+                    uint64_t *f = full + (int)(g % PFL_STAGES);
+                    mbar_expect_tx(f, 4 * ct_box);
+                    const int x = cb * PFL_BC + h * 64;
+                    tma_load_2d(sa, &tth, x, 0, f);
+                    tma_load_2d(sa + ct_box, &tth, x + 32, 0, f);
+                    tma_load_2d(sa + 2 * ct_box, &ttl, x, 0, f);
+                    tma_load_2d(sa + 3 * ct_box, &ttl, x + 32, 0, f);
+                }
+                return true;
+            };
+            int prev = -1;
+            for (int it = 0; it < my_items && ok; ++it) {
+                int r0, c0, c1, split;
+                item_range(it, r0, c0, c1, split);
+                for (int cb = c0; cb < c1 && ok; ++cb) {
+                    for (int kb = 0; kb < nkb; ++kb, ++g) {
+                        uint8_t *sa = acquire(g);
+                        if (!sa || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        uint64_t *f = full + (int)(g % PFL_STAGES);
+                        mbar_expect_tx(f, PFL_STAGE_BYTES);
+                        tma_load_2d(sa, &trh, kb * 64, r0, f);
+                        tma_load_2d(sa + HALF, &trl, kb * 64, r0, f);
+                        tma_load_2d(sa + 2 * HALF, &tch, kb * 64, cb * PFL_BC, f);
+                        tma_load_2d(sa + 3 * HALF, &tcl, kb * 64, cb * PFL_BC, f);
+                    }
+                    if (ok && prev >= 0) ok = load_ct(prev);
+                    prev = cb;
+                }
+            }
+            if (ok && prev >= 0) ok = load_ct(prev);
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+            }
+            // the copies in flight land before the CTA ends (bounded waits)
+            for (int64_t q = std::max<int64_t>(0, g - PFL_STAGES); q < g; ++q)
+                mbar_wait(full + (int)(q % PFL_STAGES), (uint32_t)((q / PFL_STAGES) & 1));
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA1: kind::f16 (bf16 A / B), M = 128, N = 128; MMA2: kind::tf32, M = 128, N = dn
+            const uint32_t id1 = idesc_tc<0>(TC_BM, PFL_BC);
+            const uint32_t id2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.dn >> 3) << 17) |
+                                 ((uint32_t)(TC_BM >> 4) << 24);
+            int64_t g = 0;
+            int64_t T = 0;  // blocks issued (MMA1)
+            bool ok = true;
+            auto take = [&]() -> uint8_t * {
+                const int s = (int)(g % PFL_STAGES);
+                if (!mbar_wait(full + s, (uint32_t)((g / PFL_STAGES) & 1)) || *abort_flag) return nullptr;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                return base + s * PFL_STAGE_BYTES;
+            };
+            // MMA2 of block U (P in buffer U & 1): first = the item's first block (O starts at 0),
+            // last = its last (O complete), item_no = the item's index on this CTA
+            auto mma2 = [&](int64_t U, bool first, bool last, int item_no) -> bool {
+                if (!mbar_wait(pready + (int)(U & 1), (uint32_t)((U >> 1) & 1))) return false;
+                if (first && item_no > 0 && !mbar_wait(ofree, (uint32_t)((item_no - 1) & 1))) return false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t phi = tmem + (uint32_t)((U & 1) * 128), plo = tmem + 256u, o = tmem + 384u;
+                for (int h = 0; h < 2; ++h, ++g) {
+                    uint8_t *sa = take();
+                    if (!sa) return false;
+#pragma unroll
+                    for (int blk = 0; blk < 2; ++blk) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {  // 8 tf32 of K per MMA
+                            const uint32_t kk = (uint32_t)(h * 64 + blk * 32 + k * 8);
+                            const uint64_t bh = sdesc(sa + blk * ct_box + 32 * k);
+                            const uint64_t bl = sdesc(sa + (2 + blk) * ct_box + 32 * k);
+                            const uint32_t ad[3] = {phi + kk, phi + kk, plo + kk};
+                            const uint64_t bd[3] = {bh, bl, bh};
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                const uint32_t acc = (first && h == 0 && blk == 0 && k == 0 && q == 0) ? 0u : 1u;
+                                asm volatile(
+                                    "{\n\t.reg .pred p;\n\t"
+                                    "setp.ne.b32 p, %4, 0;\n\t"
+                                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(o),
+                                    "r"(ad[q]), "l"(bd[q]), "r"(id2), "r"(acc)
+                                    : "memory");
+                            }
+                        }
+                    }
+                    mma_commit(empty + (int)((g) % PFL_STAGES));
+                }
+                mma_commit(m2done);
+                if (last) mma_commit(odone);
+                return true;
+            };
+            int64_t pU = -1;
+            bool pfirst = false, plast = false;
+            int pitem = 0;
+            for (int it = 0; it < my_items && ok; ++it) {
+                int r0, c0, c1, split;
+                item_range(it, r0, c0, c1, split);
+                for (int cb = c0; cb < c1 && ok; ++cb) {
+                    // S buffer T & 1 is free once MMA2 of block T - 2 is done
+                    if (T >= 2 && !mbar_wait(m2done, (uint32_t)((T - 2) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sacc = tmem + (uint32_t)((T & 1) * 128);
+                    for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
+                        uint8_t *sa = take();
+                        if (!sa) {
+                            ok = false;
+                            break;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {  // 16 bf16 (32 bytes) of K per MMA
+                            const uint64_t ah = sdesc(sa + 32 * k), al = sdesc(sa + HALF + 32 * k);
+                            const uint64_t bh = sdesc(sa + 2 * HALF + 32 * k), bl = sdesc(sa + 3 * HALF + 32 * k);
+                            const uint64_t ad[3] = {ah, ah, al}, bd[3] = {bh, bl, bh};
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                const uint32_t acc = (kb > 0 || k > 0 || q > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n\t.reg .pred p;\n\t"
+                                    "setp.ne.b32 p, %4, 0;\n\t"
+                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(sacc),
+                                    "l"(ad[q]), "l"(bd[q]), "r"(id1), "r"(acc)
+                                    : "memory");
+                            }
+                        }
+                        mma_commit(empty + (int)(g % PFL_STAGES));
+                    }
+                    if (!ok) break;
+                    mma_commit(sfull + (int)(T & 1));
+                    if (pU >= 0 && !mma2(pU, pfirst, plast, pitem)) {
+                        ok = false;
+                        break;
+                    }
+                    pU = T;
+                    pfirst = cb == c0;
+                    plast = cb == c1 - 1;
+                    pitem = it;
+                    ++T;
+                }
+            }
+            if (ok && pU >= 0) ok = mma2(pU, pfirst, plast, pitem);
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+            }
+            mma_commit(drain);
+            if (!mbar_wait(drain, 0)) atomicOr(p.status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warps 2..9, TMEM lane quarter warp % 4, columns 64 ((warp - 2) / 4) .. + 63
+        const int quarter = warp & 3;
+        const int cb0 = ((warp - 2) >> 2) * 64;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        int64_t T = 0;
+        bool ok = true;
+        for (int it = 0; it < my_items && ok; ++it) {
+            int r0, c0, c1, split;
+            item_range(it, r0, c0, c1, split);
+            for (int cb = c0; cb < c1; ++cb, ++T) {
+                // S of block T, and P_lo free (MMA2 of block T - 1 done)
+                if (*abort_flag || !mbar_wait(sfull + (int)(T & 1), (uint32_t)((T >> 1) & 1)) ||
+                    (T >= 1 && !mbar_wait(m2done, (uint32_t)((T - 1) & 1)))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sb = tmem + lane_off + (uint32_t)((T & 1) * 128);
+                const uint32_t lb = tmem + lane_off + 256u;
+#pragma unroll 1
+                for (int c = cb0; c < cb0 + 64; c += 32) {
+                    uint32_t r[32], hi[32], lo[32];
+                    tmem_ld32(sb + (uint32_t)c, r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float x = __uint_as_float(r[j]);
+                        const float h = tf32_rna(x);
+                        hi[j] = __float_as_uint(h);
+                        lo[j] = __float_as_uint(tf32_rna(__fsub_rn(x, h)));
+                    }
+                    tmem_st16(sb + (uint32_t)c, hi);
+                    tmem_st16(sb + (uint32_t)c + 16, hi + 16);
+                    tmem_st16(lb + (uint32_t)c, lo);
+                    tmem_st16(lb + (uint32_t)c + 16, lo + 16);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(pready + (int)(T & 1));
+            }
+            if (!ok) break;
+            // the item's O: rows r0 + 32 quarter + lane, columns [cb0 / 2 ..) of d, to its split's slot
+            if (*abort_flag || !mbar_wait(odone, (uint32_t)(it & 1))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = r0 + quarter * 32 + lane;
+            const int half = (warp - 2) >> 2;
+            const int cw = p.dn / 2;  // columns of O per warp (dn is a multiple of 16)
+            float *orow = p.out + ((int64_t)split * p.M + row) * p.d;
+            for (int c = half * cw; c < half * cw + cw; c += 8) {
+                uint32_t r[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(tmem + lane_off + 384u + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < p.M) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (c + j < p.d) orow[c + j] = __uint_as_float(r[j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(ofree);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicOr(p.status, ST_TIMEOUT);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
 // Float32-accurate projection Y = X P^T on the tensor cores: every operand is split into tf32
 // hi = tf32(v) and lo = tf32(v - hi) (both exact in tf32) and a tile product is
 // hi_x hi_p + hi_x lo_p + lo_x hi_p, three tcgen05.mma kind::tf32 (about 21 bits of each float32
@@ -1460,6 +1819,100 @@ int pair_r_tf32(const float *Ah, const float *Al, int64_t M, int64_t lda, const 
 // K splits for gemm_t_tf32 of an M x N output over K: at least four 32-wide K blocks per split and
 // about four to eight work items per SM, the count whose last wave of items is fullest (ties: fewer
 // splits); the value is the number of partial slots the call writes
+// float32 -> bf16 hi / lo pair: hi = bf16(v) (nearest), lo = bf16(v - hi) (nearest); hi + lo keeps
+// 16 significant bits of v
+__global__ void bf16_split_kernel(const float *__restrict__ v, int64_t len, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[t];
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi[t] = h;
+        lo[t] = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(h)));
+    }
+}
+
+int launch_bf16_split(const float *v, int64_t len, __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st) {
+    if (len <= 0) return LV_OK;
+    const int64_t blocks = std::min<int64_t>((len + 255) / 256, (int64_t)sm_count() * 16);
+    bf16_split_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(v, len, hi, lo);
+    LV_CHECK_LAUNCH("bf16_split_kernel");
+    return LV_OK;
+}
+
+// Column splits of pair_flash for M rows and N columns on `grid` CTAs: the number of column ranges
+// that minimises the largest per-CTA load (items taken round-robin), with at most max_splits
+// ranges; *cbps = column blocks per range.  Returns the number of non-empty ranges.
+int pair_flash_splits(int64_t M, int64_t N, int grid, int max_splits, int *cbps) {
+    const int64_t mt = (M + TC_BM - 1) / TC_BM, cb = (N + PFL_BC - 1) / PFL_BC;
+    int64_t best_cost = -1;
+    int best_s = 1, best_c = (int)cb;
+    for (int s = 1; s <= std::min<int64_t>(cb, std::max(1, max_splits)); ++s) {
+        const int64_t per = (cb + s - 1) / s, used = (cb + per - 1) / per;
+        const int64_t items = mt * used, waves = (items + grid - 1) / grid;
+        const int64_t cost = waves * per;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_s = (int)used;
+            best_c = (int)per;
+        }
+    }
+    *cbps = best_c;
+    return best_s;
+}
+
+// out[split][M][d] = partial sums over column range `split` of (Rows Cols^T) C: Rows (M x K) and
+// Cols (N x K) as bf16 hi / lo pairs (row-major, pitch K, K % 8 == 0, 16-byte aligned), C^T
+// (d x N, pitch ldt floats) as tf32 hi / lo pairs; d <= 128.  `splits` / `cbps` from
+// pair_flash_splits.  The residual tiles are recomputed in the kernel and never stored.
+int pair_flash(const __nv_bfloat16 *Rh, const __nv_bfloat16 *Rl, int64_t M, const __nv_bfloat16 *Ch,
+               const __nv_bfloat16 *Cl, int64_t N, int K, const float *Th, const float *Tl, int64_t ldt, int d,
+               int splits, int cbps, float *out, int *status, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0 || K % 8 || d < 1 || d > 128 || M >= (1ll << 31) || N >= (1ll << 31) ||
+        ldt < N || ldt % 4 || splits < 1 || cbps < 1)
+        return fail(LV_ERR_ARG, "pair_flash: unsupported sizes");
+    for (const void *q : {(const void *)Rh, (const void *)Rl, (const void *)Ch, (const void *)Cl, (const void *)Th,
+                          (const void *)Tl})
+        if ((uintptr_t)q & 15) return fail(LV_ERR_ARG, "pair_flash: operands must be 16-byte aligned");
+    auto fn = encode_fn();
+    if (!fn) return fail(LV_ERR_CUDA, "pair_flash: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap trh, trl, tch, tcl, tth, ttl;
+    int rc = make_map(&trh, Rh, M, K, K, TC_BM, 2);
+    if (!rc) rc = make_map(&trl, Rl, M, K, K, TC_BM, 2);
+    if (!rc) rc = make_map(&tch, Ch, N, K, K, PFL_BC, 2);
+    if (!rc) rc = make_map(&tcl, Cl, N, K, K, PFL_BC, 2);
+    if (rc) return rc;
+    const int dn = (d + 15) / 16 * 16;
+    auto tmap = [&](CUtensorMap *mp, const float *ptr) -> bool {
+        cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)d};
+        cuuint64_t strides[1] = {(cuuint64_t)ldt * 4};
+        cuuint32_t box[2] = {32, (cuuint32_t)dn};
+        cuuint32_t es[2] = {1, 1};
+        return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!tmap(&tth, Th) || !tmap(&ttl, Tl)) return fail(LV_ERR_CUDA, "pair_flash: cuTensorMapEncodeTiled failed");
+    PflParams p;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.K = K;
+    p.d = d;
+    p.dn = dn;
+    p.cblocks = (int)((N + PFL_BC - 1) / PFL_BC);
+    p.cbps = cbps;
+    p.splits = splits;
+    p.out = out;
+    p.status = status;
+    if ((int64_t)(splits - 1) * cbps >= p.cblocks) return fail(LV_ERR_ARG, "pair_flash: an empty column range");
+    const int64_t items = ((M + TC_BM - 1) / TC_BM) * splits;
+    const int grid = (int)std::min<int64_t>(items, std::max(1, sm_count()));
+    const size_t sm = (size_t)PFL_STAGES * PFL_STAGE_BYTES + 256 + 1024;
+    LV_CUDA(cudaFuncSetAttribute(pair_flash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    pair_flash_kernel<<<grid, 64 + 32 * PFL_EPI_WARPS, sm, st>>>(trh, trl, tch, tcl, tth, ttl, p);
+    LV_CHECK_LAUNCH("pair_flash_kernel");
+    return LV_OK;
+}
+
 int gemm_t_tf32_splits(int64_t M, int64_t N, int64_t K) {
     const int64_t sms = std::max(1, sm_count());
     const int64_t tiles = pair_items(M, N, 1), nkb = (K + 31) / 32;

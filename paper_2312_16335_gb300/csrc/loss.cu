@@ -4,13 +4,14 @@
 //   dL/dA = -2/(nm) sum_ij r_ij (B x_i) q_j^T = -2/(nm) (R X')^T Q
 //   dL/dB = -2/(nm) sum_ij r_ij (A q_j) x_i^T = -2/(nm) (R^T Q')^T X
 // with Q' = Q A^T (m x d), X' = X B^T (n x d) and R (m x n) the residual matrix.
-// D % 4 == 0 (the tensor-core form): r_ij = qt_j^T x_i with qt_j = q_j - B^T A q_j formed first in
-// float32, so that no tile product carries the cancellation, and every product over pairs runs in
-// tf32x3 form (hi / lo splits, three tf32 MMAs, float32-accurate): the loss as a fused sum of
-// squares, the gradients through R kept per chunk of database rows (ood_loss_bwd_tc).
-// Other D: R is never stored; 64 x 64 pair tiles are recomputed from Q, X, Q', X' on the CUDA cores
-// in float32 (one kernel walks the database tiles for each query tile: loss, U = R X'; another the
-// query tiles for each database tile: V = R^T Q').
+// Tensor-core forms: r_ij = qt_j^T x_i with qt_j = q_j - B^T A q_j formed first in float32, so that
+// no tile product carries the cancellation.  The loss (D % 4 == 0) is a fused sum of squares of
+// tf32x3 tile products; the gradients (D % 8 == 0, d <= 128) recompute each residual tile in TMEM
+// (bf16x3) and contract it there with X' or Q' (tf32x3) -- R is never stored (ood_loss_bwd_tc).
+// Other shapes: 64 x 64 pair tiles are recomputed from Q, X, Q', X' on the CUDA cores in float32
+// (one kernel walks the database tiles for each query tile: loss, U = R X'; another the query tiles
+// for each database tile: V = R^T Q').
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -204,9 +205,11 @@ int pair_sq_tf32(const float *Qh, const float *Ql, int64_t m, const float *Xh, c
 int launch_tf32_split(const float *v, int64_t len, float *hi, float *lo, cudaStream_t st);
 int launch_transpose_tf32_split(const float *Y, int64_t rows, int cols, float *hi, float *lo, int64_t ldt,
                                 cudaStream_t st);
-int pair_r_tf32(const float *Ah, const float *Al, int64_t M, int64_t lda, const float *Bh, const float *Bl, int64_t N,
-                int64_t ldb, int64_t K, float *ch, float *cl, int64_t ldc, float *th, float *tl, int64_t ldt,
-                int *status, cudaStream_t st);
+int launch_bf16_split(const float *v, int64_t len, __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st);
+int pair_flash_splits(int64_t M, int64_t N, int grid, int max_splits, int *cbps);
+int pair_flash(const __nv_bfloat16 *Rh, const __nv_bfloat16 *Rl, int64_t M, const __nv_bfloat16 *Ch,
+               const __nv_bfloat16 *Cl, int64_t N, int K, const float *Th, const float *Tl, int64_t ldt, int d,
+               int splits, int cbps, float *out, int *status, cudaStream_t st);
 int gemm_t_tf32_splits(int64_t M, int64_t N, int64_t K);
 bool project_bf16_fused_ok(const float *X, int D, int d);
 size_t project_tc_ws_bytes(int prec, int64_t n, int D, int d, const float *X);
@@ -284,30 +287,38 @@ static void pair_free(PairWork &w, cudaStream_t st) {
     tmp_free(w.part, st);
 }
 
-// Gradients on the tensor cores (D % 4 == 0), every contraction in tf32x3 form (float32 accurate):
-//   Q' = Q A^T, Qt = Q - Q' B (so that r_ij = qt_j^T x_i), X' = X B^T;
-//   per chunk of database rows [c0, c0 + nc): R_c = Qt X_c^T (m x nc) kept as tf32 hi / lo pairs,
-//   row-major and transposed; U += R_c X'_c and V_c = R_c^T Q' with the d-wide side as M and K
-//   split over the SMs (partial slots summed in order afterwards);
-//   dL/dA = c U^T Q, dL/dB = c V^T X the same way (D-wide side as M, K = m or n), c = -2 scale / (n m).
-// R and R^T of one chunk take at most 4 GiB of scratch, so any n runs in bounded memory.
+// Gradients on the tensor cores (D % 8 == 0, d <= 128):
+//   Q' = Q A^T, Qt = Q - Q' B (so that r_ij = qt_j^T x_i carries no cancellation), X' = X B^T;
+//   U = R X' and V = R^T Q' by pair_flash: every residual tile is recomputed from Qt and X
+//   (bf16x3 products in TMEM) and contracted there with X' or Q' (tf32x3), never stored -- the
+//   scratch is O((m + n) D + splits (m + n) d), with no m x n term; the column ranges' partial
+//   slots are summed in order;
+//   dL/dA = c U^T Q, dL/dB = c V^T X (tf32x3 GEMMs, the D-wide side as M, K = m or n split over
+//   the SMs), c = -2 scale / (n m).
 static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64_t m, const float *X, int64_t n, int D,
                            int d, float scale, float *gA, float *gB, cudaStream_t st) {
     const int64_t ldm = round_up(m, 4), ldn = round_up(n, 4);
-    int64_t nc = ((int64_t)1 << 32) / (16 * ldm);
-    nc = std::min<int64_t>(std::max<int64_t>(256, nc / 256 * 256), n);
-    const int64_t ldr = round_up(nc, 4);
-    const int su = gemm_t_tf32_splits(d, m, nc), sv = gemm_t_tf32_splits(d, nc, m);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // column splits of the two passes, their partial slots capped at 512 MB each
+    const int64_t cap = (int64_t)512 << 20;
+    int cu = 0, cv = 0;
+    const int su = pair_flash_splits(m, n, sms, (int)std::max<int64_t>(1, cap / (4 * m * d)), &cu);
+    const int sv = pair_flash_splits(n, m, sms, (int)std::max<int64_t>(1, cap / (4 * n * d)), &cv);
     const int sa = gemm_t_tf32_splits(D, d, m), sb = gemm_t_tf32_splits(D, d, n);
     const bool proj_tc = project_bf16_fused_ok(X, D, d);
-    float *Qp = nullptr, *Bt = nullptr, *QB = nullptr, *Qt = nullptr, *Qth = nullptr, *Xh = nullptr, *Xl = nullptr,
-          *Xp = nullptr, *XpTh = nullptr, *XpTl = nullptr, *QpTh = nullptr, *QpTl = nullptr, *Rh = nullptr,
-          *Rl = nullptr, *RTh = nullptr, *RTl = nullptr, *Up = nullptr, *Vp = nullptr, *U = nullptr, *V = nullptr,
+    float *Qp = nullptr, *Bt = nullptr, *QB = nullptr, *Qt = nullptr, *Xp = nullptr, *XpTh = nullptr,
+          *XpTl = nullptr, *QpTh = nullptr, *QpTl = nullptr, *Up = nullptr, *Vp = nullptr, *U = nullptr, *V = nullptr,
           *Pw = nullptr, *Gp = nullptr;
+    __nv_bfloat16 *Qbh = nullptr, *Qbl = nullptr, *Xbh = nullptr, *Xbl = nullptr;
     int *status = nullptr, h = 0;
     int rc = LV_OK;
     auto grab = [&](float **p, int64_t count) {
         if (rc == LV_OK && tmp_alloc((void **)p, sizeof(float) * (size_t)count, st))
+            rc = fail(LV_ERR_OOM, "ood_loss_bwd: allocation failed");
+    };
+    auto grab16 = [&](__nv_bfloat16 **p, int64_t count) {
+        if (rc == LV_OK && tmp_alloc((void **)p, sizeof(__nv_bfloat16) * (size_t)count, st))
             rc = fail(LV_ERR_OOM, "ood_loss_bwd: allocation failed");
     };
     const size_t pw_bytes = proj_tc ? project_tc_ws_bytes(LV_PREC_TF32X3, n, D, d, X) : 0;
@@ -315,18 +326,15 @@ static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64
     grab(&Bt, (int64_t)d * D);
     grab(&QB, m * D);
     grab(&Qt, m * D);
-    grab(&Qth, m * D);
-    grab(&Xh, n * D);
-    grab(&Xl, n * D);
+    grab16(&Qbh, m * D);
+    grab16(&Qbl, m * D);
+    grab16(&Xbh, n * D);
+    grab16(&Xbl, n * D);
     grab(&Xp, n * d);
     grab(&XpTh, d * ldn);
     grab(&XpTl, d * ldn);
     grab(&QpTh, d * ldm);
     grab(&QpTl, d * ldm);
-    grab(&Rh, m * ldr);
-    grab(&Rl, m * ldr);
-    grab(&RTh, nc * ldm);
-    grab(&RTl, nc * ldm);
     grab(&Up, su * m * d);
     grab(&Vp, sv * n * d);
     grab(&U, m * d);
@@ -346,9 +354,9 @@ static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64
         rc = fail(LV_ERR_CUDA, "ood_loss_bwd: copy failed");
     if (rc == LV_OK) {
         sub_inplace_kernel<<<(unsigned)(((int64_t)m * D + 255) / 256), 256, 0, st>>>(Qt, QB, (int64_t)m * D);
-        rc = launch_tf32_split(Qt, m * D, Qth, QB, st);  // QB now holds Qt's lo part
+        rc = launch_bf16_split(Qt, m * D, Qbh, Qbl, st);
     }
-    if (rc == LV_OK) rc = launch_tf32_split(X, n * D, Xh, Xl, st);
+    if (rc == LV_OK) rc = launch_bf16_split(X, n * D, Xbh, Xbl, st);
     if (rc == LV_OK) {  // X'
         if (proj_tc) {
             void *ws = Pw;
@@ -360,14 +368,9 @@ static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64
     }
     if (rc == LV_OK) rc = launch_transpose_tf32_split(Xp, n, d, XpTh, XpTl, ldn, st);
     if (rc == LV_OK) rc = launch_transpose_tf32_split(Qp, m, d, QpTh, QpTl, ldm, st);
-    for (int64_t c0 = 0; rc == LV_OK && c0 < n; c0 += nc) {
-        const int64_t nk = std::min(nc, n - c0);
-        rc = pair_r_tf32(Qth, QB, m, D, Xh + c0 * D, Xl + c0 * D, nk, D, D, Rh, Rl, ldr, RTh, RTl, ldm, status, st);
-        if (rc == LV_OK)  // U (m x d) += R_c X'_c: M = d, N = m, K = nk
-            rc = gemm_t_tf32(XpTh + c0, XpTl + c0, d, ldn, Rh, Rl, m, ldr, nk, Up, d, m * d, c0 > 0, su, status, st);
-        if (rc == LV_OK)  // V rows c0 .. c0 + nk: M = d, N = nk, K = m
-            rc = gemm_t_tf32(QpTh, QpTl, d, ldm, RTh, RTl, nk, ldm, m, Vp + c0 * d, d, n * d, 0, sv, status, st);
-    }
+    // U (m x d) = R X': rows Qt, columns X; V (n x d) = R^T Q': rows X, columns Qt
+    if (rc == LV_OK) rc = pair_flash(Qbh, Qbl, m, Xbh, Xbl, n, D, XpTh, XpTl, ldn, d, su, cu, Up, status, st);
+    if (rc == LV_OK) rc = pair_flash(Xbh, Xbl, n, Qbh, Qbl, m, D, QpTh, QpTl, ldm, d, sv, cv, Vp, status, st);
     auto sum = [&](const float *part, int splits, int64_t len, float *out, float sc) {
         split_sum_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, splits, len, out, sc);
     };
@@ -375,9 +378,11 @@ static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64
         sum(Up, su, m * d, U, 1.f);
         sum(Vp, sv, n * d, V, 1.f);
     }
-    // the gradient products reuse the chunk buffers' memory: Q^T, U^T, X^T, V^T as tf32 pairs
-    for (float *p : {Rh, Rl, RTh, RTl, Up, Vp}) tmp_free(p, st);
-    Rh = Rl = RTh = RTl = Up = Vp = nullptr;
+    // the gradient products reuse the passes' memory: Q^T, U^T, X^T, V^T as tf32 pairs
+    for (float *p : {Up, Vp}) tmp_free(p, st);
+    for (__nv_bfloat16 *p : {Qbh, Qbl, Xbh, Xbl}) tmp_free(p, st);
+    Up = Vp = nullptr;
+    Qbh = Qbl = Xbh = Xbl = nullptr;
     float *QTh = nullptr, *QTl = nullptr, *UTh = nullptr, *UTl = nullptr, *XTh = nullptr, *XTl = nullptr,
           *VTh = nullptr, *VTl = nullptr;
     grab(&QTh, D * ldm);
@@ -408,8 +413,8 @@ static int ood_loss_bwd_tc(const float *A, const float *B, const float *Q, int64
                         cudaStreamSynchronize(st) != cudaSuccess))
         rc = fail(LV_ERR_CUDA, "ood_loss_bwd: sync failed");
     if (rc == LV_OK && h) rc = fail(LV_ERR_TIMEOUT, "ood_loss_bwd: a tensor-core pipeline wait timed out");
-    for (float *p : {Qp, Bt, QB, Qt, Qth, Xh, Xl, Xp, XpTh, XpTl, QpTh, QpTl, U, V, Pw, Gp, QTh, QTl, UTh, UTl, XTh,
-                     XTl, VTh, VTl})
+    for (float *p : {Qp, Bt, QB, Qt, Xp, XpTh, XpTl, QpTh, QpTl, U, V, Pw, Gp, QTh, QTl, UTh, UTl, XTh, XTl, VTh,
+                     VTl})
         tmp_free(p, st);
     tmp_free(status, st);
     return rc;
@@ -510,7 +515,8 @@ int leanvec_ood_loss_bwd(const float *A, const float *B, const float *Q, int64_t
         return fail(LV_ERR_ARG, "ood_loss_bwd: invalid sizes or null pointer");
     if (d > DMAX) return fail(LV_ERR_ARG, "ood_loss_bwd: d <= 256 is supported");
     cudaStream_t st = (cudaStream_t)stream;
-    if (D % 4 == 0 && m < (1ll << 31) && n < (1ll << 31)) return ood_loss_bwd_tc(A, B, Q, m, X, n, D, d, scale, gA, gB, st);
+    if (D % 8 == 0 && d <= 128 && m < (1ll << 31) && n < (1ll << 31))
+        return ood_loss_bwd_tc(A, B, Q, m, X, n, D, d, scale, gA, gB, st);
     PairWork w;
     int rc = pair_prepare(A, B, Q, m, X, n, D, d, w, true, st);
     // U = R X' (query tiles, the database split in column ranges whose partials are summed in

@@ -76,10 +76,14 @@ def test_line_search_and_bf16_second_moments(lv, data):
 
 
 @pytest.mark.parametrize("m,n,D,d", [(70, 130, 24, 5), (300, 1000, 64, 16), (129, 257, 200, 64),
-                                     (1000, 5000, 128, 40), (257, 3000, 256, 160), (100, 300, 30, 7)])
+                                     (1000, 5000, 128, 40), (600, 4000, 512, 128), (257, 3000, 256, 160),
+                                     (100, 300, 30, 7), (90, 400, 132, 12)])
 def test_pair_loss_forward_backward(lv, m, n, D, d):
-    """D % 4 == 0 takes the tensor-core form (tf32x3 products; 1000 x 5000 splits the gradient
-    contractions over K, d = 160 gives them two 128-row tiles); D = 30 the CUDA-core form."""
+    """The tensor-core forms: the loss for D % 4 == 0 (tf32x3 tile products), the gradients for
+    D % 8 == 0 and d <= 128 with the residual tiles recomputed in TMEM (bf16x3) and contracted
+    there (tf32x3) -- ragged row tiles (70, 129), column blocks (130, 257) and K blocks (24, 200),
+    d from 5 to 128 (MMA N rounded up to 16), the C3 shape D = 512, d = 128; d = 160, D = 30 and
+    D = 132 take the CUDA-core sweeps (also recomputing)."""
     rng = np.random.default_rng(m + n)
     Q = (rng.standard_normal((m, D)) / np.sqrt(D)).astype(np.float32)
     X = (rng.standard_normal((n, D)) / np.sqrt(D)).astype(np.float32)
@@ -96,10 +100,11 @@ def test_pair_loss_forward_backward(lv, m, n, D, d):
     np.testing.assert_allclose(gA.cpu().numpy(), tA / (n * m), rtol=0, atol=1e-4 * np.abs(tA / (n * m)).max())
 
 
-def test_pair_loss_backward_in_chunks(lv):
-    """20000 queries x 30000 database rows: R and R^T of 6e8 pairs exceed the 4 GiB chunk budget,
-    so the gradients run over three chunks of database rows (U accumulated across them).  Checked
-    against the closed-form gradients built from K_Q and K_X in FP64 (Eq. leanvec_gradients / (n m))."""
+def test_pair_loss_backward_large(lv):
+    """20000 queries x 30000 database rows (6e8 pairs, whose residual matrix would take 2.4 GB):
+    the gradients recompute every residual tile, with many column ranges per pass (partial slots
+    summed in order).  Checked against the closed-form gradients built from K_Q and K_X in FP64
+    (Eq. leanvec_gradients / (n m))."""
     m, n, D, d = 20000, 30000, 64, 24
     rng = np.random.default_rng(17)
     Q = (rng.standard_normal((m, D)) / np.sqrt(D)).astype(np.float32)
