@@ -482,8 +482,10 @@ def ground_truth_big(X, Q, k, qchunk=8192, xchunk=131072):
 def bench_uneven(args, dev):
     """Uneven batching: 10M x 200 database (text-to-image shape, OOD queries), LeanVec-OOD
     d = 64 LVQ-8; 50k queries with k in {1, 10, 100} and L uniform in [20, 300] (L >= k,
-    rerank = L) served by one persistent launch captured in a CUDA graph; launch shape and
-    visited-cache size picked by the autotuner."""
+    rerank = L) served by one CUDA-graph launch of the plan the autotuner picks
+    (autotune_uneven: the caller's order, longest first, or beam-width classes with their own
+    capacities; warps per query, visited-cache slots and warps per block per launch); the
+    recall of each beam-width class is reported with its launch."""
     from paper_2312_16335_gb300 import build_lib
     build_lib.build()
     import paper_2312_16335_gb300 as lv
@@ -518,34 +520,62 @@ def bench_uneven(args, dev):
     truth = ground_truth_big(X, Q, kmax)
     t_truth = time.time() - t0
     log(f"uneven: data {t_data:.1f}s fit {t_fit:.1f}s encode {t_enc:.1f}s build {t_build:.1f}s truth {t_truth:.1f}s")
+    # one launch over the whole batch (capacity of the largest L), launch shape tuned
     tune = lv.autotune(idx, Q, A, k=kmax, L=Lmax, rerank=Lmax, desc=desc, width=args.width,
                        projection=lv.PREC_BF16)
     best = tune["best"]
-    g = lv.SearchGraph(idx, Q, A, k=kmax, L=Lmax, rerank=Lmax, desc=desc, width=args.width,
-                       projection=lv.PREC_BF16, hash_slots=best["hash_slots"],
-                       warps_per_block=best["warps_per_block"])
-    for _ in range(args.warmup):
-        g.replay()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(dev.index) as clk:
+    g1 = lv.SearchGraph(idx, Q, A, k=kmax, L=Lmax, rerank=Lmax, desc=desc, width=args.width,
+                        projection=lv.PREC_BF16, hash_slots=best["hash_slots"],
+                        warps_per_block=best["warps_per_block"])
+    # the batching form's autotuner: beam-width classes, each with its own capacity, warps per
+    # query, visited-cache slots and warps per block, all in one CUDA graph
+    plan = lv.autotune_uneven(idx, Q, A, desc, ldo=kmax, width=args.width, projection=lv.PREC_BF16)
+    g = lv.UnevenGraph(idx, Q, A, desc, plan, ldo=kmax, width=args.width, projection=lv.PREC_BF16)
+
+    def timed(replay):
+        for _ in range(args.warmup):
+            replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            g.replay()
+            replay()
         e1.record()
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    ids = g.ids
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_one = timed(g1.replay)
+    with Clocks(dev.index) as clk:
+        ms = timed(g.replay)
+    ids = g.unsorted(g.ids)
+    same = bool((ids == g1.ids).all())  # the tuned classes answer exactly as the one launch
     per = {}
     for kc in sorted(set(kl[:, 0].tolist())):
         sel = kl[:, 0] == kc
         a = ids[sel][:, :kc].long()
         hit = (a.unsqueeze(2) == truth[sel][:, :kc].unsqueeze(1)).any(dim=2) & (a >= 0)
         per[int(kc)] = {"queries": int(sel.sum()), "recall": float(hit.float().mean())}
+    for c in plan["plan_launches"]["classes"]:
+        sel = plan["plan_orders"]["classes"][c["slice"][0]:c["slice"][1]]
+        kk = kl[sel, 0]
+        a = ids[sel].long()
+        tr = truth[sel]
+        hits = 0.0
+        for kc in sorted(set(kk.tolist())):
+            s2 = kk == kc
+            hits += float(((a[s2][:, :kc].unsqueeze(2) == tr[s2][:, :kc].unsqueeze(1)).any(dim=2) &
+                           (a[s2][:, :kc] >= 0)).float().sum()) / kc
+        c["recall"] = hits / c["queries"]
     out = {"metric": "QPS of one uneven batch (one CUDA-graph launch) and k-recall@k per class",
            "workload": f"uneven-{n // 1000000}M-200 OOD, {m} queries, k in {{1,10,100}}, L ~ U[20,300], rerank = L",
-           "value": m / (ms / 1e3), "unit": "queries/s", "ms_per_batch": ms, "per_class": per,
-           "autotune": tune, "fit": {k: v for k, v in rep.items() if k != "loss_trace"},
+           "value": m / (ms / 1e3), "unit": "queries/s", "ms_per_batch": ms, "per_k_class": per,
+           "tuned_plan": plan["plan"], "plan_ms": plan["plans"], "tuned_launches": plan["classes"],
+           "class_launches": plan["plan_launches"]["classes"], "code_width_d": d,
+           "code_width_note": "d = 64 is fixed by the configuration; autotune_target_d picks d for an index "
+                              "(--workload dsweep)",
+           "one_launch": {"qps": m / (ms_one / 1e3), "ms_per_batch": ms_one, "autotune": tune,
+                          "same_results_as_classes": same},
+           "fit": {k: v for k, v in rep.items() if k != "loss_trace"},
            "setup_seconds": {"data": t_data, "fit": t_fit, "encode": t_enc, "build": t_build, "truth": t_truth},
            "build_reverse_pool_clamped": clamped,
            "clocks": clk.summary(), "data": "synthetic"}
@@ -612,6 +642,7 @@ def bench_precision(args, dev):
         ms, _ = time_steps(lambda ev: idx.search(Q, A, k=10, L=L90, rerank=L90, width=args.width, projection=prec),
                            nst, 2)
         res[pname] = {"L_for_0.90": L90, "recall_trace": trace, "qps": m * nst / (ms / 1e3)}
+    diag = precision_diagnosis(args, dev, lv, X, Q, A, idx, truth[:1000]) if args.diagnose else None
     out = {"metric": "QPS at 10-recall@10 = 0.90 with FP8 (e4m3, per-row scaled) query projection; "
                      "precision errors vs FP64",
            "workload": f"prec-{n // 1000000}M-768: 10,000-component mixture, {m} queries (recall on {mt}), "
@@ -620,8 +651,69 @@ def bench_precision(args, dev):
            "errors_vs_fp64": {"second_moment_bf16_max_rel": k_err, "fit_id_bf16_projector_dist": sub_err,
                               "projection_fp8_rel_to_norms": p_err},
            "setup_seconds": {"data": t_data, "fit": t_fit, "encode_fp8": t_enc, "build": t_build},
-           "build_reverse_pool_clamped": clamped, "data": "synthetic"}
+           "build_reverse_pool_clamped": clamped, "diagnosis": diag, "data": "synthetic"}
     print(json.dumps(out), flush=True)
+
+
+def precision_diagnosis(args, dev, lv, X, Q, A, idx, truth, rs=(64, 128, 256, 512)):
+    """Where prec-10M-768's recall is lost, on the first 1000 queries: the fraction of the true top
+    10 that the top r of an exhaustive ranking by primary score contains -- with float32 projected
+    vectors (the d = 160 projection's ceiling) and with the decoded LVQ-4 primaries of the index (the
+    quantisation's) -- and the search on a graph built on full-D LVQ-8 codes instead of the LVQ-4
+    primaries (the graph's share)."""
+    mq = truth.shape[0]
+    qp = Q[:mq] @ A.T
+    # decoded LVQ-4 primaries: code 2j in the low nibble, 2j + 1 in the high one; constants
+    # {delta, lower} right after the code chunks
+    inf = idx.info()
+    d = inf["d"]
+    rec = idx.primary_records()
+    cb = -(-((d + 1) // 2) // 16) * 16
+    mean = idx.primary_mean()
+    best = {"float32": None, "lvq4": None}
+    for name in best:
+        vals, ids = [], []
+        for s0 in range(0, X.shape[0], 1 << 20):
+            if name == "float32":
+                Y = X[s0:s0 + (1 << 20)] @ A.T
+            else:
+                r = rec[s0:s0 + (1 << 20)]
+                codes = torch.stack([r[:, :cb] & 15, r[:, :cb] >> 4], dim=2).reshape(r.shape[0], 2 * cb)[:, :d].float()
+                c = r[:, cb:cb + 8].contiguous().view(torch.float32)
+                Y = mean[None, :] + c[:, 1:2] + c[:, 0:1] * codes
+            S = qp @ Y.T
+            v, i = torch.topk(S, max(rs), dim=1)
+            vals.append(v)
+            ids.append(i + s0)
+        v, i = torch.topk(torch.cat(vals, 1), max(rs), dim=1)
+        best[name] = torch.gather(torch.cat(ids, 1), 1, i)
+    ceiling = {name: {r: float((b[:, :r].unsqueeze(2) == truth[:, :10].unsqueeze(1)).any(dim=1).float().mean())
+                      for r in rs} for name, b in best.items()}
+    # the same search on a graph built on full-D LVQ-8 codes (alpha, rule, R, L_build as configured)
+    gi = lv.Index(dev.index).set_primary(X, None, 8, X.shape[1])
+    t0 = time.time()
+    gi.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
+                   seed=workloads.SEED_GRAPH + 4)
+    try:
+        gi.sync_status()
+    except lv.LeanVecError as e:
+        if e.code != -4:
+            raise
+    g, e = gi.get_graph()
+    t_full = time.time() - t0
+    del gi
+    mean_deg_full = float((g >= 0).sum(1).float().mean())
+    g0, _ = idx.get_graph()
+    mean_deg_prim = float((g0 >= 0).sum(1).float().mean())
+    del g0
+    idx.set_graph(g, e)
+    trace = []
+    for L in (128, 256, 384, 512):
+        ids = idx.search(Q[:mq], A, k=10, L=L, rerank=L, width=args.width, projection=lv.PREC_FP8)[0]
+        trace.append((L, recall_at(ids, truth, 10)))
+    return {"queries": mq, "exhaustive_primary_ceiling": ceiling,
+            "full_graph": {"build_seconds": t_full, "mean_degree": mean_deg_full, "recall_trace_fp8": trace},
+            "primary_graph_mean_degree": mean_deg_prim}
 
 
 def bench_buildstudy(args, dev):
@@ -789,81 +881,107 @@ def bench_c1(args, dev):
     sigma 0.3, unit norm), 1000 ID queries, LeanVec-ID d = 32 (PCA of the full database), LVQ-8
     primary + LVQ-8 secondary, GPU-built graph R = 32, L_build = 64, alpha = 0.95 (alpha-scaled
     rule), k = 10, L = rerank = 50.  The index (about 3 MB) stays in L2, so the roofline is the
-    L2 bandwidth measured in this run, and L2 is flushed (a 256 MB write) before every timed step."""
+    L2 bandwidth measured in this run, and L2 is flushed (a 256 MB write) before every timed step.
+    Also reported: the same search on the graph built with the benchmark's default rule (unit-norm
+    L2 rule, alpha 1.02), at L = 50 and at the smallest L with recall@10 >= 0.90, and a batch of
+    100k queries from the same mixture (the configured 1000 fill a fraction of one wave)."""
     from paper_2312_16335_gb300 import build_lib
     build_lib.build()
     import paper_2312_16335_gb300 as lv
     import oracle
-    n, m, D, d, k, L = 10_000, 1000, 128, 32, 10, 50
-    w = workloads.workload_id_small(n=n, m=m)
-    X, Q = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Q).to(dev)
-    A = lv.leanvec_fit_id(X, d)
-    idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8)
-    idx.build_graph(R=32, L_build=64, alpha=0.95, passes=2, batch=1024, rule=0, seed=workloads.SEED_GRAPH + 1)
-    idx.sync_status()
-    graph, entry = idx.get_graph()
-    truth = ground_truth(X, Q, k)
-    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
-    ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
-    sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
-    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
-
-    def search(ev=None, stats=False):
-        return idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_buf, sc_buf),
-                          events=ev, stats=stats)
-
-    rec = recall_at(search()[0], truth, k)
-    _, _, st = search(stats=True)
-    for _ in range(5):
-        search()
-    times, kern = [], []
-    st_ = torch.cuda.current_stream(dev)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        ev[0].record(st_)
-        ev[1].record(st_)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st_)
-        search(ev)
-        e1.record(st_)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        kern.append(ev[0].elapsed_time(ev[1]))
-    step_ms = statistics.median(times)
-    kern_ms = statistics.median(kern)
-    # the method's own bytes: the oracle's exact visited counts on the same inputs
-    Xh, Ah = w.X, A.cpu().numpy()
-    Y = (Xh.astype(np.float64) @ Ah.astype(np.float64).T).astype(np.float32)
     from oracle import rounding
-    prim = oracle.lvq_encode(Y, oracle.mean_fp32(Y), 8)
-    sec = oracle.lvq_encode(Xh, oracle.mean_fp32(Xh), 8)
-    qp = rounding.project(w.Q, Ah, args.projection)
-    t0 = time.perf_counter()
-    r = oracle.search(graph.cpu().numpy(), entry, qp, k=k, L=L, rerank=L, prim=prim, sec=sec,
-                      qs=w.Q.astype(np.float64), width=args.width)
-    cpu_s = time.perf_counter() - t0
-    same = float((ids_buf.cpu().numpy() == r["ids"]).mean())
-    hops_o, scored_o = float(r["hops"].mean()), float(r["scored"].mean())
-    bq = method_bytes_per_query(D, d, 8, 32, hops_o, scored_o, L)
+    n, D, d, k = 10_000, 128, 32, 10
+    big = 100_000
+    w = workloads.make_workload("isotropic", n, big, D, 100, cfg=1, sigma=0.3, m_learn=0)
+    X = torch.from_numpy(w.X).to(dev)
+    Qall = torch.from_numpy(w.Q).to(dev)
+    A = lv.leanvec_fit_id(X, d)
+    proj = lv.PREC_BF16 if args.projection == "bf16" else lv.PREC_FP32
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
+    truth_all = ground_truth(X, Qall, k)
     l2_gbs = l2_bandwidth(dev)
-    achieved = bq * m / (kern_ms / 1e3) / 1e9
-    # e2e through the C ABI with host buffers (one batch per step)
-    Qh = Q.cpu().pin_memory()
-    ids_h = torch.empty((m, k), dtype=torch.int32).pin_memory()
-    sc_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    Ah = A.cpu().numpy()
+    Y = (w.X.astype(np.float64) @ Ah.astype(np.float64).T).astype(np.float32)
+    prim = oracle.lvq_encode(Y, oracle.mean_fp32(Y), 8)
+    sec = oracle.lvq_encode(w.X, oracle.mean_fp32(w.X), 8)
+    st_ = torch.cuda.current_stream(dev)
+
+    def timed(idx, Q, L):
+        m = Q.shape[0]
+        ids_buf = torch.empty((m, k), dtype=torch.int32, device=dev)
+        sc_buf = torch.empty((m, k), dtype=torch.float32, device=dev)
+
+        def search(ev=None, stats=False):
+            return idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_buf, sc_buf),
+                              events=ev, stats=stats)
+        for _ in range(5):
+            search()
+        times, kern = [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(st_)
+            ev[1].record(st_)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st_)
+            search(ev)
+            e1.record(st_)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            kern.append(ev[0].elapsed_time(ev[1]))
+        _, _, st = search(stats=True)
+        return ids_buf, statistics.median(times), statistics.median(kern), float(st[:, 1].double().mean())
+
+    def run(rule, alpha, L_fixed, m):
+        idx = lv.Index(dev.index).encode(X, A, primary_bits=8, secondary_bits=8)
+        idx.build_graph(R=32, L_build=64, alpha=alpha, passes=2, batch=1024, rule=rule, seed=workloads.SEED_GRAPH + 1)
+        idx.sync_status()
+        graph, entry = idx.get_graph()
+        Q, truth = Qall[:m], truth_all[:m]
+        if L_fixed:
+            L = L_fixed
+        else:
+            L, _ = calibrate(lambda L: idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, projection=proj)[0],
+                             truth, k)
+            L = L or L_GRID[-1]
+        ids, step_ms, kern_ms, scored_gpu = timed(idx, Q, L)
+        rec = recall_at(ids, truth, k)
+        # the method's own bytes and the parity of ids: the oracle on (up to) the first 1000 queries
+        mo = min(m, 1000)
+        t0 = time.perf_counter()
+        r = oracle.search(graph.cpu().numpy(), entry, rounding.project(w.Q[:mo], Ah, args.projection), k=k, L=L,
+                          rerank=L, prim=prim, sec=sec, qs=w.Q[:mo].astype(np.float64), width=args.width)
+        cpu_s = time.perf_counter() - t0
+        bq = method_bytes_per_query(D, d, 8, 32, float(r["hops"].mean()), float(r["scored"].mean()), L)
+        achieved = bq * m / (kern_ms / 1e3) / 1e9
+        return idx, {"graph": f"rule {rule}, alpha {alpha}", "mean_degree": float((graph >= 0).sum(1).float().mean()),
+                     "queries": m, "L": L, "recall_at_10": rec, "qps": m / (step_ms / 1e3), "step_ms": step_ms,
+                     "ids_equal_oracle": float((ids[:mo].cpu().numpy() == r["ids"]).mean()),
+                     "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
+                                  "frac": achieved / l2_gbs, "kernel_ms": kern_ms, "bytes_per_query": bq,
+                                  "hops_per_query": float(r["hops"].mean()),
+                                  "scored_per_query": float(r["scored"].mean()), "gpu_scored_per_query": scored_gpu},
+                     "cpu_oracle_qps": mo / cpu_s}
+
+    idx, main = run(0, 0.95, 50, 1000)
+    others = [run(0, 0.95, 50, big)[1], run(1, 1.02, 50, 1000)[1], run(1, 1.02, 0, 1000)[1],
+              run(1, 1.02, 0, big)[1]]
+    # e2e through the C ABI with host buffers (one call per step) on the configured case
+    Qh = Qall[:1000].cpu().pin_memory()
+    ids_h = torch.empty((1000, k), dtype=torch.int32).pin_memory()
+    sc_h = torch.empty((1000, k), dtype=torch.float32).pin_memory()
     for _ in range(3):
-        idx.search_host(Qh, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_h, sc_h))
+        idx.search_host(Qh, A, k=k, L=50, rerank=50, width=args.width, projection=proj, out=(ids_h, sc_h))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        idx.search_host(Qh, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_h, sc_h))
+        idx.search_host(Qh, A, k=k, L=50, rerank=50, width=args.width, projection=proj, out=(ids_h, sc_h))
     e1.record()
     torch.cuda.synchronize()
-    e2e = m * args.steps / (e0.elapsed_time(e1) / 1e3)
+    e2e = 1000 * args.steps / (e0.elapsed_time(e1) / 1e3)
     out = {"metric": "QPS at k=10, L = rerank = 50 (recall@10 reported), id-10k-128; L2 GB/s",
-           "value": m / (step_ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+           "value": main["qps"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
            "higher_is_better": True, "dtype": "f32 (u8 LVQ codes decoded to f32)", "data": "synthetic",
            "config": {"workload": "id-10k-128: isotropic Gaussian mixture (100 components, sigma 0.3), unit norm, "
                                   "inner product; 1000 ID queries; LeanVec-ID d=32, LVQ-8 primary + LVQ-8 "
@@ -871,18 +989,16 @@ def bench_c1(args, dev):
                                   "k=10, L=rerank=50, no expansion budget",
                       "projection": args.projection, "width": args.width,
                       "l2": "index about 3 MB, L2-resident; L2 flushed (256 MB written) before every timed step"},
-           "recall_at_10": rec, "ids_equal_oracle": same,
-           "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": m * D * 4, "d2h_bytes_per_step": m * k * 8,
-                   "api": "leanvec_search_host (C ABI), one call per step"},
-           "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
-                        "kernel": "beam_kernel + rerank_kernel", "kernel_ms": kern_ms, "bytes_per_query": bq,
-                        "hops_per_query": hops_o, "scored_per_query": scored_o,
-                        "gpu_scored_per_query": float(st[:, 1].double().mean()),
-                        "peak_kind": "measured in this run: L2-resident device copy (2 x 32 MB, graph-replayed)",
-                        "note": "1000 queries are one partial wave of the persistent grid's query slots "
-                                "(one warp each): the step is the latency of the longest searches"},
-           "cpu_baseline": {"value": m / cpu_s, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"all {m} queries"}}
+           "recall_at_10": main["recall_at_10"], "ids_equal_oracle": main["ids_equal_oracle"],
+           "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": 1000 * D * 4,
+                   "d2h_bytes_per_step": 1000 * k * 8, "api": "leanvec_search_host (C ABI), one call per step"},
+           "roofline": dict(main["roofline"], kernel="beam_kernel + rerank_kernel",
+                            peak_kind="measured in this run: L2-resident device copy (2 x 32 MB, graph-replayed)",
+                            note="1000 queries fill a fraction of one wave of the persistent grid's query slots (one "
+                                 "warp each): the step is the latency of the longest searches; see the 100k-query rows"),
+           "cpu_baseline": {"value": main["cpu_oracle_qps"], "unit": "queries/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": "all 1000 queries"},
+           "other_rows": others}
     print(json.dumps(out), flush=True)
 
 
@@ -922,15 +1038,26 @@ def bench_loss(args, dev):
         tb += ev[1].elapsed_time(ev[2]) / 1e3
     tf /= args.steps
     tb /= args.steps
-    ex_f, ex_b = 3 * 2.0 * m * n * D, 3 * 2.0 * m * n * (D + 2 * d)
-    out = {"metric": "pair loss forward / backward, seconds per call (tf32x3 tensor cores)", "data": "synthetic",
+    # forward: tf32x3 tile products (three tf32 MMAs per product over K = D)
+    ex_f = 3 * 2.0 * m * n * D
+    # backward: two passes (U = R X', V = R^T Q'), each recomputing R in bf16x3 (three bf16 MMAs
+    # over K = D) and contracting it in tf32x3 (three tf32 MMAs over the d outputs); then the
+    # tf32x3 gradient GEMMs U^T Q, V^T X
+    bf_b = 2 * 3 * 2.0 * m * n * D
+    tf_b = 2 * 3 * 2.0 * m * n * d + 3 * 2.0 * D * d * (m + n)
+    ideal_b = bf_b / (bf16 * 1e12) + tf_b / (tf32_peak * 1e12)
+    out = {"metric": "pair loss forward / backward, seconds per call (tensor cores)", "data": "synthetic",
            "workload": f"ood-{n // 1000}k-512: {m} learning queries x {n} database samples, d = 128, "
                        "A = B = LeanVec-ID",
            "steps": args.steps, "warmup": args.warmup, "loss": L,
-           "forward": {"seconds": tf, "executed_tflops": ex_f / tf / 1e12, "frac": ex_f / tf / 1e12 / tf32_peak},
-           "backward": {"seconds": tb, "executed_tflops": ex_b / tb / 1e12, "frac": ex_b / tb / 1e12 / tf32_peak},
-           "bound": "tensor (tf32, three MMAs per product)", "peak_tflops": tf32_peak,
-           "peak_source": src + " bf16 x nominal tf32/bf16 ratio"}
+           "forward": {"seconds": tf, "executed_tflops": ex_f / tf / 1e12, "frac": ex_f / tf / 1e12 / tf32_peak,
+                       "bound": "tensor (tf32, three MMAs per product)"},
+           "backward": {"seconds": tb, "executed_bf16_tflop": bf_b / 1e12, "executed_tf32_tflop": tf_b / 1e12,
+                        "ideal_seconds": ideal_b, "frac": ideal_b / tb,
+                        "bound": "tensor (bf16x3 residual tiles + tf32x3 contractions; frac = time at the "
+                                 "peaks / measured time)"},
+           "peak_tflops": {"bf16": bf16, "tf32": tf32_peak},
+           "peak_source": src + " bf16; tf32 = measured bf16 x nominal tf32/bf16 ratio"}
     print(json.dumps(out), flush=True)
 
 
@@ -1218,6 +1345,8 @@ def main():
                          "kernels: the offline / auxiliary kernels alone against their rooflines; "
                          "samples: fit sample-size study (second moments, projectors, exhaustive-search recall); "
                          "loss: the pair loss forward / backward of the differentiation form alone")
+    ap.add_argument("--diagnose", action="store_true",
+                    help="precision workload: where recall is lost (exhaustive primary ceiling, full-D graph)")
     ap.add_argument("--grad-steps", type=int, default=100, help="ood workload: Adam steps of the gradient optimiser")
     ap.add_argument("--grad-lr", type=float, default=1e-2, help="ood workload: Adam learning rate")
     ap.add_argument("--profile", action="store_true",

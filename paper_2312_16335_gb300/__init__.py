@@ -19,7 +19,7 @@ from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearch
 __all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
-           "autotune", "autotune_target_d", "SearchGraph", "leanvec_trim_scratch", "leanvec_index_file_check", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
+           "autotune", "autotune_target_d", "autotune_uneven", "SearchGraph", "UnevenGraph", "leanvec_trim_scratch", "leanvec_index_file_check", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
 
 PREC_FP32, PREC_BF16, PREC_FP8, PREC_TF32X3 = 0, 1, 2, 3
 PRUNE_SCALED, PRUNE_UNIT_L2 = 0, 1
@@ -468,6 +468,153 @@ def autotune(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, k: int, L:
             if best is None or ms < best["ms"]:
                 best = table[-1]
     return {"best": best, "table": table}
+
+
+def autotune_uneven(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, desc: torch.Tensor, ldo: int,
+                    width: int = 2, projection: int = PREC_FP32, bounds=(64, 128, 192, 256, 320),
+                    teams=(1, 2), hash_slots=(0, 512, 1024, 2048), warps=(4, 8), reps: int = 3) -> dict:
+    """The batching form's autotuner for an uneven batch (per-query k, L, rerank in `desc`).
+    Three plans, each a reordering of the batch (done once) followed by one or more launches of
+    contiguous slices, all captured in one CUDA graph by UnevenGraph:
+      "one"      -- the batch in the caller's order, one launch;
+      "longest"  -- the batch sorted by L, largest first, one launch: the persistent kernel takes
+                    the longest searches first and fills the end of the launch with short ones;
+      "classes"  -- beam-width classes L in (b_{c-1}, b_c] (`bounds`; the last class takes every
+                    larger L), one launch per class, each with its own beam capacity (its largest
+                    L rounded up to 32, which sizes a query's shared memory and so the queries
+                    resident per SM).
+    For every launch of every plan the fastest warps per query (`teams`, dividing `width`),
+    visited-cache slots (0 = the library's default) and warps per block are picked by timing the
+    launch alone with CUDA events; the plan with the smallest total wins.  None of the knobs or
+    plans changes a query's result.  Returns {"plan": name, "order": the permutation (device,
+    int64) of the winning plan, "classes": its launches [{slice, L range, queries, k / L / rerank
+    maxima, capacity, the chosen knobs, ms, qps}], "plans": {name: total ms}, "table": every timed
+    candidate}; UnevenGraph runs it."""
+    dev = index.device
+    desc = desc.to(device=dev, dtype=torch.int32)
+    Lq = desc[:, 1].to(torch.int64)
+    m = Q.shape[0]
+    ids = torch.empty((m, ldo), dtype=torch.int32, device=dev)
+    sc = torch.empty((m, ldo), dtype=torch.float32, device=dev)
+    table = []
+
+    def tune(name, c, Qs, ds, sl, lo, hi):
+        dc = ds[sl]
+        kmax, Lmax, rmax = (int(dc[:, j].max()) for j in range(3))
+        best = None
+        for T in teams:
+            if width % T:
+                continue
+            for h in hash_slots:
+                if h and h < 2 * ((Lmax + 31) // 32 * 32):
+                    continue
+                for w in warps:
+                    if w % T:
+                        continue
+                    kw = dict(k=kmax, L=Lmax, rerank=rmax, desc=dc, ldo=ldo, out=(ids[sl], sc[sl]), width=width,
+                              projection=projection, hash_slots=h, warps_per_block=w, warps_per_query=T)
+                    try:
+                        index.search(Qs[sl], A, **kw)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        for _ in range(reps):
+                            index.search(Qs[sl], A, **kw)
+                        e1.record()
+                        torch.cuda.synchronize(dev)
+                        ms = e0.elapsed_time(e1) / reps
+                    except LeanVecError:
+                        continue
+                    row = {"plan": name, "launch": c, "warps_per_query": T, "hash_slots": h, "warps_per_block": w,
+                           "ms": ms}
+                    table.append(row)
+                    if best is None or ms < best["ms"]:
+                        best = row
+        n_c = sl.stop - sl.start
+        return {"slice": (sl.start, sl.stop), "L_range": (lo, hi), "queries": n_c, "k_max": kmax, "L_max": Lmax,
+                "rerank_max": rmax, "beam_capacity": (Lmax + 31) // 32 * 32,
+                "warps_per_query": best["warps_per_query"], "hash_slots": best["hash_slots"],
+                "warps_per_block": best["warps_per_block"], "ms": best["ms"], "qps": n_c / (best["ms"] / 1e3)}
+
+    b = torch.tensor(list(bounds), dtype=torch.int64, device=dev)
+    cls = torch.clamp(torch.bucketize(Lq, b, right=False), max=len(bounds) - 1)
+    orders = {"one": torch.arange(m, device=dev), "longest": torch.argsort(-Lq, stable=True),
+              "classes": torch.argsort(cls, stable=True)}
+    plans = {}
+    for name, order in orders.items():
+        Qs = Q.index_select(0, order).contiguous()
+        ds = desc.index_select(0, order).contiguous()
+        launches = []
+        if name == "classes":
+            counts = torch.bincount(cls, minlength=len(bounds)).tolist()
+            a0 = 0
+            for c, cnt in enumerate(counts):
+                if cnt == 0:
+                    continue
+                lo = 1 if c == 0 else bounds[c - 1] + 1
+                launches.append(tune(name, c, Qs, ds, slice(a0, a0 + cnt), lo,
+                                     None if c == len(bounds) - 1 else bounds[c]))
+                a0 += cnt
+        else:
+            launches.append(tune(name, 0, Qs, ds, slice(0, m), int(Lq.min()), int(Lq.max())))
+        plans[name] = {"order": order, "classes": launches, "ms": sum(x["ms"] for x in launches)}
+    win = min(plans, key=lambda k: plans[k]["ms"])
+    return {"plan": win, "order": plans[win]["order"], "classes": plans[win]["classes"],
+            "plans": {k: v["ms"] for k, v in plans.items()},
+            "plan_launches": {k: v["classes"] for k, v in plans.items()},
+            "plan_orders": {k: v["order"] for k, v in plans.items()}, "table": table}
+
+
+class UnevenGraph:
+    """An uneven batch served by the plan of autotune_uneven: the batch sorted by class once
+    (outside the graph), then every class searched with its own capacity and launch shape, all
+    captured in one CUDA graph and replayed per batch.  Q and desc are the caller's (unsorted)
+    batch; the graph reads sorted copies (update them with ``load`` to serve a new batch of the
+    same classes).  ``replay`` returns ids / scores in sorted order, ``unsorted`` maps rows
+    back to the caller's order."""
+
+    def __init__(self, index: "Index", Q: torch.Tensor, A: torch.Tensor | None, desc: torch.Tensor, plan: dict,
+                 ldo: int, width: int = 2, projection: int = PREC_FP32):
+        dev = index.device
+        self.index, self.A, self.plan, self.ldo = index, A, plan, ldo
+        self.order = plan["order"]
+        self.Qs = Q.index_select(0, self.order).contiguous()
+        self.ds = desc.to(device=dev, dtype=torch.int32).index_select(0, self.order).contiguous()
+        self.ids = torch.empty((Q.shape[0], ldo), dtype=torch.int32, device=dev)
+        self.scores = torch.empty((Q.shape[0], ldo), dtype=torch.float32, device=dev)
+        self.calls = []
+        for c in plan["classes"]:
+            sl = slice(*c["slice"])
+            self.calls.append((sl, dict(k=c["k_max"], L=c["L_max"], rerank=c["rerank_max"], desc=self.ds[sl], ldo=ldo,
+                                        out=(self.ids[sl], self.scores[sl]), width=width, projection=projection,
+                                        hash_slots=c["hash_slots"], warps_per_block=c["warps_per_block"],
+                                        warps_per_query=c["warps_per_query"])))
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            self._run()  # warm-up: sizes the index's workspaces for every class outside the capture
+        torch.cuda.current_stream(dev).wait_stream(s)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self._run()
+
+    def _run(self):
+        for sl, kw in self.calls:
+            self.index.search(self.Qs[sl], self.A, **kw)
+
+    def load(self, Q: torch.Tensor):
+        """Copy a new batch (same size and classes, caller's order) into the graph's sorted input."""
+        torch.index_select(Q, 0, self.order, out=self.Qs)
+
+    def replay(self):
+        self.graph.replay()
+        return self.ids, self.scores
+
+    def unsorted(self, t: torch.Tensor) -> torch.Tensor:
+        """Rows of a sorted result back in the caller's order."""
+        out = torch.empty_like(t)
+        out.index_copy_(0, self.order, t)
+        return out
 
 
 def _recall(ids: torch.Tensor, truth: torch.Tensor, k: int) -> float:

@@ -387,3 +387,35 @@ def test_search_host_descriptors(lv, pb):
     torch.testing.assert_close(ids_h, ids.cpu(), rtol=0, atol=0)
     torch.testing.assert_close(sc_h, sc.cpu(), rtol=0, atol=0)
     idx.sync_status()
+
+
+def test_autotune_uneven_graph_matches_eager(lv, pb):
+    """The batching form's autotuner: every plan (caller's order, longest first, beam-width
+    classes each with its own capacity and timed knobs), run from one CUDA-graph replay, returns
+    the same ids and scores, bit for bit, as one eager launch over the whole batch; each plan covers
+    every query once and the winner is the fastest."""
+    idx = gpu_index(lv, pb)
+    Q, P = t(pb["Q"]), t(pb["P"])
+    m = Q.shape[0]
+    rng = np.random.default_rng(21)
+    L = rng.integers(10, 200, m)
+    k = np.minimum(rng.choice([1, 5, 10], m), L)
+    desc = t(np.stack([k, L, L, np.zeros(m, int)], 1).astype(np.int32))
+    ref_ids, ref_sc = idx.search(Q, P, k=10, L=200, rerank=200, desc=desc, ldo=10, width=2)
+    tuned = lv.autotune_uneven(idx, Q, P, desc, ldo=10, width=2, bounds=(32, 64, 128, 200), reps=1)
+    assert tuned["plans"][tuned["plan"]] == min(tuned["plans"].values())
+    assert len(tuned["plan_launches"]["classes"]) >= 3
+    for name in ("one", "longest", "classes"):
+        plan = {"order": tuned["plan_orders"][name], "classes": tuned["plan_launches"][name]}
+        assert sorted(plan["order"].tolist()) == list(range(m))
+        assert sum(c["queries"] for c in plan["classes"]) == m
+        for c in plan["classes"]:
+            assert c["beam_capacity"] % 32 == 0 and c["L_max"] <= c["beam_capacity"]
+            assert c["warps_per_query"] in (1, 2)
+        g = lv.UnevenGraph(idx, Q, P, desc, plan, ldo=10, width=2)
+        for _ in range(2):
+            ids, sc = g.replay()
+            torch.cuda.synchronize()
+            torch.testing.assert_close(g.unsorted(ids), ref_ids, rtol=0, atol=0)
+            torch.testing.assert_close(g.unsorted(sc), ref_sc, rtol=0, atol=0)
+    idx.sync_status()
