@@ -621,15 +621,22 @@ def bench_precision(args, dev):
     torch.cuda.synchronize()
     t_enc = time.time() - t0
     t0 = time.time()
-    idx.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
-                    seed=workloads.SEED_GRAPH + 4)
+    # the searched graph: built on LVQ-8 codes of the unreduced vectors (the full-precision
+    # stand-in, as the id workload's), or with --graph primary on the LVQ-4 primaries
+    gi = lv.Index(dev.index).set_primary(X, None, 8, D) if args.graph == "full" else idx
+    gi.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
+                   seed=workloads.SEED_GRAPH + 4)
     clamped = False
     try:
-        idx.sync_status()
+        gi.sync_status()
     except lv.LeanVecError as e:
         if e.code != -4:
             raise
         clamped = True
+    if gi is not idx:
+        idx.set_graph(*gi.get_graph())
+        del gi
+    torch.cuda.synchronize()
     t_build = time.time() - t0
     mt = min(10_000, m)
     truth = ground_truth_big(X, Q[:mt], 10)
@@ -646,7 +653,9 @@ def bench_precision(args, dev):
     out = {"metric": "QPS at 10-recall@10 = 0.90 with FP8 (e4m3, per-row scaled) query projection; "
                      "precision errors vs FP64",
            "workload": f"prec-{n // 1000000}M-768: 10,000-component mixture, {m} queries (recall on {mt}), "
-                       f"d=160 LVQ-4 primary + LVQ-8 secondary, R={args.R}",
+                       f"d=160 LVQ-4 primary + LVQ-8 secondary, R={args.R}, L_build={args.L_build}, "
+                       f"alpha={args.alpha} (rule {args.rule}), graph built on "
+                       f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the LVQ-4 primaries'}",
            "results": res,
            "errors_vs_fp64": {"second_moment_bf16_max_rel": k_err, "fit_id_bf16_projector_dist": sub_err,
                               "projection_fp8_rel_to_norms": p_err},
@@ -659,8 +668,8 @@ def precision_diagnosis(args, dev, lv, X, Q, A, idx, truth, rs=(64, 128, 256, 51
     """Where prec-10M-768's recall is lost, on the first 1000 queries: the fraction of the true top
     10 that the top r of an exhaustive ranking by primary score contains -- with float32 projected
     vectors (the d = 160 projection's ceiling) and with the decoded LVQ-4 primaries of the index (the
-    quantisation's) -- and the search on a graph built on full-D LVQ-8 codes instead of the LVQ-4
-    primaries (the graph's share)."""
+    quantisation's) -- and the search on the searched graph and on the other one (built on the LVQ-4
+    primaries or on full-D LVQ-8 codes): the graph's share."""
     mq = truth.shape[0]
     qp = Q[:mq] @ A.T
     # decoded LVQ-4 primaries: code 2j in the low nibble, 2j + 1 in the high one; constants
@@ -689,8 +698,12 @@ def precision_diagnosis(args, dev, lv, X, Q, A, idx, truth, rs=(64, 128, 256, 51
         best[name] = torch.gather(torch.cat(ids, 1), 1, i)
     ceiling = {name: {r: float((b[:, :r].unsqueeze(2) == truth[:, :10].unsqueeze(1)).any(dim=1).float().mean())
                       for r in rs} for name, b in best.items()}
-    # the same search on a graph built on full-D LVQ-8 codes (alpha, rule, R, L_build as configured)
-    gi = lv.Index(dev.index).set_primary(X, None, 8, X.shape[1])
+    # the same search on the other graph: built on the LVQ-4 primaries when the searched one is on
+    # full-D LVQ-8 codes, and the other way round (alpha, rule, R, L_build as configured)
+    other = "primary" if args.graph == "full" else "full"
+    gi = lv.Index(dev.index).set_primary(X, None, 8, X.shape[1]) if other == "full" else lv.Index(dev.index)
+    if other == "primary":
+        gi.encode(X, A, primary_bits=4, secondary_bits=0, precision=lv.PREC_FP8)
     t0 = time.time()
     gi.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
                    seed=workloads.SEED_GRAPH + 4)
@@ -700,20 +713,24 @@ def precision_diagnosis(args, dev, lv, X, Q, A, idx, truth, rs=(64, 128, 256, 51
         if e.code != -4:
             raise
     g, e = gi.get_graph()
-    t_full = time.time() - t0
+    t_other = time.time() - t0
     del gi
-    mean_deg_full = float((g >= 0).sum(1).float().mean())
-    g0, _ = idx.get_graph()
-    mean_deg_prim = float((g0 >= 0).sum(1).float().mean())
-    del g0
+    g0, e0 = idx.get_graph()
+
+    def trace_of():
+        out = []
+        for L in (128, 256, 384, 512):
+            ids = idx.search(Q[:mq], A, k=10, L=L, rerank=L, width=args.width, projection=lv.PREC_FP8)[0]
+            out.append((L, recall_at(ids, truth, 10)))
+        return out
+
+    searched = {"graph": args.graph, "mean_degree": float((g0 >= 0).sum(1).float().mean()),
+                "recall_trace_fp8": trace_of()}
     idx.set_graph(g, e)
-    trace = []
-    for L in (128, 256, 384, 512):
-        ids = idx.search(Q[:mq], A, k=10, L=L, rerank=L, width=args.width, projection=lv.PREC_FP8)[0]
-        trace.append((L, recall_at(ids, truth, 10)))
-    return {"queries": mq, "exhaustive_primary_ceiling": ceiling,
-            "full_graph": {"build_seconds": t_full, "mean_degree": mean_deg_full, "recall_trace_fp8": trace},
-            "primary_graph_mean_degree": mean_deg_prim}
+    alt = {"graph": other, "build_seconds": t_other, "mean_degree": float((g >= 0).sum(1).float().mean()),
+           "recall_trace_fp8": trace_of()}
+    idx.set_graph(g0, e0)
+    return {"queries": mq, "exhaustive_primary_ceiling": ceiling, "searched_graph": searched, "other_graph": alt}
 
 
 def bench_buildstudy(args, dev):
@@ -1312,8 +1329,8 @@ def main():
                     help="id workload: LVQ-8 secondaries (the configured encoding) or FP16 ones (the paper's "
                          "default in its experiments)")
     ap.add_argument("--graph", default="full", choices=["full", "primary"],
-                    help="id workload: build the shared graph on LVQ-8 codes of the unreduced vectors (full, the "
-                         "paper's setting for its search comparisons) or on the d-dim primaries")
+                    help="id and precision workloads: build the searched graph on LVQ-8 codes of the unreduced "
+                         "vectors (full, the paper's setting for its search comparisons) or on the d-dim primaries")
     ap.add_argument("--rule", type=int, default=None,
                     help="RobustPrune rule: 0 alpha-scaled similarity, 1 Vamana's L2 rule on unit-norm vectors "
                          "(default 1; 0 for the l2 workload, whose build scores are negative squared distances)")
