@@ -1365,7 +1365,9 @@ def main():
     ap.add_argument("--diagnose", action="store_true",
                     help="precision workload: where recall is lost (exhaustive primary ceiling, full-D graph)")
     ap.add_argument("--grad-steps", type=int, default=100, help="ood workload: Adam steps of the gradient optimiser")
-    ap.add_argument("--grad-lr", type=float, default=1e-2, help="ood workload: Adam learning rate")
+    ap.add_argument("--grad-lr", type=float, default=1e-4,
+                    help="ood workload: Adam learning rate (at D = 512 the projected iteration is unstable above "
+                         "about 3e-4; the best iterate is kept)")
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
