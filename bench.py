@@ -566,6 +566,7 @@ def bench_uneven(args, dev):
             hits += float(((a[s2][:, :kc].unsqueeze(2) == tr[s2][:, :kc].unsqueeze(1)).any(dim=2) &
                            (a[s2][:, :kc] >= 0)).float().sum()) / kc
         c["recall"] = hits / c["queries"]
+    tuned_d = uneven_code_width(args, dev, lv, X, Q, Ql, sub, desc, kl, truth, kmax) if args.tune_d else None
     out = {"metric": "QPS of one uneven batch (one CUDA-graph launch) and k-recall@k per class",
            "workload": f"uneven-{n // 1000000}M-200 OOD, {m} queries, k in {{1,10,100}}, L ~ U[20,300], rerank = L",
            "value": m / (ms / 1e3), "unit": "queries/s", "ms_per_batch": ms, "per_k_class": per,
@@ -577,9 +578,69 @@ def bench_uneven(args, dev):
                           "same_results_as_classes": same},
            "fit": {k: v for k, v in rep.items() if k != "loss_trace"},
            "setup_seconds": {"data": t_data, "fit": t_fit, "encode": t_enc, "build": t_build, "truth": t_truth},
-           "build_reverse_pool_clamped": clamped,
+           "build_reverse_pool_clamped": clamped, "code_width_autotune": tuned_d,
            "clocks": clk.summary(), "data": "synthetic"}
     print(json.dumps(out), flush=True)
+
+
+def uneven_code_width(args, dev, lv, X, Q, Ql, sub, desc, kl, truth, kmax, ds=(64, 96, 128, 160, 192)):
+    """The code width d for the uneven workload by the project's autotuner (autotune_target_d): on
+    a graph built once on full-D LVQ-8 codes (so that it does not change with d), for each d the
+    LeanVec-OOD eigenvector-search projection is learned, the database encoded, and the smallest L
+    with recall@10 >= 0.90 on 10k validation queries (k = 10, max_hops = L) timed; then the uneven
+    batch itself on that graph at the configured d and at the tuned d (autotuned plan, per-class
+    k-recall@k)."""
+    gi = lv.Index(dev.index).set_primary(X, None, 8, X.shape[1])
+    t0 = time.time()
+    gi.build_graph(R=args.R, L_build=args.L_build, alpha=args.alpha, passes=2, batch=args.batch, rule=args.rule,
+                   seed=workloads.SEED_GRAPH + 5)
+    try:
+        gi.sync_status()
+    except lv.LeanVecError as e:
+        if e.code != -4:
+            raise
+    graph, entry = gi.get_graph()
+    t_graph = time.time() - t0
+    del gi
+    Xs = X.index_select(0, sub).contiguous()
+
+    def fit(X_, d_):
+        A, B, _ = lv.leanvec_fit_ood(Xs, Ql, d_, method=lv.FIT_ES)
+        return A, B
+
+    mv = min(10_000, Q.shape[0])
+    tune = lv.autotune_target_d(X, Q[:mv], truth[:mv, :10], graph, entry, ds=ds, k=10, fit=fit, hop_factor=1.0)
+    table = [{k_: v for k_, v in r.items() if k_ != "A"} for r in tune["table"]]
+    res = {"graph": {"built_on": "full-D LVQ-8 codes", "seconds": t_graph,
+                     "mean_degree": float((graph >= 0).sum(1).float().mean())},
+           "validation": f"{mv} queries, k = 10, recall@10 >= 0.90, max_hops = L", "table": table,
+           "best_d": tune["best"]["d"] if tune["best"] else None, "uneven_batch": {}}
+    for d in sorted({64, res["best_d"] or 64}):
+        A, B = fit(X, d)
+        ix = lv.Index(dev.index).encode(X, B, 8, 8, precision=lv.PREC_BF16).set_graph(graph, entry)
+        plan = lv.autotune_uneven(ix, Q, A, desc, ldo=kmax, width=args.width, projection=lv.PREC_BF16)
+        g = lv.UnevenGraph(ix, Q, A, desc, plan, ldo=kmax, width=args.width, projection=lv.PREC_BF16)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        ids = g.unsorted(g.ids)
+        per = {}
+        for kc in sorted(set(kl[:, 0].tolist())):
+            sel = kl[:, 0] == kc
+            a = ids[sel][:, :kc].long()
+            hit = (a.unsqueeze(2) == truth[sel][:, :kc].unsqueeze(1)).any(dim=2) & (a >= 0)
+            per[int(kc)] = float(hit.float().mean())
+        res["uneven_batch"][int(d)] = {"qps": Q.shape[0] / (ms / 1e3), "ms": ms, "plan": plan["plan"],
+                                       "k_recall_at_k": per}
+        del g, ix
+    return res
 
 
 def bench_precision(args, dev):
@@ -1362,6 +1423,9 @@ def main():
                          "kernels: the offline / auxiliary kernels alone against their rooflines; "
                          "samples: fit sample-size study (second moments, projectors, exhaustive-search recall); "
                          "loss: the pair loss forward / backward of the differentiation form alone")
+    ap.add_argument("--tune-d", action="store_true",
+                    help="uneven workload: the code width d by the autotuner on a full-D graph, and the uneven "
+                         "batch at the configured and the tuned d")
     ap.add_argument("--diagnose", action="store_true",
                     help="precision workload: where recall is lost (exhaustive primary ceiling, full-D graph)")
     ap.add_argument("--grad-steps", type=int, default=100, help="ood workload: Adam steps of the gradient optimiser")
