@@ -72,6 +72,15 @@ TRAFFIC_RECORDS = [
     {"src_sha1": "adabdf5c923b6df5930577829fe01484d40bee83", "n": 1_000_000, "m": 10_000, "L": 128, "max_hops": 128,
      "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
      "bytes": 3144495360 + 8056832},
+    # the calibrated budget, hop factor 0.5 (L = 152, max_hops = 76): beam 0.962 + 0.371 GB read,
+    # rerank 0.779 + 0.344 GB read, 3.8 MB written
+    {"src_sha1": "adabdf5c923b6df5930577829fe01484d40bee83", "n": 1_000_000, "m": 10_000, "L": 152, "max_hops": 76,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
+     "bytes": 2459870720},
+    # hop factor 0.6 (L = 140, max_hops = 84)
+    {"src_sha1": "adabdf5c923b6df5930577829fe01484d40bee83", "n": 1_000_000, "m": 10_000, "L": 140, "max_hops": 84,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
+     "bytes": 2505062656},
 ]
 
 
@@ -202,7 +211,7 @@ def calibrate(search_fn, truth, k):
     return chosen, trace
 
 
-HOP_FACTORS = (0.0, 1.5, 1.33, 1.2, 1.1, 1.0, 0.9, 0.8)
+HOP_FACTORS = (0.0, 1.5, 1.33, 1.2, 1.1, 1.0, 0.9, 0.8, 0.7, 0.6, 0.5, 0.4)
 
 
 def hop_limit(c, L):
@@ -1435,6 +1444,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="setup, then only `steps` searches at --L inside an NVTX range 'timed' (for ncu)")
     args = ap.parse_args()
+    # the id workload calibrates the expansion budget per arm (the fastest hop factor whose
+    # smallest L reaches recall 0.90) unless a factor is given
+    if args.workload == "id" and "--hop-factor" not in sys.argv:
+        args.hop_sweep = True
     sizes = {"id": (1_000_000, 10_000), "c1": (10_000, 1000), "ood": (1_000_000, 10_000), "uneven": (10_000_000, 50_000),
              "precision": (10_000_000, 100_000), "dsweep": (1_000_000, 10_000),
              "buildstudy": (1_000_000, 10_000), "l2": (1_000_000, 10_000),
@@ -1494,7 +1507,9 @@ def main():
                 f"LVQ-8 primary + LVQ-8 secondary; GPU-built graph R={args.R}, L_build={args.L_build}, "
                 f"alpha={args.alpha} ({'unit-norm L2' if args.rule else 'alpha-scaled IP'} prune rule), built on "
                 f"{'full-D LVQ-8 codes' if args.graph == 'full' else 'the primaries'}; k=10, rerank=L, "
-                f"{'max_hops=ceil(%g L)' % args.hop_factor if args.hop_factor else 'no expansion budget'}")
+                + ("max_hops=ceil(c L) with the hop factor c of each arm calibrated (the fastest of %s whose "
+                   "smallest L reaches recall@10 0.90; 0 = no budget)" % (HOP_FACTORS,) if args.hop_sweep else
+                   'max_hops=ceil(%g L)' % args.hop_factor if args.hop_factor else 'no expansion budget'))
     if args.secondary == "fp16":
         workload = workload.replace("LVQ-8 primary + LVQ-8 secondary", "LVQ-8 primary + FP16 secondary")
     metric = "QPS at 10-recall@10=0.90, LeanVec vs full-D FP32 graph search; HBM GB/s"
@@ -1641,7 +1656,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u8 LVQ codes decoded to f32)",
         "data": "synthetic",
         "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
-                   "rerank": L, "max_hops": mh, "recall_at_10": rec, "hop_budget_table": hop_table, "R": args.R,
+                   "rerank": L, "max_hops": mh, "recall_at_10": rec,
+                   "hop_factor": (max((t for t in hop_table if t.get("qps")), key=lambda t: t["qps"])["hop_factor"]
+                                  if any(t.get("qps") for t in hop_table) else args.hop_factor),
+                   "hop_budget_table": hop_table, "R": args.R,
                    "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary, "projection": args.projection,
                    "hash_slots": args.hash or "default", "width": args.width,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
@@ -1668,6 +1686,8 @@ def main():
                                                      (-(-(inf["d"] + 8) // 32) * 32),
                      "peak_kind": peak_kind},
         "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "max_hops": mhb, "recall_at_10": rec_b,
+                          "hop_factor": (max((t for t in hop_table_b if t.get("qps")), key=lambda t: t["qps"])
+                                         ["hop_factor"] if any(t.get("qps") for t in hop_table_b) else None),
                           "hop_budget_table": hop_table_b, "bytes_per_query": bytes_b,
                           "speedup_leanvec": qps / world / qps_b},
         "cpu_baseline": cpu,

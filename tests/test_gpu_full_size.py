@@ -1,6 +1,7 @@
 """The search at full size, id-1M-768 (10^6 x 768 database, 10^4 queries, d = 160, LVQ-8 primaries
 and secondaries, R = 64), in the launch configuration the benchmark times: one call for the 10^4
-queries (two sub-batches on two streams), k = 10, L = rerank = 128, max_hops = 128, width 2.
+queries (two sub-batches on two streams), k = 10, L = rerank = 152, max_hops = 76 (the calibrated
+expansion budget), width 2.
 
 The oracle computes every input the GPU search gets: the LeanVec-ID projection (FP64 eigenvectors
 of a 10^5-row second moment), the projected database in FP64 rounded to float32, the FP64 means,
@@ -21,7 +22,7 @@ from oracle import fit, rounding
 pytestmark = pytest.mark.gpu
 
 N, M, D, d, R = 1_000_000, 10_000, 768, 160, 64
-K, L, MAXH, W = 10, 128, 128, 2
+K, L, MAXH, W = 10, 152, 76, 2
 SAMPLE = 64
 
 
