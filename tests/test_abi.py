@@ -50,6 +50,9 @@ def test_argument_errors_need_no_gpu(native):
     assert lib.leanvec_column_mean(None, 0, 4, None, None) == -1
     assert lib.leanvec_lvq_encode(None, 4, 8, None, 8, None, None) == -1
     assert lib.leanvec_search(None, None, 1, None, None, None, None, None, 10, None, None) == -1
+    assert lib.leanvec_search_host(None, None, 1, None, None, None, None, None, 10, 0, None) == -1
+    assert b"search_host" in lib.leanvec_last_error()
+    assert lib.leanvec_search_noalloc(None, None, 1, None, None, None, None, None, 10, None, None) == -1
     assert lib.leanvec_index_free(None) == 0
     # the scratch pool: a negative ordinal is an argument error; a device without a pool is a no-op
     assert lib.leanvec_trim_scratch(-1) == -1
