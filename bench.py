@@ -1533,7 +1533,12 @@ def main():
         out = {"impl": "reference", "metric": metric, "value": v, "unit": "queries/s", "n_gpus": 1,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": workload, "L": L, "max_hops": mh, "impl_note": "CPU oracle on the host cores"},
+               "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": S["Q"].shape[0],
+                          "k": 10, "L": L, "rerank": L, "max_hops": mh, "R": args.R, "L_build": args.L_build,
+                          "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph,
+                          "secondary": args.secondary, "projection": args.projection, "width": args.width,
+                          "impl_note": "CPU oracle on the host cores (the same graph, stores and queries; the "
+                                       "projection's bf16 operand rounding applied in FP64)"},
                "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                                              "d2h_bytes_per_step": 0}}
         print(json.dumps(out), flush=True)
