@@ -253,7 +253,7 @@ def choose_config(args, S, proj, k=10):
     idx, Q, A, truth = S["idx"], S["Q"], S["A"], S["truth"]
 
     def lv_search(L, mh):
-        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash,
+        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
                           projection=proj)
 
     if args.L:
@@ -535,7 +535,7 @@ def bench_uneven(args, dev):
     best = tune["best"]
     g1 = lv.SearchGraph(idx, Q, A, k=kmax, L=Lmax, rerank=Lmax, desc=desc, width=args.width,
                         projection=lv.PREC_BF16, hash_slots=best["hash_slots"],
-                        warps_per_block=best["warps_per_block"])
+                        warps_per_block=best["warps_per_block"], queries_per_warp=best["queries_per_warp"])
     # the batching form's autotuner: beam-width classes, each with its own capacity, warps per
     # query, visited-cache slots and warps per block, all in one CUDA graph
     plan = lv.autotune_uneven(idx, Q, A, desc, ldo=kmax, width=args.width, projection=lv.PREC_BF16)
@@ -1000,7 +1000,7 @@ def bench_c1(args, dev):
 
         def search(ev=None, stats=False):
             return idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_buf, sc_buf),
-                              events=ev, stats=stats)
+                              events=ev, stats=stats, queries_per_warp=args.qpw)
         for _ in range(5):
             search()
         times, kern = [], []
@@ -1074,7 +1074,7 @@ def bench_c1(args, dev):
                                   "inner product; 1000 ID queries; LeanVec-ID d=32, LVQ-8 primary + LVQ-8 "
                                   "secondary; GPU-built graph R=32, L_build=64, alpha=0.95 (alpha-scaled rule); "
                                   "k=10, L=rerank=50, no expansion budget",
-                      "projection": args.projection, "width": args.width,
+                      "projection": args.projection, "width": args.width, "queries_per_warp": args.qpw or 1,
                       "l2": "index about 3 MB, L2-resident; L2 flushed (256 MB written) before every timed step"},
            "recall_at_10": main["recall_at_10"], "ids_equal_oracle": main["ids_equal_oracle"],
            "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": 1000 * D * 4,
@@ -1419,6 +1419,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hash", type=int, default=0, help="visited-cache slots per query (0 = library default)")
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
+    ap.add_argument("--queries-per-warp", dest="qpw", type=int, default=0, choices=[0, 1, 2],
+                    help="queries per warp of the beam kernel (0 = the library default, 1)")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
     ap.add_argument("--workload", default="id", choices=["id", "c1", "ood", "uneven", "precision", "dsweep",
@@ -1552,12 +1554,12 @@ def main():
     if args.profile:
         L = args.L or 64
         for _ in range(args.warmup):
-            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash,
+            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
                        projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
-            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash,
+            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
                        projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
@@ -1569,7 +1571,7 @@ def main():
 
     # -- choose L (and the expansion budget) for recall 0.90 (untimed)
     def lv_search(L, mh, **kw):
-        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash,
+        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
                           projection=proj, **kw)
 
     def base_search(L, mh, **kw):
@@ -1611,7 +1613,7 @@ def main():
     Qh = Q.cpu().repeat(e2e_steps, 1).pin_memory()
     ids_h = torch.empty((m * e2e_steps, k), dtype=torch.int32).pin_memory()
     sc_h = torch.empty((m * e2e_steps, k), dtype=torch.float32).pin_memory()
-    host_kw = dict(k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, projection=proj,
+    host_kw = dict(k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, projection=proj,
                    batch=m)
     idx.search_host(Qh[:2 * m], A, out=(ids_h[:2 * m], sc_h[:2 * m]), **host_kw)  # slots sized, streams made
     torch.cuda.synchronize()
@@ -1666,7 +1668,7 @@ def main():
                                   if any(t.get("qps") for t in hop_table) else args.hop_factor),
                    "hop_budget_table": hop_table, "R": args.R,
                    "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary, "projection": args.projection,
-                   "hash_slots": args.hash or "default", "width": args.width,
+                   "hash_slots": args.hash or "default", "width": args.width, "queries_per_warp": args.qpw or 1,
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
@@ -1680,7 +1682,8 @@ def main():
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": recorded_traffic(args, L, mh),
-                     "kernel": "beam_kernel<LvqIntScorer<3,8>,search> + rerank_kernel",
+                     "kernel": ("beam_half_kernel<3,8>" if args.qpw == 2 else "beam_kernel<LvqIntScorer<3,8>,search>")
+                               + " + rerank_kernel",
                      "kernel_ms": kern_avg, "bytes_per_query": bytes_q,
                      "bytes_model": "4 D + hops (4 R + 4) + scored x %d + rerank x (D + 8)" %
                                     (-(-(inf["d"] + 8) // 32) * 32),

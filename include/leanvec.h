@@ -393,6 +393,17 @@ typedef struct {
     void *event_begin;       /* optional cudaEvent_t recorded on `stream` right before the */
     void *event_end;         /* beam-search kernel and right after the rerank kernel (or the
                                 beam-search kernel without rerank) (profiling); may be NULL */
+    int32_t queries_per_warp; /* 1: one query per warp (or per team of warps_per_query warps);
+                                2: two queries per warp, one per 16 lanes, with a visited cache of
+                                16-bit tags -- needs LVQ primaries, warps_per_query 1, width <= 2,
+                                width * R <= 128 and n <= 65535 * hash_slots / 4 (the effective
+                                slots: hash_slots is raised to 2 x L rounded up to 32, to a power
+                                of two); 0 = 1.  Results do not depend on it: the same rounds,
+                                beam and answers; the visited cache may forget different ids, so
+                                lv_search_stats.scored may differ.  Both run the same number of
+                                instructions per query; 2 holds 40 queries per SM instead of 24 and
+                                is faster when the index's primaries and graph sit in L2 and the
+                                batch spans several waves, 1 when they stream from DRAM */
 } lv_search_params;
 
 /* Per-query counters (device, m entries) when stats != NULL. */

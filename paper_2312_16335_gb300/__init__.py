@@ -353,13 +353,14 @@ class Index:
                desc: torch.Tensor | None = None, ldo: int | None = None, stats: bool = False,
                projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0,
                out: tuple[torch.Tensor, torch.Tensor] | None = None, events=None, width: int = 1,
-               warps_per_query: int = 0):
+               warps_per_query: int = 0, queries_per_warp: int = 0):
         """Search m queries. desc: optional (m, 4) int32 CUDA tensor of per-query
         (k, L, rerank, max_hops); then k/L are the upper bounds used for capacity.
         events: optional pair of torch.cuda.Event recorded around the search kernels.
         width: beam members expanded per round (1 = classic best-first).
-        warps_per_query: warps sharing one query (1, 2, 4; divides width; 0 = 1); the
-        results do not depend on it."""
+        warps_per_query: warps sharing one query (1, 2, 4; divides width; 0 = 1);
+        queries_per_warp: 1, or 2 (one query per 16 lanes; LVQ primaries, width <= 2,
+        width * R <= 128), 0 = 1.  The results depend on neither."""
         Q = _f32(Q)
         m = Q.shape[0]
         ldo = k if ldo is None else ldo
@@ -371,7 +372,7 @@ class Index:
         st = torch.empty((m, 2), dtype=torch.int32, device=self.device) if stats else None
         ev0, ev1 = (None, None) if events is None else (events[0].cuda_event, events[1].cuda_event)
         prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width,
-                             warps_per_query, ev0, ev1)
+                             warps_per_query, ev0, ev1, queries_per_warp)
         if desc is not None:
             desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None
@@ -383,7 +384,7 @@ class Index:
                     max_hops: int = 0, desc: torch.Tensor | None = None, ldo: int | None = None,
                     out: tuple[torch.Tensor, torch.Tensor] | None = None, batch: int = 0,
                     projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0, width: int = 1,
-                    warps_per_query: int = 0):
+                    warps_per_query: int = 0, queries_per_warp: int = 0):
         """leanvec_search_host: queries Qh (m x D float32) and the results in host memory (use
         pinned tensors, ``.pin_memory()``, for the copies to overlap the searches); searched in
         batches of `batch` rows (0 = one batch), each exactly as ``search`` over those rows.
@@ -398,7 +399,7 @@ class Index:
         else:
             ids, sc = out
         prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width,
-                             warps_per_query, None, None)
+                             warps_per_query, None, None, queries_per_warp)
         if desc is not None:
             desc = desc.to(dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None
@@ -409,7 +410,7 @@ class Index:
     def search_noalloc(self, Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
                        max_hops: int = 0, ldo: int | None = None,
                        out: tuple[torch.Tensor, torch.Tensor] | None = None, projection: int = PREC_FP32,
-                       width: int = 1, desc: torch.Tensor | None = None):
+                       width: int = 1, desc: torch.Tensor | None = None, queries_per_warp: int = 0):
         """leanvec_search_noalloc: the same search for callers that cannot let the
         library allocate device memory; its scratch is a static 16 MiB device array
         shared by all calls on a device (serialise overlapping calls).  The output
@@ -424,7 +425,8 @@ class Index:
             sc = torch.empty((m, ldo), dtype=torch.float32, device=self.device)
         else:
             ids, sc = out
-        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, 0, 0, width, 0, None, None)
+        prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, 0, 0, width, 0, None, None,
+                             queries_per_warp)
         if desc is not None:
             desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None
@@ -436,43 +438,52 @@ class Index:
         return check(lib().leanvec_sync_status(self._h, _stream(self.device)))
 
 
+# warps per block tried for two queries per warp (20 warps, 40 queries per SM at 96 registers)
+HALF_WARPS = (5, 10)
+
+
 def autotune(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, k: int, L: int, rerank: int = 0,
              desc: torch.Tensor | None = None, width: int = 1, projection: int = PREC_FP32,
-             warps=(4, 8), hash_slots=(512, 1024, 2048, 4096), reps: int = 3) -> dict:
-    """Pick the launch shape (warps per block, i.e. queries per CTA) and the visited-cache
-    size for this batch by timing each candidate with CUDA events.  Neither knob changes
-    the result (the visited cache is exact-preserving), only occupancy versus re-scoring."""
+             warps=(4, 8), hash_slots=(512, 1024, 2048, 4096), queries_per_warp=(1, 2), reps: int = 3) -> dict:
+    """Pick the launch shape (queries per warp, warps per block, i.e. queries per CTA) and the
+    visited-cache size for this batch by timing each candidate with CUDA events (two queries per
+    warp with the block sizes of HALF_WARPS, where the index and width allow it).  None of the
+    knobs changes the result (the visited cache is exact-preserving), only occupancy versus
+    re-scoring."""
     best = None
     table = []
     ldo = k
     ids = torch.empty((Q.shape[0], ldo), dtype=torch.int32, device=index.device)
     sc = torch.empty((Q.shape[0], ldo), dtype=torch.float32, device=index.device)
-    for w in warps:
-        for h in hash_slots:
-            if h < 2 * ((L + 31) // 32 * 32):
-                continue
-            try:
-                run = lambda: index.search(Q, A, k=k, L=L, rerank=rerank, desc=desc, ldo=ldo, out=(ids, sc),
-                                           width=width, projection=projection, hash_slots=h, warps_per_block=w)
-                run()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(reps):
+    for qpw in queries_per_warp:
+        for w in (HALF_WARPS if qpw == 2 else warps):
+            for h in hash_slots:
+                if h < 2 * ((L + 31) // 32 * 32):
+                    continue
+                try:
+                    run = lambda: index.search(Q, A, k=k, L=L, rerank=rerank, desc=desc, ldo=ldo, out=(ids, sc),
+                                               width=width, projection=projection, hash_slots=h, warps_per_block=w,
+                                               queries_per_warp=qpw)
                     run()
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
-            except LeanVecError:
-                continue
-            table.append({"warps_per_block": w, "hash_slots": h, "ms": ms})
-            if best is None or ms < best["ms"]:
-                best = table[-1]
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        run()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                except LeanVecError:
+                    continue
+                table.append({"queries_per_warp": qpw, "warps_per_block": w, "hash_slots": h, "ms": ms})
+                if best is None or ms < best["ms"]:
+                    best = table[-1]
     return {"best": best, "table": table}
 
 
 def autotune_uneven(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, desc: torch.Tensor, ldo: int,
                     width: int = 2, projection: int = PREC_FP32, bounds=(64, 128, 192, 256, 320),
-                    teams=(1, 2), hash_slots=(0, 512, 1024, 2048), warps=(4, 8), reps: int = 3) -> dict:
+                    teams=(1, 2), hash_slots=(0, 512, 1024, 2048), warps=(4, 8), queries_per_warp=(1, 2),
+                    reps: int = 3) -> dict:
     """The batching form's autotuner for an uneven batch (per-query k, L, rerank in `desc`).
     Three plans, each a reordering of the batch (done once) followed by one or more launches of
     contiguous slices, all captured in one CUDA graph by UnevenGraph:
@@ -483,9 +494,10 @@ def autotune_uneven(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, des
                     larger L), one launch per class, each with its own beam capacity (its largest
                     L rounded up to 32, which sizes a query's shared memory and so the queries
                     resident per SM).
-    For every launch of every plan the fastest warps per query (`teams`, dividing `width`),
-    visited-cache slots (0 = the library's default) and warps per block are picked by timing the
-    launch alone with CUDA events; the plan with the smallest total wins.  None of the knobs or
+    For every launch of every plan the fastest warps per query (`teams`, dividing `width`), queries
+    per warp (two with one warp per query, where the index allows it, with the block sizes of
+    HALF_WARPS), visited-cache slots (0 = the library's default) and warps per block are picked by
+    timing the launch alone with CUDA events; the plan with the smallest total wins.  None of the knobs or
     plans changes a query's result.  Returns {"plan": name, "order": the permutation (device,
     int64) of the winning plan, "classes": its launches [{slice, L range, queries, k / L / rerank
     maxima, capacity, the chosen knobs, ms, qps}], "plans": {name: total ms}, "table": every timed
@@ -502,17 +514,19 @@ def autotune_uneven(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, des
         dc = ds[sl]
         kmax, Lmax, rmax = (int(dc[:, j].max()) for j in range(3))
         best = None
-        for T in teams:
-            if width % T:
+        shapes = [(T, 1) for T in teams] + [(1, 2)] * (2 in queries_per_warp)
+        for T, qpw in shapes:
+            if width % T or (qpw == 1 and 1 not in queries_per_warp):
                 continue
             for h in hash_slots:
                 if h and h < 2 * ((Lmax + 31) // 32 * 32):
                     continue
-                for w in warps:
+                for w in (HALF_WARPS if qpw == 2 else warps):
                     if w % T:
                         continue
                     kw = dict(k=kmax, L=Lmax, rerank=rmax, desc=dc, ldo=ldo, out=(ids[sl], sc[sl]), width=width,
-                              projection=projection, hash_slots=h, warps_per_block=w, warps_per_query=T)
+                              projection=projection, hash_slots=h, warps_per_block=w, warps_per_query=T,
+                              queries_per_warp=qpw)
                     try:
                         index.search(Qs[sl], A, **kw)
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -524,16 +538,17 @@ def autotune_uneven(index: "Index", Q: torch.Tensor, A: torch.Tensor | None, des
                         ms = e0.elapsed_time(e1) / reps
                     except LeanVecError:
                         continue
-                    row = {"plan": name, "launch": c, "warps_per_query": T, "hash_slots": h, "warps_per_block": w,
-                           "ms": ms}
+                    row = {"plan": name, "launch": c, "warps_per_query": T, "queries_per_warp": qpw,
+                           "hash_slots": h, "warps_per_block": w, "ms": ms}
                     table.append(row)
                     if best is None or ms < best["ms"]:
                         best = row
         n_c = sl.stop - sl.start
         return {"slice": (sl.start, sl.stop), "L_range": (lo, hi), "queries": n_c, "k_max": kmax, "L_max": Lmax,
                 "rerank_max": rmax, "beam_capacity": (Lmax + 31) // 32 * 32,
-                "warps_per_query": best["warps_per_query"], "hash_slots": best["hash_slots"],
-                "warps_per_block": best["warps_per_block"], "ms": best["ms"], "qps": n_c / (best["ms"] / 1e3)}
+                "warps_per_query": best["warps_per_query"], "queries_per_warp": best["queries_per_warp"],
+                "hash_slots": best["hash_slots"], "warps_per_block": best["warps_per_block"], "ms": best["ms"],
+                "qps": n_c / (best["ms"] / 1e3)}
 
     b = torch.tensor(list(bounds), dtype=torch.int64, device=dev)
     cls = torch.clamp(torch.bucketize(Lq, b, right=False), max=len(bounds) - 1)
@@ -587,7 +602,8 @@ class UnevenGraph:
             self.calls.append((sl, dict(k=c["k_max"], L=c["L_max"], rerank=c["rerank_max"], desc=self.ds[sl], ldo=ldo,
                                         out=(self.ids[sl], self.scores[sl]), width=width, projection=projection,
                                         hash_slots=c["hash_slots"], warps_per_block=c["warps_per_block"],
-                                        warps_per_query=c["warps_per_query"])))
+                                        warps_per_query=c["warps_per_query"],
+                                        queries_per_warp=c.get("queries_per_warp", 1))))
         s = torch.cuda.Stream(device=dev)
         s.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(s):

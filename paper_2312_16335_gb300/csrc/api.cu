@@ -97,6 +97,69 @@ int ensure_ws(void **p, size_t *have, size_t want) {
 
 int *index_status(lv_index *idx) { return idx->status; }
 int index_num_sms(lv_index *idx) { return idx->num_sms; }
+
+static int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int search_shape(const lv_index *idx, const lv_search_params *params, BeamParams &p, int *block, size_t *smem,
+                 const char *who) {
+    const std::string w(who);
+    const lv_query_desc &u = params->uniform;
+    p.Lcap = (int)round_up(u.L, 32);
+    int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(4 * u.L)));
+    if (hs & (hs - 1)) return fail(LV_ERR_ARG, w + ": hash_slots must be a power of two");
+    hs = std::max(hs, next_pow2(2 * p.Lcap));
+    p.Hcap = hs;
+    p.hbits = 0;
+    while ((1 << p.hbits) < hs) p.hbits++;
+    p.W = params->width > 0 ? params->width : 1;
+    if (p.W > WMAX || p.W * idx->R > CMAX) return fail(LV_ERR_ARG, w + ": need width <= 4 and width * R <= 256");
+    p.T = params->warps_per_query > 0 ? params->warps_per_query : 1;
+    if ((p.T != 1 && p.T != 2 && p.T != 4) || p.W % p.T)
+        return fail(LV_ERR_ARG, w + ": warps_per_query must be 1, 2 or 4 and divide width");
+    const int qpw = params->queries_per_warp;
+    if (qpw < 0 || qpw > 2) return fail(LV_ERR_ARG, w + ": queries_per_warp must be 0, 1 or 2");
+    const bool half_ok = idx->pbits != 32 && p.T == 1 && p.W <= 2 && p.W * idx->R <= 16 * HALF_IDS &&
+                         half_tags_fit(idx->n, hs);
+    if (qpw == 2 && !half_ok)
+        return fail(LV_ERR_ARG, w + ": two queries per warp need LVQ primaries, warps_per_query 1, width <= 2, "
+                                    "width * R <= 128 and n <= 65535 * hash_slots / 4");
+    p.qpw = qpw == 2 ? 2 : 1;
+    const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
+    const int qbytes = lvq_query_bytes(idx->pbits, nc_q);
+    int warps = params->warps_per_block;
+    if (warps > 32) return fail(LV_ERR_ARG, w + ": warps_per_block must be <= 32");
+    if (p.qpw == 2) {
+        p.Rcap = half_rcap(p.W, idx->R);
+        p.warp_smem = half_query_smem(p.Lcap, p.Hcap, p.Rcap, qbytes);
+        if (warps <= 0) warps = 10;
+        while (warps > 1 && (size_t)2 * warps * p.warp_smem > 227 * 1024) warps >>= 1;
+        *smem = (size_t)2 * warps * p.warp_smem;
+    } else {
+        p.Rcap = beam_rcap(p.W, p.T, idx->R);
+        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, qbytes);
+        if (warps <= 0) warps = 8;
+        if (warps % p.T) return fail(LV_ERR_ARG, w + ": warps_per_block must be a multiple of warps_per_query");
+        while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
+        *smem = (size_t)(warps / p.T) * p.warp_smem;
+    }
+    if (*smem > 227 * 1024) return fail(LV_ERR_CAPACITY, w + ": L / hash_slots too large for shared memory");
+    *block = warps * 32;
+    return LV_OK;
+}
+
+int launch_beam_search(const lv_index *idx, const BeamParams &p, int block, size_t smem, cudaStream_t st) {
+    if (idx->pbits == 32) return launch_search_fp32(p, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, st);
+    const int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;  // codes + constants chunks over 4 lanes
+    if (p.qpw == 2)
+        return idx->pbits == 8 ? launch_search_half8(p, nc, block, smem, idx->num_sms, st)
+                               : launch_search_half4(p, nc, block, smem, idx->num_sms, st);
+    return idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
+                           : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
+}
 }  // namespace lv
 
 extern "C" {
@@ -465,12 +528,6 @@ int leanvec_build_graph(lv_index *idx, int R, int L_build, float alpha, int pass
     return build_graph_impl(idx, R, L_build, alpha, passes, batch, seed, prune_rule, (cudaStream_t)stream);
 }
 
-static int next_pow2(int x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
 int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, const lv_search_params *params,
                    const lv_query_desc *desc, int32_t *ids, float *scores, int ldo, lv_search_stats *stats,
                    lv_stream_t stream) {
@@ -546,25 +603,10 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
     p.status = idx->status;
     p.work = idx->status + 1;
     p.slots = nullptr;
-    p.Lcap = (int)round_up(u.L, 32);
-    int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(4 * u.L)));
-    if (hs & (hs - 1)) return fail(LV_ERR_ARG, "search: hash_slots must be a power of two");
-    hs = std::max(hs, next_pow2(2 * p.Lcap));
-    p.Hcap = hs;
-    p.hbits = 0;
-    while ((1 << p.hbits) < hs) p.hbits++;
-    p.W = params->width > 0 ? params->width : 1;
-    if (p.W > WMAX || p.W * idx->R > CMAX) return fail(LV_ERR_ARG, "search: need width <= 4 and width * R <= 256");
-    p.T = params->warps_per_query > 0 ? params->warps_per_query : 1;
-    if ((p.T != 1 && p.T != 2 && p.T != 4) || p.W % p.T)
-        return fail(LV_ERR_ARG, "search: warps_per_query must be 1, 2 or 4 and divide width");
-    p.Rcap = beam_rcap(p.W, p.T, idx->R);
-    const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
-    p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
-    int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
-    if (warps % p.T || warps > 32) return fail(LV_ERR_ARG, "search: warps_per_block must be <= 32 and a multiple of warps_per_query");
-    while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
-    if ((size_t)(warps / p.T) * p.warp_smem > 227 * 1024) return fail(LV_ERR_CAPACITY, "search: L / hash_slots too large for shared memory");
+    int block = 0;
+    size_t smem = 0;
+    rc = search_shape(idx, params, p, &block, &smem, "search");
+    if (rc) return rc;
     if (idx->sbits == 8 && idx->sg.code_chunks + 1 + idx->metric > 64)
         return fail(LV_ERR_ARG, "search: D > 1008 (992 with L2) is not supported by the rerank");
     if (idx->sbits == 16 && idx->sg.code_chunks > 128) return fail(LV_ERR_ARG, "search: D > 1024 is not supported by the FP16 rerank");
@@ -577,14 +619,7 @@ int leanvec_search(lv_index *idx, const float *Q, int64_t m, const float *A, con
         p.cand_n = idx->ws_cand + (size_t)m * p.ldc;
     }
     LV_CUDA(cudaMemsetAsync(p.work, 0, 2 * sizeof(int), st));  // the work counters of both sub-batches
-    const size_t smem = (size_t)(warps / p.T) * p.warp_smem;
-    const int block = warps * 32;
-    auto beam = [&](const BeamParams &q, cudaStream_t s) -> int {
-        if (idx->pbits == 32) return launch_search_fp32(q, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, s);
-        const int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;  // codes + constants chunks over 4 lanes
-        return idx->pbits == 8 ? launch_search_lvq8(q, nc, block, smem, idx->num_sms, s)
-                               : launch_search_lvq4(q, nc, block, smem, idx->num_sms, s);
-    };
+    auto beam = [&](const BeamParams &q, cudaStream_t s) -> int { return launch_beam_search(idx, q, block, smem, s); };
     // Sub-batches: with rerank and m above one wave of resident query slots (slots = blocks per SM
     // x SMs x queries per block) and not a multiple of it, the first batch takes the whole waves
     // but the last 10 % of the last one, the rest forms a second batch launched on a second stream:

@@ -66,7 +66,8 @@ struct BeamParams {
     int Rcap;   // candidate buffer capacity (multiple of 32, >= W * R)
     int W;      // search width: parents expanded per round (1..4, W * R <= 256)
     int T;      // warps per query (1, 2 or 4; divides W); Rcap = T * (W / T * R rounded up to 32)
-    int warp_smem;  // shared bytes of one query (one team of T warps)
+    int warp_smem;  // shared bytes of one query (one team of T warps, or one half warp)
+    int qpw;        // queries per warp: 1 (beam_kernel) or 2 (beam_half_kernel, beam_half.cuh)
     int64_t *slots;  // host side: when set, the search launchers report the query slots one
                      // launch keeps resident (blocks per SM x SMs x teams per block) and launch nothing
 };
@@ -83,6 +84,22 @@ inline int beam_warp_smem(int Lcap, int Hcap, int Rcap, int qbytes) {
 inline int beam_rcap(int W, int T, int R) { return T * ((W / T * R + 31) / 32 * 32); }
 // shared bytes of the LVQ scorer's query limbs (nc chunks per lane, see LvqIntScorer)
 inline int lvq_query_bytes(int bits, int nc) { return bits == 32 ? 0 : 4 * nc * 3 * (bits == 8 ? 1 : 2) * 16; }
+
+// Two queries per warp (beam_half.cuh).  Shared bytes of one query: beam (8 Lcap), visited cache
+// of 16-bit tags (2 Hcap), candidate ids, scores and beam positions (12 Rcap), positions by rank
+// (2 Rcap), the scorer's query
+constexpr int HALF_IDS = 8;  // adjacency ids one lane gathers per round: width * R <= 16 * 8
+inline int half_query_smem(int Lcap, int Hcap, int Rcap, int qbytes) {
+    return 8 * Lcap + 2 * Hcap + 14 * Rcap + qbytes;
+}
+// candidate capacity: the round's width * R ids, rounded up to 16 (keeps the layout 16-byte aligned)
+inline int half_rcap(int W, int R) { return (W * R + 15) / 16 * 16; }
+// the 16-bit tags of a visited cache of hcap slots (hcap / 4 buckets) name every id below n
+inline bool half_tags_fit(int64_t n, int hcap) {
+    int b = 0;
+    while ((4 << b) < hcap) ++b;
+    return hcap >= 64 && n >= 1 && ((n - 1) >> b) < 0xFFFF;
+}
 
 // --------------------------------------------------------------------------------
 // Primary scorer with an integer query: q' is held as 24-bit fixed point
@@ -961,9 +978,20 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
 int launch_search_lvq8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_search_lvq4(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_search_fp32(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st);
+// two queries per warp: LVQ-8 primaries with nc = 1..4 chunks per lane, LVQ-4 with 1..3
+int launch_search_half8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
+int launch_search_half4(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_build_search(const BeamParams &p, int bits, int nc, int block, size_t smem, int num_sms,
                         cudaStream_t st);
 // scores the candidates the RERANK beam kernel handed over (p.cand, p.cand_n) and writes p.ids / p.scores
 int launch_rerank(const BeamParams &p, int num_sms, cudaStream_t st);
+
+// The search's launch shape (api.cu): beam / visited-cache / candidate capacities, width, warps and
+// queries per warp (p.Lcap .. p.qpw) from the index and the caller's parameters, the block size and
+// the dynamic shared memory.  `who` prefixes the error messages.
+int search_shape(const lv_index *idx, const lv_search_params *params, BeamParams &p, int *block, size_t *smem,
+                 const char *who);
+// launches the beam kernel that fits the index's stores and p.qpw
+int launch_beam_search(const lv_index *idx, const BeamParams &p, int block, size_t smem, cudaStream_t st);
 
 }  // namespace lv

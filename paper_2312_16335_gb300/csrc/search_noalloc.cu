@@ -147,44 +147,10 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
         p.stats = reinterpret_cast<int2 *>(stats);
         p.status = idx->status;
         p.work = work;
-        p.Lcap = (int)round_up(u.L, 32);
-        int hs = 1024;
-        if (params->hash_slots > 0) {
-            hs = params->hash_slots;
-        } else {
-            while (hs < 4 * u.L && hs < 8192) hs <<= 1;
-        }
-        if (hs & (hs - 1)) {
-            rc = fail(LV_ERR_ARG, "search_noalloc: hash_slots must be a power of two");
-            break;
-        }
-        while (hs < 2 * p.Lcap) hs <<= 1;
-        p.Hcap = hs;
-        p.hbits = 0;
-        while ((1 << p.hbits) < hs) p.hbits++;
-        p.W = params->width > 0 ? params->width : 1;
-        if (p.W > WMAX || p.W * idx->R > CMAX) {
-            rc = fail(LV_ERR_ARG, "search_noalloc: need width <= 4 and width * R <= 256");
-            break;
-        }
-        p.T = params->warps_per_query > 0 ? params->warps_per_query : 1;
-        if ((p.T != 1 && p.T != 2 && p.T != 4) || p.W % p.T) {
-            rc = fail(LV_ERR_ARG, "search_noalloc: warps_per_query must be 1, 2 or 4 and divide width");
-            break;
-        }
-        p.Rcap = beam_rcap(p.W, p.T, idx->R);
-        const int nc_q = idx->pbits == 32 ? 0 : (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
-        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, lvq_query_bytes(idx->pbits, nc_q));
-        int warps = params->warps_per_block > 0 ? params->warps_per_block : 8;
-        if (warps % p.T || warps > 32) {
-            rc = fail(LV_ERR_ARG, "search_noalloc: warps_per_block must be <= 32 and a multiple of warps_per_query");
-            break;
-        }
-        while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;
-        if ((size_t)(warps / p.T) * p.warp_smem > 227 * 1024) {
-            rc = fail(LV_ERR_CAPACITY, "search_noalloc: L / hash_slots too large for shared memory");
-            break;
-        }
+        int block = 0;
+        size_t smem = 0;
+        rc = search_shape(idx, params, p, &block, &smem, "search_noalloc");
+        if (rc) break;
         if (rerank) {
             p.ldc = p.Lcap;
             p.cand = cand;
@@ -196,20 +162,12 @@ extern "C" int leanvec_search_noalloc(lv_index *idx, const float *Q, int64_t m, 
             rc = cuda_fail(e, "search_noalloc: cudaMemsetAsync");
             break;
         }
-        const size_t smem = (size_t)(warps / p.T) * p.warp_smem;
-        const int block = warps * 32;
         if (params->event_begin && (e = cudaEventRecord((cudaEvent_t)params->event_begin, st)) != cudaSuccess) {
             rc = cuda_fail(e, "search_noalloc: cudaEventRecord(event_begin)");
             break;
         }
-        if (idx->pbits == 32) {
-            rc = launch_search_fp32(p, (idx->pg.code_chunks + 31) / 32, block, smem, idx->num_sms, st);
-        } else {
-            const int nc = (idx->pg.code_chunks + 1 + idx->metric + 3) / 4;
-            rc = idx->pbits == 8 ? launch_search_lvq8(p, nc, block, smem, idx->num_sms, st)
-                                 : launch_search_lvq4(p, nc, block, smem, idx->num_sms, st);
-            if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
-        }
+        rc = launch_beam_search(idx, p, block, smem, st);
+        if (!rc && rerank) rc = launch_rerank(p, idx->num_sms, st);
         if (rc) break;
         if (params->event_end && (e = cudaEventRecord((cudaEvent_t)params->event_end, st)) != cudaSuccess) {
             rc = cuda_fail(e, "search_noalloc: cudaEventRecord(event_end)");

@@ -268,7 +268,8 @@ def test_argument_errors(lv, pb):
 
 def test_cuda_graph_replay_and_autotune(lv, pb):
     """Batching form: an uneven batch captured once in a CUDA graph and replayed gives the
-    eager result; the autotuner's choice (launch shape, visited cache) does not change it."""
+    eager result; the autotuner's choice (queries per warp, launch shape, visited cache) does not
+    change it."""
     idx = gpu_index(lv, pb)
     m = pb["Q"].shape[0]
     rng = np.random.default_rng(11)
@@ -280,7 +281,8 @@ def test_cuda_graph_replay_and_autotune(lv, pb):
     tune = lv.autotune(idx, Q, P, k=10, L=96, rerank=96, desc=desc)
     assert tune["best"] is not None and len(tune["table"]) >= 2
     g = lv.SearchGraph(idx, Q, P, k=10, L=96, rerank=96, desc=desc, hash_slots=tune["best"]["hash_slots"],
-                       warps_per_block=tune["best"]["warps_per_block"])
+                       warps_per_block=tune["best"]["warps_per_block"],
+                       queries_per_warp=tune["best"]["queries_per_warp"])
     for _ in range(3):
         ids, sc = g.replay()
         torch.cuda.synchronize()
