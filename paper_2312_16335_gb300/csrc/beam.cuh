@@ -130,6 +130,11 @@ struct LvqIntScorer {
     // The limbs live in the warp's shared memory, chunk c at lq[(3 c + limb) V4 ..], limb 0 = h,
     // 1 = m, 2 = l, for the 4 NC chunks a group of 4 lanes covers (chunks >= CH are zero).
     static constexpr int QBYTES = 4 * NC * 3 * V4 * 16;
+    // the 128-byte lines holding a record's first and last byte are prefetched into L2 as soon as the
+    // visited test admits its id, so that the scorer's passes after the first one find the record
+    // there (all of it when it spans at most two lines, as the 192-byte records of d = 160 do)
+    static constexpr bool PREFETCH = true;
+    __device__ __forceinline__ int rec_bytes() const { return 16 * (CH + 1 + (L2 ? 1 : 0)); }
     const uint4 *lq;
     float cq, sq, scale;
     int CH;
@@ -314,6 +319,7 @@ struct BuildScorer {
     int64_t stride;
 
     static constexpr int QBYTES = 0;
+    static constexpr bool PREFETCH = false;
     __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *, bool) {
         CH = p.prim_chunks;
         base = p.prim;
@@ -402,6 +408,7 @@ struct BuildScorer {
 template <int BITS, bool L2 = false>
 struct BuildWarpScorer {
     static constexpr int QBYTES = 0;
+    static constexpr bool PREFETCH = false;
     static constexpr int U = 4;
     uint4 qc[2];
     float qd, ql, qG, qH, qN, mu2, fdim;
@@ -500,6 +507,7 @@ struct WarpScorer {
     }
 
     static constexpr int QBYTES = 0;
+    static constexpr bool PREFETCH = false;
     __device__ __forceinline__ void setup(const BeamParams &p, int64_t qi, int lane, void *, bool) {
         // full-dimensional float32 search: padded queries, no constants
         setup_row(p.qp + qi * p.ldq, p.ldq, p.prim_chunks, p.prim, p.prim_stride, 0.f, 0.f, lane);
@@ -727,7 +735,14 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (isnew[h]) hash[slot[h]] = u[h];
+                    if (isnew[h]) {
+                        hash[slot[h]] = u[h];
+                        if constexpr (PS::PREFETCH) {
+                            const uint8_t *rec = ps.base + (int64_t)u[h] * ps.stride;
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(rec));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(rec + ps.rec_bytes() - 1));
+                        }
+                    }
                     const unsigned bal = __ballot_sync(FULL, isnew[h]);
                     if (isnew[h]) wI[cnt + __popc(bal & lt)] = u[h];
                     cnt += __popc(bal);
