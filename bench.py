@@ -81,6 +81,11 @@ TRAFFIC_RECORDS = [
     {"src_sha1": "adabdf5c923b6df5930577829fe01484d40bee83", "n": 1_000_000, "m": 10_000, "L": 140, "max_hops": 84,
      "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
      "bytes": 2505062656},
+    # records prefetched into L2 at the visited test, L = 152, max_hops = 76: beam 0.865 + 0.366 GB
+    # read, rerank 0.778 + 0.344 GB read, 6.8 MB written (mean of the two profiled searches)
+    {"src_sha1": "9c0aada7abc74f8df81a778ce8e0f6cdc14a6801", "n": 1_000_000, "m": 10_000, "L": 152, "max_hops": 76,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
+     "bytes": 2361016064},
 ]
 
 
