@@ -1196,11 +1196,14 @@ def bench_kernels(args, dev):
     n, D, d = args.n, args.D, args.d
     X, Q, Ql = workloads.make_workload_torch("anisotropic", n, args.m, D, args.components, cfg=2, device=dev)
     torch.cuda.synchronize()
-    # a13: second moments K = sum x x^T (bf16 operands, tcgen05, FP32 accumulation)
+    # a13: second moments K = sum x x^T (bf16 operands, tcgen05, FP32 accumulation); K is symmetric,
+    # so the algorithmic flops are 2 n per distinct entry: n D (D + 1)
     for ns in (100_000, n):
         Xs = X[:ns]
         t = timed(lambda: lv.leanvec_second_moment(Xs, precision=lv.PREC_BF16), 5)
-        tensor_row(f"second_moment_bf16_{ns // 1000}k_x_{D}", 2.0 * ns * D * D, t, bf16, src)
+        tensor_row(f"second_moment_bf16_{ns // 1000}k_x_{D}", float(ns) * D * (D + 1), t, bf16, src)
+        res[f"second_moment_bf16_{ns // 1000}k_x_{D}"]["hbm_frac"] = 4.0 * ns * D / t / 1e9 / hbm
+        res[f"second_moment_bf16_{ns // 1000}k_x_{D}"]["tflops_as_full_product"] = 2.0 * ns * D * D / t / 1e12
     t = timed(lambda: lv.leanvec_second_moment(X[:100_000], precision=lv.PREC_FP32), 3)
     res[f"second_moment_fp32_100k_x_{D}"] = {"seconds": t, "tflops": 2.0 * 100_000 * D * D / t / 1e12,
                                              "bound": "fp32 CUDA cores", "peak_tflops_nominal": fp32_cc}

@@ -2112,7 +2112,344 @@ int project_fp8(const float *X, int64_t n, int D, const float *P, int d, float *
 }
 
 // K (D x D) = X^T X over the n rows of X with bf16 operands (X^T staged in bf16).
+// ---------------------------------------------------------------------------------------------
+// Second moment K = X^T X (Sec. 2.2 "Efficiency") with the float32 rows of X rounded to bf16
+// inside the GEMM (bf16 products, float32 accumulation -- the operand rounding of the bf16 path
+// through a converted copy of X, without the copy).  K is symmetric: only the 256 x 256 tiles on or
+// above the diagonal are computed (two M = 128 halves in two TMEM accumulators of 256 columns),
+// each over a range of 64-row blocks of X (split-K); gram_reduce_kernel sums the ranges in a fixed
+// order and writes both triangles, so K is exactly symmetric.  One work item (tile, range) per CTA.
+//   warps 0-3  : epilogue: their TMEM lane quarter of both halves -> a column-major partial tile
+//                (each store instruction writes 32 consecutive rows of one column)
+//   warps 4-11 : converters.  A block of 64 rows arrives as four pieces of 16 rows x 256 float32
+//                columns of the tile's row range (A) and column range (B; the same data on the
+//                diagonal).  Thread (op, kql, mg) reads rows 8 kql .. 8 kql + 7 of a piece at
+//                columns 4 mg .. 4 mg + 3 (16-byte shared loads; eight consecutive threads read one
+//                row's consecutive chunks) and writes each column's eight values as one 16-byte
+//                bf16 K chunk of a 128-byte-swizzled K-major operand row (the stores meet four-way
+//                bank conflicts, which cost less than the selects of a conflict-free store order).
+//                Shared-memory traffic per 64-row block (off the diagonal): 128 KB of float32 in by
+//                TMA and out to the converters, 64 KB of bf16 operands in, 96 KB read by the MMAs,
+//                about 3250 cycles at 128 B / clock against 1170 cycles of MMAs: this kernel is
+//                bound by shared-memory bandwidth
+//   warp 12    : lane 0 moves the pieces from global memory by TMA into a 3-slot ring
+//   warp 13    : TMEM allocation; lane 0 issues tcgen05.mma (M 128, N 256, K 16, both halves) per
+//                block and commits each operand stage back to the converters
+// Two 64 KB operand stages and three 32 KB pieces: 224 KB of shared memory.  Every wait is
+// bounded as in gemm_tc_kernel.
+constexpr int GR_TILE = 256, GR_OSTAGES = 2, GR_SLOTS = 3, GR_CONV_WARPS = 8;
+constexpr int GR_THREADS = 32 * (4 + GR_CONV_WARPS + 2);
+constexpr uint32_t GR_OP_BYTES = GR_TILE * 128;     // one bf16 operand of a stage: 256 rows x 64
+constexpr uint32_t GR_STAGE_BYTES = 2 * GR_OP_BYTES;
+constexpr uint32_t GR_PIECE_OP = 16 * GR_TILE * 4;  // one operand's float32 piece: 16 rows x 256
+constexpr uint32_t GR_SLOT_BYTES = 2 * GR_PIECE_OP;
+
+struct GrParams {
+    int64_t n;
+    int D, nb, tiles, kbps, nkb;  // nb column blocks of 256, tiles = nb (nb + 1) / 2
+    int boxw;                     // float32 columns per TMA row (min(256, D)); row pitch 4 boxw bytes
+    float *partial;               // [range][tile][half][column 256][row 128]
+    int *status;
+};
+
+// upper-triangle tile t (row-major over bi <= bj) -> block row bi, block column bj
+__host__ __device__ __forceinline__ void gram_tile(int t, int nb, int &bi, int &bj) {
+    bi = 0;
+    while (t >= nb - bi) {
+        t -= nb - bi;
+        ++bi;
+    }
+    bj = bi + t;
+}
+
+__device__ __forceinline__ float f4c(const float4 &v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+
+__global__ void __launch_bounds__(GR_THREADS, 1)
+    gram_f32in_kernel(const __grid_constant__ CUtensorMap tx, const GrParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *slots = base + GR_OSTAGES * GR_STAGE_BYTES;
+    uint64_t *ofull = reinterpret_cast<uint64_t *>(slots + GR_SLOTS * GR_SLOT_BYTES);
+    uint64_t *oempty = ofull + GR_OSTAGES;
+    uint64_t *sfull = oempty + GR_OSTAGES;
+    uint64_t *sempty = sfull + GR_SLOTS;
+    uint64_t *tfull = sempty + GR_SLOTS;
+    uint64_t *drain = tfull + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = (int)blockIdx.x % p.tiles, range = (int)blockIdx.x / p.tiles;
+    int bi, bj;
+    gram_tile(t, p.nb, bi, bj);
+    const bool diag = bi == bj;
+    const int kb0 = range * p.kbps, nq = min(p.nkb, kb0 + p.kbps) - kb0;  // >= 1 block
+    const int npieces = 4 * nq;
+    const int conv = 32 * GR_CONV_WARPS;
+    const int W_PROD = 4 + GR_CONV_WARPS, W_MMA = W_PROD + 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GR_OSTAGES; ++s) {
+            mbar_init(ofull + s, conv);
+            mbar_init(oempty + s, 1);
+        }
+        for (int z = 0; z < GR_SLOTS; ++z) {
+            mbar_init(sfull + z, 1);
+            mbar_init(sempty + z, conv);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == W_MMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == W_PROD) {
+        // ---- TMA producer: piece g = 4 q + pc holds rows 64 (kb0 + q) + 16 pc .. + 15
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(diag ? 1 : 2) * 16 * p.boxw * 4;
+            for (int g = 0; g < npieces; ++g) {
+                const int z = g % GR_SLOTS, w = g / GR_SLOTS;
+                if (w > 0 && !mbar_wait(sempty + z, (uint32_t)((w - 1) & 1))) {
+                    *abort_flag = 1;
+                    atomicOr(p.status, ST_TIMEOUT);
+                }
+                if (*abort_flag) {
+                    // drain: the copies already started must land before the CTA exits
+                    for (int h = max(0, g - GR_SLOTS); h < g; ++h)
+                        mbar_wait(sfull + h % GR_SLOTS, (uint32_t)((h / GR_SLOTS) & 1));
+                    break;
+                }
+                const int row = (kb0 + (g >> 2)) * 64 + 16 * (g & 3);
+                uint8_t *dst = slots + (size_t)z * GR_SLOT_BYTES;
+                mbar_expect_tx(sfull + z, bytes);
+                tma_load_2d(dst, &tx, GR_TILE * bi, row, sfull + z);
+                if (!diag) tma_load_2d(dst + GR_PIECE_OP, &tx, GR_TILE * bj, row, sfull + z);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4 && warp < W_PROD) {
+        // ---- converters
+        const int ct = threadIdx.x - 128;
+        const int mg = ct & 63, kql = (ct >> 6) & 1, op = ct >> 7;
+        const bool active = (op == 0 || !diag) && 4 * mg < p.boxw;
+        const int pitch = 4 * p.boxw;
+        for (int q = 0; q < nq; ++q) {
+            const int s = q % GR_OSTAGES;
+            uint8_t *dst = base + (size_t)s * GR_STAGE_BYTES + op * GR_OP_BYTES;
+            bool ok = !*abort_flag;
+            for (int pc = 0; pc < 4 && ok; ++pc) {
+                const int g = 4 * q + pc, z = g % GR_SLOTS;
+                if (!mbar_wait(sfull + z, (uint32_t)((g / GR_SLOTS) & 1))) {
+                    ok = false;
+                    break;
+                }
+                float4 v[8];
+                if (active) {
+                    const uint8_t *src = slots + (size_t)z * GR_SLOT_BYTES + op * GR_PIECE_OP + 16 * mg;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        v[i] = *reinterpret_cast<const float4 *>(src + (8 * kql + i) * pitch);
+                }
+                mbar_arrive(sempty + z);  // the piece is in registers
+                if (pc == 0 && q >= GR_OSTAGES && !mbar_wait(oempty + s, (uint32_t)((q / GR_OSTAGES - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                if (active) {
+                    const int kq = 2 * pc + kql;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int row = 4 * mg + j;
+                        uint4 o;
+                        o.x = pack_bf16x2(f4c(v[0], j), f4c(v[1], j));
+                        o.y = pack_bf16x2(f4c(v[2], j), f4c(v[3], j));
+                        o.z = pack_bf16x2(f4c(v[4], j), f4c(v[5], j));
+                        o.w = pack_bf16x2(f4c(v[6], j), f4c(v[7], j));
+                        *reinterpret_cast<uint4 *>(dst + (row >> 3) * 1024 + (row & 7) * 128 + ((kq ^ (row & 7)) << 4)) = o;
+                    }
+                }
+            }
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(ofull + s);
+        }
+    } else if (warp == W_MMA) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tc<0>(TC_BM, GR_TILE);
+            bool ok = true;
+            for (int q = 0; q < nq; ++q) {
+                const int s = q % GR_OSTAGES;
+                if (!mbar_wait(ofull + s, (uint32_t)((q / GR_OSTAGES) & 1)) || *abort_flag) {
+                    *abort_flag = 1;
+                    atomicOr(p.status, ST_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint8_t *sa = base + (size_t)s * GR_STAGE_BYTES;
+                uint8_t *sb = diag ? sa : sa + GR_OP_BYTES;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t ad = sdesc(sa + h * (GR_OP_BYTES / 2) + 32 * k);
+                        const uint64_t bd = sdesc(sb + 32 * k);
+                        const uint32_t acc = (q > 0 || k > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\t"
+                            "setp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(h * 256)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(oempty + s))
+                             : "memory");
+            }
+            if (ok)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(tfull))
+                             : "memory");
+            // every MMA this thread issued has completed once `drain` flips
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(drain))
+                         : "memory");
+            if (!mbar_wait(drain, 0)) atomicOr(p.status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: TMEM lanes 32 warp .. of both halves -> partial[range][t][half][column][row]
+        if (!*abort_flag && mbar_wait(tfull, 0)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float *out = p.partial + ((int64_t)range * p.tiles + t) * 2 * GR_TILE * 128;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+                for (int c0 = 0; c0 < GR_TILE; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 256 + c0), r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        out[((int64_t)h * GR_TILE + c0 + j) * 128 + warp * 32 + lane] = __uint_as_float(r[j]);
+                }
+            }
+        } else {
+            *abort_flag = 1;
+            atomicOr(p.status, ST_TIMEOUT);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == W_MMA)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// K from the partial tiles: a block sums one 32 x 32 piece of a tile over the ranges (fixed order),
+// writes it transposed (K[j][i], coalesced along i) and, off the diagonal, as is through a shared
+// slab (K[i][j], coalesced along j); on a diagonal tile only the pairs i <= j are used, so that
+// K[i][j] and K[j][i] are the same float.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const float *__restrict__ part, int ranges, int tiles,
+                                                          int nb, int D, float *__restrict__ K) {
+    __shared__ float sm[32][33];
+    const int t = blockIdx.y;
+    int bi, bj;
+    gram_tile(t, nb, bi, bj);
+    const int R0 = (int)(blockIdx.x >> 3) * 32, C0 = (int)(blockIdx.x & 7) * 32;
+    if (bi == bj && R0 > C0) return;  // the mirror block writes these
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int row = R0 + tx, h = row >> 7, rr = row & 127;
+    const int64_t I = (int64_t)GR_TILE * bi + row;
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int col = C0 + cc;
+        float acc = 0.f;
+        for (int s = 0; s < ranges; ++s)
+            acc += part[((((int64_t)s * tiles + t) * 2 + h) * GR_TILE + col) * 128 + rr];
+        const int64_t J = (int64_t)GR_TILE * bj + col;
+        if (I < D && J < D && (bi < bj || row <= col)) K[J * D + I] = acc;
+        sm[cc][tx] = acc;
+    }
+    __syncthreads();
+    for (int a = ty; a < 32; a += 8) {
+        const int64_t I2 = (int64_t)GR_TILE * bi + R0 + a, J2 = (int64_t)GR_TILE * bj + C0 + tx;
+        if (I2 < D && J2 < D && (bi < bj || R0 + a < C0 + tx)) K[I2 * D + J2] = sm[tx][a];
+    }
+}
+
+// the float32-input second moment applies: 16-byte aligned rows (D % 4 == 0), at least one 64-row
+// block (the TMA box's 16 rows and min(256, D) columns lie inside X)
+static bool gram_fused_ok(const float *X, int64_t n, int D) {
+    return D % 4 == 0 && ((uintptr_t)X & 15) == 0 && n >= 64 && (n + 63) / 64 < ((int64_t)1 << 31);
+}
+
+static int second_moment_f32in(const float *X, int64_t n, int D, float *K, int *status, cudaStream_t st) {
+    const int nb = (D + GR_TILE - 1) / GR_TILE, tiles = nb * (nb + 1) / 2;
+    const int nkb = (int)((n + 63) / 64);
+    const int boxw = std::min(GR_TILE, D);
+    CUtensorMap tx;
+    {
+        // X as float32 pieces of 16 rows x boxw columns (no swizzle); rows >= n and columns >= D
+        // read as zeros
+        auto fn = encode_fn();
+        if (!fn) return fail(LV_ERR_CUDA, "second_moment: cuTensorMapEncodeTiled unavailable");
+        cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)n};
+        cuuint64_t strides[1] = {(cuuint64_t)D * 4};
+        cuuint32_t box[2] = {(cuuint32_t)boxw, 16};
+        cuuint32_t es[2] = {1, 1};
+        if (fn(&tx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fail(LV_ERR_CUDA, "second_moment: cuTensorMapEncodeTiled failed for the float32 rows");
+    }
+    int ranges = std::max(1, std::min(nkb, std::max(1, sm_count()) / tiles));
+    const int kbps = (nkb + ranges - 1) / ranges;
+    ranges = (nkb + kbps - 1) / kbps;
+    float *part = nullptr;
+    if (tmp_alloc((void **)&part, sizeof(float) * (size_t)ranges * tiles * 2 * GR_TILE * 128, st))
+        return fail(LV_ERR_OOM, "second_moment: allocation failed");
+    GrParams p;
+    p.n = n;
+    p.D = D;
+    p.nb = nb;
+    p.tiles = tiles;
+    p.kbps = kbps;
+    p.nkb = nkb;
+    p.boxw = boxw;
+    p.partial = part;
+    p.status = status;
+    const size_t sm = (size_t)GR_OSTAGES * GR_STAGE_BYTES + (size_t)GR_SLOTS * GR_SLOT_BYTES + 256 + 1024;
+    int rc = LV_OK;
+    if (cudaFuncSetAttribute(gram_f32in_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        rc = fail(LV_ERR_CUDA, "second_moment: shared-memory attribute failed");
+    if (rc == LV_OK) {
+        gram_f32in_kernel<<<(unsigned)(ranges * tiles), GR_THREADS, sm, st>>>(tx, p);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(LV_ERR_CUDA, "second_moment: gram_f32in_kernel launch failed");
+    }
+    if (rc == LV_OK) {
+        gram_reduce_kernel<<<dim3(64, (unsigned)tiles), dim3(32, 8), 0, st>>>(part, ranges, tiles, nb, D, K);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(LV_ERR_CUDA, "second_moment: gram_reduce_kernel launch failed");
+    }
+    tmp_free(part, st);
+    return rc;
+}
+
 int second_moment_bf16(const float *X, int64_t n, int D, float *K, int *status, cudaStream_t st) {
+    if (gram_fused_ok(X, n, D)) return second_moment_f32in(X, n, D, K, status, st);
+    // otherwise through a transposed bf16 copy of X and the general GEMM
     const int64_t ldt = round_up(n, 8);
     const int tiles = (int)(((D + TC_BM - 1) / TC_BM) * ((D + 255) / 256));
     const int splits = std::max(1, std::min(64, 148 / std::max(1, tiles)));

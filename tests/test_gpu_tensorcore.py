@@ -52,8 +52,8 @@ def test_projection_bf16(lv, n, D, d, ldy):
 
 @pytest.mark.parametrize("n,D", [(1000, 64), (20000, 768), (3001, 200), (3001, 100), (517, 77)])
 def test_second_moment_bf16(lv, n, D):
-    """D % 4 == 0 transposes 64 x 64 tiles with 16-byte accesses (ragged row and column tiles for
-    n = 3001, D = 100); D = 77 takes the element-wise transposing cast."""
+    """Against the FP64 second moment of the unrounded rows (D = 77 takes the transposed bf16 copy of
+    X and the general GEMM, the others the float32-input kernel)."""
     rng = np.random.default_rng(n * 7 + D)
     X = rng.standard_normal((n, D)).astype(np.float32)
     K = lv.leanvec_second_moment(t(X), precision=lv.PREC_BF16).cpu().numpy().astype(np.float64)
@@ -61,6 +61,28 @@ def test_second_moment_bf16(lv, n, D):
     norms = np.linalg.norm(X, axis=0)
     assert np.all(np.abs(K - ref) <= TOL * np.outer(norms, norms))
     np.testing.assert_allclose(K, K.T, rtol=0, atol=1e-3 * norms.max() ** 2)
+
+
+@pytest.mark.parametrize("n,D", [(1000, 64), (20000, 768), (3001, 200), (5, 8), (129, 260), (100, 1024),
+                                 (70001, 256), (4000, 516)])
+def test_second_moment_bf16_float32_input(lv, n, D):
+    """D % 4 == 0: the rows are rounded to bf16 inside the GEMM (upper-triangle 256 x 256 tiles, two
+    TMEM halves, split over row ranges): against the FP64 product of the same rounded rows only the
+    float32 accumulation differs; K is exactly symmetric.  Ragged shapes: fewer rows than one 64-row
+    block (n = 5), a column block with 4 valid columns (D = 260, 516), ten tiles (D = 1024), more
+    rows than one range (n = 70001)."""
+    rng = np.random.default_rng(n * 13 + D)
+    X = rng.standard_normal((n, D)).astype(np.float32)
+    K = lv.leanvec_second_moment(t(X), precision=lv.PREC_BF16).cpu().numpy()
+    assert np.array_equal(K, K.T)
+    K = K.astype(np.float64)
+    Xb = rounding.bf16_round(X).astype(np.float64)
+    ref = Xb.T @ Xb
+    nb = np.linalg.norm(Xb, axis=0)
+    tol = (2e-7 * np.sqrt(n) + 1e-6) * np.outer(nb, nb)
+    assert np.all(np.abs(K - ref) <= tol), float(np.max(np.abs(K - ref) / np.outer(nb, nb)))
+    norms = np.linalg.norm(X, axis=0)
+    assert np.all(np.abs(K - fit.second_moment(X)) <= TOL * np.outer(norms, norms))
 
 
 @pytest.mark.parametrize("prec", ["bf16", "e4m3"])
