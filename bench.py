@@ -1234,8 +1234,12 @@ def bench_kernels(args, dev):
     # a14: FP64 Jacobi eigh of a D x D second moment; LeanVec-ID fit end to end
     K = lv.leanvec_second_moment(X[:100_000], precision=lv.PREC_FP32).double()
     t = timed(lambda: lv.leanvec_eigh(K), 1)
-    res[f"eigh_fp64_{D}"] = {"seconds": t}
+    res[f"eigh_fp64_{D}"] = {"seconds": t, "method": "cyclic Jacobi, all D pairs"}
     log("eigh", res[f"eigh_fp64_{D}"])
+    t = timed(lambda: lv.leanvec_eigh_top(K, d), 3)
+    res[f"eigh_top_fp64_{D}_{d}"] = {"seconds": t, "method": "tridiagonal reduction + bisection + inverse "
+                                     "iteration, the d leading pairs (the fits' path)"}
+    log("eigh_top", res[f"eigh_top_fp64_{D}_{d}"])
     t = timed(lambda: lv.leanvec_fit_id(X[:100_000], d, precision=lv.PREC_BF16), 1)
     res[f"fit_id_bf16_100k_{D}_to_{d}"] = {"seconds": t}
     log("fit_id", res[f"fit_id_bf16_100k_{D}_to_{d}"])

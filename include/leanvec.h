@@ -147,6 +147,18 @@ int leanvec_second_moment(const float *X, int64_t n, int D, float *K, int precis
  * largest-magnitude entry positive (first index on ties).  Synchronises `stream`. */
 int leanvec_eigh(const double *K, int D, double *evals, double *evecs, lv_stream_t stream);
 
+/* The nout leading eigenpairs of a symmetric D x D FP64 matrix K (device; 8 <= D <= 4096,
+ * 1 <= nout <= D), the part that LeanVec-ID (Sec. 2.1) and the eigenvector search (Algorithm 2)
+ * use: Householder reduction to tridiagonal form (all SMs, one cooperative launch), bisection on
+ * Sturm counts for the nout largest eigenvalues, inverse iteration for their tridiagonal
+ * eigenvectors (Gram-Schmidt among eigenvalues closer than 1e-5 of the largest magnitude), and
+ * the back-transformation; FP64 throughout.  evals (nout, device, nullable) descending, evecs
+ * (nout x D, device) rows = unit eigenvectors with the largest-magnitude entry positive (first
+ * index on ties), as leanvec_eigh.  Returns LV_ERR_TIMEOUT if a grid barrier of the reduction
+ * gave up (seconds).  Synchronises `stream`.  leanvec_fit_id and leanvec_fit_ood use this path
+ * whenever they need fewer than D eigenvectors. */
+int leanvec_eigh_top(const double *K, int D, int nout, double *evals, double *evecs, lv_stream_t stream);
+
 /* LeanVec-ID (Sec. 2.1, problem "pca"): A = B = M, the d leading eigenvectors of
  * K_X = sum x x^T over the n rows of X (the left singular vectors of the paper's
  * X), computed as second moment (`precision`) + FP64 eigh.  A_out, B_out: d x D

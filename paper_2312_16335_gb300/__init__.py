@@ -16,7 +16,7 @@ import torch
 
 from ._native import (LVFitOpts, LVFitReport, LVIndexInfo, LVQueryDesc, LVSearchParams, LeanVecError, check, lib)
 
-__all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode",
+__all__ = ["Index", "LeanVecError", "leanvec_record_stride", "leanvec_column_mean", "leanvec_lvq_encode", "leanvec_eigh_top",
            "leanvec_project", "leanvec_second_moment", "leanvec_eigh", "leanvec_fit_id", "leanvec_fit_ood",
            "leanvec_ood_loss_fwd", "leanvec_ood_loss_bwd", "leanvec_spectral_clip", "OODLoss", "fit_ood_gradient",
            "autotune", "autotune_target_d", "autotune_uneven", "SearchGraph", "UnevenGraph", "leanvec_trim_scratch", "leanvec_index_file_check", "PREC_FP32", "PREC_BF16", "PREC_FP8", "PREC_TF32X3", "FIT_FW", "FIT_ES", "FIT_ES_FW"]
@@ -118,6 +118,19 @@ def leanvec_eigh(K: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
     w = torch.empty(D, dtype=torch.float64, device=K.device)
     V = torch.empty((D, D), dtype=torch.float64, device=K.device)
     check(lib().leanvec_eigh(_ptr(K), D, _ptr(w), _ptr(V), _stream(K.device)))
+    return w, V
+
+
+def leanvec_eigh_top(K: torch.Tensor, nout: int) -> tuple[torch.Tensor, torch.Tensor]:
+    """The nout leading eigenpairs of symmetric FP64 K (tridiagonal reduction, bisection,
+    inverse iteration): eigenvalues descending, eigenvectors as rows."""
+    if K.dtype != torch.float64:
+        raise TypeError("expected float64")
+    K = K.contiguous()
+    D = K.shape[0]
+    w = torch.empty(nout, dtype=torch.float64, device=K.device)
+    V = torch.empty((nout, D), dtype=torch.float64, device=K.device)
+    check(lib().leanvec_eigh_top(_ptr(K), D, nout, _ptr(w), _ptr(V), _stream(K.device)))
     return w, V
 
 

@@ -75,6 +75,7 @@ SIGNATURES = {
                                        c_i32, c_vp, c_vp]),
     "leanvec_second_moment": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_i32, c_vp]),
     "leanvec_eigh": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "leanvec_eigh_top": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]),
     "leanvec_fit_id": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp]),
     "leanvec_ood_loss_fwd": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_i64, c_i32, c_i32,
                                      ctypes.POINTER(ctypes.c_double), c_vp]),

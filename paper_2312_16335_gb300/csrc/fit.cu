@@ -277,9 +277,18 @@ __global__ void f64_to_f32_kernel(const double *__restrict__ a, int64_t n, float
     if (t < n) b[t] = (float)a[t];
 }
 
+bool eigh_top_ok(int D, int nout);
+int eigh_top(const double *K, int D, int nout, double *evals, double *evecs, cudaStream_t st);
+
 // Eigen-decomposition of symmetric K (D x D FP64, device).  Writes the nout leading
-// eigenpairs (descending eigenvalue) to evals (nullable) / evecs (nout x D).
+// eigenpairs (descending eigenvalue) to evals (nullable) / evecs (nout x D).  Fewer than D pairs
+// of a matrix of 8 .. 4096 rows: tridiagonal reduction + bisection + inverse iteration
+// (eigh_tri.cu); all of them: cyclic Jacobi.
 int eigh_impl(const double *K, int D, int nout, double *evals, double *evecs, cudaStream_t st, int *sweeps_out) {
+    if (nout < D && eigh_top_ok(D, nout)) {
+        if (sweeps_out) *sweeps_out = 0;
+        return eigh_top(K, D, nout, evals, evecs, st);
+    }
     const int Dp = D + (D & 1);
     double *A = nullptr, *V = nullptr, *acc = nullptr, *dg = nullptr;
     double2 *cs = nullptr;
