@@ -42,7 +42,8 @@ L_GRID = [10, 12, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88
 
 # DRAM bytes (read + write) of the search kernels of one search, from one ncu capture of the same
 # configuration (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources
-# it was taken on (the sha1 of beam.cuh, search_lvq8.cu and rerank.cu).
+# it was taken on (the sha1 of beam.cuh, search_lvq8.cu and rerank.cu, and since the visited cache
+# of 16-bit tags also of search_launch.cuh and search_lvq8_tags.cu) and the visited-cache slot width.
 TRAFFIC_RECORDS = [
     # beam_kernel (3.067 GB read + 10.7 MB written) + rerank_kernel (1.198 GB + 0.15 MB) of one search
     {"src_sha1": "9fb2aadd90f9d3ae629c84c792cada92736d15aa", "n": 1_000_000, "m": 10_000, "L": 160, "width": 2, "hash": 0,
@@ -93,7 +94,7 @@ def beam_src_sha1() -> str:
     import hashlib
     root = os.path.join(ROOT, "paper_2312_16335_gb300", "csrc")
     h = hashlib.sha1()
-    for f in ("beam.cuh", "search_lvq8.cu", "rerank.cu"):
+    for f in ("beam.cuh", "search_lvq8.cu", "rerank.cu", "search_launch.cuh", "search_lvq8_tags.cu"):
         h.update(open(os.path.join(root, f), "rb").read())
     return h.hexdigest()
 
@@ -106,7 +107,8 @@ def recorded_traffic(args, L, max_hops=0):
                 r["width"] == args.width and r["hash"] == args.hash and r["projection"] == args.projection and
                 r.get("alpha") == args.alpha and r.get("rule") == args.rule and
                 r.get("graph", "primary") == getattr(args, "graph", "primary") and
-                r.get("secondary", "lvq8") == getattr(args, "secondary", "lvq8")):
+                r.get("secondary", "lvq8") == getattr(args, "secondary", "lvq8") and
+                r.get("vbits", 32) == (getattr(args, "vbits", 0) or 32)):
             return r["bytes"]
     return None
 TARGET = 0.90
@@ -258,7 +260,7 @@ def choose_config(args, S, proj, k=10):
     idx, Q, A, truth = S["idx"], S["Q"], S["A"], S["truth"]
 
     def lv_search(L, mh):
-        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
+        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, visited_bits=args.vbits,
                           projection=proj)
 
     if args.L:
@@ -382,8 +384,9 @@ def method_bytes_per_query(D, d, bits, R, hops, scored, rerank):
     return 4 * D + hops * (4 * R + 4) + scored * prim + rerank * (D + 8)
 
 
-def cpu_oracle_sample(O, L, budget_s, nthreads=0, max_hops=0):
-    """Time the CPU oracle (C, OpenMP over queries) on a bounded query sample."""
+def cpu_oracle_sample(O, L, budget_s, nthreads=0, max_hops=0, width=1):
+    """Time the CPU oracle (C, OpenMP over queries) on a bounded query sample, with the GPU
+    search's L, rerank, expansion budget and width."""
     import oracle
     cores = nthreads or os.cpu_count()
     Qh = O["Qh"]
@@ -391,7 +394,7 @@ def cpu_oracle_sample(O, L, budget_s, nthreads=0, max_hops=0):
     while True:
         t0 = time.perf_counter()
         r = oracle.search(O["g"], O["entry"], O["qp"][:m], k=10, L=L, rerank=L, prim=O["prim"], sec=O["sec"],
-                          qs=Qh[:m], nthreads=cores, max_hops=max_hops)
+                          qs=Qh[:m], nthreads=cores, max_hops=max_hops, width=width)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or m >= Qh.shape[0]:
             break
@@ -399,7 +402,7 @@ def cpu_oracle_sample(O, L, budget_s, nthreads=0, max_hops=0):
     rec = oracle.recall(r["ids"], O["truth"][:m], 10)
     return {"value": m / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": f"first {m} of {Qh.shape[0]} queries, same graph/projection, L = rerank = {L}, "
-                      f"max_hops = {max_hops or 'none'}, k = 10",
+                      f"max_hops = {max_hops or 'none'}, width {width}, k = 10",
             "recall_at_10": rec, "seconds": dt, "scored_per_query": float(r["scored"].mean()),
             "hops_per_query": float(r["hops"].mean())}
 
@@ -1005,7 +1008,7 @@ def bench_c1(args, dev):
 
         def search(ev=None, stats=False):
             return idx.search(Q, A, k=k, L=L, rerank=L, width=args.width, projection=proj, out=(ids_buf, sc_buf),
-                              events=ev, stats=stats, queries_per_warp=args.qpw)
+                              events=ev, stats=stats, queries_per_warp=args.qpw, visited_bits=args.vbits)
         for _ in range(5):
             search()
         times, kern = [], []
@@ -1079,7 +1082,7 @@ def bench_c1(args, dev):
                                   "inner product; 1000 ID queries; LeanVec-ID d=32, LVQ-8 primary + LVQ-8 "
                                   "secondary; GPU-built graph R=32, L_build=64, alpha=0.95 (alpha-scaled rule); "
                                   "k=10, L=rerank=50, no expansion budget",
-                      "projection": args.projection, "width": args.width, "queries_per_warp": args.qpw or 1,
+                      "projection": args.projection, "width": args.width, "queries_per_warp": args.qpw or 1, "visited_bits": args.vbits or "default",
                       "l2": "index about 3 MB, L2-resident; L2 flushed (256 MB written) before every timed step"},
            "recall_at_10": main["recall_at_10"], "ids_equal_oracle": main["ids_equal_oracle"],
            "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": 1000 * D * 4,
@@ -1433,6 +1436,8 @@ def main():
     ap.add_argument("--width", type=int, default=2, help="search width (beam members expanded per round)")
     ap.add_argument("--queries-per-warp", dest="qpw", type=int, default=0, choices=[0, 1, 2],
                     help="queries per warp of the beam kernel (0 = the library default, 1)")
+    ap.add_argument("--visited-bits", dest="vbits", type=int, default=0, choices=[0, 16, 32],
+                    help="visited-cache slot width: 32-bit ids (0 = the library default) or 16-bit tags")
     ap.add_argument("--projection", default="bf16", choices=["fp32", "bf16"],
                     help="query projection GEMM: bf16 tcgen05 tensor cores or fp32 CUDA cores")
     ap.add_argument("--workload", default="id", choices=["id", "c1", "ood", "uneven", "precision", "dsweep",
@@ -1538,7 +1543,8 @@ def main():
         cb = None
         O = oracle_prepare(S)
         for i in range(args.warmup + args.steps):
-            r = cpu_oracle_sample(O, L, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)), max_hops=mh)
+            r = cpu_oracle_sample(O, L, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)), max_hops=mh,
+                                  width=args.width)
             if i >= args.warmup:
                 vals.append(r["value"])
                 cb = r
@@ -1566,12 +1572,12 @@ def main():
     if args.profile:
         L = args.L or 64
         for _ in range(args.warmup):
-            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
+            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, visited_bits=args.vbits,
                        projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
-            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
+            idx.search(Q, A, k=k, L=L, rerank=L, max_hops=args.max_hops, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, visited_bits=args.vbits,
                        projection=proj)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
@@ -1583,7 +1589,7 @@ def main():
 
     # -- choose L (and the expansion budget) for recall 0.90 (untimed)
     def lv_search(L, mh, **kw):
-        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw,
+        return idx.search(Q, A, k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, visited_bits=args.vbits,
                           projection=proj, **kw)
 
     def base_search(L, mh, **kw):
@@ -1625,7 +1631,7 @@ def main():
     Qh = Q.cpu().repeat(e2e_steps, 1).pin_memory()
     ids_h = torch.empty((m * e2e_steps, k), dtype=torch.int32).pin_memory()
     sc_h = torch.empty((m * e2e_steps, k), dtype=torch.float32).pin_memory()
-    host_kw = dict(k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, projection=proj,
+    host_kw = dict(k=k, L=L, rerank=L, max_hops=mh, width=args.width, hash_slots=args.hash, queries_per_warp=args.qpw, visited_bits=args.vbits, projection=proj,
                    batch=m)
     idx.search_host(Qh[:2 * m], A, out=(ids_h[:2 * m], sc_h[:2 * m]), **host_kw)  # slots sized, streams made
     torch.cuda.synchronize()
@@ -1656,7 +1662,7 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_oracle_sample(O, L, args.cpu_budget, max_hops=mh)
+            cpu = cpu_oracle_sample(O, L, args.cpu_budget, max_hops=mh, width=args.width)
         except Exception as e:  # the GPU result stands without the CPU leg
             cpu = {"error": repr(e)}
     if cpu and "scored_per_query" in cpu:
@@ -1680,7 +1686,7 @@ def main():
                                   if any(t.get("qps") for t in hop_table) else args.hop_factor),
                    "hop_budget_table": hop_table, "R": args.R,
                    "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary, "projection": args.projection,
-                   "hash_slots": args.hash or "default", "width": args.width, "queries_per_warp": args.qpw or 1,
+                   "hash_slots": args.hash or "default", "width": args.width, "queries_per_warp": args.qpw or 1, "visited_bits": args.vbits or "default",
                    "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
                          ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
                    "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},

@@ -394,7 +394,9 @@ typedef struct {
 typedef struct {
     lv_query_desc uniform;   /* used for every query when desc == NULL */
     int32_t projection;      /* lv_precision of the q -> A q GEMM */
-    int32_t hash_slots;      /* visited-cache slots per query (power of two; 0 = max(1024, 4 L) up to 8192) */
+    int32_t hash_slots;      /* visited-cache slots per query (power of two; 0 = max(1024, 4 L) up to
+                                8192 slots of 32-bit ids, or twice as many 16-bit tags, see
+                                visited_bits) */
     int32_t warps_per_block; /* 0 = default */
     int32_t width;           /* search width: beam members expanded per round, 1..4 (0 = 1);
                                 width * R <= 256.  1 is the classic best-first traversal */
@@ -416,6 +418,16 @@ typedef struct {
                                 instructions per query; 2 holds 40 queries per SM instead of 24 and
                                 is faster when the index's primaries and graph sit in L2 and the
                                 batch spans several waves, 1 when they stream from DRAM */
+    int32_t visited_bits;     /* slot width of the visited cache of one query per warp: 32 (whole
+                                ids, buckets of 4 slots; 0 = 32) or 16 (tags, buckets of 8: id x is
+                                kept as x >> b in bucket (x xor (x >> b)) mod 2^b of the 2^b =
+                                slots / 8 buckets, which names x exactly; needs n <= 65535 * slots
+                                / 8, else LV_ERR_ARG; with hash_slots 0 the default slot count is
+                                doubled: the same bytes).  Results do not depend on it (the cache
+                                may forget ids but never reports an unvisited one); 16 forgets
+                                fewer ids, so fewer records are scored again
+                                (lv_search_stats.scored), at a slightly longer lookup.  Ignored
+                                with queries_per_warp 2 */
 } lv_search_params;
 
 /* Per-query counters (device, m entries) when stats != NULL. */

@@ -366,14 +366,16 @@ class Index:
                desc: torch.Tensor | None = None, ldo: int | None = None, stats: bool = False,
                projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0,
                out: tuple[torch.Tensor, torch.Tensor] | None = None, events=None, width: int = 1,
-               warps_per_query: int = 0, queries_per_warp: int = 0):
+               warps_per_query: int = 0, queries_per_warp: int = 0, visited_bits: int = 0):
         """Search m queries. desc: optional (m, 4) int32 CUDA tensor of per-query
         (k, L, rerank, max_hops); then k/L are the upper bounds used for capacity.
         events: optional pair of torch.cuda.Event recorded around the search kernels.
         width: beam members expanded per round (1 = classic best-first).
         warps_per_query: warps sharing one query (1, 2, 4; divides width; 0 = 1);
         queries_per_warp: 1, or 2 (one query per 16 lanes; LVQ primaries, width <= 2,
-        width * R <= 128), 0 = 1.  The results depend on neither."""
+        width * R <= 128), 0 = 1.  visited_bits: slot width of the visited cache, 32 (ids; 0 =
+        32) or 16 (tags, twice the default slots in the same bytes; n <= 65535 * slots / 8).  The
+        results depend on none of these."""
         Q = _f32(Q)
         m = Q.shape[0]
         ldo = k if ldo is None else ldo
@@ -385,7 +387,7 @@ class Index:
         st = torch.empty((m, 2), dtype=torch.int32, device=self.device) if stats else None
         ev0, ev1 = (None, None) if events is None else (events[0].cuda_event, events[1].cuda_event)
         prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width,
-                             warps_per_query, ev0, ev1, queries_per_warp)
+                             warps_per_query, ev0, ev1, queries_per_warp, visited_bits)
         if desc is not None:
             desc = desc.to(device=self.device, dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None
@@ -397,7 +399,7 @@ class Index:
                     max_hops: int = 0, desc: torch.Tensor | None = None, ldo: int | None = None,
                     out: tuple[torch.Tensor, torch.Tensor] | None = None, batch: int = 0,
                     projection: int = PREC_FP32, hash_slots: int = 0, warps_per_block: int = 0, width: int = 1,
-                    warps_per_query: int = 0, queries_per_warp: int = 0):
+                    warps_per_query: int = 0, queries_per_warp: int = 0, visited_bits: int = 0):
         """leanvec_search_host: queries Qh (m x D float32) and the results in host memory (use
         pinned tensors, ``.pin_memory()``, for the copies to overlap the searches); searched in
         batches of `batch` rows (0 = one batch), each exactly as ``search`` over those rows.
@@ -412,7 +414,7 @@ class Index:
         else:
             ids, sc = out
         prm = LVSearchParams(LVQueryDesc(k, L, rerank, max_hops), projection, hash_slots, warps_per_block, width,
-                             warps_per_query, None, None, queries_per_warp)
+                             warps_per_query, None, None, queries_per_warp, visited_bits)
         if desc is not None:
             desc = desc.to(dtype=torch.int32).contiguous()
         Ac = _f32(A) if A is not None else None

@@ -23,7 +23,8 @@ class LVQueryDesc(ctypes.Structure):
 class LVSearchParams(ctypes.Structure):
     _fields_ = [("uniform", LVQueryDesc), ("projection", c_i32), ("hash_slots", c_i32),
                 ("warps_per_block", c_i32), ("width", c_i32), ("warps_per_query", c_i32), ("event_begin", c_vp),
-                ("event_end", c_vp), ("queries_per_warp", c_i32)]
+                ("event_end", c_vp), ("queries_per_warp", c_i32),
+                ("visited_bits", c_i32)]
 
 
 class LVIndexInfo(ctypes.Structure):

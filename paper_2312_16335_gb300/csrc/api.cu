@@ -109,9 +109,22 @@ int search_shape(const lv_index *idx, const lv_search_params *params, BeamParams
     const std::string w(who);
     const lv_query_desc &u = params->uniform;
     p.Lcap = (int)round_up(u.L, 32);
-    int hs = params->hash_slots > 0 ? params->hash_slots : std::min(8192, std::max(1024, next_pow2(4 * u.L)));
+    const int hs32 = std::min(8192, std::max(1024, next_pow2(4 * u.L)));  // default slots of 32-bit ids
+    int hs = params->hash_slots > 0 ? params->hash_slots : hs32;
     if (hs & (hs - 1)) return fail(LV_ERR_ARG, w + ": hash_slots must be a power of two");
     hs = std::max(hs, next_pow2(2 * p.Lcap));
+    // visited-cache slots of one query per warp: 32-bit ids, or on request 16-bit tags (by default
+    // twice the slots of 32-bit ids, in the same bytes); two queries per warp always hold tags, in
+    // buckets of 4
+    const int vb = params->visited_bits;
+    if (vb != 0 && vb != 16 && vb != 32) return fail(LV_ERR_ARG, w + ": visited_bits must be 0, 16 or 32");
+    p.vbits = 32;
+    if (vb == 16 && params->queries_per_warp != 2) {
+        const int hs16 = params->hash_slots > 0 ? hs : std::max(hs, 2 * hs32);
+        if (!tags_fit(idx->n, hs16)) return fail(LV_ERR_ARG, w + ": visited_bits 16 needs n <= 65535 * hash_slots / 8");
+        p.vbits = 16;
+        hs = hs16;
+    }
     p.Hcap = hs;
     p.hbits = 0;
     while ((1 << p.hbits) < hs) p.hbits++;
@@ -140,7 +153,7 @@ int search_shape(const lv_index *idx, const lv_search_params *params, BeamParams
         *smem = (size_t)2 * warps * p.warp_smem;
     } else {
         p.Rcap = beam_rcap(p.W, p.T, idx->R);
-        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.Rcap, qbytes);
+        p.warp_smem = beam_warp_smem(p.Lcap, p.Hcap, p.vbits, p.Rcap, qbytes);
         if (warps <= 0) warps = 8;
         if (warps % p.T) return fail(LV_ERR_ARG, w + ": warps_per_block must be a multiple of warps_per_query");
         while (warps > p.T && (size_t)(warps / p.T) * p.warp_smem > 227 * 1024) warps >>= 1;

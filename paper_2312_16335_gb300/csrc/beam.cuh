@@ -5,12 +5,17 @@
 //
 // Per warp, shared memory holds the beam (scores + ids sorted best first, the top bit
 // of an id marks "expanded"; merged in place), a visited cache, and the candidate
-// buffers of one expansion.  The visited cache is an open-addressing table that may forget ids
-// (overwrite when a probe run is full) but never reports an unvisited id as visited;
+// buffers of one expansion.  The visited cache is a set-associative table that may forget ids
+// (overwrite when a bucket is full) but never reports an unvisited id as visited;
 // a forgotten id that is met again is rescored and then rejected by the merge,
 // because it is either still in the beam (exact key match) or worse than the beam's
 // last member (the last member only improves).  The beam is therefore identical to
 // the one of an exact visited set.
+//
+// The cache holds either whole 32-bit ids (buckets of 4) or 16-bit tags (buckets of 8, twice
+// the slots in the same bytes).  A tag names its id exactly: with 2^b buckets, id x is stored
+// as the tag x >> b in bucket (x xor (x >> b)) mod 2^b, so the bucket and the tag give x back;
+// tags run below 0xFFFF (the empty mark) while n <= 0xFFFF * 2^b.
 #pragma once
 
 #include "common.cuh"
@@ -63,6 +68,7 @@ struct BeamParams {
     int Lcap;   // beam capacity (multiple of 32)
     int Hcap;   // visited cache slots (power of two, >= 2 * Lcap)
     int hbits;  // log2(Hcap)
+    int vbits;  // bits of a visited-cache slot: 32 (ids, buckets of 4) or 16 (tags, buckets of 8)
     int Rcap;   // candidate buffer capacity (multiple of 32, >= W * R)
     int W;      // search width: parents expanded per round (1..4, W * R <= 256)
     int T;      // warps per query (1, 2 or 4; divides W); Rcap = T * (W / T * R rounded up to 32)
@@ -75,10 +81,16 @@ struct BeamParams {
 constexpr int WMAX = 4;
 constexpr int CMAX = 256;  // candidates of one round (W * R)
 
-// shared memory of one query: beam (8 Lcap), visited cache (4 Hcap), 4 candidate arrays (16 Rcap),
-// the scorer's query (qbytes, a multiple of 16), control words (64)
-inline int beam_warp_smem(int Lcap, int Hcap, int Rcap, int qbytes) {
-    return 8 * Lcap + 4 * Hcap + 16 * Rcap + qbytes + 64;  // + 16 control words
+// shared memory of one query: beam (8 Lcap), visited cache (Hcap slots of vbits / 8 bytes), 4
+// candidate arrays (16 Rcap), the scorer's query (qbytes, a multiple of 16), control words (64)
+inline int beam_warp_smem(int Lcap, int Hcap, int vbits, int Rcap, int qbytes) {
+    return 8 * Lcap + vbits / 8 * Hcap + 16 * Rcap + qbytes + 64;  // + 16 control words
+}
+// every id below n has a 16-bit tag in a cache of hcap slots (hcap / 8 buckets of 8 tags)
+inline bool tags_fit(int64_t n, int hcap) {
+    int b = 0;
+    while ((8 << b) < hcap) ++b;
+    return hcap >= 64 && n >= 1 && ((n - 1) >> b) < 0xFFFF;
 }
 // candidate capacity of a team: T slices of W / T parents' neighbours, each rounded up to 32
 inline int beam_rcap(int W, int T, int R) { return T * ((W / T * R + 31) / 32 * 32); }
@@ -589,6 +601,20 @@ __device__ __forceinline__ void team_sync(int T, int team) {
         asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(32 * T) : "memory");
 }
 
+// The top bit of each 16-bit half of w that is zero.  A borrow can also flag the upper half above
+// a zero lower half: "some half is zero" is exact, and so is each flag when a zero lower half
+// implies a zero upper one.
+__device__ __forceinline__ unsigned zero_halves(unsigned w) { return (w - 0x00010001u) & ~w & 0x80008000u; }
+
+// A bucket of 8 16-bit tags (empty = 0xFFFF; the empty slots are the bucket's last ones): true if
+// `tag` is not in it, with the number of empty slots in `ne`
+__device__ __forceinline__ bool bucket_tag_free(const uint4 v, unsigned tag, int &ne) {
+    const unsigned tt = tag * 0x10001u;
+    if (zero_halves(v.x ^ tt) | zero_halves(v.y ^ tt) | zero_halves(v.z ^ tt) | zero_halves(v.w ^ tt)) return false;
+    ne = __popc(zero_halves(~v.x)) + __popc(zero_halves(~v.y)) + __popc(zero_halves(~v.z)) + __popc(zero_halves(~v.w));
+    return true;
+}
+
 // --------------------------------------------------------------------------------
 // The beam kernel.  A team of T = p.T warps serves one query: per round the W best
 // unexpanded beam members are the parents, warp w of the team expands parents
@@ -598,8 +624,9 @@ __device__ __forceinline__ void team_sync(int T, int team) {
 // BUILD: queries are nodes (p.qnodes), output = the final beam.
 // RERANK: hand the top-r of the beam to the rerank kernel (rerank.cu).
 // --------------------------------------------------------------------------------
-// WT: the search width fixed at compile time (1 or 2; 0 = p.W, up to WMAX)
-template <class PS, bool BUILD, bool RERANK, int WT>
+// WT: the search width fixed at compile time (1 or 2; 0 = p.W, up to WMAX); TAGS: the visited
+// cache holds 16-bit tags in buckets of 8 (p.vbits = 16) instead of ids in buckets of 4
+template <class PS, bool BUILD, bool RERANK, int WT, bool TAGS = false>
 __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     constexpr int WC = WT ? WT : WMAX;  // parents per round at most
     const int Wr = WT ? WT : p.W;
@@ -610,8 +637,9 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     unsigned char *my = smem_raw + (size_t)team * p.warp_smem;
     float *const bS = reinterpret_cast<float *>(my);           // beam scores (sorted, best first)
     int *const bI = reinterpret_cast<int *>(bS + p.Lcap);      // beam ids, top bit = expanded
-    int *const hash = bI + p.Lcap;                             // visited cache
-    int *const cI = hash + p.Hcap;                             // ids of one expansion, then of
+    int *const hash = bI + p.Lcap;                             // visited cache (ids or tags)
+    uint16_t *const tags = reinterpret_cast<uint16_t *>(hash);
+    int *const cI = hash + (TAGS ? p.Hcap / 2 : p.Hcap);      // ids of one expansion, then of
     float *const cS = reinterpret_cast<float *>(cI + p.Rcap);  // the candidates that enter (in place)
     int *const vPB = reinterpret_cast<int *>(cS + p.Rcap);     // beam members ahead of each (| rank << 16)
     int *const sPB = vPB + p.Rcap;                             // the same in candidate-rank order
@@ -623,9 +651,12 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
     int *const wI = cI + tw * Rw;
     float *const wS = cS + tw * Rw;
     int *const wPB = vPB + tw * Rw;
-    // visited cache: Hcap / 4 buckets of 4 ids, one 16-byte load per lookup
+    // visited cache: Hcap / 4 buckets of 4 ids or Hcap / 8 buckets of 8 tags, one 16-byte load
+    // per lookup
     int4 *const hash4 = reinterpret_cast<int4 *>(hash);
-    const int bshift = 34 - p.hbits;  // 32 - log2(buckets)
+    const int bshift = 34 - p.hbits;  // ids: 32 - log2(buckets)
+    const int tb = p.hbits - 3;       // tags: log2(buckets)
+    const unsigned tmask = (1u << tb) - 1u;
     const bool lead = tw == 0;
     PS ps;
 
@@ -644,14 +675,19 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
         }
         r = min(max(r, 0), L);
         ps.setup(p, qi, lane, qsm, lead);
-        for (int t = (tw * 32 + lane) * 4; t < p.Hcap; t += 128 * T)
-            *reinterpret_cast<int4 *>(hash + t) = make_int4(-1, -1, -1, -1);
+        for (int t = (tw * 32 + lane) * 4; t < (TAGS ? p.Hcap / 2 : p.Hcap); t += 128 * T)
+            *reinterpret_cast<int4 *>(hash + t) = make_int4(-1, -1, -1, -1);  // empty: every bit set
         team_sync(T, team);
         const int entry = p.entry;
         if (lead) {
             if (lane == 0) {
                 cI[0] = entry;
-                hash[4 * (int)(((unsigned)entry * 0x9E3779B1u) >> bshift)] = entry;
+                if (TAGS) {
+                    const unsigned tag = (unsigned)entry >> tb;
+                    tags[8 * (((unsigned)entry ^ tag) & tmask)] = (uint16_t)tag;
+                } else {
+                    hash[4 * (int)(((unsigned)entry * 0x9E3779B1u) >> bshift)] = entry;
+                }
             }
             __syncwarp();
             ps.score(cI, cS, 1, lane);
@@ -718,34 +754,71 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
                     u[h] = j < nst ? stage[j] : -1;
                     if (u[h] >= p.n) { atomicOr(p.status, ST_CORRUPT); u[h] = -1; }
                 }
+                if constexpr (TAGS) {
+                    // both halves' lookups first (one 16-byte load of 8 tags each), then the inserts:
+                    // two new ids of one chunk that fall into one bucket take the same slot, and the
+                    // one written last stays (the other may be scored again later)
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    isnew[h] = false;
-                    slot[h] = 0;
-                    if (u[h] >= 0) {
-                        const unsigned hv = (unsigned)u[h] * 0x9E3779B1u;
-                        const int b = (int)(hv >> bshift);
-                        const int4 v = hash4[b];
-                        const int x = u[h];
-                        if (v.x != x && v.y != x && v.z != x && v.w != x) {
-                            isnew[h] = true;
-                            slot[h] = 4 * b + (v.x < 0 ? 0 : v.y < 0 ? 1 : v.z < 0 ? 2 : v.w < 0 ? 3 : (int)((hv >> (bshift - 2)) & 3u));
+                    for (int h = 0; h < 2; ++h) {
+                        isnew[h] = false;
+                        slot[h] = 0;
+                        if (u[h] < 0) continue;
+                        const unsigned x = (unsigned)u[h], tag = x >> tb;
+                        const unsigned b = (x ^ tag) & tmask;
+                        int ne = 0;
+                        isnew[h] = bucket_tag_free(reinterpret_cast<const uint4 *>(hash4)[b], tag, ne);
+                        // a bucket fills from its first slot and is overwritten only when full, so its
+                        // empty slots are its last ne ones; when full, a hashed victim
+                        slot[h] = 8 * (int)b + (ne ? 8 - ne : (int)((x * 0x85EBCA6Bu) >> 29));
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (isnew[h]) {
+                            tags[slot[h]] = (uint16_t)((unsigned)u[h] >> tb);
+                            if constexpr (PS::PREFETCH) {
+                                const uint8_t *rec = ps.base + (int64_t)u[h] * ps.stride;
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(rec));
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(rec + ps.rec_bytes() - 1));
+                            }
+                        }
+                        const unsigned bal = __ballot_sync(FULL, isnew[h]);
+                        if (isnew[h]) wI[cnt + __popc(bal & lt)] = u[h];
+                        cnt += __popc(bal);
+                    }
+                    // keep the next chunk's lookups (another parent's row) after these inserts: the
+                    // 16-bit tag stores and the 16-byte bucket loads have different types, which the
+                    // compiler may otherwise reorder (a warp's shared-memory accesses run in order)
+                    asm volatile("" ::: "memory");
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        isnew[h] = false;
+                        slot[h] = 0;
+                        if (u[h] >= 0) {
+                            const unsigned hv = (unsigned)u[h] * 0x9E3779B1u;
+                            const int b = (int)(hv >> bshift);
+                            const int4 v = hash4[b];
+                            const int x = u[h];
+                            if (v.x != x && v.y != x && v.z != x && v.w != x) {
+                                isnew[h] = true;
+                                slot[h] = 4 * b + (v.x < 0 ? 0 : v.y < 0 ? 1 : v.z < 0 ? 2 : v.w < 0 ? 3 : (int)((hv >> (bshift - 2)) & 3u));
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (isnew[h]) {
-                        hash[slot[h]] = u[h];
-                        if constexpr (PS::PREFETCH) {
-                            const uint8_t *rec = ps.base + (int64_t)u[h] * ps.stride;
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(rec));
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(rec + ps.rec_bytes() - 1));
+                    for (int h = 0; h < 2; ++h) {
+                        if (isnew[h]) {
+                            hash[slot[h]] = u[h];
+                            if constexpr (PS::PREFETCH) {
+                                const uint8_t *rec = ps.base + (int64_t)u[h] * ps.stride;
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(rec));
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(rec + ps.rec_bytes() - 1));
+                            }
                         }
+                        const unsigned bal = __ballot_sync(FULL, isnew[h]);
+                        if (isnew[h]) wI[cnt + __popc(bal & lt)] = u[h];
+                        cnt += __popc(bal);
                     }
-                    const unsigned bal = __ballot_sync(FULL, isnew[h]);
-                    if (isnew[h]) wI[cnt + __popc(bal & lt)] = u[h];
-                    cnt += __popc(bal);
                 }
             }
             __syncwarp();
@@ -993,6 +1066,10 @@ __global__ void __launch_bounds__(256, 3) beam_kernel(const BeamParams p) {
 int launch_search_lvq8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_search_lvq4(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_search_fp32(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st);
+// the same with p.vbits = 16 (visited cache of 16-bit tags); the three above pass such calls on
+int launch_search_lvq8_tags(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
+int launch_search_lvq4_tags(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
+int launch_search_fp32_tags(const BeamParams &p, int ncw, int block, size_t smem, int num_sms, cudaStream_t st);
 // two queries per warp: LVQ-8 primaries with nc = 1..4 chunks per lane, LVQ-4 with 1..3
 int launch_search_half8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);
 int launch_search_half4(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st);

@@ -583,7 +583,8 @@ int build_graph_impl(lv_index *idx, int R, int Lb, float alpha, int passes, int 
     bp.W = 1;
     bp.T = 1;
     bp.Rcap = beam_rcap(1, 1, R);
-    bp.warp_smem = beam_warp_smem(bp.Lcap, bp.Hcap, bp.Rcap, 0);  // the build scorer keeps its query in registers
+    bp.vbits = 32;
+    bp.warp_smem = beam_warp_smem(bp.Lcap, bp.Hcap, 32, bp.Rcap, 0);  // the build scorer keeps its query in registers
     int warps = 8;
     while (warps > 1 && (size_t)warps * bp.warp_smem > 227 * 1024) warps >>= 1;
     const size_t bsmem = (size_t)warps * bp.warp_smem;

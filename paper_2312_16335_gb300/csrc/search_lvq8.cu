@@ -1,49 +1,11 @@
-// Search + rerank instantiations for LVQ-8 primaries (chunks per lane 1..4).
-#include "beam.cuh"
+// Search + rerank instantiations for LVQ-8 primaries, visited cache of 32-bit ids.
+#include "search_launch.cuh"
 
 namespace lv {
 
-template <int NC, int WT, bool L2>
-static int go_w(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
-    auto k = beam_kernel<LvqIntScorer<NC, 8, L2>, false, true, WT>;
-    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LV_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    int per_sm = 0;
-    LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem));
-    if (per_sm < 1) return fail(LV_ERR_CAPACITY, "search: beam/visited capacity does not fit in shared memory");
-    const int teams = block / 32 / p.T;  // queries served at once by one block
-    if (p.slots) {
-        *p.slots = (int64_t)per_sm * num_sms * teams;
-        return LV_OK;
-    }
-    int64_t want = (p.m + teams - 1) / teams;
-    int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
-    k<<<(unsigned)std::max<int64_t>(grid, 1), block, smem, st>>>(p);
-    LV_CHECK_LAUNCH("beam_kernel<lvq8>");
-    return LV_OK;
-}
-
-template <int NC>
-static int go(const BeamParams &p, int block, size_t smem, int num_sms, cudaStream_t st) {
-    // widths 1 and 2 get their own instantiations (fixed-trip parent loops); 3 and 4 the generic one
-    if (p.metric) {
-        if (p.W == 1) return go_w<NC, 1, true>(p, block, smem, num_sms, st);
-        if (p.W == 2) return go_w<NC, 2, true>(p, block, smem, num_sms, st);
-        return go_w<NC, 0, true>(p, block, smem, num_sms, st);
-    }
-    if (p.W == 1) return go_w<NC, 1, false>(p, block, smem, num_sms, st);
-    if (p.W == 2) return go_w<NC, 2, false>(p, block, smem, num_sms, st);
-    return go_w<NC, 0, false>(p, block, smem, num_sms, st);
-}
-
 int launch_search_lvq8(const BeamParams &p, int nc, int block, size_t smem, int num_sms, cudaStream_t st) {
-    switch (nc) {
-        case 1: return go<1>(p, block, smem, num_sms, st);
-        case 2: return go<2>(p, block, smem, num_sms, st);
-        case 3: return go<3>(p, block, smem, num_sms, st);
-        case 4: return go<4>(p, block, smem, num_sms, st);
-        default: return fail(LV_ERR_ARG, "search: primary dimension too large for LVQ-8 (d <= 240)");
-    }
+    if (p.vbits == 16) return launch_search_lvq8_tags(p, nc, block, smem, num_sms, st);
+    return launch_search_lvq<8, false>(p, nc, block, smem, num_sms, st);
 }
 
 }  // namespace lv

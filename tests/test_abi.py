@@ -65,3 +65,25 @@ def test_index_create_fails_cleanly_without_gpu(native):
     h = ctypes.c_void_p()
     rc = lib.leanvec_index_create(ctypes.byref(h), 0)
     assert rc < 0 and not h.value
+
+
+def _header_structs():
+    """{typedef name: [field names]} of the plain structs include/leanvec.h declares."""
+    src = open(os.path.join(ROOT, "include", "leanvec.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        out[name] = [re.findall(r"(\w+)\s*(?:\[\w*\])?$", f.strip())[0] for f in body.split(";") if f.strip()]
+    return out
+
+
+def test_binding_structs_mirror_the_header(native):
+    """The ctypes structures have the header's fields in the header's order (a field added to
+    one side only would shift every later field)."""
+    hs = _header_structs()
+    pairs = {"lv_query_desc": native.LVQueryDesc, "lv_search_params": native.LVSearchParams,
+             "lv_index_info": native.LVIndexInfo, "lv_fit_opts": native.LVFitOpts,
+             "lv_fit_report": native.LVFitReport}
+    for cname, py in pairs.items():
+        assert cname in hs, cname
+        assert hs[cname] == [f[0] for f in py._fields_], cname
