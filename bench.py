@@ -87,6 +87,16 @@ TRAFFIC_RECORDS = [
     {"src_sha1": "9c0aada7abc74f8df81a778ce8e0f6cdc14a6801", "n": 1_000_000, "m": 10_000, "L": 152, "max_hops": 76,
      "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full",
      "bytes": 2361016064},
+    # the same kernel after the search launchers moved into search_launch.cuh (visited cache of
+    # 32-bit ids, the default): beam 2.465 GB read, rerank 2.246 GB read, 13.7 MB written (two searches)
+    {"src_sha1": "1a2d083cdc2fc77fbe3145b0f3ead1ea2711fa9f", "n": 1_000_000, "m": 10_000, "L": 152, "max_hops": 76,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full", "vbits": 32,
+     "bytes": 2362186752},
+    # the visited cache of 16-bit tags (--visited-bits 16): beam 2.367 GB read, rerank 2.246 GB read,
+    # 12.7 MB written (two searches)
+    {"src_sha1": "1a2d083cdc2fc77fbe3145b0f3ead1ea2711fa9f", "n": 1_000_000, "m": 10_000, "L": 152, "max_hops": 76,
+     "width": 2, "hash": 0, "projection": "bf16", "alpha": 1.02, "rule": 1, "graph": "full", "vbits": 16,
+     "bytes": 2312933760},
 ]
 
 
