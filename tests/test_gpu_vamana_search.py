@@ -85,3 +85,15 @@ def test_search_parity_on_oracle_vamana_graph(lv, problem):
     rescored = float(st[s][same, 1].mean() / ref["scored"][same].mean() - 1)
     print(f"GPU re-scores on the oracle's Vamana graph: {100 * rescored:.1f} % above the exact visits")
     assert rescored < 0.5
+    # the visited cache of 16-bit tags (8-way buckets, twice the slots in the same bytes): the same
+    # answers, and fewer re-scores than the 32-bit id cache
+    ids16, sc16, st16 = idx.search(Qd, Pd, k=K, L=L, rerank=L, max_hops=MAXH, width=W, projection=lv.PREC_BF16,
+                                   stats=True, visited_bits=16)
+    idx.sync_status()
+    assert np.array_equal(ids16.cpu().numpy(), ids) and np.array_equal(sc16.cpu().numpy(), sc)
+    st16 = st16.cpu().numpy()
+    assert np.array_equal(st16[:, 0], st[:, 0])
+    assert np.all(st16[s][same, 1] >= ref["scored"][same])
+    rescored16 = float(st16[s][same, 1].mean() / ref["scored"][same].mean() - 1)
+    print(f"with 16-bit tags: {100 * rescored16:.1f} % above the exact visits")
+    assert rescored16 < rescored and rescored16 < 0.05
