@@ -412,7 +412,8 @@ int eigh_top(const double *K, int D, int nout, double *evals, double *evecs, cud
         lo -= pad;
         hi += pad;
         const double pivmin = DBL_MIN * std::max(1.0, e2max);
-        bisect_kernel<<<(nout + 3) / 4, 128, 0, st>>>(dg, ofd, D, nout, lo, hi, pivmin, lam);
+        // one warp per block, so that the eigenvalues' warps spread over all SMs
+        bisect_kernel<<<nout, 32, 0, st>>>(dg, ofd, D, nout, lo, hi, pivmin, lam);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(hl.data(), lam, sizeof(double) * nout, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
