@@ -299,8 +299,9 @@ int leanvec_index_info(const lv_index *idx, lv_index_info *out);
  * then it replaces the index's stores (and metric) with the file's on the index's device and
  * synchronises `stream`.  Validation holds the whole file in host memory (about 11.6 GB for
  * 10^7 x 768 with LVQ-4 primaries and LVQ-8 secondaries); a device allocation or copy that fails
- * after it (LV_ERR_OOM / LV_ERR_CUDA) leaves the index without stores (load again or re-encode).  leanvec_index_file_check performs the same validation without a
- * device and fills `out` (nullable) from the header. */
+ * after it (LV_ERR_OOM / LV_ERR_CUDA) leaves the index without stores (load again or re-encode).
+ * leanvec_index_file_check performs the same validation without a device and fills `out`
+ * (nullable) from the header. */
 int leanvec_index_save(const lv_index *idx, const char *path, lv_stream_t stream);
 int leanvec_index_load(lv_index *idx, const char *path, lv_stream_t stream);
 int leanvec_index_file_check(const char *path, lv_index_info *out);
