@@ -26,8 +26,10 @@
  * with <q, x> approximated exactly as for the inner product (Eq. 1) and ||x||^2
  * the squared norm of the original vector, kept per record.
  *
- * Parity unpinned: none of the functions below has a printed worked example
- * in the paper; each is pinned by closed forms and brute force in tests/.
+ * Pins: the paper prints no worked example for these functions; each is pinned
+ * against something other than itself -- closed forms, invariants, special
+ * cases that reduce to a textbook routine, brute force on tiny inputs and an
+ * independent sequential replay -- in tests/test_oracle_*.py.
  */
 #include <stdint.h>
 #include <stdlib.h>
