@@ -295,6 +295,24 @@ def choose_config(args, S, proj, k=10):
     return L, mh, rec, table
 
 
+def best_hop_factor(table, default):
+    """The hop factor of the fastest calibrated row (the chosen configuration)."""
+    ok = [t for t in table if t.get("qps")]
+    return max(ok, key=lambda t: t["qps"])["hop_factor"] if ok else default
+
+
+def id_config(args, workload, n_queries, L, mh, hop_factor, inf):
+    """The id workload's configuration, the same dict in both arms' lines: what is searched and how,
+    no results."""
+    return {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": n_queries, "k": 10, "L": L,
+            "rerank": L, "max_hops": mh, "hop_factor": hop_factor, "R": args.R, "L_build": args.L_build,
+            "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary,
+            "projection": args.projection, "hash_slots": args.hash or "default", "width": args.width,
+            "queries_per_warp": args.qpw or 1, "visited_bits": args.vbits or "default",
+            "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
+                  ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9)}
+
+
 def replica_throughput(total_ms, units_per_step, steps, device=None):
     """Whole-job throughput of N independent replicas (one per rank, no data exchange): every rank
     timed the same number of steps; the job lasts as long as the slowest rank (max over ranks) and
@@ -1559,7 +1577,7 @@ def main():
             return
         S = setup(args, dev, with_base=False)
         proj = S["lv"].PREC_BF16 if args.projection == "bf16" else S["lv"].PREC_FP32
-        L, mh, _, _ = choose_config(args, S, proj)
+        L, mh, _, table = choose_config(args, S, proj)
         vals = []
         cb = None
         O = oracle_prepare(S)
@@ -1574,12 +1592,10 @@ def main():
         out = {"impl": "reference", "metric": metric, "value": v, "unit": "queries/s", "n_gpus": 1,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": S["Q"].shape[0],
-                          "k": 10, "L": L, "rerank": L, "max_hops": mh, "R": args.R, "L_build": args.L_build,
-                          "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph,
-                          "secondary": args.secondary, "projection": args.projection, "width": args.width,
-                          "impl_note": "CPU oracle on the host cores (the same graph, stores and queries; the "
-                                       "projection's bf16 operand rounding applied in FP64)"},
+               "config": id_config(args, workload, S["Q"].shape[0], L, mh, best_hop_factor(table, args.hop_factor),
+                                   S["idx"].info()),
+               "impl_note": "CPU oracle on the host cores (the same graph, stores and queries; the projection's "
+                            "bf16 operand rounding applied in FP64)",
                "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                                              "d2h_bytes_per_step": 0}}
         print(json.dumps(out), flush=True)
@@ -1701,16 +1717,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u8 LVQ codes decoded to f32)",
         "data": "synthetic",
-        "config": {"workload": workload, "n": args.n, "D": args.D, "d": args.d, "queries": m, "k": k, "L": L,
-                   "rerank": L, "max_hops": mh, "recall_at_10": rec,
-                   "hop_factor": (max((t for t in hop_table if t.get("qps")), key=lambda t: t["qps"])["hop_factor"]
-                                  if any(t.get("qps") for t in hop_table) else args.hop_factor),
-                   "hop_budget_table": hop_table, "R": args.R,
-                   "L_build": args.L_build, "alpha": args.alpha, "prune_rule": args.rule, "graph_built_on": args.graph, "secondary": args.secondary, "projection": args.projection,
-                   "hash_slots": args.hash or "default", "width": args.width, "queries_per_warp": args.qpw or 1, "visited_bits": args.vbits or "default",
-                   "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2)" %
-                         ((inf["primary_stride"] + inf["secondary_stride"] + 4 * inf["R"]) * args.n / 1e9),
-                   "build_seconds": S["t_build"], "fit_seconds": S["t_fit"], "encode_seconds": S["t_enc"]},
+        "config": id_config(args, workload, m, L, mh, best_hop_factor(hop_table, args.hop_factor), inf),
+        "recall_at_10": rec, "hop_budget_table": hop_table,
+        "setup_seconds": {"build": S["t_build"], "fit": S["t_fit"], "encode": S["t_enc"]},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * args.D * 4,
                 "d2h_bytes_per_step": m * k * 8, "api": "leanvec_search_host (C ABI): one call over %d batches of "
                 "the %d queries in pinned host memory, each batch copied in, searched and its ids and scores "
@@ -1733,8 +1742,7 @@ def main():
                                                      (-(-(inf["d"] + 8) // 32) * 32),
                      "peak_kind": peak_kind},
         "baseline_fp32": {"value": qps_b, "unit": "queries/s", "L": Lb, "max_hops": mhb, "recall_at_10": rec_b,
-                          "hop_factor": (max((t for t in hop_table_b if t.get("qps")), key=lambda t: t["qps"])
-                                         ["hop_factor"] if any(t.get("qps") for t in hop_table_b) else None),
+                          "hop_factor": best_hop_factor(hop_table_b, None),
                           "hop_budget_table": hop_table_b, "bytes_per_query": bytes_b,
                           "speedup_leanvec": qps / world / qps_b},
         "cpu_baseline": cpu,

@@ -98,3 +98,18 @@ def test_clock_summary():
                "garbage"]
     s = c.summary()
     assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_best_hop_factor_and_shared_config():
+    table = [{"hop_factor": 0.0, "L": None}, {"hop_factor": 0.5, "L": 152, "qps": 8.8e6},
+             {"hop_factor": 0.6, "L": 140, "qps": 8.6e6}]
+    assert bench.best_hop_factor(table, 1.0) == 0.5
+    assert bench.best_hop_factor([{"hop_factor": 0.5, "L": None}], 1.0) == 1.0
+    args = types.SimpleNamespace(n=1_000_000, D=768, d=160, R=64, L_build=128, alpha=1.02, rule=1, graph="full",
+                                 secondary="lvq8", projection="bf16", hash=0, width=2, qpw=0, vbits=0)
+    inf = {"primary_stride": 192, "secondary_stride": 800, "R": 64}
+    c = bench.id_config(args, "id-1000k-768", 10_000, 152, 76, 0.5, inf)
+    # what is searched and how, no results: the same dict in the benchmark's and the reference's line
+    assert c["L"] == c["rerank"] == 152 and c["max_hops"] == 76 and c["width"] == 2
+    assert not any(k in c for k in ("recall_at_10", "hop_budget_table", "build_seconds", "impl_note"))
+    assert c["l2"].startswith("inputs larger than L2 (index 1.25 GB")
